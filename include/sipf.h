@@ -1,0 +1,214 @@
+/*
+ * sipf.h — C ABI of the GB300 SIPF-PIC library (libsipf.so).
+ *
+ * The library advances the stochastic interacting particle-field method with
+ * particle-in-cell acceleration (SIPF-PIC, Algorithm 4 of "A fast stochastic
+ * interacting particle-field method for 3D parabolic-parabolic chemotaxis
+ * systems", arXiv 2512.03452) for the Keller-Segel system
+ *     rho_t = div(mu grad rho - chi rho grad c),  eps c_t = Lap c - k^2 c + rho
+ * on the periodic box [-L/2, L/2)^3 (Sec. 2.2), on one CUDA GPU.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: SIPF_OK (0) or a negative SIPF_E* code; nothing throws.
+ *     sipf_strerror() names a code, sipf_last_error() gives the message of the
+ *     last failure on the calling thread.
+ *   - Host buffers are owned by the caller; the library copies them and never
+ *     keeps a caller pointer after the call returns.
+ *   - A context owns all device memory it allocates and is not thread-safe.
+ *     Its work is ordered on the CUDA stream given at sipf_init (NULL: the
+ *     library creates one).  Entry points that return host data synchronise
+ *     that stream; sipf_step / sipf_run only enqueue work.
+ *   - Device-pointer entry points (suffix _dev) take caller-owned device
+ *     memory, launch on the given stream and return without synchronising.
+ *     Positions on the device are structure-of-arrays: x, y, z arrays of P
+ *     elements, in the context's precision (float for 32, double for 64).
+ *   - Grids are H^3 real arrays, row-major with the third axis fastest:
+ *     node (i, j, k) at [(i*H + j)*H + k]; node index j in [-H/2, H/2) is
+ *     stored at j mod H and sits at x = j*L/H.
+ *   - Spectra are the r2c half layout H x H x (H/2+1) of interleaved complex
+ *     numbers (re, im); index m on an axis stands for q = m (m < H/2) or
+ *     q = m - H (m >= H/2).
+ */
+#ifndef SIPF_H
+#define SIPF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------ */
+#define SIPF_OK 0
+#define SIPF_EINVAL (-1)      /* bad argument or parameter                */
+#define SIPF_ENOMEM (-2)      /* device or host allocation failed        */
+#define SIPF_ECUDA (-3)       /* a CUDA call failed                       */
+#define SIPF_ENONFINITE (-4)  /* a position or spectrum became non-finite */
+#define SIPF_ETIMEOUT (-5)    /* a bounded device wait ran out            */
+#define SIPF_ENODEV (-6)      /* no usable CUDA device                    */
+
+/* ---- option values ------------------------------------------------------ */
+#define SIPF_SPLIT_HALF 0     /* W^- , drift at X+W^-, W^+  (Algorithm 4)       */
+#define SIPF_SPLIT_PLAIN 1    /* Euler-Maruyama, Eq. (rho_hat_update)            */
+#define SIPF_DEPOSIT_ATOMIC 0 /* floating-point atomics (order-dependent rounding) */
+#define SIPF_DEPOSIT_DETERMINISTIC 1 /* 64-bit fixed-point sums: bit-reproducible */
+#define SIPF_PROP_IMPLICIT 0  /* implicit Euler, Eq. (alpha_hat_update)           */
+#define SIPF_PROP_EXP 1       /* exponential propagator, Sec. 3.4                 */
+
+/* Parameters of one run.  Names follow the problem statement (Sec. 2.2,
+ * Eq. (system)) and Algorithm 4.  sipf_params_default() fills the defaults. */
+typedef struct sipf_params {
+  double chi;        /* chemotactic sensitivity, > 0 (>= 0 allowed)          */
+  double mu;         /* diffusivity, > 0                                      */
+  double eps;        /* relaxation rate of c, > 0                             */
+  double k;          /* degradation rate, >= 0                                */
+  double L;          /* box side; domain [-L/2, L/2)^3, periodic              */
+  double mass;       /* M0; every particle carries M0/P (Eq. (def_rho_hat))   */
+  double dt;         /* tau, > 0                                               */
+  double T;          /* final time for sipf_run: N_T = ceil(T/tau)            */
+  double H0;         /* Gaussian filter scale: < 0 auto ceil(8 H^(8/13) L^(5/13))
+                        (Sec. 5.1), 0 off, > 0 as given                       */
+  uint64_t seed;     /* key of the counter-based noise                        */
+  int64_t P;         /* number of particles, >= 1                              */
+  int32_t H;         /* modes / grid points per axis: power of 2 in [8, 256]   */
+  int32_t precision; /* 32 (float state and kernels) or 64 (double)           */
+  int32_t p2g_order; /* 4 (Gamma_4, default) or 2 (Gamma_2), Sec. 3.1         */
+  int32_t g2p_order; /* 2 (Gamma_2, default) or 4 (Gamma_4)                   */
+  int32_t splitting; /* SIPF_SPLIT_*                                           */
+  int32_t deposit_mode; /* SIPF_DEPOSIT_*                                      */
+  int32_t propagator;   /* SIPF_PROP_*                                         */
+  int32_t resort_every; /* re-bucket particles by grid tile every n steps; 0 off */
+} sipf_params;
+
+/* FP64 diagnostics of the current state (Sec. 5). */
+typedef struct sipf_diag {
+  double mass;        /* sum of the deposited mass grid I rho-hat, accumulated in FP64 */
+  double alpha0;      /* zero mode of c-hat, carried in FP64                          */
+  double peak;        /* max over the grid of rho_num = F^-1(Phi F_H I rho-hat)       */
+  double hf_frac;     /* share of sum |alpha_q|^2 in modes with ||q|| >= 4            */
+  double m2;          /* (1/P) sum_p |X_p|^2                                            */
+  double ring_radius; /* (1/P) sum_p sqrt(x1^2 + x2^2)  (R_num of Sec. 5.4)             */
+  int64_t step;       /* n of the state the numbers describe                          */
+} sipf_diag;
+
+typedef struct sipf_ctx sipf_ctx;
+
+/* Fill *p with the defaults: chi=mu=eps=k=1, L=1, mass=1, dt=1e-3, T=0,
+ * H0=-1 (auto), seed=0, P=0 (must be set), H=64, precision=32,
+ * p2g_order=4, g2p_order=2, splitting=HALF, deposit_mode=ATOMIC,
+ * propagator=IMPLICIT, resort_every=0.  Returns SIPF_EINVAL if p is NULL. */
+int sipf_params_default(sipf_params* p);
+
+/* Check a parameter set without touching the GPU.  SIPF_EINVAL names the
+ * first offending field in sipf_last_error(). */
+int sipf_validate(const sipf_params* p);
+
+/* Create a context: validate *p, allocate the state on the current CUDA
+ * device, copy X0 (host, P x 3 row-major float64, i.e. x0 y0 z0 x1 ...;
+ * points outside the box are wrapped into it), set alpha^(0) = 0 and deposit
+ * X^(0) (initialisation of Algorithm 4).  stream: a cudaStream_t or NULL.
+ * On success *out owns the context; release it with sipf_destroy. */
+int sipf_init(const sipf_params* p, const double* X0, void* stream, sipf_ctx** out);
+
+/* Advance nsteps >= 0 steps of Algorithm 4 (asynchronous on the context's
+ * stream): per step, F_H of the deposited masses, the implicit update of
+ * alpha (Eq. (alpha_hat_update)) with the filtered spectral gradient of
+ * alpha^(n-1), three inverse transforms, and the particle move (W^-, gather of
+ * grad c at X + W^- with I*, drift, W^+, periodic wrap) fused with the
+ * deposit of X^(n) for the next step. */
+int sipf_step(sipf_ctx* ctx, int64_t nsteps);
+
+/* Advance until n * dt >= T (N_T = ceil(T/dt) steps in total). */
+int sipf_run(sipf_ctx* ctx);
+
+/* Current step index n (number of steps taken since sipf_init). */
+int64_t sipf_current_step(const sipf_ctx* ctx);
+
+/* Copy X^(n) to host `out` (P x 3 row-major float64).  Synchronises. */
+int sipf_positions(sipf_ctx* ctx, double* out);
+
+/* Replace X^(n) by host `X` (P x 3 row-major float64; wrapped into the box)
+ * and re-deposit it.  The step index and alpha are kept. */
+int sipf_set_positions(sipf_ctx* ctx, const double* X);
+
+/* Host<->device copies of X in the context's own precision and layout
+ * (three arrays of P floats or doubles).  Asynchronous on the context's
+ * stream when the host buffers are pinned; the caller keeps them alive and
+ * unchanged until sipf_sync().  upload re-deposits the new positions. */
+int sipf_upload_soa(sipf_ctx* ctx, const void* x, const void* y, const void* z);
+int sipf_download_soa(sipf_ctx* ctx, void* x, void* y, void* z);
+
+/* Device pointers of the context's position arrays (x, y, z; P elements each,
+ * float or double).  The pointers stay valid until sipf_destroy. */
+int sipf_positions_dev(sipf_ctx* ctx, void** x, void** y, void** z);
+
+/* Density on the grid (host H^3 float64).  filtered = 0: I rho-hat / h^3,
+ * the deposited mass per cell volume (Def. particle2grid); filtered = 1:
+ * rho_num = F_H^-1(Phi F_H I rho-hat), rho-hat convolved with N(0,(L/H0)^2 I)
+ * (Sec. 5.2).  Synchronises. */
+int sipf_density(sipf_ctx* ctx, double* out, int filtered);
+
+/* c-hat^(n) on the grid nodes, F_H^-1 alpha^(n) (host H^3 float64). */
+int sipf_field(sipf_ctx* ctx, double* out);
+
+/* alpha^(n) (host, H*H*(H/2+1) complex as 2 float64 each). */
+int sipf_spectrum(sipf_ctx* ctx, double* out);
+
+/* The gradient grids F_H^-1(2 pi i q/L Phi alpha^(n)) used by the next move
+ * (host, 3 x H^3 float64: component-major). */
+int sipf_gradient(sipf_ctx* ctx, double* out);
+
+/* FP64 diagnostics of the current state.  Synchronises. */
+int sipf_diagnostics(sipf_ctx* ctx, sipf_diag* out);
+
+/* Wait for the context's stream; returns SIPF_ENONFINITE if a kernel saw a
+ * non-finite position since the last call (the flag is then cleared). */
+int sipf_sync(sipf_ctx* ctx);
+
+/* Free everything the context owns.  NULL is a no-op. */
+void sipf_destroy(sipf_ctx* ctx);
+
+const char* sipf_strerror(int code);
+const char* sipf_last_error(void);
+
+/* ---- stateless operators on caller-owned device memory ------------------
+ * precision: 32 or 64 (element type float / double of every real array).
+ * All are asynchronous on `stream` (cudaStream_t or NULL for the default).
+ */
+
+/* Philox4x32-10 normals: z[j*P + p] for j = 0..5, particle index first+p,
+ * counter (particle lo, particle hi, step, block), key (seed lo, seed hi),
+ * Box-Muller on uniforms (x + 1/2) 2^-32.  (Algorithm 4 draws
+ * W^-, W^+ ~ N(0, mu tau I) from z0..z2 and z3..z5.) */
+int sipf_noise_dev(int precision, uint64_t seed, int64_t step, int64_t first,
+                   int64_t P, void* z, void* stream);
+
+/* Algorithm 2 without its FFT: grid (H^3, zeroed here first) receives
+ * w * F_gamma(lambda(X_p)) at (floor(H X_p/L) + gamma) mod H for every
+ * particle, order 2 (Gamma_2) or 4 (Gamma_4). */
+int sipf_deposit_dev(int precision, const void* x, const void* y, const void* z,
+                     int64_t P, int32_t H, double L, double w, int32_t order,
+                     void* grid, void* stream);
+
+/* Algorithm 3: out[c*P + p] = sum_gamma F_gamma(lambda(X_p)) f_c[...] for
+ * ncomp component grids f (component c at f + c*H^3), order 2 or 4. */
+int sipf_gather_dev(int precision, const void* x, const void* y, const void* z,
+                    int64_t P, int32_t H, double L, const void* f, int32_t ncomp,
+                    int32_t order, void* out, void* stream);
+
+/* beta = F_H(grid) = L^-3 sum_j grid_j e^{-2 pi i q.j/H} (Sec. 3.1) into the
+ * half spectrum `spec` (H*H*(H/2+1) complex values). */
+int sipf_forward_ft_dev(int precision, int32_t H, double L, const void* grid,
+                        void* spec, void* stream);
+
+/* grid = F_H^-1(spec) = sum_q spec_q e^{+2 pi i q.j/H} (real part of the
+ * Hermitian extension); `spec` is overwritten (used as work space). */
+int sipf_inverse_ft_dev(int precision, int32_t H, void* spec, void* grid,
+                        void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIPF_H */

@@ -194,15 +194,18 @@ def stencil_indices(cell, offsets, H):
 # ---------------------------------------------------------------------------
 # Algorithm 2 (particle-to-grid) and Algorithm 3 (grid-to-particle).
 # ---------------------------------------------------------------------------
-def deposit(X, weights, H, L, order=4):
+def deposit(X, weights, H, L, order=4, chunk=1 << 20):
     """phi[q_{p,gamma}] += w_p F_{p,gamma} over all particles and stencil
     points (Algorithm 2 without its final FFT).  `weights` is w_p (scalar M0/P
-    or a per-particle array).  Returns the H^3 mass grid (float64)."""
-    cell, lam = cell_and_lambda(X, H, L)
-    offs, F = stencil(lam, order)
-    idx = stencil_indices(cell, offs, H)
+    or a per-particle array).  Particles are taken in chunks only to bound
+    memory.  Returns the H^3 mass grid (float64)."""
     w = np.broadcast_to(np.asarray(weights, dtype=np.float64), (X.shape[0],))
-    phi = np.bincount(idx.ravel(), weights=(w[:, None] * F).ravel(), minlength=H ** 3)
+    phi = np.zeros(H ** 3)
+    for s in range(0, X.shape[0], chunk):
+        cell, lam = cell_and_lambda(X[s:s + chunk], H, L)
+        offs, F = stencil(lam, order)
+        idx = stencil_indices(cell, offs, H)
+        phi += np.bincount(idx.ravel(), weights=(w[s:s + chunk, None] * F).ravel(), minlength=H ** 3)
     return phi.reshape(H, H, H)
 
 

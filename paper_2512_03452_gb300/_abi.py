@@ -1,0 +1,235 @@
+"""ctypes binding of libsipf.so (include/sipf.h): argument marshalling only.
+
+Every function here has the name of the C entry point it forwards to; all
+computation happens in the library's CUDA kernels.  Loading fails loudly when
+the compiled library is missing: there is no Python or CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsipf.so")
+
+SIPF_OK = 0
+SIPF_EINVAL = -1
+SIPF_ENOMEM = -2
+SIPF_ECUDA = -3
+SIPF_ENONFINITE = -4
+SIPF_ETIMEOUT = -5
+SIPF_ENODEV = -6
+
+SPLIT_HALF, SPLIT_PLAIN = 0, 1
+DEPOSIT_ATOMIC, DEPOSIT_DETERMINISTIC = 0, 1
+PROP_IMPLICIT, PROP_EXP = 0, 1
+
+
+class sipf_params(ctypes.Structure):
+    _fields_ = [
+        ("chi", ctypes.c_double), ("mu", ctypes.c_double), ("eps", ctypes.c_double),
+        ("k", ctypes.c_double), ("L", ctypes.c_double), ("mass", ctypes.c_double),
+        ("dt", ctypes.c_double), ("T", ctypes.c_double), ("H0", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("P", ctypes.c_int64), ("H", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("p2g_order", ctypes.c_int32),
+        ("g2p_order", ctypes.c_int32), ("splitting", ctypes.c_int32),
+        ("deposit_mode", ctypes.c_int32), ("propagator", ctypes.c_int32),
+        ("resort_every", ctypes.c_int32),
+    ]
+
+
+class sipf_diag(ctypes.Structure):
+    _fields_ = [
+        ("mass", ctypes.c_double), ("alpha0", ctypes.c_double), ("peak", ctypes.c_double),
+        ("hf_frac", ctypes.c_double), ("m2", ctypes.c_double), ("ring_radius", ctypes.c_double),
+        ("step", ctypes.c_int64),
+    ]
+
+
+class SipfError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where} failed ({code}: {msg})")
+        self.code = code
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_SIGS = {
+    "sipf_params_default": (ctypes.c_int, [ctypes.POINTER(sipf_params)]),
+    "sipf_validate": (ctypes.c_int, [ctypes.POINTER(sipf_params)]),
+    "sipf_init": (ctypes.c_int, [ctypes.POINTER(sipf_params), _D, _P, ctypes.POINTER(_P)]),
+    "sipf_step": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "sipf_run": (ctypes.c_int, [_P]),
+    "sipf_current_step": (ctypes.c_int64, [_P]),
+    "sipf_positions": (ctypes.c_int, [_P, _D]),
+    "sipf_set_positions": (ctypes.c_int, [_P, _D]),
+    "sipf_upload_soa": (ctypes.c_int, [_P, _P, _P, _P]),
+    "sipf_download_soa": (ctypes.c_int, [_P, _P, _P, _P]),
+    "sipf_positions_dev": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "sipf_density": (ctypes.c_int, [_P, _D, ctypes.c_int]),
+    "sipf_field": (ctypes.c_int, [_P, _D]),
+    "sipf_spectrum": (ctypes.c_int, [_P, _D]),
+    "sipf_gradient": (ctypes.c_int, [_P, _D]),
+    "sipf_diagnostics": (ctypes.c_int, [_P, ctypes.POINTER(sipf_diag)]),
+    "sipf_sync": (ctypes.c_int, [_P]),
+    "sipf_destroy": (None, [_P]),
+    "sipf_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "sipf_last_error": (ctypes.c_char_p, []),
+    "sipf_noise_dev": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64,
+                                      ctypes.c_int64, _P, _P]),
+    "sipf_deposit_dev": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, ctypes.c_int64, ctypes.c_int32,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_int32, _P, _P]),
+    "sipf_gather_dev": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, ctypes.c_int64, ctypes.c_int32,
+                                       ctypes.c_double, _P, ctypes.c_int32, ctypes.c_int32, _P, _P]),
+    "sipf_forward_ft_dev": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, ctypes.c_double, _P, _P, _P]),
+    "sipf_inverse_ft_dev": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, _P, _P, _P]),
+}
+
+
+def exported_symbols():
+    """Names of the C entry points this binding expects the library to export."""
+    return sorted(_SIGS)
+
+
+def load(path: str = LIB_PATH):
+    """Load libsipf.so (once) and attach the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libsipf.so not built at {path}: run paper_2512_03452_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code: int, where: str):
+    if code != SIPF_OK:
+        lib = load()
+        raise SipfError(code, where, (lib.sipf_last_error() or b"").decode() or lib.sipf_strerror(code).decode())
+
+
+def _dptr(a):
+    """ctypes double* of a contiguous float64 numpy array."""
+    return a.ctypes.data_as(_D)
+
+
+# ---- same-name wrappers ------------------------------------------------------
+def sipf_params_default() -> sipf_params:
+    p = sipf_params()
+    _check(load().sipf_params_default(ctypes.byref(p)), "sipf_params_default")
+    return p
+
+
+def sipf_validate(p: sipf_params) -> None:
+    _check(load().sipf_validate(ctypes.byref(p)), "sipf_validate")
+
+
+def sipf_init(p: sipf_params, X0, stream: int | None = None) -> int:
+    """X0: contiguous (P, 3) float64 numpy array.  Returns the context handle."""
+    import numpy as np
+    X0 = np.ascontiguousarray(X0, dtype=np.float64)
+    h = _P()
+    _check(load().sipf_init(ctypes.byref(p), _dptr(X0), _P(stream or 0), ctypes.byref(h)), "sipf_init")
+    return h.value
+
+
+def sipf_step(ctx: int, nsteps: int) -> None:
+    _check(load().sipf_step(_P(ctx), int(nsteps)), "sipf_step")
+
+
+def sipf_run(ctx: int) -> None:
+    _check(load().sipf_run(_P(ctx)), "sipf_run")
+
+
+def sipf_current_step(ctx: int) -> int:
+    return int(load().sipf_current_step(_P(ctx)))
+
+
+def sipf_positions(ctx: int, out) -> None:
+    _check(load().sipf_positions(_P(ctx), _dptr(out)), "sipf_positions")
+
+
+def sipf_set_positions(ctx: int, X) -> None:
+    _check(load().sipf_set_positions(_P(ctx), _dptr(X)), "sipf_set_positions")
+
+
+def sipf_upload_soa(ctx: int, x: int, y: int, z: int) -> None:
+    _check(load().sipf_upload_soa(_P(ctx), _P(x), _P(y), _P(z)), "sipf_upload_soa")
+
+
+def sipf_download_soa(ctx: int, x: int, y: int, z: int) -> None:
+    _check(load().sipf_download_soa(_P(ctx), _P(x), _P(y), _P(z)), "sipf_download_soa")
+
+
+def sipf_positions_dev(ctx: int):
+    x, y, z = _P(), _P(), _P()
+    _check(load().sipf_positions_dev(_P(ctx), ctypes.byref(x), ctypes.byref(y), ctypes.byref(z)),
+           "sipf_positions_dev")
+    return x.value, y.value, z.value
+
+
+def sipf_density(ctx: int, out, filtered: int) -> None:
+    _check(load().sipf_density(_P(ctx), _dptr(out), int(filtered)), "sipf_density")
+
+
+def sipf_field(ctx: int, out) -> None:
+    _check(load().sipf_field(_P(ctx), _dptr(out)), "sipf_field")
+
+
+def sipf_spectrum(ctx: int, out) -> None:
+    _check(load().sipf_spectrum(_P(ctx), _dptr(out)), "sipf_spectrum")
+
+
+def sipf_gradient(ctx: int, out) -> None:
+    _check(load().sipf_gradient(_P(ctx), _dptr(out)), "sipf_gradient")
+
+
+def sipf_diagnostics(ctx: int) -> sipf_diag:
+    d = sipf_diag()
+    _check(load().sipf_diagnostics(_P(ctx), ctypes.byref(d)), "sipf_diagnostics")
+    return d
+
+
+def sipf_sync(ctx: int) -> None:
+    _check(load().sipf_sync(_P(ctx)), "sipf_sync")
+
+
+def sipf_destroy(ctx: int) -> None:
+    load().sipf_destroy(_P(ctx))
+
+
+def sipf_strerror(code: int) -> str:
+    return load().sipf_strerror(int(code)).decode()
+
+
+def sipf_last_error() -> str:
+    return (load().sipf_last_error() or b"").decode()
+
+
+def sipf_noise_dev(precision, seed, step, first, P, z, stream=0) -> None:
+    _check(load().sipf_noise_dev(precision, seed, step, first, P, _P(z), _P(stream)), "sipf_noise_dev")
+
+
+def sipf_deposit_dev(precision, x, y, z, P, H, L, w, order, grid, stream=0) -> None:
+    _check(load().sipf_deposit_dev(precision, _P(x), _P(y), _P(z), P, H, L, w, order, _P(grid), _P(stream)),
+           "sipf_deposit_dev")
+
+
+def sipf_gather_dev(precision, x, y, z, P, H, L, f, ncomp, order, out, stream=0) -> None:
+    _check(load().sipf_gather_dev(precision, _P(x), _P(y), _P(z), P, H, L, _P(f), ncomp, order, _P(out),
+                                  _P(stream)), "sipf_gather_dev")
+
+
+def sipf_forward_ft_dev(precision, H, L, grid, spec, stream=0) -> None:
+    _check(load().sipf_forward_ft_dev(precision, H, L, _P(grid), _P(spec), _P(stream)), "sipf_forward_ft_dev")
+
+
+def sipf_inverse_ft_dev(precision, H, spec, grid, stream=0) -> None:
+    _check(load().sipf_inverse_ft_dev(precision, H, _P(spec), _P(grid), _P(stream)), "sipf_inverse_ft_dev")

@@ -1,0 +1,497 @@
+// Pencil FFTs of the SIPF-PIC field solve (Sec. 3.2, Algorithm 4) on H^3 grids,
+// H a power of two in [8, 256], float or double.
+//
+// Forward F_H:  rows r2c along the fastest axis (two real rows per complex
+// FFT), then c2c along the middle axis, then the x-axis pass fused with the
+// implicit spectral update and the filtered gradient; the inverse runs the
+// x-axis back inside that same kernel, then the middle axis, then c2r rows.
+// Every pass stages its pencils in shared memory and runs an in-place radix-2
+// decimation-in-time transform there; global traffic is one read and one
+// write of the array per pass, coalesced along the contiguous axis.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <mutex>
+#include <type_traits>
+#include <vector>
+
+#include "sipf_internal.h"
+
+namespace sipf {
+
+// e^{-2 pi i m / 256}, m < 128, per device (written once by ensure_device_tables).
+__device__ double2 g_twiddle[kNmax / 2];
+
+cudaError_t ensure_device_tables() {
+  static std::mutex mu;
+  static std::vector<bool> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if ((int)done.size() <= dev) done.resize(dev + 1, false);
+  if (done[dev]) return cudaSuccess;
+  double2 h[kNmax / 2];
+  for (int m = 0; m < kNmax / 2; ++m) {
+    const double a = -2.0 * M_PI * (double)m / (double)kNmax;
+    h[m] = make_double2(cos(a), sin(a));
+  }
+  e = cudaMemcpyToSymbol(g_twiddle, h, sizeof(h));
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
+}
+
+__device__ __forceinline__ int brev(int j, int lg) { return (int)(__brev((unsigned)j) >> (32 - lg)); }
+
+template <typename T>
+__device__ __forceinline__ void load_twiddles(cpx<T>* tw) {
+  for (int i = threadIdx.x; i < kNmax / 2; i += blockDim.x) tw[i] = cpx<T>{(T)g_twiddle[i].x, (T)g_twiddle[i].y};
+}
+
+// In-place radix-2 DIT transform of `ncol` pencils of length n = 2^lgn in
+// shared memory; element (j, c) at buf[j*ldj + c*ldc].  Input in bit-reversed
+// order, output in natural order.  DIR = -1: e^{-i...} (forward), +1: inverse
+// (unnormalised).  COLFAST: consecutive threads walk the pencil index c (use
+// when ldc == 1), else the butterfly index.  ncol must be a power of two.
+template <typename T, int DIR, bool COLFAST>
+__device__ void smem_fft(cpx<T>* buf, const cpx<T>* tw, int lgn, int lgc, int ldj, int ldc) {
+  const int n = 1 << lgn;
+  const int nbf = (n >> 1) << lgc;
+  for (int s = 0; s < lgn; ++s) {
+    const int half = 1 << s;
+    const int tws = (kNmax / 2) >> s;
+    for (int t = threadIdx.x; t < nbf; t += blockDim.x) {
+      int b, c;
+      if (COLFAST) {
+        c = t & ((1 << lgc) - 1);
+        b = t >> lgc;
+      } else {
+        b = t & ((n >> 1) - 1);
+        c = t >> (lgn - 1);
+      }
+      const int k = b & (half - 1);
+      const int i0 = ((b >> s) << (s + 1)) + k;
+      cpx<T> w = tw[k * tws];
+      if (DIR > 0) w.y = -w.y;
+      cpx<T>* p0 = buf + i0 * ldj + c * ldc;
+      cpx<T>* p1 = p0 + half * ldj;
+      const cpx<T> a = *p0;
+      const cpx<T> v = cmul(*p1, w);
+      *p0 = cadd(a, v);
+      *p1 = csub(a, v);
+    }
+    __syncthreads();
+  }
+}
+
+static inline int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
+
+// ---------------------------------------------------------------------------
+// Rows r2c: rows 2c and 2c+1 of the block form z = a + i b; after the FFT,
+// A_k = (Z_k + conj Z_{n-k})/2 and B_k = -i (Z_k - conj Z_{n-k})/2.
+// ---------------------------------------------------------------------------
+template <typename T, typename Tin>
+__global__ void __launch_bounds__(kThreads)
+k_rows_r2c(Tin* __restrict__ in, double in_scale, int zero_input, cpx<T>* __restrict__ out,
+           int lgH, int rows, int RP, double* mass_acc) {
+  extern __shared__ unsigned char smem_raw[];
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* buf = tw + kNmax / 2;
+  const int H = 1 << lgH, nh = H / 2 + 1, ld = H + 1;
+  const int lgc = ilog2_dev(RP);
+  load_twiddles(tw);
+  const int row0 = blockIdx.x * 2 * RP;
+  const int nrow = min(2 * RP, rows - row0);
+  double msum = 0.0;
+  for (int t = threadIdx.x; t < 2 * RP * H; t += blockDim.x) {
+    const int r = t >> lgH, j = t & (H - 1);
+    T v = T(0);
+    if (r < nrow) {
+      const size_t gi = (size_t)(row0 + r) * H + j;
+      if constexpr (sizeof(Tin) == 8 && !std::is_floating_point<Tin>::value) {
+        v = (T)((double)(long long)in[gi] * in_scale);
+      } else {
+        v = (T)in[gi];
+      }
+      if (zero_input) in[gi] = Tin(0);
+      msum += (double)v;
+    }
+    cpx<T>& e = buf[(r >> 1) * ld + brev(j, lgH)];
+    if (r & 1) e.y = v; else e.x = v;
+  }
+  __syncthreads();
+  smem_fft<T, -1, false>(buf, tw, lgH, lgc, 1, ld);
+  for (int t = threadIdx.x; t < RP * nh; t += blockDim.x) {
+    const int c = t / nh, k = t - c * nh;
+    if (2 * c >= nrow) continue;
+    const cpx<T> zk = buf[c * ld + k];
+    const cpx<T> zm = cconj(buf[c * ld + ((H - k) & (H - 1))]);
+    const cpx<T> A{(zk.x + zm.x) * T(0.5), (zk.y + zm.y) * T(0.5)};
+    const cpx<T> d = csub(zk, zm);
+    const cpx<T> B{d.y * T(0.5), -d.x * T(0.5)};
+    out[(size_t)(row0 + 2 * c) * nh + k] = A;
+    out[(size_t)(row0 + 2 * c + 1) * nh + k] = B;
+  }
+  if (mass_acc) {
+    for (int o = 16; o > 0; o >>= 1) msum += __shfl_xor_sync(0xffffffffu, msum, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(mass_acc, msum);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// c2c along the middle axis of [A][H][B]: block = (column chunk, a, component).
+// ---------------------------------------------------------------------------
+template <typename T, int DIR>
+__global__ void __launch_bounds__(kThreads)
+k_cols(cpx<T>* __restrict__ data, int lgH, int B, int lgBC, size_t comp_stride, T scale) {
+  extern __shared__ unsigned char smem_raw[];
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* buf = tw + kNmax / 2;
+  const int H = 1 << lgH, BC = 1 << lgBC;
+  load_twiddles(tw);
+  cpx<T>* base = data + blockIdx.z * comp_stride + (size_t)blockIdx.y * H * B;
+  const int b0 = blockIdx.x * BC;
+  const int nb = min(BC, B - b0);
+  for (int t = threadIdx.x; t < H * BC; t += blockDim.x) {
+    const int j = t >> lgBC, c = t & (BC - 1);
+    cpx<T> v{T(0), T(0)};
+    if (c < nb) v = base[(size_t)j * B + b0 + c];
+    buf[brev(j, lgH) * BC + c] = v;
+  }
+  __syncthreads();
+  smem_fft<T, DIR, true>(buf, tw, lgH, lgBC, BC, 1);
+  for (int t = threadIdx.x; t < H * BC; t += blockDim.x) {
+    const int j = t >> lgBC, c = t & (BC - 1);
+    if (c < nb) {
+      cpx<T> v = buf[j * BC + c];
+      base[(size_t)j * B + b0 + c] = cpx<T>{v.x * scale, v.y * scale};
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// x-axis pass fused with the spectral work.  Columns m = ky*(H/2+1) + kz of the
+// flattened (ky, kz) plane, all kx.  Slots of the shared buffer: 0 = beta,
+// 1..3 = the outputs (inverse-transformed along x before they are stored).
+//   kModeStep:     alpha^n = kappa alpha^{n-1} + src beta^{n-1}  (Eq. (alpha_hat_update)
+//                  or the exponential propagator of Sec. 3.4) and
+//                  G_d = i (2 pi q_d / L) Phi_q alpha^{n-1}, zero where q_d = -H/2.
+//   kModeGradOnly: only G_d (alpha read, not updated; T1 unused).
+//   kModeDensity:  G_0 = Phi_q beta_q  (rho_num, Sec. 5.2).
+//   kModeField:    G_0 = alpha_q.
+// ---------------------------------------------------------------------------
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreads)
+k_spectral_x(const cpx<T>* __restrict__ T1, cpx<T>* __restrict__ alpha, cpx<T>* __restrict__ T2,
+             int lgH, int lgBC, SpecParams sp, double* alpha0_shadow) {
+  extern __shared__ unsigned char smem_raw[];
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* buf = tw + kNmax / 2;
+  const int H = 1 << lgH, BC = 1 << lgBC, nh = H / 2 + 1;
+  const int B = H * nh;
+  const size_t S = (size_t)H * B;
+  const int ld = 4 * BC;
+  load_twiddles(tw);
+  const int b0 = blockIdx.x * BC;
+  const int nb = min(BC, B - b0);
+  constexpr bool needs_beta = (MODE == kModeStep || MODE == kModeDensity);
+  if (needs_beta) {
+    for (int t = threadIdx.x; t < H * BC; t += blockDim.x) {
+      const int j = t >> lgBC, c = t & (BC - 1);
+      cpx<T> v{T(0), T(0)};
+      if (c < nb) v = T1[(size_t)j * B + b0 + c];
+      buf[brev(j, lgH) * ld + c] = v;
+    }
+    __syncthreads();
+    smem_fft<T, -1, true>(buf, tw, lgH, lgBC, ld, 1);
+  }
+  const T two_pi_L = (T)(2.0 * M_PI / sp.L);
+  const T inv_L3 = (T)sp.inv_L3;
+  const T tau_eps = (T)(sp.tau / sp.eps), eps_tau = (T)(sp.eps / sp.tau), k2 = (T)sp.k2, tau = (T)sp.tau;
+  const T filt = sp.H0 > 0 ? (T)(-2.0 * M_PI * M_PI / (sp.H0 * sp.H0)) : T(0);
+  for (int t = threadIdx.x; t < H * BC; t += blockDim.x) {
+    const int j = t >> lgBC, c = t & (BC - 1);
+    const int m = b0 + c;
+    const int jr = brev(j, lgH);
+    cpx<T> o1{T(0), T(0)}, o2{T(0), T(0)}, o3{T(0), T(0)};
+    if (c < nb) {
+      const int ky = m / nh, kz = m - ky * nh;
+      const int qx = j < H / 2 ? j : j - H;
+      const int qy = ky < H / 2 ? ky : ky - H;
+      const int qz = kz < H / 2 ? kz : kz - H;
+      const T q2 = (T)(qx * qx + qy * qy + qz * qz);
+      const T Phi = sp.H0 > 0 ? t_exp(filt * q2) : T(1);
+      const size_t gi = (size_t)j * B + m;
+      if (MODE == kModeStep || MODE == kModeGradOnly) {
+        const cpx<T> a = alpha[gi];
+        if (MODE == kModeStep) {
+          cpx<T> beta = buf[j * ld + c];
+          beta.x *= inv_L3;
+          beta.y *= inv_L3;
+          const T lam = two_pi_L * two_pi_L * q2 + k2;
+          cpx<T> an;
+          if (sp.propagator == 0) {
+            const T kappa = T(1) / (T(1) + tau_eps * lam);
+            const T src = T(1) / (lam + eps_tau);
+            an = cpx<T>{kappa * a.x + src * beta.x, kappa * a.y + src * beta.y};
+          } else {
+            const T kappa = t_exp(-tau_eps * lam);
+            an = cpx<T>{kappa * (a.x + tau * beta.x), kappa * (a.y + tau * beta.y)};
+          }
+          alpha[gi] = an;
+          if (m == 0 && j == 0 && alpha0_shadow) {
+            const double lam0 = sp.k2;
+            double s = *alpha0_shadow;
+            if (sp.propagator == 0) s = s / (1.0 + sp.tau / sp.eps * lam0) + sp.beta0 / (lam0 + sp.eps / sp.tau);
+            else s = exp(-sp.tau / sp.eps * lam0) * (s + sp.tau * sp.beta0);
+            *alpha0_shadow = s;
+          }
+        }
+        const T yx = two_pi_L * (T)qx * Phi, yy = two_pi_L * (T)qy * Phi, yz = two_pi_L * (T)qz * Phi;
+        // i y a = (-y a.y, y a.x)
+        if (qx != -H / 2) o1 = cpx<T>{-yx * a.y, yx * a.x};
+        if (qy != -H / 2) o2 = cpx<T>{-yy * a.y, yy * a.x};
+        if (qz != -H / 2) o3 = cpx<T>{-yz * a.y, yz * a.x};
+      } else if (MODE == kModeDensity) {
+        const cpx<T> beta = buf[j * ld + c];
+        o1 = cpx<T>{beta.x * inv_L3 * Phi, beta.y * inv_L3 * Phi};
+      } else {
+        o1 = alpha[gi];
+      }
+    }
+    buf[jr * ld + BC + c] = o1;
+    buf[jr * ld + 2 * BC + c] = o2;
+    buf[jr * ld + 3 * BC + c] = o3;
+  }
+  __syncthreads();
+  constexpr int nout = (MODE == kModeStep || MODE == kModeGradOnly) ? 3 : 1;
+  // inverse transform of slots 1..3 (slot 0 rides along as a fourth pencil)
+  smem_fft<T, +1, true>(buf, tw, lgH, lgBC + 2, ld, 1);
+  for (int t = threadIdx.x; t < H * BC; t += blockDim.x) {
+    const int j = t >> lgBC, c = t & (BC - 1);
+    if (c < nb) {
+#pragma unroll
+      for (int d = 0; d < nout; ++d) T2[d * S + (size_t)j * B + b0 + c] = buf[j * ld + (d + 1) * BC + c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Rows c2r: rows 2c, 2c+1 (Hermitian half spectra A, B) form Z = A + i B over
+// the full index range (Z_{n-k} = conj A_k + i conj B_k); the inverse FFT
+// gives a + i b.  The imaginary parts of the k = 0 and k = n/2 entries are
+// dropped (they carry no real signal).
+// ---------------------------------------------------------------------------
+template <typename T, int NCOMP>
+__global__ void __launch_bounds__(kThreads)
+k_rows_c2r(const cpx<T>* __restrict__ in, size_t comp_stride, T* __restrict__ out, int lgH, int rows,
+           int RP, double* max_acc) {
+  extern __shared__ unsigned char smem_raw[];
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* buf = tw + kNmax / 2;
+  const int H = 1 << lgH, nh = H / 2 + 1, ld = H + 1;
+  constexpr int NOUT = NCOMP == 3 ? 4 : 1;
+  T* obuf = reinterpret_cast<T*>(buf + RP * ld);
+  const int lgc = ilog2_dev(RP);
+  load_twiddles(tw);
+  const int row0 = blockIdx.x * 2 * RP;
+  const int nrow = min(2 * RP, rows - row0);
+  for (int d = 0; d < NCOMP; ++d) {
+    const cpx<T>* src = in + d * comp_stride;
+    for (int t = threadIdx.x; t < RP * H; t += blockDim.x) {
+      const int c = t >> lgH, k = t & (H - 1);
+      cpx<T> z{T(0), T(0)};
+      if (2 * c < nrow) {
+        const size_t ra = (size_t)(row0 + 2 * c) * nh, rb = ra + nh;
+        cpx<T> A, Bv;
+        if (k <= H / 2) {
+          A = src[ra + k];
+          Bv = src[rb + k];
+          if (k == 0 || k == H / 2) { A.y = T(0); Bv.y = T(0); }
+        } else {
+          A = cconj(src[ra + (H - k)]);
+          Bv = cconj(src[rb + (H - k)]);
+        }
+        z = cpx<T>{A.x - Bv.y, A.y + Bv.x};
+      }
+      buf[c * ld + brev(k, lgH)] = z;
+    }
+    __syncthreads();
+    smem_fft<T, +1, false>(buf, tw, lgH, lgc, 1, ld);
+    for (int t = threadIdx.x; t < 2 * RP * H; t += blockDim.x) {
+      const int r = t >> lgH, j = t & (H - 1);
+      const cpx<T> v = buf[(r >> 1) * ld + j];
+      obuf[(r * H + j) * NOUT + d] = (r & 1) ? v.y : v.x;
+    }
+    __syncthreads();
+  }
+  double mx = -INFINITY;
+  if (NOUT == 4) {
+    for (int t = threadIdx.x; t < 2 * RP * H; t += blockDim.x) {
+      const int r = t >> lgH;
+      if (r < nrow) {
+        const int j = t & (H - 1);
+        T* o = out + ((size_t)(row0 + r) * H + j) * 4;
+        const T* s = obuf + (r * H + j) * 4;
+        if constexpr (sizeof(T) == 4) {
+          *reinterpret_cast<float4*>(o) = make_float4(s[0], s[1], s[2], 0.f);
+        } else {
+          reinterpret_cast<double2*>(o)[0] = make_double2(s[0], s[1]);
+          reinterpret_cast<double2*>(o)[1] = make_double2(s[2], 0.0);
+        }
+      }
+    }
+  } else {
+    for (int t = threadIdx.x; t < 2 * RP * H; t += blockDim.x) {
+      const int r = t >> lgH;
+      if (r < nrow) {
+        const T v = obuf[t];
+        out[(size_t)row0 * H + t] = v;
+        mx = fmax(mx, (double)v);
+      }
+    }
+    if (max_acc) {
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if ((threadIdx.x & 31) == 0) {
+        // order-preserving map of doubles onto signed 64-bit integers
+        long long b = __double_as_longlong(mx);
+        if (b < 0) b ^= 0x7fffffffffffffffLL;
+        atomicMax(reinterpret_cast<long long*>(max_acc), b);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaSuccess;
+}
+
+static int rows_per_pair_block(int H, size_t elem, bool with_out4) {
+  // row pairs per block: up to 8, bounded so the shared buffers stay <= ~96 KB
+  int rp = 8;
+  auto bytes = [&](int r) {
+    size_t b = (size_t)r * (H + 1) * 2 * elem;
+    if (with_out4) b += (size_t)2 * r * H * 4 * elem;
+    return b;
+  };
+  while (rp > 1 && bytes(rp) > 96 * 1024) rp >>= 1;
+  return rp;
+}
+
+template <typename T>
+cudaError_t launch_rows_r2c(const void* in, int in_kind, double in_scale, bool zero_input, cpx<T>* out,
+                            int H, int rows, double* mass_acc, cudaStream_t s) {
+  const int lgH = ilog2(H);
+  const int RP = rows_per_pair_block(H, sizeof(T), false);
+  const size_t smem = (kNmax / 2 + (size_t)RP * (H + 1)) * sizeof(cpx<T>);
+  const int blocks = (rows + 2 * RP - 1) / (2 * RP);
+  cudaError_t e;
+  if (in_kind == 0) {
+    auto k = k_rows_r2c<T, T>;
+    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
+    k<<<blocks, kThreads, smem, s>>>((T*)in, in_scale, zero_input ? 1 : 0, out, lgH, rows, RP, mass_acc);
+  } else {
+    auto k = k_rows_r2c<T, unsigned long long>;
+    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
+    k<<<blocks, kThreads, smem, s>>>((unsigned long long*)in, in_scale, zero_input ? 1 : 0, out, lgH, rows,
+                                     RP, mass_acc);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+static int col_chunk(int H, int slots) {
+  // columns per block: power of two, shared buffer <= ~96 KB
+  int bc = 32;
+  while (bc > 1 && (size_t)H * slots * bc * sizeof(cpx<T>) > 96 * 1024) bc >>= 1;
+  return bc;
+}
+
+template <typename T>
+cudaError_t launch_cols(cpx<T>* data, int H, int A, int B, int ncomp, size_t comp_stride, int dir, double scale,
+                        cudaStream_t s) {
+  const int lgH = ilog2(H);
+  int BC = col_chunk<T>(H, 1);
+  if (BC > 16) BC = 16;
+  const int lgBC = ilog2(BC);
+  const size_t smem = (kNmax / 2 + (size_t)H * BC) * sizeof(cpx<T>);
+  dim3 grid((B + BC - 1) / BC, A, ncomp);
+  cudaError_t e;
+  if (dir < 0) {
+    auto k = k_cols<T, -1>;
+    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
+    k<<<grid, kThreads, smem, s>>>(data, lgH, B, lgBC, comp_stride, (T)scale);
+  } else {
+    auto k = k_cols<T, +1>;
+    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
+    k<<<grid, kThreads, smem, s>>>(data, lgH, B, lgBC, comp_stride, (T)scale);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+static cudaError_t spectral_mode(const cpx<T>* T1, cpx<T>* alpha, cpx<T>* T2, int H, SpecParams sp,
+                                 double* shadow, cudaStream_t s) {
+  const int lgH = ilog2(H);
+  int BC = col_chunk<T>(H, 4);
+  if (BC > 16) BC = 16;
+  const int lgBC = ilog2(BC);
+  const int B = H * (H / 2 + 1);
+  const size_t smem = (kNmax / 2 + (size_t)H * 4 * BC) * sizeof(cpx<T>);
+  auto k = k_spectral_x<T, MODE>;
+  cudaError_t e = set_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  k<<<(B + BC - 1) / BC, kThreads, smem, s>>>(T1, alpha, T2, lgH, lgBC, sp, shadow);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spectral_x(const cpx<T>* T1, cpx<T>* alpha, cpx<T>* T2, int H, SpecParams sp, int mode,
+                              double* alpha0_shadow, cudaStream_t s) {
+  switch (mode) {
+    case kModeStep: return spectral_mode<T, kModeStep>(T1, alpha, T2, H, sp, alpha0_shadow, s);
+    case kModeDensity: return spectral_mode<T, kModeDensity>(T1, alpha, T2, H, sp, nullptr, s);
+    case kModeField: return spectral_mode<T, kModeField>(T1, alpha, T2, H, sp, nullptr, s);
+    case kModeGradOnly: return spectral_mode<T, kModeGradOnly>(T1, alpha, T2, H, sp, nullptr, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_rows_c2r(const cpx<T>* in, int ncomp, size_t comp_stride, T* out, int H, int rows,
+                            double* max_acc, cudaStream_t s) {
+  const int lgH = ilog2(H);
+  const int RP = rows_per_pair_block(H, sizeof(T), true);
+  const int NOUT = ncomp == 3 ? 4 : 1;
+  const size_t smem = (kNmax / 2 + (size_t)RP * (H + 1)) * sizeof(cpx<T>) + (size_t)2 * RP * H * NOUT * sizeof(T);
+  const int blocks = (rows + 2 * RP - 1) / (2 * RP);
+  cudaError_t e;
+  if (ncomp == 3) {
+    auto k = k_rows_c2r<T, 3>;
+    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
+    k<<<blocks, kThreads, smem, s>>>(in, comp_stride, out, lgH, rows, RP, nullptr);
+  } else {
+    auto k = k_rows_c2r<T, 1>;
+    if ((e = set_smem(k, smem)) != cudaSuccess) return e;
+    k<<<blocks, kThreads, smem, s>>>(in, comp_stride, out, lgH, rows, RP, max_acc);
+  }
+  return cudaGetLastError();
+}
+
+#define SIPF_INST(T)                                                                                          \
+  template cudaError_t launch_rows_r2c<T>(const void*, int, double, bool, cpx<T>*, int, int, double*,        \
+                                          cudaStream_t);                                                    \
+  template cudaError_t launch_cols<T>(cpx<T>*, int, int, int, int, size_t, int, double, cudaStream_t);       \
+  template cudaError_t launch_spectral_x<T>(const cpx<T>*, cpx<T>*, cpx<T>*, int, SpecParams, int, double*,  \
+                                            cudaStream_t);                                                  \
+  template cudaError_t launch_rows_c2r<T>(const cpx<T>*, int, size_t, T*, int, int, double*, cudaStream_t);
+SIPF_INST(float)
+SIPF_INST(double)
+#undef SIPF_INST
+
+}  // namespace sipf

@@ -1,0 +1,601 @@
+// C ABI of libsipf: parameter validation, the context (device state of one
+// SIPF-PIC run), the step loop of Algorithm 4 and the stateless operators.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/sipf.h"
+#include "sipf_internal.h"
+
+using namespace sipf;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(e == cudaErrorMemoryAllocation ? SIPF_ENOMEM : SIPF_ECUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define SIPF_CK(call)                                          \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);        \
+  } while (0)
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+double effective_H0(const sipf_params& p) {
+  if (p.H0 < 0) return ceil(8.0 * pow((double)p.H, 8.0 / 13.0) * pow(p.L, 5.0 / 13.0));
+  return p.H0;
+}
+
+int validate(const sipf_params* p) {
+  if (!p) return fail(SIPF_EINVAL, "params is NULL");
+  auto bad = [](const char* f) { return fail(SIPF_EINVAL, std::string("invalid parameter: ") + f); };
+  if (!(p->P >= 1)) return bad("P (must be >= 1)");
+  if (!is_pow2(p->H) || p->H < 8 || p->H > kNmax) return bad("H (power of two in [8, 256])");
+  if (p->precision != 32 && p->precision != 64) return bad("precision (32 or 64)");
+  if (!(isfinite(p->L) && p->L > 0)) return bad("L (> 0)");
+  if (!(isfinite(p->dt) && p->dt > 0)) return bad("dt (> 0)");
+  if (!(isfinite(p->eps) && p->eps > 0)) return bad("eps (> 0)");
+  if (!(isfinite(p->mu) && p->mu >= 0)) return bad("mu (>= 0)");
+  if (!(isfinite(p->chi) && p->chi >= 0)) return bad("chi (>= 0)");
+  if (!(isfinite(p->k) && p->k >= 0)) return bad("k (>= 0)");
+  if (!(isfinite(p->mass) && p->mass > 0)) return bad("mass (> 0)");
+  if (!(isfinite(p->T) && p->T >= 0)) return bad("T (>= 0)");
+  if (!isfinite(p->H0)) return bad("H0 (finite)");
+  if (p->p2g_order != 2 && p->p2g_order != 4) return bad("p2g_order (2 or 4)");
+  if (p->g2p_order != 2 && p->g2p_order != 4) return bad("g2p_order (2 or 4)");
+  if (p->splitting != SIPF_SPLIT_HALF && p->splitting != SIPF_SPLIT_PLAIN) return bad("splitting");
+  if (p->deposit_mode != SIPF_DEPOSIT_ATOMIC && p->deposit_mode != SIPF_DEPOSIT_DETERMINISTIC)
+    return bad("deposit_mode");
+  if (p->propagator != SIPF_PROP_IMPLICIT && p->propagator != SIPF_PROP_EXP) return bad("propagator");
+  if (p->resort_every < 0) return bad("resort_every (>= 0)");
+  if (p->k == 0 && p->propagator == SIPF_PROP_IMPLICIT && p->eps / p->dt == 0) return bad("eps/dt");
+  return SIPF_OK;
+}
+
+// 2^60: fixed-point unit of the deterministic deposit (one particle's stencil
+// weights F are stored as llrint(F * 2^60 / P); a node sum is bounded by
+// 2 * 2^60 because sum |F_gamma| <= 2 for Gamma_4).
+constexpr double kFixOne = 1152921504606846976.0;
+
+}  // namespace
+
+struct sipf_ctx {
+  sipf_params p{};
+  double H0 = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t n = 0;
+  size_t esz = 4;
+  void* X[3] = {nullptr, nullptr, nullptr};
+  void* phi = nullptr;     // H^3 T, or H^3 int64 (deterministic deposit)
+  void* T1 = nullptr;      // S complex: forward intermediate
+  void* alpha = nullptr;   // S complex: alpha^(n)
+  void* T2 = nullptr;      // 3 S complex: gradient spectra
+  void* grad = nullptr;    // 4 H^3 T: (gx, gy, gz, 0) per node; scratch between steps
+  double* dsc = nullptr;   // FP64 accumulators (see kDsc*)
+  int* err = nullptr;
+  int64_t H3() const { return (int64_t)p.H * p.H * p.H; }
+  int64_t S() const { return (int64_t)p.H * p.H * (p.H / 2 + 1); }
+  bool fixed() const { return p.deposit_mode == SIPF_DEPOSIT_DETERMINISTIC; }
+};
+
+enum { kDscMass = 0, kDscAlpha0 = 1, kDscM2 = 2, kDscRing = 3, kDscHF = 4, kDscTot = 5, kDscMax = 6, kDscCount = 8 };
+
+namespace {
+
+SpecParams spec_params(const sipf_ctx* c) {
+  SpecParams sp;
+  sp.L = c->p.L;
+  sp.inv_L3 = 1.0 / (c->p.L * c->p.L * c->p.L);
+  sp.tau = c->p.dt;
+  sp.eps = c->p.eps;
+  sp.k2 = c->p.k * c->p.k;
+  sp.H0 = c->H0;
+  sp.beta0 = c->p.mass * sp.inv_L3;
+  sp.propagator = c->p.propagator;
+  return sp;
+}
+
+template <typename T> T particle_weight(const sipf_ctx* c) {
+  return c->fixed() ? (T)(kFixOne / (double)c->p.P) : (T)(c->p.mass / (double)c->p.P);
+}
+
+double fixed_in_scale(const sipf_ctx* c) { return c->p.mass / kFixOne; }
+
+template <typename T> int deposit_positions(sipf_ctx* c) {
+  const size_t gb = (size_t)c->H3() * (c->fixed() ? 8 : sizeof(T));
+  SIPF_CK(cudaMemsetAsync(c->phi, 0, gb, c->stream));
+  SIPF_CK(launch_deposit<T>((T*)c->X[0], (T*)c->X[1], (T*)c->X[2], c->p.P, make_geo<T>(c->p.L, c->p.H),
+                            particle_weight<T>(c), c->phi, c->p.p2g_order, c->fixed() ? 1 : 0, c->stream));
+  return SIPF_OK;
+}
+
+template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
+  const int H = c->p.H;
+  const int nh = H / 2 + 1;
+  const size_t S = (size_t)c->S();
+  const SpecParams sp = spec_params(c);
+  MoveArgs<T> a;
+  a.x = (T*)c->X[0];
+  a.y = (T*)c->X[1];
+  a.z = (T*)c->X[2];
+  a.P = c->p.P;
+  a.grad4 = (const T*)c->grad;
+  a.phi = c->phi;
+  a.g = make_geo<T>(c->p.L, H);
+  a.s_noise = (T)(c->p.splitting == SIPF_SPLIT_HALF ? sqrt(c->p.mu * c->p.dt) : sqrt(2.0 * c->p.mu * c->p.dt));
+  a.chitau = (T)(c->p.chi * c->p.dt);
+  a.w = particle_weight<T>(c);
+  a.seed = c->p.seed;
+  a.p2g = c->p.p2g_order;
+  a.g2p = c->p.g2p_order;
+  a.split = c->p.splitting;
+  a.fixed = c->fixed() ? 1 : 0;
+  a.err = c->err;
+  cpx<T>* T1 = (cpx<T>*)c->T1;
+  cpx<T>* T2 = (cpx<T>*)c->T2;
+  cpx<T>* al = (cpx<T>*)c->alpha;
+  for (int64_t s = 0; s < nsteps; ++s) {
+    const int64_t n = c->n + 1;
+    // beta^(n-1) = F_H I(rho-hat^(n-1)); the deposit grid is cleared as it is read
+    SIPF_CK(launch_rows_r2c<T>(c->phi, c->fixed() ? 1 : 0, fixed_in_scale(c), true, T1, H, H * H, nullptr,
+                               c->stream));
+    SIPF_CK(launch_cols<T>(T1, H, H, nh, 1, 0, -1, 1.0, c->stream));
+    // alpha^n and G(alpha^(n-1)), x axis back-transformed
+    SIPF_CK(launch_spectral_x<T>(T1, al, T2, H, sp, kModeStep, c->dsc + kDscAlpha0, c->stream));
+    SIPF_CK(launch_cols<T>(T2, H, H, nh, 3, S, +1, 1.0, c->stream));
+    SIPF_CK(launch_rows_c2r<T>(T2, 3, S, (T*)c->grad, H, H * H, nullptr, c->stream));
+    // X^(n-1) -> X^n, deposit X^n
+    a.n = (uint32_t)n;
+    SIPF_CK(launch_move_deposit<T>(a, c->stream));
+    c->n = n;
+  }
+  return SIPF_OK;
+}
+
+// rho_num (filtered) or the plain deposited density into the grad scratch
+// buffer as an H^3 real grid; FP64 mass sum and max into dsc.
+template <typename T> int density_impl(sipf_ctx* c, int filtered, T** out_grid) {
+  const int H = c->p.H, nh = H / 2 + 1;
+  const size_t S = (size_t)c->S();
+  cpx<T>* T1 = (cpx<T>*)c->T1;
+  cpx<T>* T2 = (cpx<T>*)c->T2;
+  SpecParams sp = spec_params(c);
+  if (!filtered) sp.H0 = 0.0;
+  SIPF_CK(launch_rows_r2c<T>(c->phi, c->fixed() ? 1 : 0, fixed_in_scale(c), false, T1, H, H * H,
+                             c->dsc + kDscMass, c->stream));
+  SIPF_CK(launch_cols<T>(T1, H, H, nh, 1, 0, -1, 1.0, c->stream));
+  SIPF_CK(launch_spectral_x<T>(T1, (cpx<T>*)c->alpha, T2, H, sp, kModeDensity, nullptr, c->stream));
+  SIPF_CK(launch_cols<T>(T2, H, H, nh, 1, S, +1, 1.0, c->stream));
+  SIPF_CK(launch_rows_c2r<T>(T2, 1, S, (T*)c->grad, H, H * H, c->dsc + kDscMax, c->stream));
+  *out_grid = (T*)c->grad;
+  return SIPF_OK;
+}
+
+template <typename T> int copy_grid_to_host(sipf_ctx* c, const T* dev, int64_t count, double* out, double scale) {
+  std::vector<T> h((size_t)count);
+  SIPF_CK(cudaMemcpyAsync(h.data(), dev, (size_t)count * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+  SIPF_CK(cudaStreamSynchronize(c->stream));
+  for (int64_t i = 0; i < count; ++i) out[i] = (double)h[(size_t)i] * scale;
+  return SIPF_OK;
+}
+
+template <typename T> int density_host(sipf_ctx* c, double* out, int filtered) {
+  const double h3 = pow(c->p.L / c->p.H, 3);
+  if (!filtered) {
+    // I rho-hat / h^3 straight from the deposit grid
+    if (c->fixed()) {
+      std::vector<long long> h((size_t)c->H3());
+      SIPF_CK(cudaMemcpyAsync(h.data(), c->phi, h.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+      SIPF_CK(cudaStreamSynchronize(c->stream));
+      const double sc = fixed_in_scale(c) / h3;
+      for (size_t i = 0; i < h.size(); ++i) out[i] = (double)h[i] * sc;
+      return SIPF_OK;
+    }
+    return copy_grid_to_host<T>(c, (const T*)c->phi, c->H3(), out, 1.0 / h3);
+  }
+  T* g = nullptr;
+  int r = density_impl<T>(c, 1, &g);
+  if (r) return r;
+  return copy_grid_to_host<T>(c, g, c->H3(), out, 1.0);
+}
+
+template <typename T> int field_host(sipf_ctx* c, double* out) {
+  const int H = c->p.H, nh = H / 2 + 1;
+  const size_t S = (size_t)c->S();
+  SpecParams sp = spec_params(c);
+  SIPF_CK(launch_spectral_x<T>(nullptr, (cpx<T>*)c->alpha, (cpx<T>*)c->T2, H, sp, kModeField, nullptr, c->stream));
+  SIPF_CK(launch_cols<T>((cpx<T>*)c->T2, H, H, nh, 1, S, +1, 1.0, c->stream));
+  SIPF_CK(launch_rows_c2r<T>((cpx<T>*)c->T2, 1, S, (T*)c->grad, H, H * H, nullptr, c->stream));
+  return copy_grid_to_host<T>(c, (const T*)c->grad, c->H3(), out, 1.0);
+}
+
+template <typename T> int gradient_host(sipf_ctx* c, double* out) {
+  const int H = c->p.H, nh = H / 2 + 1;
+  const size_t S = (size_t)c->S();
+  SpecParams sp = spec_params(c);
+  SIPF_CK(launch_spectral_x<T>(nullptr, (cpx<T>*)c->alpha, (cpx<T>*)c->T2, H, sp, kModeGradOnly, nullptr, c->stream));
+  SIPF_CK(launch_cols<T>((cpx<T>*)c->T2, H, H, nh, 3, S, +1, 1.0, c->stream));
+  SIPF_CK(launch_rows_c2r<T>((cpx<T>*)c->T2, 3, S, (T*)c->grad, H, H * H, nullptr, c->stream));
+  const int64_t N = c->H3();
+  std::vector<T> h((size_t)N * 4);
+  SIPF_CK(cudaMemcpyAsync(h.data(), c->grad, h.size() * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+  SIPF_CK(cudaStreamSynchronize(c->stream));
+  for (int d = 0; d < 3; ++d)
+    for (int64_t i = 0; i < N; ++i) out[d * N + i] = (double)h[(size_t)i * 4 + d];
+  return SIPF_OK;
+}
+
+template <typename T> int diagnostics_impl(sipf_ctx* c, sipf_diag* d) {
+  const double neg_inf_key = -INFINITY;
+  double init[kDscCount];
+  SIPF_CK(cudaMemcpyAsync(init, c->dsc, sizeof(init), cudaMemcpyDeviceToHost, c->stream));
+  SIPF_CK(cudaStreamSynchronize(c->stream));
+  init[kDscMass] = 0;
+  init[kDscM2] = init[kDscRing] = init[kDscHF] = init[kDscTot] = 0;
+  {
+    long long b;
+    memcpy(&b, &neg_inf_key, 8);
+    b ^= 0x7fffffffffffffffLL;   // order-preserving key of -inf
+    memcpy(&init[kDscMax], &b, 8);
+  }
+  SIPF_CK(cudaMemcpyAsync(c->dsc, init, sizeof(init), cudaMemcpyHostToDevice, c->stream));
+  T* g = nullptr;
+  int r = density_impl<T>(c, c->H0 > 0 ? 1 : 0, &g);
+  if (r) return r;
+  SIPF_CK(launch_moments<T>((T*)c->X[0], (T*)c->X[1], (T*)c->X[2], c->p.P, c->dsc + kDscM2, c->stream));
+  SIPF_CK(launch_alpha_energy<T>((cpx<T>*)c->alpha, c->p.H, c->dsc + kDscHF, c->stream));
+  double out[kDscCount];
+  SIPF_CK(cudaMemcpyAsync(out, c->dsc, sizeof(out), cudaMemcpyDeviceToHost, c->stream));
+  SIPF_CK(cudaStreamSynchronize(c->stream));
+  long long b;
+  memcpy(&b, &out[kDscMax], 8);
+  if (b < 0) b ^= 0x7fffffffffffffffLL;
+  double mx;
+  memcpy(&mx, &b, 8);
+  d->mass = out[kDscMass];
+  d->alpha0 = out[kDscAlpha0];
+  d->peak = mx;
+  d->hf_frac = out[kDscTot] > 0 ? out[kDscHF] / out[kDscTot] : 0.0;
+  d->m2 = out[kDscM2] / (double)c->p.P;
+  d->ring_radius = out[kDscRing] / (double)c->p.P;
+  d->step = c->n;
+  return SIPF_OK;
+}
+
+template <typename T> int upload_aos(sipf_ctx* c, const double* X) {
+  const size_t bytes = (size_t)c->p.P * 3 * sizeof(double);
+  double* stage = nullptr;
+  SIPF_CK(cudaMalloc(&stage, bytes));
+  cudaError_t e = cudaMemcpyAsync(stage, X, bytes, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = launch_aos_to_soa<T>(stage, c->p.P, make_geo<T>(c->p.L, c->p.H), (T*)c->X[0], (T*)c->X[1], (T*)c->X[2],
+                             c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(stage);
+  if (e != cudaSuccess) return cuda_fail(e, "upload positions");
+  return deposit_positions<T>(c);
+}
+
+template <typename T> int positions_host(sipf_ctx* c, double* out) {
+  const size_t P = (size_t)c->p.P;
+  std::vector<T> h(3 * P);
+  for (int d = 0; d < 3; ++d)
+    SIPF_CK(cudaMemcpyAsync(h.data() + d * P, c->X[d], P * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+  SIPF_CK(cudaStreamSynchronize(c->stream));
+  for (size_t i = 0; i < P; ++i)
+    for (int d = 0; d < 3; ++d) out[3 * i + d] = (double)h[d * P + i];
+  return SIPF_OK;
+}
+
+template <typename T> int spectrum_host(sipf_ctx* c, double* out) {
+  const size_t n = (size_t)c->S() * 2;
+  std::vector<T> h(n);
+  SIPF_CK(cudaMemcpyAsync(h.data(), c->alpha, n * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+  SIPF_CK(cudaStreamSynchronize(c->stream));
+  for (size_t i = 0; i < n; ++i) out[i] = (double)h[i];
+  return SIPF_OK;
+}
+
+void free_ctx(sipf_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (int d = 0; d < 3; ++d) cudaFree(c->X[d]);
+  cudaFree(c->phi);
+  cudaFree(c->T1);
+  cudaFree(c->alpha);
+  cudaFree(c->T2);
+  cudaFree(c->grad);
+  cudaFree(c->dsc);
+  cudaFree(c->err);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+#define DISPATCH(ctx, fn, ...) ((ctx)->p.precision == 64 ? fn<double>(__VA_ARGS__) : fn<float>(__VA_ARGS__))
+
+}  // namespace
+
+extern "C" {
+
+int sipf_params_default(sipf_params* p) {
+  if (!p) return fail(SIPF_EINVAL, "params is NULL");
+  memset(p, 0, sizeof(*p));
+  p->chi = p->mu = p->eps = p->k = 1.0;
+  p->L = 1.0;
+  p->mass = 1.0;
+  p->dt = 1e-3;
+  p->T = 0.0;
+  p->H0 = -1.0;
+  p->seed = 0;
+  p->P = 0;
+  p->H = 64;
+  p->precision = 32;
+  p->p2g_order = 4;
+  p->g2p_order = 2;
+  p->splitting = SIPF_SPLIT_HALF;
+  p->deposit_mode = SIPF_DEPOSIT_ATOMIC;
+  p->propagator = SIPF_PROP_IMPLICIT;
+  p->resort_every = 0;
+  return SIPF_OK;
+}
+
+int sipf_validate(const sipf_params* p) { return validate(p); }
+
+int sipf_init(const sipf_params* p, const double* X0, void* stream, sipf_ctx** out) {
+  if (!out) return fail(SIPF_EINVAL, "out is NULL");
+  *out = nullptr;
+  int r = validate(p);
+  if (r) return r;
+  if (!X0) return fail(SIPF_EINVAL, "X0 is NULL");
+  for (int64_t i = 0; i < 3 * p->P; ++i)
+    if (!isfinite(X0[i])) return fail(SIPF_ENONFINITE, "X0 holds a non-finite coordinate");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(SIPF_ENODEV, "no CUDA device");
+  SIPF_CK(ensure_device_tables());
+  sipf_ctx* c = new sipf_ctx();
+  c->p = *p;
+  c->H0 = effective_H0(*p);
+  c->esz = p->precision == 64 ? 8 : 4;
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaStreamCreate"); }
+    c->own_stream = true;
+  }
+  const size_t P = (size_t)p->P;
+  const size_t N = (size_t)c->H3();
+  const size_t S = (size_t)c->S();
+  cudaError_t e = cudaSuccess;
+  for (int d = 0; d < 3 && e == cudaSuccess; ++d) e = cudaMalloc(&c->X[d], P * c->esz);
+  if (e == cudaSuccess) e = cudaMalloc(&c->phi, N * (c->fixed() ? 8 : c->esz));
+  if (e == cudaSuccess) e = cudaMalloc(&c->T1, S * 2 * c->esz);
+  if (e == cudaSuccess) e = cudaMalloc(&c->alpha, S * 2 * c->esz);
+  if (e == cudaSuccess) e = cudaMalloc(&c->T2, 3 * S * 2 * c->esz);
+  if (e == cudaSuccess) e = cudaMalloc(&c->grad, 4 * N * c->esz);
+  if (e == cudaSuccess) e = cudaMalloc(&c->dsc, kDscCount * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->alpha, 0, S * 2 * c->esz, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->dsc, 0, kDscCount * sizeof(double), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
+  if (e != cudaSuccess) {
+    free_ctx(c);
+    return cuda_fail(e, "sipf_init allocation");
+  }
+  r = DISPATCH(c, upload_aos, c, X0);
+  if (r) { free_ctx(c); return r; }
+  *out = c;
+  return SIPF_OK;
+}
+
+int sipf_step(sipf_ctx* c, int64_t nsteps) {
+  if (!c) return fail(SIPF_EINVAL, "ctx is NULL");
+  if (nsteps < 0) return fail(SIPF_EINVAL, "nsteps < 0");
+  if (c->n + nsteps > 0xFFFFFFFFLL) return fail(SIPF_EINVAL, "step counter would exceed 2^32 - 1");
+  return DISPATCH(c, step_impl, c, nsteps);
+}
+
+int sipf_run(sipf_ctx* c) {
+  if (!c) return fail(SIPF_EINVAL, "ctx is NULL");
+  const int64_t NT = (int64_t)ceil(c->p.T / c->p.dt - 1e-9);
+  return sipf_step(c, NT > c->n ? NT - c->n : 0);
+}
+
+int64_t sipf_current_step(const sipf_ctx* c) { return c ? c->n : -1; }
+
+int sipf_positions(sipf_ctx* c, double* out) {
+  if (!c || !out) return fail(SIPF_EINVAL, "NULL argument");
+  return DISPATCH(c, positions_host, c, out);
+}
+
+int sipf_set_positions(sipf_ctx* c, const double* X) {
+  if (!c || !X) return fail(SIPF_EINVAL, "NULL argument");
+  for (int64_t i = 0; i < 3 * c->p.P; ++i)
+    if (!isfinite(X[i])) return fail(SIPF_ENONFINITE, "X holds a non-finite coordinate");
+  return DISPATCH(c, upload_aos, c, X);
+}
+
+int sipf_upload_soa(sipf_ctx* c, const void* x, const void* y, const void* z) {
+  if (!c || !x || !y || !z) return fail(SIPF_EINVAL, "NULL argument");
+  const void* src[3] = {x, y, z};
+  for (int d = 0; d < 3; ++d)
+    SIPF_CK(cudaMemcpyAsync(c->X[d], src[d], (size_t)c->p.P * c->esz, cudaMemcpyHostToDevice, c->stream));
+  return c->p.precision == 64 ? deposit_positions<double>(c) : deposit_positions<float>(c);
+}
+
+int sipf_download_soa(sipf_ctx* c, void* x, void* y, void* z) {
+  if (!c || !x || !y || !z) return fail(SIPF_EINVAL, "NULL argument");
+  void* dst[3] = {x, y, z};
+  for (int d = 0; d < 3; ++d)
+    SIPF_CK(cudaMemcpyAsync(dst[d], c->X[d], (size_t)c->p.P * c->esz, cudaMemcpyDeviceToHost, c->stream));
+  return SIPF_OK;
+}
+
+int sipf_positions_dev(sipf_ctx* c, void** x, void** y, void** z) {
+  if (!c || !x || !y || !z) return fail(SIPF_EINVAL, "NULL argument");
+  *x = c->X[0];
+  *y = c->X[1];
+  *z = c->X[2];
+  return SIPF_OK;
+}
+
+int sipf_density(sipf_ctx* c, double* out, int filtered) {
+  if (!c || !out) return fail(SIPF_EINVAL, "NULL argument");
+  return DISPATCH(c, density_host, c, out, filtered);
+}
+
+int sipf_field(sipf_ctx* c, double* out) {
+  if (!c || !out) return fail(SIPF_EINVAL, "NULL argument");
+  return DISPATCH(c, field_host, c, out);
+}
+
+int sipf_spectrum(sipf_ctx* c, double* out) {
+  if (!c || !out) return fail(SIPF_EINVAL, "NULL argument");
+  return DISPATCH(c, spectrum_host, c, out);
+}
+
+int sipf_gradient(sipf_ctx* c, double* out) {
+  if (!c || !out) return fail(SIPF_EINVAL, "NULL argument");
+  return DISPATCH(c, gradient_host, c, out);
+}
+
+int sipf_diagnostics(sipf_ctx* c, sipf_diag* d) {
+  if (!c || !d) return fail(SIPF_EINVAL, "NULL argument");
+  return DISPATCH(c, diagnostics_impl, c, d);
+}
+
+int sipf_sync(sipf_ctx* c) {
+  if (!c) return fail(SIPF_EINVAL, "ctx is NULL");
+  SIPF_CK(cudaStreamSynchronize(c->stream));
+  int flag = 0;
+  SIPF_CK(cudaMemcpy(&flag, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    SIPF_CK(cudaMemset(c->err, 0, sizeof(int)));
+    return fail(SIPF_ENONFINITE, "a particle position became non-finite");
+  }
+  return SIPF_OK;
+}
+
+void sipf_destroy(sipf_ctx* c) { free_ctx(c); }
+
+const char* sipf_strerror(int code) {
+  switch (code) {
+    case SIPF_OK: return "ok";
+    case SIPF_EINVAL: return "invalid argument";
+    case SIPF_ENOMEM: return "out of memory";
+    case SIPF_ECUDA: return "CUDA error";
+    case SIPF_ENONFINITE: return "non-finite value";
+    case SIPF_ETIMEOUT: return "device wait timed out";
+    case SIPF_ENODEV: return "no CUDA device";
+  }
+  return "unknown error";
+}
+
+const char* sipf_last_error(void) { return g_last_error.c_str(); }
+
+// ---- stateless operators ------------------------------------------------------
+
+int sipf_noise_dev(int precision, uint64_t seed, int64_t step, int64_t first, int64_t P, void* z, void* stream) {
+  if (precision != 32 && precision != 64) return fail(SIPF_EINVAL, "precision");
+  if (P < 0 || first < 0 || step < 0 || step > 0xFFFFFFFFLL || (!z && P > 0)) return fail(SIPF_EINVAL, "noise args");
+  if (P == 0) return SIPF_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  SIPF_CK(precision == 64 ? launch_noise<double>(seed, step, first, P, (double*)z, s)
+                          : launch_noise<float>(seed, step, first, P, (float*)z, s));
+  return SIPF_OK;
+}
+
+int sipf_deposit_dev(int precision, const void* x, const void* y, const void* z, int64_t P, int32_t H, double L,
+                     double w, int32_t order, void* grid, void* stream) {
+  if (precision != 32 && precision != 64) return fail(SIPF_EINVAL, "precision");
+  if (!is_pow2(H) || H < 8 || H > kNmax || !(L > 0) || P < 0 || (order != 2 && order != 4) || !grid)
+    return fail(SIPF_EINVAL, "deposit args");
+  if (P > 0 && (!x || !y || !z)) return fail(SIPF_EINVAL, "NULL positions");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t N = (size_t)H * H * H;
+  SIPF_CK(cudaMemsetAsync(grid, 0, N * (precision == 64 ? 8 : 4), s));
+  if (P == 0) return SIPF_OK;
+  if (precision == 64)
+    SIPF_CK(launch_deposit<double>((const double*)x, (const double*)y, (const double*)z, P, make_geo<double>(L, H),
+                                   w, grid, order, 0, s));
+  else
+    SIPF_CK(launch_deposit<float>((const float*)x, (const float*)y, (const float*)z, P, make_geo<float>(L, H),
+                                  (float)w, grid, order, 0, s));
+  return SIPF_OK;
+}
+
+int sipf_gather_dev(int precision, const void* x, const void* y, const void* z, int64_t P, int32_t H, double L,
+                    const void* f, int32_t ncomp, int32_t order, void* out, void* stream) {
+  if (precision != 32 && precision != 64) return fail(SIPF_EINVAL, "precision");
+  if (!is_pow2(H) || H < 8 || H > kNmax || !(L > 0) || P < 0 || (order != 2 && order != 4) || !f || ncomp < 1 ||
+      ncomp > 16)
+    return fail(SIPF_EINVAL, "gather args");
+  if (P == 0) return SIPF_OK;
+  if (!x || !y || !z || !out) return fail(SIPF_EINVAL, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == 64)
+    SIPF_CK(launch_gather<double>((const double*)x, (const double*)y, (const double*)z, P, make_geo<double>(L, H),
+                                  (const double*)f, ncomp, 0, order, (double*)out, s));
+  else
+    SIPF_CK(launch_gather<float>((const float*)x, (const float*)y, (const float*)z, P, make_geo<float>(L, H),
+                                 (const float*)f, ncomp, 0, order, (float*)out, s));
+  return SIPF_OK;
+}
+
+int sipf_forward_ft_dev(int precision, int32_t H, double L, const void* grid, void* spec, void* stream) {
+  if (precision != 32 && precision != 64) return fail(SIPF_EINVAL, "precision");
+  if (!is_pow2(H) || H < 8 || H > kNmax || !(L > 0) || !grid || !spec) return fail(SIPF_EINVAL, "forward_ft args");
+  SIPF_CK(ensure_device_tables());
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nh = H / 2 + 1;
+  const double sc = 1.0 / (L * L * L);
+  if (precision == 64) {
+    cpx<double>* o = (cpx<double>*)spec;
+    SIPF_CK(launch_rows_r2c<double>(grid, 0, 1.0, false, o, H, H * H, nullptr, s));
+    SIPF_CK(launch_cols<double>(o, H, H, nh, 1, 0, -1, 1.0, s));
+    SIPF_CK(launch_cols<double>(o, H, 1, H * nh, 1, 0, -1, sc, s));
+  } else {
+    cpx<float>* o = (cpx<float>*)spec;
+    SIPF_CK(launch_rows_r2c<float>(grid, 0, 1.0, false, o, H, H * H, nullptr, s));
+    SIPF_CK(launch_cols<float>(o, H, H, nh, 1, 0, -1, 1.0, s));
+    SIPF_CK(launch_cols<float>(o, H, 1, H * nh, 1, 0, -1, sc, s));
+  }
+  return SIPF_OK;
+}
+
+int sipf_inverse_ft_dev(int precision, int32_t H, void* spec, void* grid, void* stream) {
+  if (precision != 32 && precision != 64) return fail(SIPF_EINVAL, "precision");
+  if (!is_pow2(H) || H < 8 || H > kNmax || !grid || !spec) return fail(SIPF_EINVAL, "inverse_ft args");
+  SIPF_CK(ensure_device_tables());
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nh = H / 2 + 1;
+  if (precision == 64) {
+    cpx<double>* o = (cpx<double>*)spec;
+    SIPF_CK(launch_cols<double>(o, H, 1, H * nh, 1, 0, +1, 1.0, s));
+    SIPF_CK(launch_cols<double>(o, H, H, nh, 1, 0, +1, 1.0, s));
+    SIPF_CK(launch_rows_c2r<double>(o, 1, 0, (double*)grid, H, H * H, nullptr, s));
+  } else {
+    cpx<float>* o = (cpx<float>*)spec;
+    SIPF_CK(launch_cols<float>(o, H, 1, H * nh, 1, 0, +1, 1.0, s));
+    SIPF_CK(launch_cols<float>(o, H, H, nh, 1, 0, +1, 1.0, s));
+    SIPF_CK(launch_rows_c2r<float>(o, 1, 0, (float*)grid, H, H * H, nullptr, s));
+  }
+  return SIPF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,219 @@
+// Device-side building blocks of the SIPF-PIC step: complex type, Philox4x32-10
+// noise, periodic wrap and the Gamma_2 / Gamma_4 particle-grid stencils.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sipf {
+
+template <typename T> struct cpx { T x, y; };
+
+__device__ __forceinline__ int ilog2_dev(int v) { return 31 - __clz(v); }   // v a power of two
+__device__ __forceinline__ float t_floor(float v) { return floorf(v); }
+__device__ __forceinline__ double t_floor(double v) { return ::floor(v); }
+__device__ __forceinline__ float t_exp(float v) { return expf(v); }
+__device__ __forceinline__ double t_exp(double v) { return ::exp(v); }
+__device__ __forceinline__ bool t_finite(float v) { return isfinite(v); }
+__device__ __forceinline__ bool t_finite(double v) { return isfinite(v); }
+
+template <typename T> __device__ __forceinline__ cpx<T> cadd(cpx<T> a, cpx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T> __device__ __forceinline__ cpx<T> csub(cpx<T> a, cpx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T> __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T> __device__ __forceinline__ cpx<T> cconj(cpx<T> a) { return {a.x, -a.y}; }
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of
+//   (hi0,lo0) = M0*c0, (hi1,lo1) = M1*c2, c <- (hi1^c1^k0, lo1, hi0^c3^k1, lo0)
+// with the key bumped by (W0, W1) between rounds.  Two counter blocks that
+// share a key are run together so the key schedule is computed once.
+// ---------------------------------------------------------------------------
+struct u32x4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ void philox_round(u32x4& c, uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+  const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+  c = u32x4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+}
+
+__device__ __forceinline__ void philox2blocks(u32x4& a, u32x4& b, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    philox_round(a, k0, k1);
+    philox_round(b, k0, k1);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+// Six standard normals for particle p at step n (blocks 0 and 1 of the counter
+// (p lo, p hi, n, block)); Box-Muller pairs (u0,u1), (u2,u3), (u4,u5) with
+// u = (x + 1/2) 2^-32.  Double: libdevice-accurate log / sincos.
+__device__ __forceinline__ void normals6(uint64_t seed, uint64_t p, uint32_t n, double z[6]) {
+  u32x4 a{(uint32_t)p, (uint32_t)(p >> 32), n, 0u};
+  u32x4 b{(uint32_t)p, (uint32_t)(p >> 32), n, 1u};
+  philox2blocks(a, b, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const uint32_t w[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+  const double two_m32 = 2.3283064365386963e-10;   // 2^-32
+  const double two_pi = 6.283185307179586;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const double u1 = ((double)w[2 * j] + 0.5) * two_m32;
+    const double u2 = ((double)w[2 * j + 1] + 0.5) * two_m32;
+    const double r = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincos(two_pi * u2, &s, &c);
+    z[2 * j] = r * c;
+    z[2 * j + 1] = r * s;
+  }
+}
+
+// Float: hardware approximations (lg2, sin, cos) on the same uniforms.  The
+// angle is taken as 2 pi (u - 1/2) in [-pi, pi] (the accurate range of the
+// sine unit); cos/sin of 2 pi u are the negated values.
+__device__ __forceinline__ void normals6(uint64_t seed, uint64_t p, uint32_t n, float z[6]) {
+  u32x4 a{(uint32_t)p, (uint32_t)(p >> 32), n, 0u};
+  u32x4 b{(uint32_t)p, (uint32_t)(p >> 32), n, 1u};
+  philox2blocks(a, b, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const uint32_t w[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+  const float two_m32 = 2.3283064365386963e-10f;
+  const float two_pi = 6.28318530717958648f;
+  const float ln2x2 = 1.3862943611198906f;          // 2 ln 2
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float u1 = __fmaf_rn((float)w[2 * j], two_m32, 0.5f * two_m32);
+    const float u2 = __fmaf_rn((float)w[2 * j + 1], two_m32, 0.5f * two_m32);
+    const float r = sqrtf(fmaxf(-ln2x2 * __log2f(u1), 0.0f));
+    float s, c;
+    __sincosf(two_pi * (u2 - 0.5f), &s, &c);
+    z[2 * j] = -r * c;
+    z[2 * j + 1] = -r * s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Geometry helpers.
+// ---------------------------------------------------------------------------
+template <typename T> struct Geo {
+  T L, invL, half_L;   // box side, 1/L, L/2
+  T inv_h;             // H / L
+  int H, mask;         // H and H - 1 (H a power of two)
+};
+
+// Periodic wrap into [-L/2, L/2): x - L floor(x/L + 1/2), with the rounding
+// edge cases pushed back inside.
+template <typename T> __device__ __forceinline__ T wrap_coord(T x, const Geo<T>& g) {
+  T y = x - g.L * t_floor(x * g.invL + T(0.5));
+  if (y >= g.half_L) y -= g.L;
+  if (y < -g.half_L) y += g.L;
+  return y;
+}
+
+// cell = floor(H x / L), lambda = H x / L - cell.
+template <typename T> __device__ __forceinline__ void cell_lambda(T x, const Geo<T>& g, int& cell, T& lam) {
+  const T u = x * g.inv_h;
+  const T f = t_floor(u);
+  cell = (int)f;
+  lam = u - f;
+}
+
+// 1D factors of the stencils for one axis: index -1, 0, 1, 2 of Gamma_4 and
+// the inner pair of Gamma_2.
+template <typename T> struct Axis4 { T om, l0, l1, o2; };
+
+template <typename T> __device__ __forceinline__ Axis4<T> axis4(T l) {
+  Axis4<T> a;
+  a.l0 = T(1) - l;
+  a.l1 = l;
+  const T c = l * (T(1) - l) * T(1.0 / 6.0);
+  a.om = -(T(2) - l) * c;   // -(2 - l) l (1 - l) / 6     (index -1)
+  a.o2 = -(T(1) + l) * c;   // -(1 + l)(1 - l) l / 6      (index  2)
+  return a;
+}
+
+// Visit the 32 nodes of Gamma_4 (Eq. (4ord)) around cell (cx,cy,cz) with
+// in-cell offsets lambda: fn(flat_index, weight).  Inner nodes carry the
+// trilinear weight times 1 + sum_k lambda_k(1-lambda_k)/2; the outer node with
+// index -1 or 2 on one axis carries that axis' cubic factor times the bilinear
+// weight of the other two axes.
+template <typename T, typename Fn>
+__device__ __forceinline__ void gamma4_visit(int cx, int cy, int cz, T lx, T ly, T lz, int H, int mask, Fn&& fn) {
+  const Axis4<T> ax = axis4(lx), ay = axis4(ly), az = axis4(lz);
+  const int HH = H * H;
+  int ix[4], iy[4], iz[4];
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    ix[o] = ((cx + o - 1) & mask) * HH;
+    iy[o] = ((cy + o - 1) & mask) * H;
+    iz[o] = (cz + o - 1) & mask;
+  }
+  const T boost = T(1) + T(0.5) * (lx * ax.l0 + ly * ay.l0 + lz * az.l0);
+  const T wx[2] = {ax.l0, ax.l1}, wy[2] = {ay.l0, ay.l1}, wz[2] = {az.l0, az.l1};
+  T byz[2][2], bxz[2][2], bxy[2][2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      byz[a][b] = wy[a] * wz[b];
+      bxz[a][b] = wx[a] * wz[b];
+      bxy[a][b] = wx[a] * wy[b];
+    }
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const T fa = wx[a] * boost;
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) fn(ix[a + 1] + iy[b + 1] + iz[c + 1], fa * byz[b][c]);
+  }
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      fn(ix[0] + iy[b + 1] + iz[c + 1], ax.om * byz[b][c]);
+      fn(ix[3] + iy[b + 1] + iz[c + 1], ax.o2 * byz[b][c]);
+    }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      fn(ix[a + 1] + iy[0] + iz[c + 1], ay.om * bxz[a][c]);
+      fn(ix[a + 1] + iy[3] + iz[c + 1], ay.o2 * bxz[a][c]);
+    }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      fn(ix[a + 1] + iy[b + 1] + iz[0], az.om * bxy[a][b]);
+      fn(ix[a + 1] + iy[b + 1] + iz[3], az.o2 * bxy[a][b]);
+    }
+}
+
+// The 8 nodes of Gamma_2 (Eq. (2ord)): trilinear weights.
+template <typename T, typename Fn>
+__device__ __forceinline__ void gamma2_visit(int cx, int cy, int cz, T lx, T ly, T lz, int H, int mask, Fn&& fn) {
+  const int HH = H * H;
+  const int ix[2] = {(cx & mask) * HH, ((cx + 1) & mask) * HH};
+  const int iy[2] = {(cy & mask) * H, ((cy + 1) & mask) * H};
+  const int iz[2] = {cz & mask, (cz + 1) & mask};
+  const T wx[2] = {T(1) - lx, lx}, wy[2] = {T(1) - ly, ly}, wz[2] = {T(1) - lz, lz};
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const T wab = wx[a] * wy[b];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) fn(ix[a] + iy[b] + iz[c], wab * wz[c]);
+    }
+}
+
+template <typename T, typename Fn>
+__device__ __forceinline__ void stencil_visit(int order, int cx, int cy, int cz, T lx, T ly, T lz, int H, int mask, Fn&& fn) {
+  if (order == 4) gamma4_visit<T>(cx, cy, cz, lx, ly, lz, H, mask, fn);
+  else gamma2_visit<T>(cx, cy, cz, lx, ly, lz, H, mask, fn);
+}
+
+}  // namespace sipf
