@@ -70,7 +70,7 @@ typedef struct sipf_params {
   double H0;         /* Gaussian filter scale: < 0 auto ceil(8 H^(8/13) L^(5/13))
                         (Sec. 5.1), 0 off, > 0 as given                       */
   uint64_t seed;     /* key of the counter-based noise                        */
-  int64_t P;         /* number of particles, >= 1                              */
+  int64_t P;         /* number of particles, 1 <= P <= 2^30                    */
   int32_t H;         /* modes / grid points per axis: power of 2 in [8, 256]   */
   int32_t precision; /* 32 (float state and kernels) or 64 (double)           */
   int32_t p2g_order; /* 4 (Gamma_4, default) or 2 (Gamma_2), Sec. 3.1         */
@@ -78,7 +78,8 @@ typedef struct sipf_params {
   int32_t splitting; /* SIPF_SPLIT_*                                           */
   int32_t deposit_mode; /* SIPF_DEPOSIT_*                                      */
   int32_t propagator;   /* SIPF_PROP_*                                         */
-  int32_t resort_every; /* re-bucket particles by grid tile every n steps; 0 off */
+  int32_t resort_every; /* rebuild the tile-bin capacities every n steps (0: 16);
+                           results do not depend on it                         */
 } sipf_params;
 
 /* FP64 diagnostics of the current state (Sec. 5). */
@@ -97,7 +98,7 @@ typedef struct sipf_ctx sipf_ctx;
 /* Fill *p with the defaults: chi=mu=eps=k=1, L=1, mass=1, dt=1e-3, T=0,
  * H0=-1 (auto), seed=0, P=0 (must be set), H=64, precision=32,
  * p2g_order=4, g2p_order=2, splitting=HALF, deposit_mode=ATOMIC,
- * propagator=IMPLICIT, resort_every=0.  Returns SIPF_EINVAL if p is NULL. */
+ * propagator=IMPLICIT, resort_every=0 (16).  Returns SIPF_EINVAL if p is NULL. */
 int sipf_params_default(sipf_params* p);
 
 /* Check a parameter set without touching the GPU.  SIPF_EINVAL names the
@@ -139,9 +140,11 @@ int sipf_set_positions(sipf_ctx* ctx, const double* X);
 int sipf_upload_soa(sipf_ctx* ctx, const void* x, const void* y, const void* z);
 int sipf_download_soa(sipf_ctx* ctx, void* x, void* y, void* z);
 
-/* Device pointers of the context's position arrays (x, y, z; P elements each,
- * float or double).  The pointers stay valid until sipf_destroy. */
-int sipf_positions_dev(sipf_ctx* ctx, void** x, void** y, void** z);
+/* Write X^(n) in particle order into caller-owned device arrays x, y, z (P
+ * elements each, float or double as the context's precision).  Internally the
+ * particles are kept grouped by grid tile; this gathers them back by id.
+ * Asynchronous on the context's stream. */
+int sipf_positions_dev(sipf_ctx* ctx, void* x, void* y, void* z);
 
 /* Density on the grid (host H^3 float64).  filtered = 0: I rho-hat / h^3,
  * the deposited mass per cell volume (Def. particle2grid); filtered = 1:

@@ -92,8 +92,9 @@ class Simulation:
         d = _abi.sipf_diagnostics(self.ctx)
         return {name: getattr(d, name) for name, _ in d._fields_}
 
-    def positions_dev(self):
-        return _abi.sipf_positions_dev(self.ctx)
+    def positions_dev(self, x: int, y: int, z: int):
+        """Write X in particle order into device arrays (pointers) x, y, z."""
+        _abi.sipf_positions_dev(self.ctx, x, y, z)
 
     def close(self):
         if self.ctx:

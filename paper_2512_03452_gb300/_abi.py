@@ -67,7 +67,7 @@ _SIGS = {
     "sipf_set_positions": (ctypes.c_int, [_P, _D]),
     "sipf_upload_soa": (ctypes.c_int, [_P, _P, _P, _P]),
     "sipf_download_soa": (ctypes.c_int, [_P, _P, _P, _P]),
-    "sipf_positions_dev": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "sipf_positions_dev": (ctypes.c_int, [_P, _P, _P, _P]),
     "sipf_density": (ctypes.c_int, [_P, _D, ctypes.c_int]),
     "sipf_field": (ctypes.c_int, [_P, _D]),
     "sipf_spectrum": (ctypes.c_int, [_P, _D]),
@@ -168,11 +168,8 @@ def sipf_download_soa(ctx: int, x: int, y: int, z: int) -> None:
     _check(load().sipf_download_soa(_P(ctx), _P(x), _P(y), _P(z)), "sipf_download_soa")
 
 
-def sipf_positions_dev(ctx: int):
-    x, y, z = _P(), _P(), _P()
-    _check(load().sipf_positions_dev(_P(ctx), ctypes.byref(x), ctypes.byref(y), ctypes.byref(z)),
-           "sipf_positions_dev")
-    return x.value, y.value, z.value
+def sipf_positions_dev(ctx: int, x: int, y: int, z: int) -> None:
+    _check(load().sipf_positions_dev(_P(ctx), _P(x), _P(y), _P(z)), "sipf_positions_dev")
 
 
 def sipf_density(ctx: int, out, filtered: int) -> None:

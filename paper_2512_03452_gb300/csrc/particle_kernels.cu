@@ -1,7 +1,15 @@
-// Particle kernels of the SIPF-PIC step: the move of Algorithm 4 (noise,
-// gather of grad c with I* (Algorithm 3), drift, periodic wrap) fused with the
-// deposit I of the new positions (Algorithm 2), plus the stand-alone deposit,
-// gather, noise and FP64 reduction kernels.
+// Particle kernels of the SIPF-PIC step.
+//
+// Particles live in tile bins: the grid is cut into tiles of E^3 cells and the
+// particle arrays (x, y, z, id) are grouped by the tile of their cell, each bin
+// with some spare capacity, plus an overflow bin.  The move of Algorithm 4
+// (noise keyed by the particle id, gather of grad c with I* (Algorithm 3),
+// drift, periodic wrap) is fused with the deposit I of the new position
+// (Algorithm 2) and with re-binning into the other buffer.  A block works on a
+// chunk of one bin and deposits into a shared-memory window that covers the
+// tile plus a margin; the window is then added to the global grid with
+// coalesced reductions.  Particles that left the window, or sit in the overflow
+// bin, deposit with global reductions.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -29,28 +37,34 @@ static inline int grid_for(int64_t n, int threads) {
   return (int)b;
 }
 
-// Deposit one particle's stencil into the grid: floating-point reductions, or
-// 64-bit fixed point (w already holds 2^60 / P) for a result that does not
-// depend on the order of the additions.
-template <typename T>
-__device__ __forceinline__ void deposit_one(void* phi, int fixed, int order, T px, T py, T pz, const Geo<T>& g,
-                                            T w) {
-  int cx, cy, cz;
-  T lx, ly, lz;
-  cell_lambda(px, g, cx, lx);
-  cell_lambda(py, g, cy, ly);
-  cell_lambda(pz, g, cz, lz);
-  if (!fixed) {
-    T* grid = static_cast<T*>(phi);
-    stencil_visit<T>(order, cx, cy, cz, lx, ly, lz, g.H, g.mask,
-                     [&](int idx, T f) { atomicAdd(grid + idx, w * f); });
-  } else {
-    unsigned long long* acc = static_cast<unsigned long long*>(phi);
-    stencil_visit<T>(order, cx, cy, cz, lx, ly, lz, g.H, g.mask, [&](int idx, T f) {
-      const long long v = (long long)llrint((double)(w * f));
-      atomicAdd(acc + idx, (unsigned long long)v);
-    });
-  }
+// ---------------------------------------------------------------------------
+// Accumulation.  The shared-memory window holds integers (native shared
+// atomics): int32 for float runs, int64 for double runs, in units of 2^-K of
+// a stencil weight F.  In the default mode K is chosen per chunk so that no
+// node sum can overflow (|F| <= 1, at most `len` particles per chunk), and the
+// window is added to the floating-point grid as v * (M0/P) * 2^-K.  In the
+// deterministic mode K is fixed for the run and the global grid is an int64
+// fixed-point sum in the same units, so every addition is exact and the
+// result does not depend on the order of the additions.
+// ---------------------------------------------------------------------------
+template <typename T> struct WinType;
+template <> struct WinType<float> {
+  using type = int;
+  static constexpr int bits = 30;
+  static __device__ __forceinline__ int round(float v) { return __float2int_rn(v); }
+};
+template <> struct WinType<double> {
+  using type = long long;
+  static constexpr int bits = 62;
+  static __device__ __forceinline__ long long round(double v) { return __double2ll_rn(v); }
+};
+
+__device__ __forceinline__ int ceil_log2(int v) { return v <= 1 ? 0 : 32 - __clz(v - 1); }
+
+// two's-complement integer adds into the shared window
+__device__ __forceinline__ void win_add(int* p, int v) { atomicAdd(p, v); }
+__device__ __forceinline__ void win_add(long long* p, long long v) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
 }
 
 template <typename T> struct V3 { T x, y, z; };
@@ -69,74 +83,367 @@ template <> struct Vec4<double> {
   }
 };
 
-// Gather of the three gradient components (interleaved 4-wide nodes) at (px,py,pz).
+// Gather of the three gradient components (interleaved 4-wide nodes).
 template <typename T>
-__device__ __forceinline__ void gather_grad(const T* grad4, int order, T px, T py, T pz, const Geo<T>& g, T& gx,
-                                            T& gy, T& gz) {
+__device__ __forceinline__ V3<T> gather_grad(const T* __restrict__ grad4, int order, T px, T py, T pz,
+                                             const Geo<T>& g) {
   int cx, cy, cz;
   T lx, ly, lz;
   cell_lambda(px, g, cx, lx);
   cell_lambda(py, g, cy, ly);
   cell_lambda(pz, g, cz, lz);
-  T ax = 0, ay = 0, az = 0;
-  stencil_visit<T>(order, cx, cy, cz, lx, ly, lz, g.H, g.mask, [&](int idx, T f) {
-    const auto v = Vec4<T>::load(grad4 + (size_t)idx * 4);
-    ax += f * v.x;
-    ay += f * v.y;
-    az += f * v.z;
+  V3<T> acc{T(0), T(0), T(0)};
+  stencil_visit_global<T>(order, cx, cy, cz, lx, ly, lz, T(1), g, [&](int idx, T f) {
+    const V3<T> v = Vec4<T>::load(grad4 + (size_t)idx * 4);
+    acc.x += f * v.x;
+    acc.y += f * v.y;
+    acc.z += f * v.z;
   });
-  gx = ax;
-  gy = ay;
-  gz = az;
+  return acc;
 }
 
-// One thread per particle: X^{n-1} -> X^n (Algorithm 4, particle loop), then
-// deposit X^n for the next step's F_H I(rho-hat^(n)).
-template <typename T>
-__global__ void __launch_bounds__(256) k_move_deposit(MoveArgs<T> a) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.P; p += stride) {
-    const T x = a.x[p], y = a.y[p], z = a.z[p];
-    T nz[6];
-    normals6(a.seed, (uint64_t)p, a.n, nz);
-    T nx, ny, nw;
-    if (a.split == 0) {
-      // Z = X + W^- + chi tau I*(grad c)(X + W^-),  X^n = Z + W^+
-      const T yx = x + a.s_noise * nz[0], yy = y + a.s_noise * nz[1], yz = z + a.s_noise * nz[2];
-      T gx, gy, gz;
-      gather_grad(a.grad4, a.g2p, yx, yy, yz, a.g, gx, gy, gz);
-      nx = wrap_coord((yx + a.chitau * gx) + a.s_noise * nz[3], a.g);
-      ny = wrap_coord((yy + a.chitau * gy) + a.s_noise * nz[4], a.g);
-      nw = wrap_coord((yz + a.chitau * gz) + a.s_noise * nz[5], a.g);
-    } else {
-      // X^n = X + chi tau I*(grad c)(X) + W,  W ~ N(0, 2 mu tau I)
-      T gx, gy, gz;
-      gather_grad(a.grad4, a.g2p, x, y, z, a.g, gx, gy, gz);
-      nx = wrap_coord((x + a.chitau * gx) + a.s_noise * nz[0], a.g);
-      ny = wrap_coord((y + a.chitau * gy) + a.s_noise * nz[1], a.g);
-      nw = wrap_coord((z + a.chitau * gz) + a.s_noise * nz[2], a.g);
+__device__ __forceinline__ int tile_of(int cx, int cy, int cz, int shift, int ntx) {
+  return (((cx >> shift) * ntx) + (cy >> shift)) * ntx + (cz >> shift);
+}
+
+// ---------------------------------------------------------------------------
+// The binned particle kernel.  Template flags:
+//   MOVE:    advance X^{n-1} -> X^n (Algorithm 4, particle loop)
+//   DEPOSIT: deposit the (new) positions into phi
+//   REBIN:   write each particle into the destination bins of its tile
+// WHOLE: the window is the whole (small) grid with periodic slots (H <= 16);
+// otherwise the window is the tile, a margin kM cells and the stencil halo.
+// ---------------------------------------------------------------------------
+constexpr int kTileShift = 3;                 // tiles of 8^3 cells
+constexpr int kTileE = 1 << kTileShift;
+constexpr int kMargin = 4;
+constexpr int kWin = kTileE + 2 * kMargin + 3;  // 19 nodes per axis
+constexpr int kChunk = 4096;                  // particles per work item
+
+template <typename T, bool FIXED, bool MOVE, bool DEPOSIT, bool REBIN, bool WHOLE>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
+k_binned(BinArgs<T> a) {
+  using A = typename WinType<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  A* win = reinterpret_cast<A*>(smem_raw);
+  __shared__ int s_bin, s_len;
+  __shared__ long long s_start, s_chunk;
+  const long long nchunks = a.chunk_start[a.NT + 1];
+  const int H = a.g.H, mask = a.g.mask;
+  const int wslots = WHOLE ? H * H * H : kWin * kWin * kWin;
+  const int lane = threadIdx.x & 31;
+  if (DEPOSIT)
+    for (int i = threadIdx.x; i < wslots; i += blockDim.x) win[i] = A(0);
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const long long c = (long long)atomicAdd(a.work, 1ULL);
+      s_chunk = c;
+      if (c < nchunks) {
+        int lo = 0, hi = a.NT;               // largest b with chunk_start[b] <= c
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (a.chunk_start[mid] <= c) lo = mid; else hi = mid - 1;
+        }
+        const long long j = c - a.chunk_start[lo];
+        s_bin = lo;
+        s_start = a.src_base[lo] + j * kChunk;
+        s_len = (int)min((long long)kChunk, (long long)a.src_count[lo] - j * kChunk);
+      }
     }
-    a.x[p] = nx;
-    a.y[p] = ny;
-    a.z[p] = nw;
-    if (!(t_finite(nx) && t_finite(ny) && t_finite(nw))) atomicOr(a.err, 1);
-    deposit_one<T>(a.phi, a.fixed, a.p2g, nx, ny, nw, a.g, a.w);
+    __syncthreads();
+    if (s_chunk >= nchunks) break;
+    const int bin = s_bin, len = s_len;
+    const long long start = s_start;
+    // window origin (node coordinates of slot (0,0,0))
+    bool has_win = DEPOSIT && (WHOLE || bin < a.NT);
+    int ox = 0, oy = 0, oz = 0;
+    if (!WHOLE && bin < a.NT) {
+      const int tz = bin % a.ntx, ty = (bin / a.ntx) % a.ntx, tx = bin / (a.ntx * a.ntx);
+      ox = tx * kTileE - kMargin - 1;
+      oy = ty * kTileE - kMargin - 1;
+      oz = tz * kTileE - kMargin - 1;
+    }
+    // window scale 2^K
+    const int K = FIXED ? a.fix_k : WinType<T>::bits - ceil_log2(len + 1);
+    const T wwin = (T)ldexp(1.0, K);
+    const int iters = (len + blockDim.x - 1) / blockDim.x;
+    for (int it = 0; it < iters; ++it) {
+      const int i = it * blockDim.x + threadIdx.x;
+      const bool valid = i < len;
+      T x = T(0), y = T(0), z = T(0);
+      uint32_t id = 0;
+      if (valid) {
+        const long long s = start + i;
+        x = a.sx[s];
+        y = a.sy[s];
+        z = a.sz[s];
+        id = a.sid[s];
+      }
+      if (MOVE && valid) {
+        T nz[6];
+        normals6(a.seed, (uint64_t)id, a.n, nz);
+        if (a.split == 0) {
+          // Z = X + W^- + chi tau I*(grad c)(X + W^-),  X^n = Z + W^+
+          const T yx = x + a.s_noise * nz[0], yy = y + a.s_noise * nz[1], yz = z + a.s_noise * nz[2];
+          const V3<T> gr = gather_grad(a.grad4, a.g2p, yx, yy, yz, a.g);
+          x = wrap_coord((yx + a.chitau * gr.x) + a.s_noise * nz[3], a.g);
+          y = wrap_coord((yy + a.chitau * gr.y) + a.s_noise * nz[4], a.g);
+          z = wrap_coord((yz + a.chitau * gr.z) + a.s_noise * nz[5], a.g);
+        } else {
+          // X^n = X + chi tau I*(grad c)(X) + W,  W ~ N(0, 2 mu tau I)
+          const V3<T> gr = gather_grad(a.grad4, a.g2p, x, y, z, a.g);
+          x = wrap_coord((x + a.chitau * gr.x) + a.s_noise * nz[0], a.g);
+          y = wrap_coord((y + a.chitau * gr.y) + a.s_noise * nz[1], a.g);
+          z = wrap_coord((z + a.chitau * gr.z) + a.s_noise * nz[2], a.g);
+        }
+        if (!(t_finite(x) && t_finite(y) && t_finite(z))) atomicOr(a.err, 1);
+      }
+      int cx = 0, cy = 0, cz = 0;
+      T lx = T(0), ly = T(0), lz = T(0);
+      cell_lambda(x, a.g, cx, lx);
+      cell_lambda(y, a.g, cy, ly);
+      cell_lambda(z, a.g, cz, lz);
+      if (DEPOSIT && valid) {
+        bool fits = has_win;
+        int sx = 0, sy = 0, sz = 0;
+        if (!WHOLE && fits) {
+          sx = (cx - 1 - ox) & mask;
+          sy = (cy - 1 - oy) & mask;
+          sz = (cz - 1 - oz) & mask;
+          fits = sx <= kWin - 4 && sy <= kWin - 4 && sz <= kWin - 4;
+        }
+        if (fits) {
+          int ix[4], iy[4], iz[4];
+          if (WHOLE) {
+            axis_layers_global(cx, mask, H * H, ix);
+            axis_layers_global(cy, mask, H, iy);
+            axis_layers_global(cz, mask, 1, iz);
+            stencil_visit<T>(a.p2g, ix, iy, iz, lx, ly, lz, wwin,
+                             [&](int idx, T f) { win_add(win + idx, WinType<T>::round(f)); });
+          } else {
+            // base slot plus compile-time offsets of the 4x4x4 box
+            A* wb = win + ((sx * kWin) + sy) * kWin + sz;
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+              ix[o] = o * (kWin * kWin);
+              iy[o] = o * kWin;
+              iz[o] = o;
+            }
+            stencil_visit<T>(a.p2g, ix, iy, iz, lx, ly, lz, wwin,
+                             [&](int idx, T f) { win_add(wb + idx, WinType<T>::round(f)); });
+          }
+        } else if (FIXED) {
+          unsigned long long* grid = static_cast<unsigned long long*>(a.phi);
+          stencil_visit_global<T>(a.p2g, cx, cy, cz, lx, ly, lz, wwin, a.g, [&](int idx, T f) {
+            atomicAdd(grid + idx, (unsigned long long)(long long)WinType<T>::round(f));
+          });
+        } else {
+          T* grid = static_cast<T*>(a.phi);
+          stencil_visit_global<T>(a.p2g, cx, cy, cz, lx, ly, lz, a.wmass, a.g,
+                                  [&](int idx, T f) { atomicAdd(grid + idx, f); });
+        }
+      }
+      if (REBIN) {
+        const int t = tile_of(cx & mask, cy & mask, cz & mask, a.tile_shift, a.ntx);
+        const unsigned key = valid ? (unsigned)t : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+        const int leader = __ffs(peers) - 1;
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        int b0 = 0;
+        if (valid && lane == leader) b0 = atomicAdd(a.dst_cursor + t, __popc(peers));
+        b0 = __shfl_sync(0xFFFFFFFFu, b0, leader);
+        if (valid) {
+          long long slot;
+          const int r = b0 + rank;
+          if (r < a.dst_cap[t]) {
+            slot = a.dst_base[t] + r;
+          } else {
+            const int o = atomicAdd(a.dst_cursor + a.NT, 1);
+            slot = o < a.dst_cap[a.NT] ? a.dst_base[a.NT] + o : -1;
+          }
+          if (slot >= 0) {
+            a.dx[slot] = x;
+            a.dy[slot] = y;
+            a.dz[slot] = z;
+            a.did[slot] = id;
+          } else {
+            atomicOr(a.err, 2);   // overflow bin full: the particle is lost
+          }
+        }
+      }
+    }
+    if (DEPOSIT && has_win) {
+      __syncthreads();
+      // add the window to the grid: consecutive threads walk consecutive slots
+      // along the fastest axis, so the reductions of a warp hit contiguous nodes
+      const T unit = a.wmass / wwin;   // M0/P * 2^-K
+      for (int sidx = threadIdx.x; sidx < wslots; sidx += blockDim.x) {
+        const A v = win[sidx];
+        if (v != A(0)) {
+          int gi;
+          if (WHOLE) {
+            gi = sidx;
+          } else {
+            const int c = sidx % kWin, b = (sidx / kWin) % kWin, aa = sidx / (kWin * kWin);
+            gi = (((ox + aa) & mask) * H + ((oy + b) & mask)) * H + ((oz + c) & mask);
+          }
+          if (FIXED) atomicAdd(static_cast<unsigned long long*>(a.phi) + gi, (unsigned long long)(long long)v);
+          else atomicAdd(static_cast<T*>(a.phi) + gi, (T)v * unit);
+          win[sidx] = A(0);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Bin bookkeeping.
+// ---------------------------------------------------------------------------
+// From the fill cursors of the buffer just written: valid counts (clamped to
+// capacity), the chunk prefix sum and the reset of the other buffer's cursors
+// and of the work counter.  One block.
+__global__ void __launch_bounds__(1024)
+k_chunk_list(const int* __restrict__ cursor, const int* __restrict__ cap, int* __restrict__ count,
+             long long* __restrict__ chunk_start, int* __restrict__ other_cursor, int NT,
+             unsigned long long* work) {
+  __shared__ long long s_part[1024];
+  const int nb = NT + 1;
+  const int per = (nb + blockDim.x - 1) / blockDim.x;
+  const int b0 = threadIdx.x * per;
+  long long local = 0;
+  for (int b = b0; b < min(b0 + per, nb); ++b) {
+    const int c = min(cursor[b], cap[b]);
+    count[b] = c;
+    local += (c + kChunk - 1) / kChunk;
+    other_cursor[b] = 0;
+  }
+  s_part[threadIdx.x] = local;
+  __syncthreads();
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+    const long long v = threadIdx.x >= (unsigned)off ? s_part[threadIdx.x - off] : 0;
+    __syncthreads();
+    s_part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  long long run = s_part[threadIdx.x] - local;   // exclusive prefix
+  for (int b = b0; b < min(b0 + per, nb); ++b) {
+    chunk_start[b] = run;
+    run += (count[b] + kChunk - 1) / kChunk;
+  }
+  if (threadIdx.x == blockDim.x - 1) chunk_start[nb] = s_part[threadIdx.x];
+  if (threadIdx.x == 0) *work = 0ULL;
+}
+
+// Capacities from the wanted counts (tile histogram), with spare room, and
+// their prefix sum.  The overflow bin keeps capacity ovf_cap.  One block.
+__global__ void __launch_bounds__(1024)
+k_layout(const int* __restrict__ want, int* __restrict__ cap, long long* __restrict__ base, int NT, int ovf_cap) {
+  __shared__ long long s_part[1024];
+  const int per = (NT + blockDim.x - 1) / blockDim.x;
+  const int b0 = threadIdx.x * per;
+  long long local = 0;
+  for (int b = b0; b < min(b0 + per, NT); ++b) {
+    const int w = want[b];
+    const int c = w + w / 4 + 32;
+    cap[b] = c;
+    local += c;
+  }
+  s_part[threadIdx.x] = local;
+  __syncthreads();
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+    const long long v = threadIdx.x >= (unsigned)off ? s_part[threadIdx.x - off] : 0;
+    __syncthreads();
+    s_part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  long long run = s_part[threadIdx.x] - local;
+  for (int b = b0; b < min(b0 + per, NT); ++b) {
+    base[b] = run;
+    run += cap[b];
+  }
+  if (threadIdx.x == blockDim.x - 1) {
+    base[NT] = s_part[threadIdx.x];
+    cap[NT] = ovf_cap;
+  }
+}
+
+// Tile histogram of plain (unbinned) positions.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_tile_hist(const T* __restrict__ x, const T* __restrict__ y, const T* __restrict__ z, int64_t P, Geo<T> g,
+            int shift, int ntx, int* __restrict__ hist) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n_iter = (P + stride - 1) / stride;
+  for (int64_t it = 0; it < n_iter; ++it) {
+    const int64_t p = it * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = p < P;
+    unsigned key = 0xFFFFFFFFu;
+    if (valid) {
+      int cx, cy, cz;
+      T l;
+      cell_lambda(x[p], g, cx, l);
+      cell_lambda(y[p], g, cy, l);
+      cell_lambda(z[p], g, cz, l);
+      key = (unsigned)tile_of(cx & g.mask, cy & g.mask, cz & g.mask, shift, ntx);
+    }
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+    if (valid && lane == __ffs(peers) - 1) atomicAdd(hist + key, __popc(peers));
+  }
+}
+
+// Scatter binned particles back to particle order: out[id] = X[slot].
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_unbin(BinArgs<T> a, T* __restrict__ ox, T* __restrict__ oy, T* __restrict__ oz) {
+  const long long c = blockIdx.x;
+  if (c >= a.chunk_start[a.NT + 1]) return;
+  int lo = 0, hi = a.NT;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.chunk_start[mid] <= c) lo = mid; else hi = mid - 1;
+  }
+  const long long j = c - a.chunk_start[lo];
+  const long long start = a.src_base[lo] + j * kChunk;
+  const int len = (int)min((long long)kChunk, (long long)a.src_count[lo] - j * kChunk);
+  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    const long long s = start + i;
+    const uint32_t id = a.sid[s];
+    ox[id] = a.sx[s];
+    oy[id] = a.sy[s];
+    oz[id] = a.sz[s];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_iota(uint32_t* id, int64_t P) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) id[p] = (uint32_t)p;
+}
+
+// ---------------------------------------------------------------------------
+// Stand-alone operators (stateless entry points).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_deposit(const T* __restrict__ x, const T* __restrict__ y, const T* __restrict__ z, int64_t P, Geo<T> g, T w,
+          T* __restrict__ phi, int order) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
+    int cx, cy, cz;
+    T lx, ly, lz;
+    cell_lambda(x[p], g, cx, lx);
+    cell_lambda(y[p], g, cy, ly);
+    cell_lambda(z[p], g, cz, lz);
+    stencil_visit_global<T>(order, cx, cy, cz, lx, ly, lz, w, g, [&](int idx, T f) { atomicAdd(phi + idx, f); });
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_deposit(const T* __restrict__ x, const T* __restrict__ y, const T* __restrict__ z, int64_t P, Geo<T> g, T w,
-          void* phi, int order, int fixed) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride)
-    deposit_one<T>(phi, fixed, order, x[p], y[p], z[p], g, w);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256)
 k_gather(const T* __restrict__ x, const T* __restrict__ y, const T* __restrict__ z, int64_t P, Geo<T> g,
-         const T* __restrict__ f, int ncomp, int interleaved4, int order, T* __restrict__ out) {
+         const T* __restrict__ f, int ncomp, int order, T* __restrict__ out) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const size_t N = (size_t)g.H * g.H * g.H;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
@@ -147,9 +454,8 @@ k_gather(const T* __restrict__ x, const T* __restrict__ y, const T* __restrict__
     cell_lambda(z[p], g, cz, lz);
     for (int c = 0; c < ncomp; ++c) {
       T acc = 0;
-      stencil_visit<T>(order, cx, cy, cz, lx, ly, lz, g.H, g.mask, [&](int idx, T wt) {
-        acc += wt * (interleaved4 ? f[(size_t)idx * 4 + c] : f[c * N + idx]);
-      });
+      stencil_visit_global<T>(order, cx, cy, cz, lx, ly, lz, T(1), g,
+                              [&](int idx, T wt) { acc += wt * f[c * N + idx]; });
       out[(size_t)c * P + p] = acc;
     }
   }
@@ -201,6 +507,16 @@ k_aos_to_soa(const double* __restrict__ aos, int64_t P, Geo<T> g, T* x, T* y, T*
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_wrap_soa(int64_t P, Geo<T> g, T* x, T* y, T* z) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
+    x[p] = wrap_coord(x[p], g);
+    y[p] = wrap_coord(y[p], g);
+    z[p] = wrap_coord(z[p], g);
+  }
+}
+
 // acc2[0] += sum_q mult |alpha_q|^2 over ||q|| >= 4, acc2[1] += the full sum
 // (mult = 2 for 0 < kz < H/2 accounts for the Hermitian partner).
 template <typename T>
@@ -215,8 +531,8 @@ __global__ void __launch_bounds__(256) k_alpha_energy(const cpx<T>* __restrict__
     const int kx = (int)(i / ((int64_t)nh * H));
     const int qx = kx < H / 2 ? kx : kx - H, qy = ky < H / 2 ? ky : ky - H, qz = kz < H / 2 ? kz : kz - H;
     const double mult = (kz == 0 || kz == H / 2) ? 1.0 : 2.0;
-    const cpx<T> a = alpha[i];
-    const double e = mult * ((double)a.x * a.x + (double)a.y * a.y);
+    const cpx<T> v = alpha[i];
+    const double e = mult * ((double)v.x * v.x + (double)v.y * v.y);
     tot += e;
     if (qx * qx + qy * qy + qz * qz >= 16) hi += e;
   }
@@ -229,22 +545,87 @@ __global__ void __launch_bounds__(256) k_alpha_energy(const cpx<T>* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-template <typename T> cudaError_t launch_move_deposit(const MoveArgs<T>& a, cudaStream_t s) {
-  k_move_deposit<T><<<grid_for(a.P, 256), 256, 0, s>>>(a);
+// Launchers.
+// ---------------------------------------------------------------------------
+int binned_window_slots(int H) { return H <= 16 ? H * H * H : kWin * kWin * kWin; }
+int binned_chunk() { return kChunk; }
+int binned_tile_shift(int H) { return H <= 16 ? 30 : kTileShift; }
+
+template <typename T, bool FIXED, bool MOVE, bool DEPOSIT, bool REBIN>
+static cudaError_t launch_binned_t(const BinArgs<T>& a, cudaStream_t s) {
+  const bool whole = a.g.H <= 16;
+  const size_t smem = DEPOSIT ? (size_t)binned_window_slots(a.g.H) * sizeof(typename WinType<T>::type) : 0;
+  auto kern = whole ? k_binned<T, FIXED, MOVE, DEPOSIT, REBIN, true> : k_binned<T, FIXED, MOVE, DEPOSIT, REBIN, false>;
+  cudaError_t e;
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem)) != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  kern<<<sms * per_sm, 256, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_deposit(const T* x, const T* y, const T* z, int64_t P, Geo<T> g, T w, void* phi, int order,
-                           int fixed, cudaStream_t s) {
-  k_deposit<T><<<grid_for(P, 256), 256, 0, s>>>(x, y, z, P, g, w, phi, order, fixed);
+cudaError_t launch_binned(const BinArgs<T>& a, int move, int deposit, int rebin, cudaStream_t s) {
+  if (a.fixed) {
+    if (move && deposit && rebin) return launch_binned_t<T, true, true, true, true>(a, s);
+    if (!move && deposit && !rebin) return launch_binned_t<T, true, false, true, false>(a, s);
+    if (!move && !deposit && rebin) return launch_binned_t<T, true, false, false, true>(a, s);
+  } else {
+    if (move && deposit && rebin) return launch_binned_t<T, false, true, true, true>(a, s);
+    if (!move && deposit && !rebin) return launch_binned_t<T, false, false, true, false>(a, s);
+    if (!move && !deposit && rebin) return launch_binned_t<T, false, false, false, true>(a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_chunk_list(const int* cursor, const int* cap, int* count, long long* chunk_start, int* other_cursor,
+                              int NT, unsigned long long* work, cudaStream_t s) {
+  k_chunk_list<<<1, 1024, 0, s>>>(cursor, cap, count, chunk_start, other_cursor, NT, work);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_layout(const int* want, int* cap, long long* base, int NT, int ovf_cap, cudaStream_t s) {
+  k_layout<<<1, 1024, 0, s>>>(want, cap, base, NT, ovf_cap);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_gather(const T* x, const T* y, const T* z, int64_t P, Geo<T> g, const T* f, int ncomp,
-                          int interleaved4, int order, T* out, cudaStream_t s) {
-  k_gather<T><<<grid_for(P, 256), 256, 0, s>>>(x, y, z, P, g, f, ncomp, interleaved4, order, out);
+cudaError_t launch_tile_hist(const T* x, const T* y, const T* z, int64_t P, Geo<T> g, int shift, int ntx, int* hist,
+                             cudaStream_t s) {
+  int b = grid_for(P, 256);
+  if (b > 152 * 16) b = 152 * 16;
+  k_tile_hist<T><<<b, 256, 0, s>>>(x, y, z, P, g, shift, ntx, hist);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_unbin(const BinArgs<T>& a, int64_t max_chunks, T* x, T* y, T* z, cudaStream_t s) {
+  k_unbin<T><<<(unsigned)max_chunks, 256, 0, s>>>(a, x, y, z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_iota(uint32_t* id, int64_t P, cudaStream_t s) {
+  k_iota<int><<<grid_for(P, 256), 256, 0, s>>>(id, P);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_deposit(const T* x, const T* y, const T* z, int64_t P, Geo<T> g, T w, T* phi, int order,
+                           cudaStream_t s) {
+  k_deposit<T><<<grid_for(P, 256), 256, 0, s>>>(x, y, z, P, g, w, phi, order);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gather(const T* x, const T* y, const T* z, int64_t P, Geo<T> g, const T* f, int ncomp, int order,
+                          T* out, cudaStream_t s) {
+  k_gather<T><<<grid_for(P, 256), 256, 0, s>>>(x, y, z, P, g, f, ncomp, order, out);
   return cudaGetLastError();
 }
 
@@ -268,6 +649,11 @@ cudaError_t launch_aos_to_soa(const double* aos, int64_t P, Geo<T> g, T* x, T* y
   return cudaGetLastError();
 }
 
+template <typename T> cudaError_t launch_wrap_soa(int64_t P, Geo<T> g, T* x, T* y, T* z, cudaStream_t s) {
+  k_wrap_soa<T><<<grid_for(P, 256), 256, 0, s>>>(P, g, x, y, z);
+  return cudaGetLastError();
+}
+
 template <typename T> cudaError_t launch_alpha_energy(const cpx<T>* alpha, int H, double* acc2, cudaStream_t s) {
   const int64_t n = (int64_t)H * H * (H / 2 + 1);
   int b = grid_for(n, 256);
@@ -277,14 +663,18 @@ template <typename T> cudaError_t launch_alpha_energy(const cpx<T>* alpha, int H
 }
 
 #define SIPF_INST(T)                                                                                          \
-  template cudaError_t launch_move_deposit<T>(const MoveArgs<T>&, cudaStream_t);                              \
-  template cudaError_t launch_deposit<T>(const T*, const T*, const T*, int64_t, Geo<T>, T, void*, int, int,   \
+  template cudaError_t launch_binned<T>(const BinArgs<T>&, int, int, int, cudaStream_t);                       \
+  template cudaError_t launch_tile_hist<T>(const T*, const T*, const T*, int64_t, Geo<T>, int, int, int*,     \
+                                           cudaStream_t);                                                    \
+  template cudaError_t launch_unbin<T>(const BinArgs<T>&, int64_t, T*, T*, T*, cudaStream_t);                 \
+  template cudaError_t launch_deposit<T>(const T*, const T*, const T*, int64_t, Geo<T>, T, T*, int,           \
                                          cudaStream_t);                                                      \
   template cudaError_t launch_gather<T>(const T*, const T*, const T*, int64_t, Geo<T>, const T*, int, int,   \
-                                        int, T*, cudaStream_t);                                              \
+                                        T*, cudaStream_t);                                                   \
   template cudaError_t launch_noise<T>(uint64_t, int64_t, int64_t, int64_t, T*, cudaStream_t);               \
   template cudaError_t launch_moments<T>(const T*, const T*, const T*, int64_t, double*, cudaStream_t);      \
   template cudaError_t launch_aos_to_soa<T>(const double*, int64_t, Geo<T>, T*, T*, T*, cudaStream_t);       \
+  template cudaError_t launch_wrap_soa<T>(int64_t, Geo<T>, T*, T*, T*, cudaStream_t);                        \
   template cudaError_t launch_alpha_energy<T>(const cpx<T>*, int, double*, cudaStream_t);
 SIPF_INST(float)
 SIPF_INST(double)

@@ -43,7 +43,7 @@ double effective_H0(const sipf_params& p) {
 int validate(const sipf_params* p) {
   if (!p) return fail(SIPF_EINVAL, "params is NULL");
   auto bad = [](const char* f) { return fail(SIPF_EINVAL, std::string("invalid parameter: ") + f); };
-  if (!(p->P >= 1)) return bad("P (must be >= 1)");
+  if (!(p->P >= 1 && p->P <= (1LL << 30))) return bad("P (1 <= P <= 2^30)");
   if (!is_pow2(p->H) || p->H < 8 || p->H > kNmax) return bad("H (power of two in [8, 256])");
   if (p->precision != 32 && p->precision != 64) return bad("precision (32 or 64)");
   if (!(isfinite(p->L) && p->L > 0)) return bad("L (> 0)");
@@ -66,10 +66,17 @@ int validate(const sipf_params* p) {
   return SIPF_OK;
 }
 
-// 2^60: fixed-point unit of the deterministic deposit (one particle's stencil
-// weights F are stored as llrint(F * 2^60 / P); a node sum is bounded by
-// 2 * 2^60 because sum |F_gamma| <= 2 for Gamma_4).
-constexpr double kFixOne = 1152921504606846976.0;
+// Deterministic deposit: weights are summed as integers in units of 2^-K.
+// float runs: K = 18 (an int32 shared window of 4096 particles cannot
+// overflow); double runs: K = 61 - ceil(log2 P), capped at 40, so that even a
+// node that gathered every particle stays inside int64.
+int fixed_k(const sipf_params& p) {
+  if (p.precision == 32) return 18;
+  int lg = 0;
+  while ((1LL << lg) < p.P + 1) ++lg;
+  int k = 61 - lg;
+  return k > 40 ? 40 : k;
+}
 
 }  // namespace
 
@@ -80,7 +87,27 @@ struct sipf_ctx {
   bool own_stream = false;
   int64_t n = 0;
   size_t esz = 4;
-  void* X[3] = {nullptr, nullptr, nullptr};
+  // particles: two tile-binned buffers (x, y, z, id) sharing one of two layouts
+  int NT = 1, ntx = 1, shift = 30;
+  int64_t cap_total = 0;
+  void* bx[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  uint32_t* bid[2] = {nullptr, nullptr};
+  int* lcap[2] = {nullptr, nullptr};
+  long long* lbase[2] = {nullptr, nullptr};
+  int* cursor[2] = {nullptr, nullptr};
+  int* count = nullptr;
+  long long* chunk_start = nullptr;
+  unsigned long long* work = nullptr;
+  int* hist = nullptr;
+  int cur = 0, lc = 0;            // current buffer, active layout
+  int64_t since_layout = 0;
+  // staging in particle order (x, y, z, id) and its one-bin description
+  void* st[3] = {nullptr, nullptr, nullptr};
+  uint32_t* st_id = nullptr;
+  int* st_count = nullptr;
+  int* st_cap = nullptr;
+  long long* st_base = nullptr;
+  // grid state
   void* phi = nullptr;     // H^3 T, or H^3 int64 (deterministic deposit)
   void* T1 = nullptr;      // S complex: forward intermediate
   void* alpha = nullptr;   // S complex: alpha^(n)
@@ -91,6 +118,8 @@ struct sipf_ctx {
   int64_t H3() const { return (int64_t)p.H * p.H * p.H; }
   int64_t S() const { return (int64_t)p.H * p.H * (p.H / 2 + 1); }
   bool fixed() const { return p.deposit_mode == SIPF_DEPOSIT_DETERMINISTIC; }
+  int64_t max_chunks() const { return p.P / binned_chunk() + NT + 2; }
+  int resort() const { return p.resort_every > 0 ? p.resort_every : 16; }
 };
 
 enum { kDscMass = 0, kDscAlpha0 = 1, kDscM2 = 2, kDscRing = 3, kDscHF = 4, kDscTot = 5, kDscMax = 6, kDscCount = 8 };
@@ -110,17 +139,93 @@ SpecParams spec_params(const sipf_ctx* c) {
   return sp;
 }
 
-template <typename T> T particle_weight(const sipf_ctx* c) {
-  return c->fixed() ? (T)(kFixOne / (double)c->p.P) : (T)(c->p.mass / (double)c->p.P);
+// deterministic grid: integer counts of 2^-K weight units, times M0/P
+double fixed_in_scale(const sipf_ctx* c) { return c->p.mass / (double)c->p.P * ldexp(1.0, -fixed_k(c->p)); }
+
+// Kernel arguments for src -> dst; src_buf < 0 selects the particle-order staging.
+template <typename T> BinArgs<T> bin_args(sipf_ctx* c, int src_buf, int src_lay, int dst_buf, int dst_lay) {
+  BinArgs<T> a{};
+  if (src_buf < 0) {
+    a.sx = (const T*)c->st[0];
+    a.sy = (const T*)c->st[1];
+    a.sz = (const T*)c->st[2];
+    a.sid = c->st_id;
+    a.src_base = c->st_base;
+    a.src_count = c->st_count;
+  } else {
+    a.sx = (const T*)c->bx[src_buf][0];
+    a.sy = (const T*)c->bx[src_buf][1];
+    a.sz = (const T*)c->bx[src_buf][2];
+    a.sid = c->bid[src_buf];
+    a.src_base = c->lbase[src_lay];
+    a.src_count = c->count;
+  }
+  a.chunk_start = c->chunk_start;
+  if (dst_buf >= 0) {
+    a.dx = (T*)c->bx[dst_buf][0];
+    a.dy = (T*)c->bx[dst_buf][1];
+    a.dz = (T*)c->bx[dst_buf][2];
+    a.did = c->bid[dst_buf];
+    a.dst_base = c->lbase[dst_lay];
+    a.dst_cap = c->lcap[dst_lay];
+    a.dst_cursor = c->cursor[dst_buf];
+  }
+  a.work = c->work;
+  a.NT = c->NT;
+  a.ntx = c->ntx;
+  a.tile_shift = c->shift;
+  a.phi = c->phi;
+  a.grad4 = (const T*)c->grad;
+  a.g = make_geo<T>(c->p.L, c->p.H);
+  a.s_noise = (T)(c->p.splitting == SIPF_SPLIT_HALF ? sqrt(c->p.mu * c->p.dt) : sqrt(2.0 * c->p.mu * c->p.dt));
+  a.chitau = (T)(c->p.chi * c->p.dt);
+  a.wmass = (T)(c->p.mass / (double)c->p.P);
+  a.fix_k = fixed_k(c->p);
+  a.seed = c->p.seed;
+  a.n = (uint32_t)(c->n + 1);
+  a.p2g = c->p.p2g_order;
+  a.g2p = c->p.g2p_order;
+  a.split = c->p.splitting;
+  a.fixed = c->fixed() ? 1 : 0;
+  a.err = c->err;
+  return a;
 }
 
-double fixed_in_scale(const sipf_ctx* c) { return c->p.mass / kFixOne; }
-
-template <typename T> int deposit_positions(sipf_ctx* c) {
+// Deposit the current bins into phi (initialisation of Algorithm 4 and after
+// positions are replaced).
+template <typename T> int deposit_current(sipf_ctx* c) {
   const size_t gb = (size_t)c->H3() * (c->fixed() ? 8 : sizeof(T));
   SIPF_CK(cudaMemsetAsync(c->phi, 0, gb, c->stream));
-  SIPF_CK(launch_deposit<T>((T*)c->X[0], (T*)c->X[1], (T*)c->X[2], c->p.P, make_geo<T>(c->p.L, c->p.H),
-                            particle_weight<T>(c), c->phi, c->p.p2g_order, c->fixed() ? 1 : 0, c->stream));
+  SIPF_CK(cudaMemsetAsync(c->work, 0, sizeof(unsigned long long), c->stream));
+  SIPF_CK(launch_binned<T>(bin_args<T>(c, c->cur, c->lc, -1, 0), 0, 1, 0, c->stream));
+  return SIPF_OK;
+}
+
+// Bin the particle-order staging (wrapped positions and ids) into a fresh
+// layout sized from its tile histogram, then deposit.
+template <typename T> int rebin_from_staging(sipf_ctx* c) {
+  const int d = c->cur, L = 1 - c->lc;
+  const size_t nb = (size_t)(c->NT + 1);
+  SIPF_CK(cudaMemsetAsync(c->hist, 0, nb * sizeof(int), c->stream));
+  SIPF_CK(launch_tile_hist<T>((const T*)c->st[0], (const T*)c->st[1], (const T*)c->st[2], c->p.P,
+                              make_geo<T>(c->p.L, c->p.H), c->shift, c->ntx, c->hist, c->stream));
+  SIPF_CK(launch_layout(c->hist, c->lcap[L], c->lbase[L], c->NT, (int)c->p.P, c->stream));
+  // chunk list of the staging (one bin holding all P particles); clears the destination cursors
+  SIPF_CK(launch_chunk_list(c->st_count, c->st_cap, c->count, c->chunk_start, c->cursor[d], c->NT, c->work,
+                            c->stream));
+  SIPF_CK(cudaMemsetAsync(c->work, 0, sizeof(unsigned long long), c->stream));
+  SIPF_CK(launch_binned<T>(bin_args<T>(c, -1, 0, d, L), 0, 0, 1, c->stream));
+  SIPF_CK(launch_chunk_list(c->cursor[d], c->lcap[L], c->count, c->chunk_start, c->cursor[1 - d], c->NT, c->work,
+                            c->stream));
+  c->cur = d;
+  c->lc = L;
+  c->since_layout = 0;
+  return deposit_current<T>(c);
+}
+
+// Particle order -> staging arrays (or caller-owned device arrays).
+template <typename T> int unbin_to(sipf_ctx* c, T* x, T* y, T* z) {
+  SIPF_CK(launch_unbin<T>(bin_args<T>(c, c->cur, c->lc, -1, 0), c->max_chunks(), x, y, z, c->stream));
   return SIPF_OK;
 }
 
@@ -129,28 +234,10 @@ template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
   const int nh = H / 2 + 1;
   const size_t S = (size_t)c->S();
   const SpecParams sp = spec_params(c);
-  MoveArgs<T> a;
-  a.x = (T*)c->X[0];
-  a.y = (T*)c->X[1];
-  a.z = (T*)c->X[2];
-  a.P = c->p.P;
-  a.grad4 = (const T*)c->grad;
-  a.phi = c->phi;
-  a.g = make_geo<T>(c->p.L, H);
-  a.s_noise = (T)(c->p.splitting == SIPF_SPLIT_HALF ? sqrt(c->p.mu * c->p.dt) : sqrt(2.0 * c->p.mu * c->p.dt));
-  a.chitau = (T)(c->p.chi * c->p.dt);
-  a.w = particle_weight<T>(c);
-  a.seed = c->p.seed;
-  a.p2g = c->p.p2g_order;
-  a.g2p = c->p.g2p_order;
-  a.split = c->p.splitting;
-  a.fixed = c->fixed() ? 1 : 0;
-  a.err = c->err;
   cpx<T>* T1 = (cpx<T>*)c->T1;
   cpx<T>* T2 = (cpx<T>*)c->T2;
   cpx<T>* al = (cpx<T>*)c->alpha;
   for (int64_t s = 0; s < nsteps; ++s) {
-    const int64_t n = c->n + 1;
     // beta^(n-1) = F_H I(rho-hat^(n-1)); the deposit grid is cleared as it is read
     SIPF_CK(launch_rows_r2c<T>(c->phi, c->fixed() ? 1 : 0, fixed_in_scale(c), true, T1, H, H * H, nullptr,
                                c->stream));
@@ -159,10 +246,26 @@ template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
     SIPF_CK(launch_spectral_x<T>(T1, al, T2, H, sp, kModeStep, c->dsc + kDscAlpha0, c->stream));
     SIPF_CK(launch_cols<T>(T2, H, H, nh, 3, S, +1, 1.0, c->stream));
     SIPF_CK(launch_rows_c2r<T>(T2, 3, S, (T*)c->grad, H, H * H, nullptr, c->stream));
-    // X^(n-1) -> X^n, deposit X^n
-    a.n = (uint32_t)n;
-    SIPF_CK(launch_move_deposit<T>(a, c->stream));
-    c->n = n;
+    // X^(n-1) -> X^n, deposit X^n, re-bin into the other buffer
+    const int src = c->cur, dst = 1 - c->cur;
+    SIPF_CK(cudaMemsetAsync(c->work, 0, sizeof(unsigned long long), c->stream));
+    SIPF_CK(launch_binned<T>(bin_args<T>(c, src, c->lc, dst, c->lc), 1, 1, 1, c->stream));
+    SIPF_CK(launch_chunk_list(c->cursor[dst], c->lcap[c->lc], c->count, c->chunk_start, c->cursor[src], c->NT,
+                              c->work, c->stream));
+    c->cur = dst;
+    c->n += 1;
+    if (++c->since_layout >= c->resort()) {
+      // new capacities from the tile counts just made, and a re-bin into them
+      const int L = 1 - c->lc, d2 = 1 - c->cur;
+      SIPF_CK(launch_layout(c->cursor[c->cur], c->lcap[L], c->lbase[L], c->NT, (int)c->p.P, c->stream));
+      SIPF_CK(cudaMemsetAsync(c->work, 0, sizeof(unsigned long long), c->stream));
+      SIPF_CK(launch_binned<T>(bin_args<T>(c, c->cur, c->lc, d2, L), 0, 0, 1, c->stream));
+      SIPF_CK(launch_chunk_list(c->cursor[d2], c->lcap[L], c->count, c->chunk_start, c->cursor[c->cur], c->NT,
+                                c->work, c->stream));
+      c->cur = d2;
+      c->lc = L;
+      c->since_layout = 0;
+    }
   }
   return SIPF_OK;
 }
@@ -257,7 +360,9 @@ template <typename T> int diagnostics_impl(sipf_ctx* c, sipf_diag* d) {
   T* g = nullptr;
   int r = density_impl<T>(c, c->H0 > 0 ? 1 : 0, &g);
   if (r) return r;
-  SIPF_CK(launch_moments<T>((T*)c->X[0], (T*)c->X[1], (T*)c->X[2], c->p.P, c->dsc + kDscM2, c->stream));
+  r = unbin_to<T>(c, (T*)c->st[0], (T*)c->st[1], (T*)c->st[2]);
+  if (r) return r;
+  SIPF_CK(launch_moments<T>((T*)c->st[0], (T*)c->st[1], (T*)c->st[2], c->p.P, c->dsc + kDscM2, c->stream));
   SIPF_CK(launch_alpha_energy<T>((cpx<T>*)c->alpha, c->p.H, c->dsc + kDscHF, c->stream));
   double out[kDscCount];
   SIPF_CK(cudaMemcpyAsync(out, c->dsc, sizeof(out), cudaMemcpyDeviceToHost, c->stream));
@@ -283,23 +388,47 @@ template <typename T> int upload_aos(sipf_ctx* c, const double* X) {
   SIPF_CK(cudaMalloc(&stage, bytes));
   cudaError_t e = cudaMemcpyAsync(stage, X, bytes, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess)
-    e = launch_aos_to_soa<T>(stage, c->p.P, make_geo<T>(c->p.L, c->p.H), (T*)c->X[0], (T*)c->X[1], (T*)c->X[2],
+    e = launch_aos_to_soa<T>(stage, c->p.P, make_geo<T>(c->p.L, c->p.H), (T*)c->st[0], (T*)c->st[1], (T*)c->st[2],
                              c->stream);
+  if (e == cudaSuccess) e = launch_iota(c->st_id, c->p.P, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   cudaFree(stage);
   if (e != cudaSuccess) return cuda_fail(e, "upload positions");
-  return deposit_positions<T>(c);
+  return rebin_from_staging<T>(c);
 }
 
 template <typename T> int positions_host(sipf_ctx* c, double* out) {
   const size_t P = (size_t)c->p.P;
+  int r = unbin_to<T>(c, (T*)c->st[0], (T*)c->st[1], (T*)c->st[2]);
+  if (r) return r;
   std::vector<T> h(3 * P);
   for (int d = 0; d < 3; ++d)
-    SIPF_CK(cudaMemcpyAsync(h.data() + d * P, c->X[d], P * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+    SIPF_CK(cudaMemcpyAsync(h.data() + d * P, c->st[d], P * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
   SIPF_CK(cudaStreamSynchronize(c->stream));
   for (size_t i = 0; i < P; ++i)
     for (int d = 0; d < 3; ++d) out[3 * i + d] = (double)h[d * P + i];
   return SIPF_OK;
+}
+
+template <typename T> int upload_soa_impl(sipf_ctx* c, const void* const src[3]) {
+  for (int d = 0; d < 3; ++d)
+    SIPF_CK(cudaMemcpyAsync(c->st[d], src[d], (size_t)c->p.P * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  SIPF_CK(launch_wrap_soa<T>(c->p.P, make_geo<T>(c->p.L, c->p.H), (T*)c->st[0], (T*)c->st[1], (T*)c->st[2],
+                             c->stream));
+  SIPF_CK(launch_iota(c->st_id, c->p.P, c->stream));
+  return rebin_from_staging<T>(c);
+}
+
+template <typename T> int download_soa_impl(sipf_ctx* c, void* const dst[3]) {
+  int r = unbin_to<T>(c, (T*)c->st[0], (T*)c->st[1], (T*)c->st[2]);
+  if (r) return r;
+  for (int d = 0; d < 3; ++d)
+    SIPF_CK(cudaMemcpyAsync(dst[d], c->st[d], (size_t)c->p.P * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+  return SIPF_OK;
+}
+
+template <typename T> int positions_dev_impl(sipf_ctx* c, void* x, void* y, void* z) {
+  return unbin_to<T>(c, (T*)x, (T*)y, (T*)z);
 }
 
 template <typename T> int spectrum_host(sipf_ctx* c, double* out) {
@@ -314,7 +443,22 @@ template <typename T> int spectrum_host(sipf_ctx* c, double* out) {
 void free_ctx(sipf_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
-  for (int d = 0; d < 3; ++d) cudaFree(c->X[d]);
+  for (int b = 0; b < 2; ++b) {
+    for (int d = 0; d < 3; ++d) cudaFree(c->bx[b][d]);
+    cudaFree(c->bid[b]);
+    cudaFree(c->lcap[b]);
+    cudaFree(c->lbase[b]);
+    cudaFree(c->cursor[b]);
+  }
+  for (int d = 0; d < 3; ++d) cudaFree(c->st[d]);
+  cudaFree(c->st_id);
+  cudaFree(c->st_count);
+  cudaFree(c->st_cap);
+  cudaFree(c->st_base);
+  cudaFree(c->count);
+  cudaFree(c->chunk_start);
+  cudaFree(c->work);
+  cudaFree(c->hist);
   cudaFree(c->phi);
   cudaFree(c->T1);
   cudaFree(c->alpha);
@@ -381,8 +525,29 @@ int sipf_init(const sipf_params* p, const double* X0, void* stream, sipf_ctx** o
   const size_t P = (size_t)p->P;
   const size_t N = (size_t)c->H3();
   const size_t S = (size_t)c->S();
+  c->shift = binned_tile_shift(p->H);
+  c->ntx = p->H <= 16 ? 1 : p->H >> c->shift;
+  c->NT = c->ntx * c->ntx * c->ntx;
+  const size_t nb = (size_t)c->NT + 1;
+  c->cap_total = (int64_t)(2 * P + P / 4 + 32 * (size_t)c->NT + 1024);
+  const size_t cap = (size_t)c->cap_total;
   cudaError_t e = cudaSuccess;
-  for (int d = 0; d < 3 && e == cudaSuccess; ++d) e = cudaMalloc(&c->X[d], P * c->esz);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    for (int d = 0; d < 3 && e == cudaSuccess; ++d) e = cudaMalloc(&c->bx[b][d], cap * c->esz);
+    if (e == cudaSuccess) e = cudaMalloc(&c->bid[b], cap * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&c->lcap[b], nb * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->lbase[b], nb * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&c->cursor[b], nb * sizeof(int));
+  }
+  for (int d = 0; d < 3 && e == cudaSuccess; ++d) e = cudaMalloc(&c->st[d], P * c->esz);
+  if (e == cudaSuccess) e = cudaMalloc(&c->st_id, P * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&c->st_count, nb * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->st_cap, nb * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->st_base, nb * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMalloc(&c->count, nb * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->chunk_start, (nb + 1) * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMalloc(&c->work, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&c->hist, nb * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&c->phi, N * (c->fixed() ? 8 : c->esz));
   if (e == cudaSuccess) e = cudaMalloc(&c->T1, S * 2 * c->esz);
   if (e == cudaSuccess) e = cudaMalloc(&c->alpha, S * 2 * c->esz);
@@ -393,6 +558,18 @@ int sipf_init(const sipf_params* p, const double* X0, void* stream, sipf_ctx** o
   if (e == cudaSuccess) e = cudaMemsetAsync(c->alpha, 0, S * 2 * c->esz, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->dsc, 0, kDscCount * sizeof(double), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->grad, 0, 4 * N * c->esz, c->stream);
+  if (e == cudaSuccess) {
+    // the staging described as one bin (the overflow slot) holding all P particles
+    std::vector<int> cnt(nb, 0), capv(nb, 0);
+    std::vector<long long> base(nb, 0);
+    cnt[c->NT] = (int)P;
+    capv[c->NT] = (int)P;
+    e = cudaMemcpy(c->st_count, cnt.data(), nb * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->st_cap, capv.data(), nb * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->st_base, base.data(), nb * sizeof(long long), cudaMemcpyHostToDevice);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMemsetAsync(c->cursor[b], 0, nb * sizeof(int), c->stream);
+  }
   if (e != cudaSuccess) {
     free_ctx(c);
     return cuda_fail(e, "sipf_init allocation");
@@ -432,26 +609,19 @@ int sipf_set_positions(sipf_ctx* c, const double* X) {
 
 int sipf_upload_soa(sipf_ctx* c, const void* x, const void* y, const void* z) {
   if (!c || !x || !y || !z) return fail(SIPF_EINVAL, "NULL argument");
-  const void* src[3] = {x, y, z};
-  for (int d = 0; d < 3; ++d)
-    SIPF_CK(cudaMemcpyAsync(c->X[d], src[d], (size_t)c->p.P * c->esz, cudaMemcpyHostToDevice, c->stream));
-  return c->p.precision == 64 ? deposit_positions<double>(c) : deposit_positions<float>(c);
+  const void* const src[3] = {x, y, z};
+  return DISPATCH(c, upload_soa_impl, c, src);
 }
 
 int sipf_download_soa(sipf_ctx* c, void* x, void* y, void* z) {
   if (!c || !x || !y || !z) return fail(SIPF_EINVAL, "NULL argument");
-  void* dst[3] = {x, y, z};
-  for (int d = 0; d < 3; ++d)
-    SIPF_CK(cudaMemcpyAsync(dst[d], c->X[d], (size_t)c->p.P * c->esz, cudaMemcpyDeviceToHost, c->stream));
-  return SIPF_OK;
+  void* const dst[3] = {x, y, z};
+  return DISPATCH(c, download_soa_impl, c, dst);
 }
 
-int sipf_positions_dev(sipf_ctx* c, void** x, void** y, void** z) {
+int sipf_positions_dev(sipf_ctx* c, void* x, void* y, void* z) {
   if (!c || !x || !y || !z) return fail(SIPF_EINVAL, "NULL argument");
-  *x = c->X[0];
-  *y = c->X[1];
-  *z = c->X[2];
-  return SIPF_OK;
+  return DISPATCH(c, positions_dev_impl, c, x, y, z);
 }
 
 int sipf_density(sipf_ctx* c, double* out, int filtered) {
@@ -486,7 +656,8 @@ int sipf_sync(sipf_ctx* c) {
   SIPF_CK(cudaMemcpy(&flag, c->err, sizeof(int), cudaMemcpyDeviceToHost));
   if (flag) {
     SIPF_CK(cudaMemset(c->err, 0, sizeof(int)));
-    return fail(SIPF_ENONFINITE, "a particle position became non-finite");
+    if (flag & 1) return fail(SIPF_ENONFINITE, "a particle position became non-finite");
+    return fail(SIPF_ENOMEM, "the overflow bin of the particle layout was full");
   }
   return SIPF_OK;
 }
@@ -532,10 +703,10 @@ int sipf_deposit_dev(int precision, const void* x, const void* y, const void* z,
   if (P == 0) return SIPF_OK;
   if (precision == 64)
     SIPF_CK(launch_deposit<double>((const double*)x, (const double*)y, (const double*)z, P, make_geo<double>(L, H),
-                                   w, grid, order, 0, s));
+                                   w, (double*)grid, order, s));
   else
     SIPF_CK(launch_deposit<float>((const float*)x, (const float*)y, (const float*)z, P, make_geo<float>(L, H),
-                                  (float)w, grid, order, 0, s));
+                                  (float)w, (float*)grid, order, s));
   return SIPF_OK;
 }
 
@@ -550,10 +721,10 @@ int sipf_gather_dev(int precision, const void* x, const void* y, const void* z, 
   cudaStream_t s = (cudaStream_t)stream;
   if (precision == 64)
     SIPF_CK(launch_gather<double>((const double*)x, (const double*)y, (const double*)z, P, make_geo<double>(L, H),
-                                  (const double*)f, ncomp, 0, order, (double*)out, s));
+                                  (const double*)f, ncomp, order, (double*)out, s));
   else
     SIPF_CK(launch_gather<float>((const float*)x, (const float*)y, (const float*)z, P, make_geo<float>(L, H),
-                                 (const float*)f, ncomp, 0, order, (float*)out, s));
+                                 (const float*)f, ncomp, order, (float*)out, s));
   return SIPF_OK;
 }
 

@@ -134,23 +134,30 @@ template <typename T> __device__ __forceinline__ Axis4<T> axis4(T l) {
   return a;
 }
 
-// Visit the 32 nodes of Gamma_4 (Eq. (4ord)) around cell (cx,cy,cz) with
-// in-cell offsets lambda: fn(flat_index, weight).  Inner nodes carry the
-// trilinear weight times 1 + sum_k lambda_k(1-lambda_k)/2; the outer node with
-// index -1 or 2 on one axis carries that axis' cubic factor times the bilinear
-// weight of the other two axes.
-template <typename T, typename Fn>
-__device__ __forceinline__ void gamma4_visit(int cx, int cy, int cz, T lx, T ly, T lz, int H, int mask, Fn&& fn) {
-  const Axis4<T> ax = axis4(lx), ay = axis4(ly), az = axis4(lz);
-  const int HH = H * H;
-  int ix[4], iy[4], iz[4];
+// Per-axis node indices of the four stencil layers (cell offsets -1, 0, 1, 2):
+// ia[o] is the contribution of layer o on that axis to the flat node index.
+// Global grid: ((c + o - 1) & mask) * stride.
+__device__ __forceinline__ void axis_layers_global(int c, int mask, int stride, int ia[4]) {
 #pragma unroll
-  for (int o = 0; o < 4; ++o) {
-    ix[o] = ((cx + o - 1) & mask) * HH;
-    iy[o] = ((cy + o - 1) & mask) * H;
-    iz[o] = (cz + o - 1) & mask;
-  }
+  for (int o = 0; o < 4; ++o) ia[o] = ((c + o - 1) & mask) * stride;
+}
+
+// Visit the 32 nodes of Gamma_4 (Eq. (4ord)) with in-cell offsets lambda:
+// fn(flat_index, w * F_gamma).  Inner nodes carry the trilinear weight times
+// 1 + sum_k lambda_k (1 - lambda_k)/2; the outer node with index -1 or 2 on one
+// axis carries that axis' cubic factor times the bilinear weight of the other
+// two axes.  ix/iy/iz: per-axis layer indices (see axis_layers_global).
+template <typename T, typename Fn>
+__device__ __forceinline__ void gamma4_visit(const int ix[4], const int iy[4], const int iz[4], T lx, T ly, T lz,
+                                             T w, Fn&& fn) {
+  Axis4<T> ax = axis4(lx);
+  const Axis4<T> ay = axis4(ly), az = axis4(lz);
   const T boost = T(1) + T(0.5) * (lx * ax.l0 + ly * ay.l0 + lz * az.l0);
+  // fold the particle weight into the x-axis factors
+  ax.l0 *= w;
+  ax.l1 *= w;
+  ax.om *= w;
+  ax.o2 *= w;
   const T wx[2] = {ax.l0, ax.l1}, wy[2] = {ay.l0, ay.l1}, wz[2] = {az.l0, az.l1};
   T byz[2][2], bxz[2][2], bxy[2][2];
 #pragma unroll
@@ -192,28 +199,37 @@ __device__ __forceinline__ void gamma4_visit(int cx, int cy, int cz, T lx, T ly,
     }
 }
 
-// The 8 nodes of Gamma_2 (Eq. (2ord)): trilinear weights.
+// The 8 nodes of Gamma_2 (Eq. (2ord)): trilinear weights; uses layers 1 and 2.
 template <typename T, typename Fn>
-__device__ __forceinline__ void gamma2_visit(int cx, int cy, int cz, T lx, T ly, T lz, int H, int mask, Fn&& fn) {
-  const int HH = H * H;
-  const int ix[2] = {(cx & mask) * HH, ((cx + 1) & mask) * HH};
-  const int iy[2] = {(cy & mask) * H, ((cy + 1) & mask) * H};
-  const int iz[2] = {cz & mask, (cz + 1) & mask};
-  const T wx[2] = {T(1) - lx, lx}, wy[2] = {T(1) - ly, ly}, wz[2] = {T(1) - lz, lz};
+__device__ __forceinline__ void gamma2_visit(const int ix[4], const int iy[4], const int iz[4], T lx, T ly, T lz,
+                                             T w, Fn&& fn) {
+  const T wx[2] = {(T(1) - lx) * w, lx * w}, wy[2] = {T(1) - ly, ly}, wz[2] = {T(1) - lz, lz};
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
       const T wab = wx[a] * wy[b];
 #pragma unroll
-      for (int c = 0; c < 2; ++c) fn(ix[a] + iy[b] + iz[c], wab * wz[c]);
+      for (int c = 0; c < 2; ++c) fn(ix[a + 1] + iy[b + 1] + iz[c + 1], wab * wz[c]);
     }
 }
 
 template <typename T, typename Fn>
-__device__ __forceinline__ void stencil_visit(int order, int cx, int cy, int cz, T lx, T ly, T lz, int H, int mask, Fn&& fn) {
-  if (order == 4) gamma4_visit<T>(cx, cy, cz, lx, ly, lz, H, mask, fn);
-  else gamma2_visit<T>(cx, cy, cz, lx, ly, lz, H, mask, fn);
+__device__ __forceinline__ void stencil_visit(int order, const int ix[4], const int iy[4], const int iz[4], T lx, T ly,
+                                              T lz, T w, Fn&& fn) {
+  if (order == 4) gamma4_visit<T>(ix, iy, iz, lx, ly, lz, w, fn);
+  else gamma2_visit<T>(ix, iy, iz, lx, ly, lz, w, fn);
+}
+
+// Stencil of a particle on the global periodic grid.
+template <typename T, typename Fn>
+__device__ __forceinline__ void stencil_visit_global(int order, int cx, int cy, int cz, T lx, T ly, T lz, T w,
+                                                     const Geo<T>& g, Fn&& fn) {
+  int ix[4], iy[4], iz[4];
+  axis_layers_global(cx, g.mask, g.H * g.H, ix);
+  axis_layers_global(cy, g.mask, g.H, iy);
+  axis_layers_global(cz, g.mask, 1, iz);
+  stencil_visit<T>(order, ix, iy, iz, lx, ly, lz, w, fn);
 }
 
 }  // namespace sipf

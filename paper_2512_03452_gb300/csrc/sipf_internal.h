@@ -51,35 +51,60 @@ cudaError_t launch_rows_c2r(const cpx<T>* in, int ncomp, size_t comp_stride, T* 
                             int rows, double* max_acc, cudaStream_t s);
 
 // ---- particle launchers (particle_kernels.cu) -----------------------------------
+// Arguments of the binned particle kernel (see particle_kernels.cu).
 template <typename T>
-struct MoveArgs {
-  T* x; T* y; T* z;
-  int64_t P;
-  const T* grad4;        // H^3 nodes x 4 (gx, gy, gz, 0)
-  void* phi;             // deposit target (T, or int64 fixed point)
+struct BinArgs {
+  // source bins
+  const T* sx; const T* sy; const T* sz; const uint32_t* sid;
+  const long long* src_base;     // [NT+1] first slot of each bin
+  const int* src_count;          // [NT+1] particles in each bin
+  const long long* chunk_start;  // [NT+2] prefix sum of ceil(count / chunk)
+  // destination bins
+  T* dx; T* dy; T* dz; uint32_t* did;
+  const long long* dst_base;     // [NT+1]
+  const int* dst_cap;            // [NT+1]
+  int* dst_cursor;               // [NT+1] fill cursors (zeroed before the launch)
+  unsigned long long* work;      // chunk counter of the persistent grid (zeroed before the launch)
+  int NT, ntx, tile_shift;       // tiles, tiles per axis, log2 tile edge
+  // physics
+  void* phi;                     // deposit target (T, or int64 fixed point)
+  const T* grad4;                // H^3 nodes x 4 (gx, gy, gz, 0)
   Geo<T> g;
-  T s_noise;             // sqrt(mu tau) (half) or sqrt(2 mu tau) (plain)
-  T chitau;              // chi * tau
-  T w;                   // M0 / P, or 2^60 / P in fixed-point mode
+  T s_noise;                     // sqrt(mu tau) (half) or sqrt(2 mu tau) (plain)
+  T chitau;                      // chi * tau
+  T wmass;                       // M0 / P
+  int fix_k;                     // deterministic mode: fixed-point unit 2^-fix_k of a weight
   uint64_t seed;
-  uint32_t n;            // step index used as the noise counter
-  int p2g, g2p, split;
-  int fixed;             // deposit into int64 fixed point
-  int* err;              // sticky error word (bit 0: non-finite position)
+  uint32_t n;                    // step index (noise counter)
+  int p2g, g2p, split, fixed;
+  int* err;                      // sticky error word: bit 0 non-finite position, bit 1 lost particle
 };
-template <typename T> cudaError_t launch_move_deposit(const MoveArgs<T>& a, cudaStream_t s);
+int binned_window_slots(int H);
+int binned_chunk();
+int binned_tile_shift(int H);
+template <typename T> cudaError_t launch_binned(const BinArgs<T>& a, int move, int deposit, int rebin, cudaStream_t s);
+cudaError_t launch_chunk_list(const int* cursor, const int* cap, int* count, long long* chunk_start, int* other_cursor,
+                              int NT, unsigned long long* work, cudaStream_t s);
+cudaError_t launch_layout(const int* want, int* cap, long long* base, int NT, int ovf_cap, cudaStream_t s);
 template <typename T>
-cudaError_t launch_deposit(const T* x, const T* y, const T* z, int64_t P, Geo<T> g, T w, void* phi,
-                           int order, int fixed, cudaStream_t s);
+cudaError_t launch_tile_hist(const T* x, const T* y, const T* z, int64_t P, Geo<T> g, int shift, int ntx, int* hist,
+                             cudaStream_t s);
 template <typename T>
-cudaError_t launch_gather(const T* x, const T* y, const T* z, int64_t P, Geo<T> g, const T* f,
-                          int ncomp, int interleaved4, int order, T* out, cudaStream_t s);
+cudaError_t launch_unbin(const BinArgs<T>& a, int64_t max_chunks, T* x, T* y, T* z, cudaStream_t s);
+cudaError_t launch_iota(uint32_t* id, int64_t P, cudaStream_t s);
+template <typename T>
+cudaError_t launch_deposit(const T* x, const T* y, const T* z, int64_t P, Geo<T> g, T w, T* phi, int order,
+                           cudaStream_t s);
+template <typename T>
+cudaError_t launch_gather(const T* x, const T* y, const T* z, int64_t P, Geo<T> g, const T* f, int ncomp, int order,
+                          T* out, cudaStream_t s);
 template <typename T>
 cudaError_t launch_noise(uint64_t seed, int64_t step, int64_t first, int64_t P, T* z, cudaStream_t s);
 template <typename T>
 cudaError_t launch_moments(const T* x, const T* y, const T* z, int64_t P, double* acc2, cudaStream_t s);
 template <typename T>
 cudaError_t launch_aos_to_soa(const double* aos, int64_t P, Geo<T> g, T* x, T* y, T* z, cudaStream_t s);
+template <typename T> cudaError_t launch_wrap_soa(int64_t P, Geo<T> g, T* x, T* y, T* z, cudaStream_t s);
 template <typename T>
 cudaError_t launch_alpha_energy(const cpx<T>* alpha, int H, double* acc2, cudaStream_t s);
 
