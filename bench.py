@@ -1,0 +1,336 @@
+#!/usr/bin/env python3
+"""Throughput of the SIPF-PIC step (Algorithm 4) on GB300.
+
+Workload: the ring-shaped data at scale -- P = 1e7 particles from a Gaussian
+torus (major radius 0.25 L, minor sigma 0.03 L) plus 5% uniform background,
+H = 128, L = 1, M0 = 300, chi = 1, mu = 0.5, eps = k = 1, tau = 5e-5, FP32.
+One step = one full pass of Algorithm 4 (F_H of the deposit, implicit update
+with the filtered gradient, three inverse transforms, the particle move fused
+with the deposit of the new positions).  Inputs are synthetic and seeded.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own replica
+of the workload (the method has no data-parallel exchange in this build), so
+`value` is the sum over ranks and the scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/sec at P=1e7,H=128 (FP32 vs FP64 plain) + % HBM roofline; adjoint ms/step"
+UNIT = "particle-steps/s"
+P_FULL, H_FULL = 10_000_000, 128
+# algorithmic bytes of the particle kernel per particle-step (FP32): read X (12 B) + write X (12 B)
+BYTES_PER_PARTICLE = 24
+# DRAM traffic (read + write bytes per launch) of the fused move kernel from an
+# ncu capture, keyed by the SHA-256 of the kernel source it was taken on.
+MOVE_TRAFFIC = {}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("particle_kernels.cu", "sipf_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2512_03452_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+# ----------------------------------------------------------------- clocks
+_CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def clocks_start(dev_index):
+    path = tempfile.mktemp(prefix="sipf_clocks_", suffix=".csv")
+    try:
+        f = open(path, "w")
+        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={_CLOCK_FIELDS}", "--format=csv,noheader,nounits",
+                              "-i", str(dev_index), "-lms", "50"], stdout=f, stderr=subprocess.DEVNULL)
+        return p, f, path
+    except Exception:
+        return None, None, path
+
+
+def clocks_stop(handle):
+    p, f, path = handle
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    f.close()
+    sm, mx, reasons = [], 0.0, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(path)
+    except Exception:
+        pass
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- oracle baseline
+def oracle_rate(X_sample, w, steps):
+    """Oracle (FP64 numpy, as it stands) particle-steps/s on a sample of the workload."""
+    from oracle import sipf_oracle as O
+    p = O.Params.from_workload(w, P=X_sample.shape[0])
+    s = O.init_state(X_sample, p)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s = O.step(s, p)
+    dt = time.perf_counter() - t0
+    return X_sample.shape[0] * steps / dt, dt
+
+
+# ----------------------------------------------------------------- distributed
+def dist_init(args):
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def dist_max(v, world, device=None):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(world, device=None):
+    if world > 1:
+        import torch.distributed as dist
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2512_03452_gb300 import Simulation, _abi, build, params_from_workload, workloads
+
+    build.build()
+    _abi.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workloads.torus_ring(H=H_FULL, P=P_FULL)
+    X0 = workloads.sample_positions(w, seed=w.seed + rank)
+    stream = torch.cuda.Stream(device=dev)
+    K, W = args.steps, args.warmup
+
+    sim = Simulation(params_from_workload(w, precision=32), X0, stream=stream.cuda_stream)
+    sim.step(W)
+    sim.sync()
+    dist_barrier(world, dev)
+    torch.cuda.synchronize()
+    clk = clocks_start(local)
+    time.sleep(0.2)
+    _abi.sipf_timing_enable(sim.ctx, 1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        sim.step(K)
+        e1.record(stream)
+    e1.synchronize()
+    dist_barrier(world, dev)
+    torch.cuda.synchronize()
+    clocks = clocks_stop(clk)
+    ms = e0.elapsed_time(e1)
+    tim = _abi.sipf_timing_read(sim.ctx)
+    _abi.sipf_timing_enable(sim.ctx, 0)
+    sim.sync()
+    diag = sim.diagnostics()
+    ms_max = dist_max(ms, world, dev)
+    value = world * P_FULL * K / (ms_max * 1e-3)
+
+    # roofline of the dominant kernel: the fused move + deposit + re-bin kernel
+    peak, peak_kind = measured_peaks()
+    move_ms = tim.move_ms / max(tim.steps, 1)
+    achieved = BYTES_PER_PARTICLE * P_FULL / (move_ms * 1e-3) / 1e9
+    traffic = MOVE_TRAFFIC.get(kernel_source_hash())
+    stages = {k: getattr(tim, k) / max(tim.steps, 1) for k in
+              ("forward_ms", "spectral_ms", "inverse_ms", "move_ms", "bookkeeping_ms")}
+
+    # FP64 plain path on the same workload
+    K64, W64 = max(1, min(K, 20)), min(W, 3)
+    sim64 = Simulation(params_from_workload(w, precision=64), X0, stream=stream.cuda_stream)
+    sim64.step(W64)
+    sim64.sync()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        f0.record(stream)
+        sim64.step(K64)
+        f1.record(stream)
+    f1.synchronize()
+    ms64 = dist_max(f0.elapsed_time(f1), world, dev)
+    sim64.sync()
+    sim64.close()
+
+    # end to end through the C ABI with host buffers: every step uploads the
+    # positions from pinned host memory, steps, and reads them back
+    Ke = max(1, min(K, 20))
+    hx = [torch.from_numpy(np.ascontiguousarray(X0[:, d], dtype=np.float32)).pin_memory() for d in range(3)]
+    ptrs = [t.data_ptr() for t in hx]
+    _abi.sipf_upload_soa(sim.ctx, *ptrs)
+    sim.step(1)
+    _abi.sipf_download_soa(sim.ctx, *ptrs)
+    sim.sync()
+    dist_barrier(world, dev)
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        _abi.sipf_upload_soa(sim.ctx, *ptrs)
+        sim.step(1)
+        _abi.sipf_download_soa(sim.ctx, *ptrs)
+        sim.sync()
+    te = time.perf_counter() - t0
+    te_max = dist_max(te, world, dev)
+    sim.close()
+    e2e = {"value": world * P_FULL * Ke / te_max, "unit": UNIT, "h2d_bytes_per_step": 12 * P_FULL,
+           "d2h_bytes_per_step": 12 * P_FULL, "steps": Ke,
+           "path": "sipf_upload_soa + sipf_step + sipf_download_soa, pinned host SoA float32"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ns = 200_000
+        rate, dt = oracle_rate(X0[:ns].astype(np.float64), w, 2)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {ns} particles of the same torus sample, H=128, 2 steps ({dt:.1f} s, numpy FP64)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "P": P_FULL, "H": H_FULL, "L": w.L, "M0": w.mass, "chi": w.chi,
+                       "mu": w.mu, "eps": w.eps, "k": w.k, "tau": w.dt, "precision": "fp32",
+                       "l2": "inputs larger than L2 (per step 2 x 16 B x 1e7 particle traffic + 76 MB of grids)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "kernel": "k_binned move+deposit+rebin", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_kind, "bytes_per_particle": BYTES_PER_PARTICLE,
+                         "kernel_ms": move_ms},
+            "stages_ms_per_step": stages,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(tim.kernels),
+            "clocks": clocks,
+            "fp64": {"value": world * P_FULL * K64 / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64 / K64,
+                     "steps": K64},
+            "diagnostics": {k: diag[k] for k in ("mass", "peak", "m2", "ring_radius", "step")},
+        }
+        print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args, world, rank):
+    """The FP64 oracle on the host cores, each step a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    from oracle import sipf_oracle as O
+    from paper_2512_03452_gb300 import workloads
+
+    w = workloads.torus_ring(H=H_FULL, P=P_FULL)
+    ns = 10_000
+    wsub = workloads.torus_ring(H=H_FULL, P=ns)
+    X = workloads.sample_positions(wsub)
+    p = O.Params.from_workload(w, P=ns)
+    s = O.init_state(X, p)
+    for _ in range(args.warmup):
+        s = O.step(s, p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s = O.step(s, p)
+    dt = time.perf_counter() - t0
+    value = ns * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "P": P_FULL, "H": H_FULL, "precision": "fp64 oracle",
+                       "parallelism": "host"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{ns} particles of the torus workload per step, H=128 (numpy FP64)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

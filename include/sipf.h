@@ -165,6 +165,29 @@ int sipf_gradient(sipf_ctx* ctx, double* out);
 /* FP64 diagnostics of the current state.  Synchronises. */
 int sipf_diagnostics(sipf_ctx* ctx, sipf_diag* out);
 
+/* Device time of the steps taken while timing is on, per stage, from CUDA
+ * events recorded on the context's stream around each stage of every step;
+ * `kernels` counts the library kernels those steps launched. */
+typedef struct sipf_timing {
+  double forward_ms;     /* F_H of the deposit: rows r2c + middle-axis pass  */
+  double spectral_ms;    /* x-axis pass fused with the update of alpha and G  */
+  double inverse_ms;     /* middle-axis pass + rows c2r of the 3 gradients    */
+  double move_ms;        /* fused move + deposit + re-bin kernel              */
+  double bookkeeping_ms; /* chunk lists and periodic capacity rebuilds        */
+  int64_t steps;
+  int64_t kernels;
+} sipf_timing;
+
+/* Start (enable != 0) or stop recording per-stage events; starting clears
+ * the accumulated times. */
+int sipf_timing_enable(sipf_ctx* ctx, int enable);
+
+/* Synchronise and add up the recorded stage times. */
+int sipf_timing_read(sipf_ctx* ctx, sipf_timing* out);
+
+/* Kernels launched by the context since sipf_init (host-side count). */
+int64_t sipf_kernel_launches(const sipf_ctx* ctx);
+
 /* Wait for the context's stream; returns SIPF_ENONFINITE if a kernel saw a
  * non-finite position since the last call (the flag is then cleared). */
 int sipf_sync(sipf_ctx* ctx);

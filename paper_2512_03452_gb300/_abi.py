@@ -46,6 +46,14 @@ class sipf_diag(ctypes.Structure):
     ]
 
 
+class sipf_timing(ctypes.Structure):
+    _fields_ = [
+        ("forward_ms", ctypes.c_double), ("spectral_ms", ctypes.c_double), ("inverse_ms", ctypes.c_double),
+        ("move_ms", ctypes.c_double), ("bookkeeping_ms", ctypes.c_double), ("steps", ctypes.c_int64),
+        ("kernels", ctypes.c_int64),
+    ]
+
+
 class SipfError(RuntimeError):
     def __init__(self, code: int, where: str, msg: str):
         super().__init__(f"{where} failed ({code}: {msg})")
@@ -74,6 +82,9 @@ _SIGS = {
     "sipf_gradient": (ctypes.c_int, [_P, _D]),
     "sipf_diagnostics": (ctypes.c_int, [_P, ctypes.POINTER(sipf_diag)]),
     "sipf_sync": (ctypes.c_int, [_P]),
+    "sipf_timing_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sipf_timing_read": (ctypes.c_int, [_P, ctypes.POINTER(sipf_timing)]),
+    "sipf_kernel_launches": (ctypes.c_int64, [_P]),
     "sipf_destroy": (None, [_P]),
     "sipf_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sipf_last_error": (ctypes.c_char_p, []),
@@ -196,6 +207,20 @@ def sipf_diagnostics(ctx: int) -> sipf_diag:
 
 def sipf_sync(ctx: int) -> None:
     _check(load().sipf_sync(_P(ctx)), "sipf_sync")
+
+
+def sipf_timing_enable(ctx: int, enable: int) -> None:
+    _check(load().sipf_timing_enable(_P(ctx), int(enable)), "sipf_timing_enable")
+
+
+def sipf_timing_read(ctx: int) -> sipf_timing:
+    t = sipf_timing()
+    _check(load().sipf_timing_read(_P(ctx), ctypes.byref(t)), "sipf_timing_read")
+    return t
+
+
+def sipf_kernel_launches(ctx: int) -> int:
+    return int(load().sipf_kernel_launches(_P(ctx)))
 
 
 def sipf_destroy(ctx: int) -> None:

@@ -368,12 +368,33 @@ k_layout(const int* __restrict__ want, int* __restrict__ cap, long long* __restr
   }
 }
 
-// Tile histogram of plain (unbinned) positions.
+// Tile histogram of plain (unbinned) positions.  With few enough tiles each
+// block counts its contiguous range in shared memory and adds its counts to
+// the global histogram once; otherwise warps aggregate equal tiles.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_tile_hist(const T* __restrict__ x, const T* __restrict__ y, const T* __restrict__ z, int64_t P, Geo<T> g,
-            int shift, int ntx, int* __restrict__ hist) {
+            int shift, int ntx, int NT, int* __restrict__ hist, int use_smem) {
+  extern __shared__ int s_cnt[];
   const int lane = threadIdx.x & 31;
+  if (use_smem) {
+    for (int t = threadIdx.x; t < NT; t += blockDim.x) s_cnt[t] = 0;
+    __syncthreads();
+    const int64_t per = (P + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = (int64_t)blockIdx.x * per, b1 = min(P, b0 + per);
+    for (int64_t p = b0 + threadIdx.x; p < b1; p += blockDim.x) {
+      int cx, cy, cz;
+      T l;
+      cell_lambda(x[p], g, cx, l);
+      cell_lambda(y[p], g, cy, l);
+      cell_lambda(z[p], g, cz, l);
+      atomicAdd(s_cnt + tile_of(cx & g.mask, cy & g.mask, cz & g.mask, shift, ntx), 1);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < NT; t += blockDim.x)
+      if (s_cnt[t]) atomicAdd(hist + t, s_cnt[t]);
+    return;
+  }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t n_iter = (P + stride - 1) / stride;
   for (int64_t it = 0; it < n_iter; ++it) {
@@ -390,6 +411,57 @@ k_tile_hist(const T* __restrict__ x, const T* __restrict__ y, const T* __restric
     }
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
     if (valid && lane == __ffs(peers) - 1) atomicAdd(hist + key, __popc(peers));
+  }
+}
+
+// Re-bin plain (particle-order) arrays into tile bins.  Each block takes a
+// contiguous range, counts its tiles in shared memory, reserves one range per
+// tile in the destination bins with a single global atomic, and hands out the
+// slots of that range with shared atomics.  Must run with the same grid as
+// nothing else depends on the order inside a bin.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_rebin_plain(const T* __restrict__ x, const T* __restrict__ y, const T* __restrict__ z,
+              const uint32_t* __restrict__ id, int64_t P, Geo<T> g, int shift, int ntx, int NT,
+              T* __restrict__ dx, T* __restrict__ dy, T* __restrict__ dz, uint32_t* __restrict__ did,
+              const long long* __restrict__ dst_base, const int* __restrict__ dst_cap, int* __restrict__ dst_cursor,
+              int* err) {
+  extern __shared__ int s_cnt[];
+  for (int t = threadIdx.x; t < NT; t += blockDim.x) s_cnt[t] = 0;
+  __syncthreads();
+  const int64_t per = (P + gridDim.x - 1) / gridDim.x;
+  const int64_t b0 = (int64_t)blockIdx.x * per, b1 = min(P, b0 + per);
+  auto tile = [&](int64_t p) {
+    int cx, cy, cz;
+    T l;
+    cell_lambda(x[p], g, cx, l);
+    cell_lambda(y[p], g, cy, l);
+    cell_lambda(z[p], g, cz, l);
+    return tile_of(cx & g.mask, cy & g.mask, cz & g.mask, shift, ntx);
+  };
+  for (int64_t p = b0 + threadIdx.x; p < b1; p += blockDim.x) atomicAdd(s_cnt + tile(p), 1);
+  __syncthreads();
+  for (int t = threadIdx.x; t < NT; t += blockDim.x)
+    if (s_cnt[t]) s_cnt[t] = atomicAdd(dst_cursor + t, s_cnt[t]);
+  __syncthreads();
+  for (int64_t p = b0 + threadIdx.x; p < b1; p += blockDim.x) {
+    const int t = tile(p);
+    const int r = atomicAdd(s_cnt + t, 1);
+    long long slot;
+    if (r < dst_cap[t]) {
+      slot = dst_base[t] + r;
+    } else {
+      const int o = atomicAdd(dst_cursor + NT, 1);
+      slot = o < dst_cap[NT] ? dst_base[NT] + o : -1;
+    }
+    if (slot >= 0) {
+      dx[slot] = x[p];
+      dy[slot] = y[p];
+      dz[slot] = z[p];
+      did[slot] = id[p];
+    } else {
+      atomicOr(err, 2);
+    }
   }
 }
 
@@ -595,13 +667,30 @@ cudaError_t launch_layout(const int* want, int* cap, long long* base, int NT, in
   return cudaGetLastError();
 }
 
+static int plain_blocks(int64_t P) {
+  int b = grid_for(P, 2048);
+  return b > 152 * 8 ? 152 * 8 : b;
+}
+static constexpr int kMaxSmemTiles = 8192;
+
 template <typename T>
-cudaError_t launch_tile_hist(const T* x, const T* y, const T* z, int64_t P, Geo<T> g, int shift, int ntx, int* hist,
-                             cudaStream_t s) {
-  int b = grid_for(P, 256);
-  if (b > 152 * 16) b = 152 * 16;
-  k_tile_hist<T><<<b, 256, 0, s>>>(x, y, z, P, g, shift, ntx, hist);
+cudaError_t launch_tile_hist(const T* x, const T* y, const T* z, int64_t P, Geo<T> g, int shift, int ntx, int NT,
+                             int* hist, cudaStream_t s) {
+  const int use_smem = NT <= kMaxSmemTiles ? 1 : 0;
+  const int b = use_smem ? plain_blocks(P) : (grid_for(P, 256) > 152 * 16 ? 152 * 16 : grid_for(P, 256));
+  k_tile_hist<T><<<b, 256, use_smem ? NT * sizeof(int) : 0, s>>>(x, y, z, P, g, shift, ntx, NT, hist, use_smem);
   return cudaGetLastError();
+}
+
+template <typename T>
+bool launch_rebin_plain(const T* x, const T* y, const T* z, const uint32_t* id, int64_t P, Geo<T> g, int shift,
+                        int ntx, int NT, T* dx, T* dy, T* dz, uint32_t* did, const long long* dst_base,
+                        const int* dst_cap, int* dst_cursor, int* err, cudaStream_t s, cudaError_t* e) {
+  if (NT > kMaxSmemTiles) return false;
+  k_rebin_plain<T><<<plain_blocks(P), 256, NT * sizeof(int), s>>>(x, y, z, id, P, g, shift, ntx, NT, dx, dy, dz, did,
+                                                                 dst_base, dst_cap, dst_cursor, err);
+  *e = cudaGetLastError();
+  return true;
 }
 
 template <typename T>
@@ -664,8 +753,11 @@ template <typename T> cudaError_t launch_alpha_energy(const cpx<T>* alpha, int H
 
 #define SIPF_INST(T)                                                                                          \
   template cudaError_t launch_binned<T>(const BinArgs<T>&, int, int, int, cudaStream_t);                       \
-  template cudaError_t launch_tile_hist<T>(const T*, const T*, const T*, int64_t, Geo<T>, int, int, int*,     \
+  template cudaError_t launch_tile_hist<T>(const T*, const T*, const T*, int64_t, Geo<T>, int, int, int, int*, \
                                            cudaStream_t);                                                    \
+  template bool launch_rebin_plain<T>(const T*, const T*, const T*, const uint32_t*, int64_t, Geo<T>, int, int, \
+                                      int, T*, T*, T*, uint32_t*, const long long*, const int*, int*, int*,    \
+                                      cudaStream_t, cudaError_t*);                                            \
   template cudaError_t launch_unbin<T>(const BinArgs<T>&, int64_t, T*, T*, T*, cudaStream_t);                 \
   template cudaError_t launch_deposit<T>(const T*, const T*, const T*, int64_t, Geo<T>, T, T*, int,           \
                                          cudaStream_t);                                                      \

@@ -115,6 +115,11 @@ struct sipf_ctx {
   void* grad = nullptr;    // 4 H^3 T: (gx, gy, gz, 0) per node; scratch between steps
   double* dsc = nullptr;   // FP64 accumulators (see kDsc*)
   int* err = nullptr;
+  // optional per-stage timing: 6 events per step (stage boundaries)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  int64_t timed_steps = 0, timed_kernels = 0;
+  int64_t launches = 0;
   int64_t H3() const { return (int64_t)p.H * p.H * p.H; }
   int64_t S() const { return (int64_t)p.H * p.H * (p.H / 2 + 1); }
   bool fixed() const { return p.deposit_mode == SIPF_DEPOSIT_DETERMINISTIC; }
@@ -208,13 +213,20 @@ template <typename T> int rebin_from_staging(sipf_ctx* c) {
   const size_t nb = (size_t)(c->NT + 1);
   SIPF_CK(cudaMemsetAsync(c->hist, 0, nb * sizeof(int), c->stream));
   SIPF_CK(launch_tile_hist<T>((const T*)c->st[0], (const T*)c->st[1], (const T*)c->st[2], c->p.P,
-                              make_geo<T>(c->p.L, c->p.H), c->shift, c->ntx, c->hist, c->stream));
+                              make_geo<T>(c->p.L, c->p.H), c->shift, c->ntx, c->NT, c->hist, c->stream));
   SIPF_CK(launch_layout(c->hist, c->lcap[L], c->lbase[L], c->NT, (int)c->p.P, c->stream));
   // chunk list of the staging (one bin holding all P particles); clears the destination cursors
   SIPF_CK(launch_chunk_list(c->st_count, c->st_cap, c->count, c->chunk_start, c->cursor[d], c->NT, c->work,
                             c->stream));
-  SIPF_CK(cudaMemsetAsync(c->work, 0, sizeof(unsigned long long), c->stream));
-  SIPF_CK(launch_binned<T>(bin_args<T>(c, -1, 0, d, L), 0, 0, 1, c->stream));
+  cudaError_t e = cudaSuccess;
+  if (!launch_rebin_plain<T>((const T*)c->st[0], (const T*)c->st[1], (const T*)c->st[2], c->st_id, c->p.P,
+                             make_geo<T>(c->p.L, c->p.H), c->shift, c->ntx, c->NT, (T*)c->bx[d][0], (T*)c->bx[d][1],
+                             (T*)c->bx[d][2], c->bid[d], c->lbase[L], c->lcap[L], c->cursor[d], c->err, c->stream,
+                             &e)) {
+    SIPF_CK(cudaMemsetAsync(c->work, 0, sizeof(unsigned long long), c->stream));
+    e = launch_binned<T>(bin_args<T>(c, -1, 0, d, L), 0, 0, 1, c->stream);
+  }
+  SIPF_CK(e);
   SIPF_CK(launch_chunk_list(c->cursor[d], c->lcap[L], c->count, c->chunk_start, c->cursor[1 - d], c->NT, c->work,
                             c->stream));
   c->cur = d;
@@ -237,21 +249,35 @@ template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
   cpx<T>* T1 = (cpx<T>*)c->T1;
   cpx<T>* T2 = (cpx<T>*)c->T2;
   cpx<T>* al = (cpx<T>*)c->alpha;
+  auto mark = [&](cudaEvent_t* slot) -> cudaError_t {
+    if (!c->timing) return cudaSuccess;
+    cudaError_t e = cudaEventCreate(slot);
+    if (e == cudaSuccess) e = cudaEventRecord(*slot, c->stream);
+    return e;
+  };
   for (int64_t s = 0; s < nsteps; ++s) {
+    cudaEvent_t ev[6] = {};
+    const int64_t l0 = c->launches;
+    SIPF_CK(mark(&ev[0]));
     // beta^(n-1) = F_H I(rho-hat^(n-1)); the deposit grid is cleared as it is read
     SIPF_CK(launch_rows_r2c<T>(c->phi, c->fixed() ? 1 : 0, fixed_in_scale(c), true, T1, H, H * H, nullptr,
                                c->stream));
     SIPF_CK(launch_cols<T>(T1, H, H, nh, 1, 0, -1, 1.0, c->stream));
+    SIPF_CK(mark(&ev[1]));
     // alpha^n and G(alpha^(n-1)), x axis back-transformed
     SIPF_CK(launch_spectral_x<T>(T1, al, T2, H, sp, kModeStep, c->dsc + kDscAlpha0, c->stream));
+    SIPF_CK(mark(&ev[2]));
     SIPF_CK(launch_cols<T>(T2, H, H, nh, 3, S, +1, 1.0, c->stream));
     SIPF_CK(launch_rows_c2r<T>(T2, 3, S, (T*)c->grad, H, H * H, nullptr, c->stream));
+    SIPF_CK(mark(&ev[3]));
     // X^(n-1) -> X^n, deposit X^n, re-bin into the other buffer
     const int src = c->cur, dst = 1 - c->cur;
     SIPF_CK(cudaMemsetAsync(c->work, 0, sizeof(unsigned long long), c->stream));
     SIPF_CK(launch_binned<T>(bin_args<T>(c, src, c->lc, dst, c->lc), 1, 1, 1, c->stream));
+    SIPF_CK(mark(&ev[4]));
     SIPF_CK(launch_chunk_list(c->cursor[dst], c->lcap[c->lc], c->count, c->chunk_start, c->cursor[src], c->NT,
                               c->work, c->stream));
+    c->launches += 7;
     c->cur = dst;
     c->n += 1;
     if (++c->since_layout >= c->resort()) {
@@ -262,9 +288,16 @@ template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
       SIPF_CK(launch_binned<T>(bin_args<T>(c, c->cur, c->lc, d2, L), 0, 0, 1, c->stream));
       SIPF_CK(launch_chunk_list(c->cursor[d2], c->lcap[L], c->count, c->chunk_start, c->cursor[c->cur], c->NT,
                                 c->work, c->stream));
+      c->launches += 3;
       c->cur = d2;
       c->lc = L;
       c->since_layout = 0;
+    }
+    SIPF_CK(mark(&ev[5]));
+    if (c->timing) {
+      c->ev.insert(c->ev.end(), ev, ev + 6);
+      c->timed_steps += 1;
+      c->timed_kernels += c->launches - l0;
     }
   }
   return SIPF_OK;
@@ -443,6 +476,7 @@ template <typename T> int spectrum_host(sipf_ctx* c, double* out) {
 void free_ctx(sipf_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   for (int b = 0; b < 2; ++b) {
     for (int d = 0; d < 3; ++d) cudaFree(c->bx[b][d]);
     cudaFree(c->bid[b]);
@@ -663,6 +697,41 @@ int sipf_sync(sipf_ctx* c) {
 }
 
 void sipf_destroy(sipf_ctx* c) { free_ctx(c); }
+
+int sipf_timing_enable(sipf_ctx* c, int enable) {
+  if (!c) return fail(SIPF_EINVAL, "ctx is NULL");
+  if (enable) {
+    SIPF_CK(cudaStreamSynchronize(c->stream));
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    c->ev.clear();
+    c->timed_steps = c->timed_kernels = 0;
+  }
+  c->timing = enable != 0;
+  return SIPF_OK;
+}
+
+int sipf_timing_read(sipf_ctx* c, sipf_timing* out) {
+  if (!c || !out) return fail(SIPF_EINVAL, "NULL argument");
+  SIPF_CK(cudaStreamSynchronize(c->stream));
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (size_t i = 0; i + 6 <= c->ev.size(); i += 6)
+    for (int k = 0; k < 5; ++k) {
+      float ms = 0.f;
+      SIPF_CK(cudaEventElapsedTime(&ms, c->ev[i + k], c->ev[i + k + 1]));
+      acc[k] += ms;
+    }
+  // stage 3 -> 4 is the move kernel; 4 -> 5 bookkeeping; 2 -> 3 inverse
+  out->forward_ms = acc[0];
+  out->spectral_ms = acc[1];
+  out->inverse_ms = acc[2];
+  out->move_ms = acc[3];
+  out->bookkeeping_ms = acc[4];
+  out->steps = c->timed_steps;
+  out->kernels = c->timed_kernels;
+  return SIPF_OK;
+}
+
+int64_t sipf_kernel_launches(const sipf_ctx* c) { return c ? c->launches : -1; }
 
 const char* sipf_strerror(int code) {
   switch (code) {

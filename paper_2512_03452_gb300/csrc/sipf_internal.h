@@ -87,8 +87,14 @@ cudaError_t launch_chunk_list(const int* cursor, const int* cap, int* count, lon
                               int NT, unsigned long long* work, cudaStream_t s);
 cudaError_t launch_layout(const int* want, int* cap, long long* base, int NT, int ovf_cap, cudaStream_t s);
 template <typename T>
-cudaError_t launch_tile_hist(const T* x, const T* y, const T* z, int64_t P, Geo<T> g, int shift, int ntx, int* hist,
-                             cudaStream_t s);
+cudaError_t launch_tile_hist(const T* x, const T* y, const T* z, int64_t P, Geo<T> g, int shift, int ntx, int NT,
+                             int* hist, cudaStream_t s);
+// Block-privatised re-bin of particle-order arrays; returns false (nothing
+// launched) when there are too many tiles for a shared-memory count.
+template <typename T>
+bool launch_rebin_plain(const T* x, const T* y, const T* z, const uint32_t* id, int64_t P, Geo<T> g, int shift,
+                        int ntx, int NT, T* dx, T* dy, T* dz, uint32_t* did, const long long* dst_base,
+                        const int* dst_cap, int* dst_cursor, int* err, cudaStream_t s, cudaError_t* e);
 template <typename T>
 cudaError_t launch_unbin(const BinArgs<T>& a, int64_t max_chunks, T* x, T* y, T* z, cudaStream_t s);
 cudaError_t launch_iota(uint32_t* id, int64_t P, cudaStream_t s);
