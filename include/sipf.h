@@ -115,9 +115,9 @@ int sipf_init(const sipf_params* p, const double* X0, void* stream, sipf_ctx** o
 /* Advance nsteps >= 0 steps of Algorithm 4 (asynchronous on the context's
  * stream): per step, F_H of the deposited masses, the implicit update of
  * alpha (Eq. (alpha_hat_update)) with the filtered spectral gradient of
- * alpha^(n-1), three inverse transforms, and the particle move (W^-, gather of
- * grad c at X + W^- with I*, drift, W^+, periodic wrap) fused with the
- * deposit of X^(n) for the next step. */
+ * alpha^(n-1), three inverse transforms, the particle move (W^-, gather of
+ * grad c at X + W^- with I*, drift, W^+, periodic wrap) with re-binning of
+ * the particles by grid tile, and the deposit of X^(n) for the next step. */
 int sipf_step(sipf_ctx* ctx, int64_t nsteps);
 
 /* Advance until n * dt >= T (N_T = ceil(T/dt) steps in total). */
@@ -172,10 +172,13 @@ typedef struct sipf_timing {
   double forward_ms;     /* F_H of the deposit: rows r2c + middle-axis pass  */
   double spectral_ms;    /* x-axis pass fused with the update of alpha and G  */
   double inverse_ms;     /* middle-axis pass + rows c2r of the 3 gradients    */
-  double move_ms;        /* fused move + deposit + re-bin kernel              */
+  double move_ms;        /* move + re-bin kernel (noise, gather, push)        */
   double bookkeeping_ms; /* chunk lists and periodic capacity rebuilds        */
+  double deposit_ms;     /* deposit of the new positions from their bins      */
   int64_t steps;
   int64_t kernels;
+  int64_t overflow;      /* particle-steps spent in the overflow bin (deposited
+                            with global reductions instead of a window)       */
 } sipf_timing;
 
 /* Start (enable != 0) or stop recording per-stage events; starting clears

@@ -49,8 +49,9 @@ class sipf_diag(ctypes.Structure):
 class sipf_timing(ctypes.Structure):
     _fields_ = [
         ("forward_ms", ctypes.c_double), ("spectral_ms", ctypes.c_double), ("inverse_ms", ctypes.c_double),
-        ("move_ms", ctypes.c_double), ("bookkeeping_ms", ctypes.c_double), ("steps", ctypes.c_int64),
-        ("kernels", ctypes.c_int64),
+        ("move_ms", ctypes.c_double), ("bookkeeping_ms", ctypes.c_double), ("deposit_ms", ctypes.c_double),
+        ("steps", ctypes.c_int64),
+        ("kernels", ctypes.c_int64), ("overflow", ctypes.c_int64),
     ]
 
 

@@ -109,15 +109,21 @@ __device__ __forceinline__ int tile_of(int cx, int cy, int cz, int shift, int nt
 // ---------------------------------------------------------------------------
 // The binned particle kernel.  Template flags:
 //   MOVE:    advance X^{n-1} -> X^n (Algorithm 4, particle loop)
-//   DEPOSIT: deposit the (new) positions into phi
+//   DEPOSIT: deposit the positions into phi
 //   REBIN:   write each particle into the destination bins of its tile
+// A step runs MOVE+REBIN, then DEPOSIT over the new bins: the chemotactic
+// drift can carry particles many cells in one step, so the deposit reads the
+// bins of the new positions, where every particle lies in the tile of its bin
+// and the window only needs the stencil halo.
 // WHOLE: the window is the whole (small) grid with periodic slots (H <= 16);
-// otherwise the window is the tile, a margin kM cells and the stencil halo.
+// otherwise the window is the tile plus the halo of Gamma_4 (-1, +2).
 // ---------------------------------------------------------------------------
 constexpr int kTileShift = 3;                 // tiles of 8^3 cells
 constexpr int kTileE = 1 << kTileShift;
-constexpr int kMargin = 4;
-constexpr int kWin = kTileE + 2 * kMargin + 3;  // 19 nodes per axis
+constexpr int kMargin = 0;                    // deposits read bins of the current positions
+constexpr int kWin = kTileE + 2 * kMargin + 3;  // 11 nodes per axis (tile + stencil halo)
+constexpr int kWinSlots = kWin * kWin * kWin;
+constexpr int kReplicas = 4;                  // window copies (lane mod 4)
 constexpr int kChunk = 4096;                  // particles per work item
 
 template <typename T, bool FIXED, bool MOVE, bool DEPOSIT, bool REBIN, bool WHOLE>
@@ -126,35 +132,32 @@ k_binned(BinArgs<T> a) {
   using A = typename WinType<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   A* win = reinterpret_cast<A*>(smem_raw);
-  __shared__ int s_bin, s_len;
-  __shared__ long long s_start, s_chunk;
+  __shared__ ChunkDesc s_desc[2];
   const long long nchunks = a.chunk_start[a.NT + 1];
   const int H = a.g.H, mask = a.g.mask;
-  const int wslots = WHOLE ? H * H * H : kWin * kWin * kWin;
+  const int wslots = WHOLE ? H * H * H : kWinSlots;
   const int lane = threadIdx.x & 31;
+  // lanes of a warp that land in the same cell add into different copies
+  A* const my_win = win + (lane & (kReplicas - 1)) * wslots;
   if (DEPOSIT)
-    for (int i = threadIdx.x; i < wslots; i += blockDim.x) win[i] = A(0);
-  for (;;) {
-    __syncthreads();
+    for (int i = threadIdx.x; i < kReplicas * wslots; i += blockDim.x) win[i] = A(0);
+  // work items are taken from a global counter; the next one is fetched
+  // while the current one is processed
+  if (threadIdx.x == 0) {
+    const long long c = (long long)atomicAdd(a.work, 1ULL);
+    s_desc[0] = c < nchunks ? a.chunks[c] : ChunkDesc{0, 0, 0};
+  }
+  __syncthreads();
+  for (int buf = 0;; buf ^= 1) {
+    const ChunkDesc cur = s_desc[buf];
+    if (cur.len == 0) break;
+    ChunkDesc nxt{0, 0, 0};
     if (threadIdx.x == 0) {
       const long long c = (long long)atomicAdd(a.work, 1ULL);
-      s_chunk = c;
-      if (c < nchunks) {
-        int lo = 0, hi = a.NT;               // largest b with chunk_start[b] <= c
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (a.chunk_start[mid] <= c) lo = mid; else hi = mid - 1;
-        }
-        const long long j = c - a.chunk_start[lo];
-        s_bin = lo;
-        s_start = a.src_base[lo] + j * kChunk;
-        s_len = (int)min((long long)kChunk, (long long)a.src_count[lo] - j * kChunk);
-      }
+      if (c < nchunks) nxt = a.chunks[c];
     }
-    __syncthreads();
-    if (s_chunk >= nchunks) break;
-    const int bin = s_bin, len = s_len;
-    const long long start = s_start;
+    const int bin = cur.bin, len = cur.len;
+    const long long start = cur.start;
     // window origin (node coordinates of slot (0,0,0))
     bool has_win = DEPOSIT && (WHOLE || bin < a.NT);
     int ox = 0, oy = 0, oz = 0;
@@ -168,17 +171,26 @@ k_binned(BinArgs<T> a) {
     const int K = FIXED ? a.fix_k : WinType<T>::bits - ceil_log2(len + 1);
     const T wwin = (T)ldexp(1.0, K);
     const int iters = (len + blockDim.x - 1) / blockDim.x;
+    // next particle's data is loaded one iteration ahead
+    T px = T(0), py = T(0), pz = T(0);
+    uint32_t pid = 0;
+    if ((int)threadIdx.x < len) {
+      px = a.sx[start + threadIdx.x];
+      py = a.sy[start + threadIdx.x];
+      pz = a.sz[start + threadIdx.x];
+      pid = a.sid[start + threadIdx.x];
+    }
     for (int it = 0; it < iters; ++it) {
       const int i = it * blockDim.x + threadIdx.x;
       const bool valid = i < len;
-      T x = T(0), y = T(0), z = T(0);
-      uint32_t id = 0;
-      if (valid) {
-        const long long s = start + i;
-        x = a.sx[s];
-        y = a.sy[s];
-        z = a.sz[s];
-        id = a.sid[s];
+      T x = px, y = py, z = pz;
+      const uint32_t id = pid;
+      if (i + (int)blockDim.x < len) {
+        const long long s = start + i + blockDim.x;
+        px = a.sx[s];
+        py = a.sy[s];
+        pz = a.sz[s];
+        pid = a.sid[s];
       }
       if (MOVE && valid) {
         T nz[6];
@@ -204,6 +216,16 @@ k_binned(BinArgs<T> a) {
       cell_lambda(x, a.g, cx, lx);
       cell_lambda(y, a.g, cy, ly);
       cell_lambda(z, a.g, cz, lz);
+      // reserve the destination slot first: the atomic's round trip overlaps the deposit
+      int t = 0, rank = 0, leader = 0, b0 = 0;
+      if (REBIN) {
+        t = tile_of(cx & mask, cy & mask, cz & mask, a.tile_shift, a.ntx);
+        const unsigned key = valid ? (unsigned)t : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+        leader = __ffs(peers) - 1;
+        rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && lane == leader) b0 = atomicAdd(a.dst_cursor + t, __popc(peers));
+      }
       if (DEPOSIT && valid) {
         bool fits = has_win;
         int sx = 0, sy = 0, sz = 0;
@@ -220,10 +242,10 @@ k_binned(BinArgs<T> a) {
             axis_layers_global(cy, mask, H, iy);
             axis_layers_global(cz, mask, 1, iz);
             stencil_visit<T>(a.p2g, ix, iy, iz, lx, ly, lz, wwin,
-                             [&](int idx, T f) { win_add(win + idx, WinType<T>::round(f)); });
+                             [&](int idx, T f) { win_add(my_win + idx, WinType<T>::round(f)); });
           } else {
             // base slot plus compile-time offsets of the 4x4x4 box
-            A* wb = win + ((sx * kWin) + sy) * kWin + sz;
+            A* wb = my_win + ((sx * kWin) + sy) * kWin + sz;
 #pragma unroll
             for (int o = 0; o < 4; ++o) {
               ix[o] = o * (kWin * kWin);
@@ -245,13 +267,6 @@ k_binned(BinArgs<T> a) {
         }
       }
       if (REBIN) {
-        const int t = tile_of(cx & mask, cy & mask, cz & mask, a.tile_shift, a.ntx);
-        const unsigned key = valid ? (unsigned)t : 0xFFFFFFFFu;
-        const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
-        const int leader = __ffs(peers) - 1;
-        const int rank = __popc(peers & ((1u << lane) - 1u));
-        int b0 = 0;
-        if (valid && lane == leader) b0 = atomicAdd(a.dst_cursor + t, __popc(peers));
         b0 = __shfl_sync(0xFFFFFFFFu, b0, leader);
         if (valid) {
           long long slot;
@@ -279,7 +294,13 @@ k_binned(BinArgs<T> a) {
       // along the fastest axis, so the reductions of a warp hit contiguous nodes
       const T unit = a.wmass / wwin;   // M0/P * 2^-K
       for (int sidx = threadIdx.x; sidx < wslots; sidx += blockDim.x) {
-        const A v = win[sidx];
+        A v = win[sidx];
+        win[sidx] = A(0);
+#pragma unroll
+        for (int r = 1; r < kReplicas; ++r) {
+          v += win[r * wslots + sidx];
+          win[r * wslots + sidx] = A(0);
+        }
         if (v != A(0)) {
           int gi;
           if (WHOLE) {
@@ -290,10 +311,11 @@ k_binned(BinArgs<T> a) {
           }
           if (FIXED) atomicAdd(static_cast<unsigned long long*>(a.phi) + gi, (unsigned long long)(long long)v);
           else atomicAdd(static_cast<T*>(a.phi) + gi, (T)v * unit);
-          win[sidx] = A(0);
         }
       }
     }
+    if (threadIdx.x == 0) s_desc[buf ^ 1] = nxt;
+    __syncthreads();
   }
 }
 
@@ -301,12 +323,12 @@ k_binned(BinArgs<T> a) {
 // Bin bookkeeping.
 // ---------------------------------------------------------------------------
 // From the fill cursors of the buffer just written: valid counts (clamped to
-// capacity), the chunk prefix sum and the reset of the other buffer's cursors
-// and of the work counter.  One block.
+// capacity), the chunk prefix sum, the chunk descriptors, and the reset of the
+// other buffer's cursors and of the work counter.  One block.
 __global__ void __launch_bounds__(1024)
-k_chunk_list(const int* __restrict__ cursor, const int* __restrict__ cap, int* __restrict__ count,
-             long long* __restrict__ chunk_start, int* __restrict__ other_cursor, int NT,
-             unsigned long long* work) {
+k_chunk_list(const int* __restrict__ cursor, const int* __restrict__ cap, const long long* __restrict__ base,
+             int* __restrict__ count, long long* __restrict__ chunk_start, ChunkDesc* __restrict__ chunks,
+             int* __restrict__ other_cursor, int NT, unsigned long long* work, unsigned long long* ovf_total) {
   __shared__ long long s_part[1024];
   const int nb = NT + 1;
   const int per = (nb + blockDim.x - 1) / blockDim.x;
@@ -329,23 +351,40 @@ k_chunk_list(const int* __restrict__ cursor, const int* __restrict__ cap, int* _
   long long run = s_part[threadIdx.x] - local;   // exclusive prefix
   for (int b = b0; b < min(b0 + per, nb); ++b) {
     chunk_start[b] = run;
-    run += (count[b] + kChunk - 1) / kChunk;
+    const int c = count[b];
+    for (int j = 0; j * kChunk < c; ++j)
+      chunks[run + j] = ChunkDesc{base[b] + (long long)j * kChunk, b, min(kChunk, c - j * kChunk)};
+    run += (c + kChunk - 1) / kChunk;
   }
   if (threadIdx.x == blockDim.x - 1) chunk_start[nb] = s_part[threadIdx.x];
-  if (threadIdx.x == 0) *work = 0ULL;
+  if (threadIdx.x == 0) {
+    *work = 0ULL;
+    if (ovf_total) *ovf_total += (unsigned long long)count[NT];
+  }
 }
 
-// Capacities from the wanted counts (tile histogram), with spare room, and
-// their prefix sum.  The overflow bin keeps capacity ovf_cap.  One block.
+// Capacities from the wanted counts (tile histogram) and their prefix sum.
+// Spare room: half the tile's own count, 64, and a quarter of what its six
+// face neighbours hold (particles diffuse in across steep density edges).
+// The overflow bin keeps capacity ovf_cap.  One block.
 __global__ void __launch_bounds__(1024)
-k_layout(const int* __restrict__ want, int* __restrict__ cap, long long* __restrict__ base, int NT, int ovf_cap) {
+k_layout(const int* __restrict__ want, int* __restrict__ cap, long long* __restrict__ base, int NT, int ntx,
+         int ovf_cap) {
   __shared__ long long s_part[1024];
   const int per = (NT + blockDim.x - 1) / blockDim.x;
   const int b0 = threadIdx.x * per;
   long long local = 0;
   for (int b = b0; b < min(b0 + per, NT); ++b) {
     const int w = want[b];
-    const int c = w + w / 4 + 32;
+    const int tz = b % ntx, ty = (b / ntx) % ntx, tx = b / (ntx * ntx);
+    long long nsum = 0;
+    for (int d = -1; d <= 1; d += 2) {
+      nsum += want[((((tx + d + ntx) % ntx) * ntx) + ty) * ntx + tz];
+      nsum += want[((tx * ntx) + (ty + d + ntx) % ntx) * ntx + tz];
+      nsum += want[((tx * ntx) + ty) * ntx + (tz + d + ntx) % ntx];
+    }
+    const long long cl = (long long)w + w / 2 + 64 + nsum / 4;
+    const int c = (int)(cl < 0x7fffffffLL ? cl : 0x7fffffffLL);
     cap[b] = c;
     local += c;
   }
@@ -471,16 +510,9 @@ __global__ void __launch_bounds__(256)
 k_unbin(BinArgs<T> a, T* __restrict__ ox, T* __restrict__ oy, T* __restrict__ oz) {
   const long long c = blockIdx.x;
   if (c >= a.chunk_start[a.NT + 1]) return;
-  int lo = 0, hi = a.NT;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (a.chunk_start[mid] <= c) lo = mid; else hi = mid - 1;
-  }
-  const long long j = c - a.chunk_start[lo];
-  const long long start = a.src_base[lo] + j * kChunk;
-  const int len = (int)min((long long)kChunk, (long long)a.src_count[lo] - j * kChunk);
-  for (int i = threadIdx.x; i < len; i += blockDim.x) {
-    const long long s = start + i;
+  const ChunkDesc d = a.chunks[c];
+  for (int i = threadIdx.x; i < d.len; i += blockDim.x) {
+    const long long s = d.start + i;
     const uint32_t id = a.sid[s];
     ox[id] = a.sx[s];
     oy[id] = a.sy[s];
@@ -619,7 +651,7 @@ __global__ void __launch_bounds__(256) k_alpha_energy(const cpx<T>* __restrict__
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
-int binned_window_slots(int H) { return H <= 16 ? H * H * H : kWin * kWin * kWin; }
+int binned_window_slots(int H) { return kReplicas * (H <= 16 ? H * H * H : kWinSlots); }
 int binned_chunk() { return kChunk; }
 int binned_tile_shift(int H) { return H <= 16 ? 30 : kTileShift; }
 
@@ -645,25 +677,26 @@ static cudaError_t launch_binned_t(const BinArgs<T>& a, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_binned(const BinArgs<T>& a, int move, int deposit, int rebin, cudaStream_t s) {
   if (a.fixed) {
-    if (move && deposit && rebin) return launch_binned_t<T, true, true, true, true>(a, s);
+    if (move && !deposit && rebin) return launch_binned_t<T, true, true, false, true>(a, s);
     if (!move && deposit && !rebin) return launch_binned_t<T, true, false, true, false>(a, s);
     if (!move && !deposit && rebin) return launch_binned_t<T, true, false, false, true>(a, s);
   } else {
-    if (move && deposit && rebin) return launch_binned_t<T, false, true, true, true>(a, s);
+    if (move && !deposit && rebin) return launch_binned_t<T, false, true, false, true>(a, s);
     if (!move && deposit && !rebin) return launch_binned_t<T, false, false, true, false>(a, s);
     if (!move && !deposit && rebin) return launch_binned_t<T, false, false, false, true>(a, s);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_chunk_list(const int* cursor, const int* cap, int* count, long long* chunk_start, int* other_cursor,
-                              int NT, unsigned long long* work, cudaStream_t s) {
-  k_chunk_list<<<1, 1024, 0, s>>>(cursor, cap, count, chunk_start, other_cursor, NT, work);
+cudaError_t launch_chunk_list(const int* cursor, const int* cap, const long long* base, int* count,
+                              long long* chunk_start, ChunkDesc* chunks, int* other_cursor, int NT,
+                              unsigned long long* work, unsigned long long* ovf_total, cudaStream_t s) {
+  k_chunk_list<<<1, 1024, 0, s>>>(cursor, cap, base, count, chunk_start, chunks, other_cursor, NT, work, ovf_total);
   return cudaGetLastError();
 }
 
-cudaError_t launch_layout(const int* want, int* cap, long long* base, int NT, int ovf_cap, cudaStream_t s) {
-  k_layout<<<1, 1024, 0, s>>>(want, cap, base, NT, ovf_cap);
+cudaError_t launch_layout(const int* want, int* cap, long long* base, int NT, int ntx, int ovf_cap, cudaStream_t s) {
+  k_layout<<<1, 1024, 0, s>>>(want, cap, base, NT, ntx, ovf_cap);
   return cudaGetLastError();
 }
 

@@ -97,7 +97,9 @@ struct sipf_ctx {
   int* cursor[2] = {nullptr, nullptr};
   int* count = nullptr;
   long long* chunk_start = nullptr;
+  ChunkDesc* chunks = nullptr;
   unsigned long long* work = nullptr;
+  unsigned long long* ovf = nullptr;   // particles found in the overflow bin while timing
   int* hist = nullptr;
   int cur = 0, lc = 0;            // current buffer, active layout
   int64_t since_layout = 0;
@@ -115,7 +117,7 @@ struct sipf_ctx {
   void* grad = nullptr;    // 4 H^3 T: (gx, gy, gz, 0) per node; scratch between steps
   double* dsc = nullptr;   // FP64 accumulators (see kDsc*)
   int* err = nullptr;
-  // optional per-stage timing: 6 events per step (stage boundaries)
+  // optional per-stage timing: 7 events per step (stage boundaries)
   bool timing = false;
   std::vector<cudaEvent_t> ev;
   int64_t timed_steps = 0, timed_kernels = 0;
@@ -166,6 +168,7 @@ template <typename T> BinArgs<T> bin_args(sipf_ctx* c, int src_buf, int src_lay,
     a.src_count = c->count;
   }
   a.chunk_start = c->chunk_start;
+  a.chunks = c->chunks;
   if (dst_buf >= 0) {
     a.dx = (T*)c->bx[dst_buf][0];
     a.dy = (T*)c->bx[dst_buf][1];
@@ -214,10 +217,10 @@ template <typename T> int rebin_from_staging(sipf_ctx* c) {
   SIPF_CK(cudaMemsetAsync(c->hist, 0, nb * sizeof(int), c->stream));
   SIPF_CK(launch_tile_hist<T>((const T*)c->st[0], (const T*)c->st[1], (const T*)c->st[2], c->p.P,
                               make_geo<T>(c->p.L, c->p.H), c->shift, c->ntx, c->NT, c->hist, c->stream));
-  SIPF_CK(launch_layout(c->hist, c->lcap[L], c->lbase[L], c->NT, (int)c->p.P, c->stream));
+  SIPF_CK(launch_layout(c->hist, c->lcap[L], c->lbase[L], c->NT, c->ntx, (int)c->p.P, c->stream));
   // chunk list of the staging (one bin holding all P particles); clears the destination cursors
-  SIPF_CK(launch_chunk_list(c->st_count, c->st_cap, c->count, c->chunk_start, c->cursor[d], c->NT, c->work,
-                            c->stream));
+  SIPF_CK(launch_chunk_list(c->st_count, c->st_cap, c->st_base, c->count, c->chunk_start, c->chunks, c->cursor[d],
+                            c->NT, c->work, nullptr, c->stream));
   cudaError_t e = cudaSuccess;
   if (!launch_rebin_plain<T>((const T*)c->st[0], (const T*)c->st[1], (const T*)c->st[2], c->st_id, c->p.P,
                              make_geo<T>(c->p.L, c->p.H), c->shift, c->ntx, c->NT, (T*)c->bx[d][0], (T*)c->bx[d][1],
@@ -227,8 +230,8 @@ template <typename T> int rebin_from_staging(sipf_ctx* c) {
     e = launch_binned<T>(bin_args<T>(c, -1, 0, d, L), 0, 0, 1, c->stream);
   }
   SIPF_CK(e);
-  SIPF_CK(launch_chunk_list(c->cursor[d], c->lcap[L], c->count, c->chunk_start, c->cursor[1 - d], c->NT, c->work,
-                            c->stream));
+  SIPF_CK(launch_chunk_list(c->cursor[d], c->lcap[L], c->lbase[L], c->count, c->chunk_start, c->chunks,
+                            c->cursor[1 - d], c->NT, c->work, nullptr, c->stream));
   c->cur = d;
   c->lc = L;
   c->since_layout = 0;
@@ -256,7 +259,7 @@ template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
     return e;
   };
   for (int64_t s = 0; s < nsteps; ++s) {
-    cudaEvent_t ev[6] = {};
+    cudaEvent_t ev[7] = {};
     const int64_t l0 = c->launches;
     SIPF_CK(mark(&ev[0]));
     // beta^(n-1) = F_H I(rho-hat^(n-1)); the deposit grid is cleared as it is read
@@ -270,32 +273,37 @@ template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
     SIPF_CK(launch_cols<T>(T2, H, H, nh, 3, S, +1, 1.0, c->stream));
     SIPF_CK(launch_rows_c2r<T>(T2, 3, S, (T*)c->grad, H, H * H, nullptr, c->stream));
     SIPF_CK(mark(&ev[3]));
-    // X^(n-1) -> X^n, deposit X^n, re-bin into the other buffer
+    // X^(n-1) -> X^n, re-bin into the other buffer by the new tile
     const int src = c->cur, dst = 1 - c->cur;
     SIPF_CK(cudaMemsetAsync(c->work, 0, sizeof(unsigned long long), c->stream));
-    SIPF_CK(launch_binned<T>(bin_args<T>(c, src, c->lc, dst, c->lc), 1, 1, 1, c->stream));
+    SIPF_CK(launch_binned<T>(bin_args<T>(c, src, c->lc, dst, c->lc), 1, 0, 1, c->stream));
     SIPF_CK(mark(&ev[4]));
-    SIPF_CK(launch_chunk_list(c->cursor[dst], c->lcap[c->lc], c->count, c->chunk_start, c->cursor[src], c->NT,
-                              c->work, c->stream));
+    SIPF_CK(launch_chunk_list(c->cursor[dst], c->lcap[c->lc], c->lbase[c->lc], c->count, c->chunk_start, c->chunks,
+                              c->cursor[src], c->NT, c->work, c->timing ? c->ovf : nullptr, c->stream));
     c->launches += 7;
     c->cur = dst;
     c->n += 1;
     if (++c->since_layout >= c->resort()) {
       // new capacities from the tile counts just made, and a re-bin into them
       const int L = 1 - c->lc, d2 = 1 - c->cur;
-      SIPF_CK(launch_layout(c->cursor[c->cur], c->lcap[L], c->lbase[L], c->NT, (int)c->p.P, c->stream));
+      SIPF_CK(launch_layout(c->cursor[c->cur], c->lcap[L], c->lbase[L], c->NT, c->ntx, (int)c->p.P, c->stream));
       SIPF_CK(cudaMemsetAsync(c->work, 0, sizeof(unsigned long long), c->stream));
       SIPF_CK(launch_binned<T>(bin_args<T>(c, c->cur, c->lc, d2, L), 0, 0, 1, c->stream));
-      SIPF_CK(launch_chunk_list(c->cursor[d2], c->lcap[L], c->count, c->chunk_start, c->cursor[c->cur], c->NT,
-                                c->work, c->stream));
+      SIPF_CK(launch_chunk_list(c->cursor[d2], c->lcap[L], c->lbase[L], c->count, c->chunk_start, c->chunks,
+                                c->cursor[c->cur], c->NT, c->work, nullptr, c->stream));
       c->launches += 3;
       c->cur = d2;
       c->lc = L;
       c->since_layout = 0;
     }
     SIPF_CK(mark(&ev[5]));
+    // deposit X^n from its bins (Algorithm 2) for the next step
+    SIPF_CK(cudaMemsetAsync(c->work, 0, sizeof(unsigned long long), c->stream));
+    SIPF_CK(launch_binned<T>(bin_args<T>(c, c->cur, c->lc, -1, 0), 0, 1, 0, c->stream));
+    c->launches += 1;
+    SIPF_CK(mark(&ev[6]));
     if (c->timing) {
-      c->ev.insert(c->ev.end(), ev, ev + 6);
+      c->ev.insert(c->ev.end(), ev, ev + 7);
       c->timed_steps += 1;
       c->timed_kernels += c->launches - l0;
     }
@@ -491,7 +499,9 @@ void free_ctx(sipf_ctx* c) {
   cudaFree(c->st_base);
   cudaFree(c->count);
   cudaFree(c->chunk_start);
+  cudaFree(c->chunks);
   cudaFree(c->work);
+  cudaFree(c->ovf);
   cudaFree(c->hist);
   cudaFree(c->phi);
   cudaFree(c->T1);
@@ -563,7 +573,8 @@ int sipf_init(const sipf_params* p, const double* X0, void* stream, sipf_ctx** o
   c->ntx = p->H <= 16 ? 1 : p->H >> c->shift;
   c->NT = c->ntx * c->ntx * c->ntx;
   const size_t nb = (size_t)c->NT + 1;
-  c->cap_total = (int64_t)(2 * P + P / 4 + 32 * (size_t)c->NT + 1024);
+  // bins hold at most 1.5 P + 64 NT + 6 P / 4 (capacities with spare room), the overflow bin P
+  c->cap_total = (int64_t)(4 * P + 64 * (size_t)c->NT + 1024);
   const size_t cap = (size_t)c->cap_total;
   cudaError_t e = cudaSuccess;
   for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
@@ -580,7 +591,10 @@ int sipf_init(const sipf_params* p, const double* X0, void* stream, sipf_ctx** o
   if (e == cudaSuccess) e = cudaMalloc(&c->st_base, nb * sizeof(long long));
   if (e == cudaSuccess) e = cudaMalloc(&c->count, nb * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&c->chunk_start, (nb + 1) * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMalloc(&c->chunks, (size_t)c->max_chunks() * sizeof(ChunkDesc));
   if (e == cudaSuccess) e = cudaMalloc(&c->work, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&c->ovf, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->ovf, 0, sizeof(unsigned long long), c->stream);
   if (e == cudaSuccess) e = cudaMalloc(&c->hist, nb * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&c->phi, N * (c->fixed() ? 8 : c->esz));
   if (e == cudaSuccess) e = cudaMalloc(&c->T1, S * 2 * c->esz);
@@ -705,6 +719,7 @@ int sipf_timing_enable(sipf_ctx* c, int enable) {
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     c->ev.clear();
     c->timed_steps = c->timed_kernels = 0;
+    SIPF_CK(cudaMemsetAsync(c->ovf, 0, sizeof(unsigned long long), c->stream));
   }
   c->timing = enable != 0;
   return SIPF_OK;
@@ -713,21 +728,24 @@ int sipf_timing_enable(sipf_ctx* c, int enable) {
 int sipf_timing_read(sipf_ctx* c, sipf_timing* out) {
   if (!c || !out) return fail(SIPF_EINVAL, "NULL argument");
   SIPF_CK(cudaStreamSynchronize(c->stream));
-  double acc[5] = {0, 0, 0, 0, 0};
-  for (size_t i = 0; i + 6 <= c->ev.size(); i += 6)
-    for (int k = 0; k < 5; ++k) {
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (size_t i = 0; i + 7 <= c->ev.size(); i += 7)
+    for (int k = 0; k < 6; ++k) {
       float ms = 0.f;
       SIPF_CK(cudaEventElapsedTime(&ms, c->ev[i + k], c->ev[i + k + 1]));
       acc[k] += ms;
     }
-  // stage 3 -> 4 is the move kernel; 4 -> 5 bookkeeping; 2 -> 3 inverse
   out->forward_ms = acc[0];
   out->spectral_ms = acc[1];
   out->inverse_ms = acc[2];
   out->move_ms = acc[3];
   out->bookkeeping_ms = acc[4];
+  out->deposit_ms = acc[5];
   out->steps = c->timed_steps;
   out->kernels = c->timed_kernels;
+  unsigned long long ovf = 0;
+  SIPF_CK(cudaMemcpy(&ovf, c->ovf, sizeof(ovf), cudaMemcpyDeviceToHost));
+  out->overflow = (int64_t)ovf;
   return SIPF_OK;
 }
 

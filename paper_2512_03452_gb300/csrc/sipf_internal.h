@@ -51,6 +51,12 @@ cudaError_t launch_rows_c2r(const cpx<T>* in, int ncomp, size_t comp_stride, T* 
                             int rows, double* max_acc, cudaStream_t s);
 
 // ---- particle launchers (particle_kernels.cu) -----------------------------------
+// One work item of the binned kernel: `len` particles of bin `bin` from slot `start`.
+struct ChunkDesc {
+  long long start;
+  int bin, len;
+};
+
 // Arguments of the binned particle kernel (see particle_kernels.cu).
 template <typename T>
 struct BinArgs {
@@ -59,6 +65,7 @@ struct BinArgs {
   const long long* src_base;     // [NT+1] first slot of each bin
   const int* src_count;          // [NT+1] particles in each bin
   const long long* chunk_start;  // [NT+2] prefix sum of ceil(count / chunk)
+  const ChunkDesc* chunks;       // [chunk_start[NT+1]] work items
   // destination bins
   T* dx; T* dy; T* dz; uint32_t* did;
   const long long* dst_base;     // [NT+1]
@@ -83,9 +90,13 @@ int binned_window_slots(int H);
 int binned_chunk();
 int binned_tile_shift(int H);
 template <typename T> cudaError_t launch_binned(const BinArgs<T>& a, int move, int deposit, int rebin, cudaStream_t s);
-cudaError_t launch_chunk_list(const int* cursor, const int* cap, int* count, long long* chunk_start, int* other_cursor,
-                              int NT, unsigned long long* work, cudaStream_t s);
-cudaError_t launch_layout(const int* want, int* cap, long long* base, int NT, int ovf_cap, cudaStream_t s);
+// From fill cursors: clamped counts, chunk prefix sums and chunk descriptors
+// (slots from `base`); clears other_cursor and the work counter.  ovf_total
+// (nullable) accumulates the number of particles in the overflow bin.
+cudaError_t launch_chunk_list(const int* cursor, const int* cap, const long long* base, int* count,
+                              long long* chunk_start, ChunkDesc* chunks, int* other_cursor, int NT,
+                              unsigned long long* work, unsigned long long* ovf_total, cudaStream_t s);
+cudaError_t launch_layout(const int* want, int* cap, long long* base, int NT, int ntx, int ovf_cap, cudaStream_t s);
 template <typename T>
 cudaError_t launch_tile_hist(const T* x, const T* y, const T* z, int64_t P, Geo<T> g, int shift, int ntx, int NT,
                              int* hist, cudaStream_t s);
