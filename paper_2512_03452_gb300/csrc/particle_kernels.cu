@@ -61,6 +61,13 @@ template <> struct WinType<double> {
 
 __device__ __forceinline__ int ceil_log2(int v) { return v <= 1 ? 0 : 32 - __clz(v - 1); }
 
+// 2^k from the exponent bits (no FP64 or transcendental call), |k| < 126
+template <typename T> __device__ __forceinline__ T pow2(int k);
+template <> __device__ __forceinline__ float pow2<float>(int k) { return __int_as_float((127 + k) << 23); }
+template <> __device__ __forceinline__ double pow2<double>(int k) {
+  return __longlong_as_double((long long)(1023 + k) << 52);
+}
+
 // two's-complement integer adds into the shared window
 __device__ __forceinline__ void win_add(int* p, int v) { atomicAdd(p, v); }
 __device__ __forceinline__ void win_add(long long* p, long long v) {
@@ -169,7 +176,7 @@ k_binned(BinArgs<T> a) {
     }
     // window scale 2^K
     const int K = FIXED ? a.fix_k : WinType<T>::bits - ceil_log2(len + 1);
-    const T wwin = (T)ldexp(1.0, K);
+    const T wwin = pow2<T>(K);
     const int iters = (len + blockDim.x - 1) / blockDim.x;
     // next particle's data is loaded one iteration ahead
     T px = T(0), py = T(0), pz = T(0);
@@ -320,6 +327,183 @@ k_binned(BinArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------
+// Move + re-bin (the particle loop of Algorithm 4).  A block takes a work item
+// (particles of one tile bin) in rounds of kMoveRound particles:
+//   1. move each particle, stage (x, y, z, id) in shared memory and count its
+//      destination tile among the 5^3 tiles around the source tile (shared
+//      atomics hand out the rank inside that destination);
+//   2. reserve each destination's range with one global atomic per tile;
+//   3. write the staged particles to their slots.
+// Destinations further than two tiles away (and particles of the overflow
+// bin) reserve their slot with their own global atomic.  One global atomic
+// per (round, destination tile) keeps dense tiles' cursors uncontended.
+// ---------------------------------------------------------------------------
+constexpr int kNbr = 125;   // 5^3 destination tiles around the source tile
+
+template <typename T> struct MoveRound { static constexpr int n = sizeof(T) == 4 ? 2048 : 1024; };
+
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+k_move(BinArgs<T> a) {
+  constexpr int R = MoveRound<T>::n;
+  constexpr int PER = R / 256;
+  __shared__ ChunkDesc s_desc[2];
+  __shared__ __align__(16) T s_x[R];
+  __shared__ __align__(16) T s_y[R];
+  __shared__ __align__(16) T s_z[R];
+  __shared__ __align__(16) uint32_t s_id[R];
+  __shared__ int s_meta[R];        // neighbour slot (0..124) | rank << 7, or -1 - tile for far moves
+  __shared__ int s_cnt[kNbr], s_base[kNbr], s_tile[kNbr];
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ int s_abort;
+  const long long nchunks = a.chunk_start[a.NT + 1];
+  const int mask = a.g.mask, ntx = a.ntx, tmask = a.ntx - 1;   // tiles per axis: a power of two
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar, 1);
+    s_abort = 0;
+    const long long c = (long long)atomicAdd(a.work, 1ULL);
+    s_desc[0] = c < nchunks ? a.chunks[c] : ChunkDesc{0, 0, 0};
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  for (int buf = 0;; buf ^= 1) {
+    const ChunkDesc cur = s_desc[buf];
+    if (cur.len == 0 || s_abort) break;
+    ChunkDesc nxt{0, 0, 0};
+    if (threadIdx.x == 0) {
+      const long long c = (long long)atomicAdd(a.work, 1ULL);
+      if (c < nchunks) nxt = a.chunks[c];
+    }
+    const bool in_tile = cur.bin < a.NT;
+    const int stz = cur.bin & tmask, sty = (cur.bin / ntx) & tmask, stx = cur.bin / (ntx * ntx);
+    // destination tile of each neighbour slot (periodic)
+    for (int k = threadIdx.x; k < kNbr; k += blockDim.x) {
+      const int dx = k / 25 - 2, dy = (k / 5) % 5 - 2, dz = k % 5 - 2;
+      s_tile[k] = ((((stx + dx) & tmask) * ntx) + ((sty + dy) & tmask)) * ntx + ((stz + dz) & tmask);
+    }
+    for (int r0 = 0; r0 < cur.len; r0 += R) {
+      const int n = min(R, cur.len - r0);
+      // stage the round's particles with TMA (bins start on 4-slot boundaries
+      // and have capacity rounded up to 4, so the rounded copy stays inside)
+      if (threadIdx.x == 0) {
+        const long long s0 = cur.start + r0;
+        const uint32_t n4 = (uint32_t)((n + 3) & ~3);
+        fence_proxy_async_smem();
+        mbar_expect_tx(&s_bar, n4 * (3 * (uint32_t)sizeof(T) + 4));
+        tma_load_1d(s_x, a.sx + s0, n4 * sizeof(T), &s_bar);
+        tma_load_1d(s_y, a.sy + s0, n4 * sizeof(T), &s_bar);
+        tma_load_1d(s_z, a.sz + s0, n4 * sizeof(T), &s_bar);
+        tma_load_1d(s_id, a.sid + s0, n4 * 4, &s_bar);
+      }
+      for (int k = threadIdx.x; k < kNbr; k += blockDim.x) s_cnt[k] = 0;
+      if (!mbar_wait(&s_bar, phase, 1u << 26)) {
+        atomicOr(a.err, 4);   // staging copy did not complete
+        s_abort = 1;
+      }
+      phase ^= 1;
+      __syncthreads();
+      if (s_abort) break;
+      // 1. move and stage
+#pragma unroll 1
+      for (int k = 0; k < PER; ++k) {
+        const int i = k * 256 + threadIdx.x;
+        if (i >= n) break;
+        T x = s_x[i], y = s_y[i], z = s_z[i];
+        const uint32_t id = s_id[i];
+        T nz[6];
+        normals6(a.seed, (uint64_t)id, a.n, nz);
+        if (a.split == 0) {
+          // Z = X + W^- + chi tau I*(grad c)(X + W^-),  X^n = Z + W^+
+          const T yx = x + a.s_noise * nz[0], yy = y + a.s_noise * nz[1], yz = z + a.s_noise * nz[2];
+          const V3<T> gr = gather_grad(a.grad4, a.g2p, yx, yy, yz, a.g);
+          x = wrap_coord((yx + a.chitau * gr.x) + a.s_noise * nz[3], a.g);
+          y = wrap_coord((yy + a.chitau * gr.y) + a.s_noise * nz[4], a.g);
+          z = wrap_coord((yz + a.chitau * gr.z) + a.s_noise * nz[5], a.g);
+        } else {
+          // X^n = X + chi tau I*(grad c)(X) + W,  W ~ N(0, 2 mu tau I)
+          const V3<T> gr = gather_grad(a.grad4, a.g2p, x, y, z, a.g);
+          x = wrap_coord((x + a.chitau * gr.x) + a.s_noise * nz[0], a.g);
+          y = wrap_coord((y + a.chitau * gr.y) + a.s_noise * nz[1], a.g);
+          z = wrap_coord((z + a.chitau * gr.z) + a.s_noise * nz[2], a.g);
+        }
+        if (!(t_finite(x) && t_finite(y) && t_finite(z))) atomicOr(a.err, 1);
+        int cx, cy, cz;
+        T l;
+        cell_lambda(x, a.g, cx, l);
+        cell_lambda(y, a.g, cy, l);
+        cell_lambda(z, a.g, cz, l);
+        const int ux = (cx & mask) >> a.tile_shift, uy = (cy & mask) >> a.tile_shift, uz = (cz & mask) >> a.tile_shift;
+        // destination relative to the source tile, minimum image in tile units
+        const int half = ntx >> 1;
+        const int dx = ((ux - stx + half) & tmask) - half;
+        const int dy = ((uy - sty + half) & tmask) - half;
+        const int dz = ((uz - stz + half) & tmask) - half;
+        int meta;
+        if (in_tile && dx >= -2 && dx <= 2 && dy >= -2 && dy <= 2 && dz >= -2 && dz <= 2) {
+          const int nb = ((dx + 2) * 5 + (dy + 2)) * 5 + (dz + 2);
+          meta = nb | (atomicAdd(s_cnt + nb, 1) << 7);
+        } else {
+          meta = -1 - ((ux * ntx + uy) * ntx + uz);
+        }
+        s_x[i] = x;
+        s_y[i] = y;
+        s_z[i] = z;
+        s_meta[i] = meta;
+      }
+      __syncthreads();
+      // 2. one reservation per destination tile
+      for (int k = threadIdx.x; k < kNbr; k += blockDim.x) {
+        const int c = s_cnt[k];
+        if (c) s_base[k] = atomicAdd(a.dst_cursor + s_tile[k], c);
+      }
+      __syncthreads();
+      // 3. write out
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int meta = s_meta[i];
+        int t, r;
+        if (meta >= 0) {
+          const int k = meta & 127;
+          t = s_tile[k];
+          r = s_base[k] + (meta >> 7);
+        } else {
+          t = -1 - meta;
+          r = atomicAdd(a.dst_cursor + t, 1);
+        }
+        long long slot;
+        if (r < a.dst_cap[t]) {
+          slot = a.dst_base[t] + r;
+        } else {
+          const int o = atomicAdd(a.dst_cursor + a.NT, 1);
+          slot = o < a.dst_cap[a.NT] ? a.dst_base[a.NT] + o : -1;
+        }
+        if (slot >= 0) {
+          a.dx[slot] = s_x[i];
+          a.dy[slot] = s_y[i];
+          a.dz[slot] = s_z[i];
+          a.did[slot] = s_id[i];
+        } else {
+          atomicOr(a.err, 2);   // overflow bin full: the particle is lost
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) s_desc[buf ^ 1] = nxt;
+    __syncthreads();
+  }
+}
+
+template <typename T> cudaError_t launch_move(const BinArgs<T>& a, cudaStream_t s) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_move<T>, 256, 0)) != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  k_move<T><<<sms * per_sm, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Bin bookkeeping.
 // ---------------------------------------------------------------------------
 // From the fill cursors of the buffer just written: valid counts (clamped to
@@ -383,8 +567,9 @@ k_layout(const int* __restrict__ want, int* __restrict__ cap, long long* __restr
       nsum += want[((tx * ntx) + (ty + d + ntx) % ntx) * ntx + tz];
       nsum += want[((tx * ntx) + ty) * ntx + (tz + d + ntx) % ntx];
     }
-    const long long cl = (long long)w + w / 2 + 64 + nsum / 4;
-    const int c = (int)(cl < 0x7fffffffLL ? cl : 0x7fffffffLL);
+    long long cl = (long long)w + w / 2 + 64 + nsum / 4;
+    cl = cl < 0x7ffffff0LL ? cl : 0x7ffffff0LL;
+    const int c = (int)((cl + 3) & ~3LL);   // 4-slot multiples keep every bin 16-byte aligned
     cap[b] = c;
     local += c;
   }
@@ -403,7 +588,7 @@ k_layout(const int* __restrict__ want, int* __restrict__ cap, long long* __restr
   }
   if (threadIdx.x == blockDim.x - 1) {
     base[NT] = s_part[threadIdx.x];
-    cap[NT] = ovf_cap;
+    cap[NT] = (ovf_cap + 3) & ~3;
   }
 }
 
@@ -786,6 +971,7 @@ template <typename T> cudaError_t launch_alpha_energy(const cpx<T>* alpha, int H
 
 #define SIPF_INST(T)                                                                                          \
   template cudaError_t launch_binned<T>(const BinArgs<T>&, int, int, int, cudaStream_t);                       \
+  template cudaError_t launch_move<T>(const BinArgs<T>&, cudaStream_t);                                       \
   template cudaError_t launch_tile_hist<T>(const T*, const T*, const T*, int64_t, Geo<T>, int, int, int, int*, \
                                            cudaStream_t);                                                    \
   template bool launch_rebin_plain<T>(const T*, const T*, const T*, const uint32_t*, int64_t, Geo<T>, int, int, \

@@ -276,7 +276,7 @@ template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
     // X^(n-1) -> X^n, re-bin into the other buffer by the new tile
     const int src = c->cur, dst = 1 - c->cur;
     SIPF_CK(cudaMemsetAsync(c->work, 0, sizeof(unsigned long long), c->stream));
-    SIPF_CK(launch_binned<T>(bin_args<T>(c, src, c->lc, dst, c->lc), 1, 0, 1, c->stream));
+    SIPF_CK(launch_move<T>(bin_args<T>(c, src, c->lc, dst, c->lc), c->stream));
     SIPF_CK(mark(&ev[4]));
     SIPF_CK(launch_chunk_list(c->cursor[dst], c->lcap[c->lc], c->lbase[c->lc], c->count, c->chunk_start, c->chunks,
                               c->cursor[src], c->NT, c->work, c->timing ? c->ovf : nullptr, c->stream));
@@ -574,7 +574,7 @@ int sipf_init(const sipf_params* p, const double* X0, void* stream, sipf_ctx** o
   c->NT = c->ntx * c->ntx * c->ntx;
   const size_t nb = (size_t)c->NT + 1;
   // bins hold at most 1.5 P + 64 NT + 6 P / 4 (capacities with spare room), the overflow bin P
-  c->cap_total = (int64_t)(4 * P + 64 * (size_t)c->NT + 1024);
+  c->cap_total = (int64_t)(4 * P + 68 * (size_t)c->NT + 1024);
   const size_t cap = (size_t)c->cap_total;
   cudaError_t e = cudaSuccess;
   for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
@@ -584,8 +584,10 @@ int sipf_init(const sipf_params* p, const double* X0, void* stream, sipf_ctx** o
     if (e == cudaSuccess) e = cudaMalloc(&c->lbase[b], nb * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&c->cursor[b], nb * sizeof(int));
   }
-  for (int d = 0; d < 3 && e == cudaSuccess; ++d) e = cudaMalloc(&c->st[d], P * c->esz);
-  if (e == cudaSuccess) e = cudaMalloc(&c->st_id, P * sizeof(uint32_t));
+  // staging arrays padded to a multiple of 4 elements (16-byte bulk copies)
+  const size_t P4 = (P + 3) & ~(size_t)3;
+  for (int d = 0; d < 3 && e == cudaSuccess; ++d) e = cudaMalloc(&c->st[d], P4 * c->esz);
+  if (e == cudaSuccess) e = cudaMalloc(&c->st_id, P4 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->st_count, nb * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&c->st_cap, nb * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&c->st_base, nb * sizeof(long long));

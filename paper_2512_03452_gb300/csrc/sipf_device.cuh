@@ -71,22 +71,36 @@ __device__ __forceinline__ void normals6(uint64_t seed, uint64_t p, uint32_t n, 
   }
 }
 
-// Float: hardware approximations (lg2, sin, cos) on the same uniforms.  The
-// angle is taken as 2 pi (u - 1/2) in [-pi, pi] (the accurate range of the
-// sine unit); cos/sin of 2 pi u are the negated values.
+// Float: the same uniforms built from the mantissa bits (no integer to float
+// conversion).  unit23(x) = ((x >> 9) + 1/2) 2^-23 exactly; unit32 adds the
+// low 9 bits, giving (x + 1/2) 2^-32 rounded once to float.  The radius uses
+// unit32 (the tail of sqrt(-2 ln u) is sensitive to u), the angle unit23.
+// lg2, sin and cos come from the hardware approximations; the angle is taken
+// as 2 pi (u - 1/2) in [-pi, pi] (the accurate range of the sine unit), so
+// cos/sin of 2 pi u are the negated values.
+__device__ __forceinline__ float unit23(uint32_t x) {
+  // 1 + m 2^-23 minus (1 - 2^-24): exact by Sterbenz
+  return __int_as_float(0x3F800000u | (x >> 9)) - 0.99999994039535522f;
+}
+__device__ __forceinline__ float unit32(uint32_t x) {
+  // (1 + r/512) - (1 + 255.5/512) = (r - 255.5)/512, exact; scaled by 2^-23
+  const float lo = __int_as_float(0x3F800000u | ((x & 511u) << 14)) - 1.4990234375f;
+  return fmaf(lo, 1.1920928955078125e-07f, unit23(x));
+}
+
 __device__ __forceinline__ void normals6(uint64_t seed, uint64_t p, uint32_t n, float z[6]) {
   u32x4 a{(uint32_t)p, (uint32_t)(p >> 32), n, 0u};
   u32x4 b{(uint32_t)p, (uint32_t)(p >> 32), n, 1u};
   philox2blocks(a, b, (uint32_t)seed, (uint32_t)(seed >> 32));
   const uint32_t w[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
-  const float two_m32 = 2.3283064365386963e-10f;
   const float two_pi = 6.28318530717958648f;
   const float ln2x2 = 1.3862943611198906f;          // 2 ln 2
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    const float u1 = __fmaf_rn((float)w[2 * j], two_m32, 0.5f * two_m32);
-    const float u2 = __fmaf_rn((float)w[2 * j + 1], two_m32, 0.5f * two_m32);
-    const float r = sqrtf(fmaxf(-ln2x2 * __log2f(u1), 0.0f));
+    const float u1 = unit32(w[2 * j]);
+    const float u2 = unit23(w[2 * j + 1]);
+    const float r2 = -ln2x2 * __log2f(u1);           // -2 ln u1 >= 0
+    const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));  // sqrt(r2), 0 at r2 = 0
     float s, c;
     __sincosf(two_pi * (u2 - 0.5f), &s, &c);
     z[2 * j] = -r * c;
@@ -113,11 +127,23 @@ template <typename T> __device__ __forceinline__ T wrap_coord(T x, const Geo<T>&
 }
 
 // cell = floor(H x / L), lambda = H x / L - cell.
-template <typename T> __device__ __forceinline__ void cell_lambda(T x, const Geo<T>& g, int& cell, T& lam) {
-  const T u = x * g.inv_h;
-  const T f = t_floor(u);
+__device__ __forceinline__ void cell_lambda_u(double u, int& cell, double& lam) {
+  const double f = ::floor(u);
   cell = (int)f;
   lam = u - f;
+}
+// Float: floor through round-to-nearest of u - 1/2 with the 1.5 * 2^23 shift
+// (plain FP32 adds, |u| < 2^22).  At an exact integer u the result may be
+// (u - 1, lambda = 1) instead of (u, 0); the stencils are continuous across
+// cell faces, so both give the same weights.
+__device__ __forceinline__ void cell_lambda_u(float u, int& cell, float& lam) {
+  const float magic = 12582912.0f;                  // 1.5 * 2^23
+  const float t = (u - 0.5f) + magic;
+  cell = __float_as_int(t) - 0x4B400000;
+  lam = u - (t - magic);
+}
+template <typename T> __device__ __forceinline__ void cell_lambda(T x, const Geo<T>& g, int& cell, T& lam) {
+  cell_lambda_u(x * g.inv_h, cell, lam);
 }
 
 // 1D factors of the stencils for one axis: index -1, 0, 1, 2 of Gamma_4 and
@@ -230,6 +256,46 @@ __device__ __forceinline__ void stencil_visit_global(int order, int cx, int cy, 
   axis_layers_global(cy, g.mask, g.H, iy);
   axis_layers_global(cz, g.mask, 1, iz);
   stencil_visit<T>(order, ix, iy, iz, lx, ly, lz, w, fn);
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copies (global -> shared) completed on an mbarrier.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// Order earlier generic-proxy accesses of shared memory before later TMA writes.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// bytes: multiple of 16; both addresses 16-byte aligned.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// Wait for phase `parity` of the barrier; gives up after `limit` polls and
+// returns false (the caller reports the timeout instead of hanging).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  const uint32_t a = smem_addr(bar);
+  for (uint32_t i = 0; i < limit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
 }
 
 }  // namespace sipf

@@ -90,6 +90,8 @@ int binned_window_slots(int H);
 int binned_chunk();
 int binned_tile_shift(int H);
 template <typename T> cudaError_t launch_binned(const BinArgs<T>& a, int move, int deposit, int rebin, cudaStream_t s);
+// The move + re-bin pass of a step (Algorithm 4 particle loop).
+template <typename T> cudaError_t launch_move(const BinArgs<T>& a, cudaStream_t s);
 // From fill cursors: clamped counts, chunk prefix sums and chunk descriptors
 // (slots from `base`); clears other_cursor and the work counter.  ovf_total
 // (nullable) accumulates the number of particles in the overflow bin.
