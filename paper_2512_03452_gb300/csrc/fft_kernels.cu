@@ -19,8 +19,8 @@
 
 namespace sipf {
 
-// e^{-2 pi i m / 256}, m < 128, per device (written once by ensure_device_tables).
-__device__ double2 g_twiddle[kNmax / 2];
+// e^{-2 pi i m / 256}, m < 256, per device (written once by ensure_device_tables).
+__device__ double2 g_twiddle[kNmax];
 
 cudaError_t ensure_device_tables() {
   static std::mutex mu;
@@ -31,8 +31,8 @@ cudaError_t ensure_device_tables() {
   std::lock_guard<std::mutex> lock(mu);
   if ((int)done.size() <= dev) done.resize(dev + 1, false);
   if (done[dev]) return cudaSuccess;
-  double2 h[kNmax / 2];
-  for (int m = 0; m < kNmax / 2; ++m) {
+  double2 h[kNmax];
+  for (int m = 0; m < kNmax; ++m) {
     const double a = -2.0 * M_PI * (double)m / (double)kNmax;
     h[m] = make_double2(cos(a), sin(a));
   }
@@ -362,6 +362,425 @@ k_rows_c2r(const cpx<T>* __restrict__ in, size_t comp_stride, T* __restrict__ ou
   }
 }
 
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes);
+
+// ===========================================================================
+// Warp FFTs for H = 32 E, E in {2, 4, 8}.  A warp holds one pencil of
+// length N = 32 E: lane l keeps elements j = l + 32 m (m < E) in registers.
+//   1. E-point DFTs over m in registers (radix-2, twiddles from the table);
+//   2. twiddle W_N^(l k1);
+//   3. for each k1, a 32-point decimation-in-frequency across the lanes with
+//      shfl_xor (no shared memory, no block barrier).
+// Afterwards lane l, register k1 holds X[k1 + E bitrev5(l)].
+// ===========================================================================
+template <typename T, int DIR>
+__device__ __forceinline__ cpx<T> twid(const cpx<T>* tw, int m) {
+  cpx<T> w = tw[m & (kNmax - 1)];          // e^{-2 pi i m/256}
+  if (DIR > 0) w.y = -w.y;
+  return w;
+}
+
+template <typename T, int E, int DIR>
+__device__ __forceinline__ void reg_dft(cpx<T> (&v)[E], const cpx<T>* tw) {
+  if (E == 1) return;
+  // bit-reverse the register order, then radix-2 decimation in time
+  constexpr int LG = E == 2 ? 1 : (E == 4 ? 2 : 3);
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    int r = 0;
+#pragma unroll
+    for (int b = 0; b < LG; ++b) r |= ((i >> b) & 1) << (LG - 1 - b);
+    if (r > i) {
+      const cpx<T> t = v[i];
+      v[i] = v[r];
+      v[r] = t;
+    }
+  }
+#pragma unroll
+  for (int half = 1; half < E; half <<= 1) {
+#pragma unroll
+    for (int g = 0; g < E; g += 2 * half) {
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        const cpx<T> w = twid<T, DIR>(tw, k * (kNmax / (2 * half)));
+        const cpx<T> a = v[g + k];
+        const cpx<T> b = cmul(v[g + k + half], w);
+        v[g + k] = cadd(a, b);
+        v[g + k + half] = csub(a, b);
+      }
+    }
+  }
+}
+
+template <typename T> __device__ __forceinline__ cpx<T> shfl_xor_c(cpx<T> v, int s) {
+  return cpx<T>{__shfl_xor_sync(0xFFFFFFFFu, v.x, s), __shfl_xor_sync(0xFFFFFFFFu, v.y, s)};
+}
+
+template <typename T, int E, int DIR>
+__device__ __forceinline__ void warp_fft(cpx<T> (&v)[E], int lane, const cpx<T>* tw) {
+  constexpr int N = 32 * E;
+  constexpr int SC = kNmax / N;
+  reg_dft<T, E, DIR>(v, tw);
+#pragma unroll
+  for (int k1 = 1; k1 < E; ++k1) v[k1] = cmul(v[k1], twid<T, DIR>(tw, lane * k1 * SC));
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool up = (lane & s) != 0;
+    const cpx<T> w = up ? twid<T, DIR>(tw, (lane & (s - 1)) * (kNmax / (2 * s))) : cpx<T>{T(1), T(0)};
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) {
+      const cpx<T> u = shfl_xor_c(v[k1], s);
+      const cpx<T> t = up ? csub(u, v[k1]) : cadd(v[k1], u);
+      v[k1] = cmul(t, w);
+    }
+  }
+}
+
+__device__ __forceinline__ int out_index(int k1, int E, int lane) { return k1 + E * (int)(__brev((unsigned)lane) >> 27); }
+
+template <typename T> __device__ __forceinline__ void load_tw_full(cpx<T>* tw) {
+  for (int i = threadIdx.x; i < kNmax; i += blockDim.x) tw[i] = cpx<T>{(T)g_twiddle[i].x, (T)g_twiddle[i].y};
+}
+
+// Rows r2c: each warp takes row pairs (two real rows as one complex pencil).
+template <typename T, int E, typename Tin>
+__global__ void __launch_bounds__(256)
+kw_rows_r2c(Tin* __restrict__ in, double in_scale, int zero_input, cpx<T>* __restrict__ out, int rows,
+            double* mass_acc) {
+  constexpr int N = 32 * E, NH = N / 2 + 1;
+  __shared__ cpx<T> tw[kNmax];
+  __shared__ cpx<T> zb[8][N];
+  load_tw_full(tw);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int nwarps = gridDim.x * 8;
+  double msum = 0.0;
+  for (int pr = blockIdx.x * 8 + wib; pr < rows / 2; pr += nwarps) {
+    const size_t ra = (size_t)(2 * pr) * N, rb = ra + N;
+    cpx<T> v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      T a, b;
+      if constexpr (sizeof(Tin) == 8 && !std::is_floating_point<Tin>::value) {
+        a = (T)((double)(long long)in[ra + lane + 32 * m] * in_scale);
+        b = (T)((double)(long long)in[rb + lane + 32 * m] * in_scale);
+      } else {
+        a = (T)in[ra + lane + 32 * m];
+        b = (T)in[rb + lane + 32 * m];
+      }
+      v[m] = cpx<T>{a, b};
+    }
+    if (zero_input) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        in[ra + lane + 32 * m] = Tin(0);
+        in[rb + lane + 32 * m] = Tin(0);
+      }
+    }
+    if (mass_acc) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) msum += (double)v[m].x + (double)v[m].y;
+    }
+    warp_fft<T, E, -1>(v, lane, tw);
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) zb[wib][out_index(k1, E, lane)] = v[k1];
+    __syncwarp();
+    cpx<T>* oa = out + (size_t)(2 * pr) * NH;
+    for (int k = lane; k < NH; k += 32) {
+      const cpx<T> zk = zb[wib][k];
+      const cpx<T> zm = cconj(zb[wib][(N - k) & (N - 1)]);
+      const cpx<T> d = csub(zk, zm);
+      oa[k] = cpx<T>{(zk.x + zm.x) * T(0.5), (zk.y + zm.y) * T(0.5)};
+      oa[NH + k] = cpx<T>{d.y * T(0.5), -d.x * T(0.5)};
+    }
+    __syncwarp();
+  }
+  if (mass_acc) {
+    for (int o = 16; o > 0; o >>= 1) msum += __shfl_xor_sync(0xffffffffu, msum, o);
+    if (lane == 0) atomicAdd(mass_acc, msum);
+  }
+}
+
+// c2c along the middle axis of [A][H][B]: a block stages an H x BC tile
+// (coalesced row segments), warps transform its columns from shared memory.
+template <typename T, int E, int DIR, int BC>
+__global__ void __launch_bounds__(256)
+kw_cols(cpx<T>* __restrict__ data, int B, size_t comp_stride, T scale) {
+  constexpr int N = 32 * E, LD = BC + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* buf = tw + kNmax;
+  load_tw_full(tw);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  cpx<T>* base = data + blockIdx.z * comp_stride + (size_t)blockIdx.y * N * B;
+  const int b0 = blockIdx.x * BC;
+  const int nb = min(BC, B - b0);
+  for (int t = threadIdx.x; t < N * BC; t += blockDim.x) {
+    const int j = t / BC, c = t - j * BC;
+    buf[j * LD + c] = c < nb ? base[(size_t)j * B + b0 + c] : cpx<T>{T(0), T(0)};
+  }
+  __syncthreads();
+  for (int c = wib; c < nb; c += 8) {
+    cpx<T> v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = buf[(lane + 32 * m) * LD + c];
+    warp_fft<T, E, DIR>(v, lane, tw);
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) buf[out_index(k1, E, lane) * LD + c] = v[k1];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < N * BC; t += blockDim.x) {
+    const int j = t / BC, c = t - j * BC;
+    if (c < nb) {
+      const cpx<T> v = buf[j * LD + c];
+      base[(size_t)j * B + b0 + c] = cpx<T>{v.x * scale, v.y * scale};
+    }
+  }
+}
+
+// x-axis pass fused with the spectral work (as k_spectral_x), warp FFTs.
+// Shared tile: [N][4 BC + 1]; slot 0 = beta, slots 1..3 the outputs.
+template <typename T, int E, int MODE, int BC>
+__global__ void __launch_bounds__(256)
+kw_spectral_x(const cpx<T>* __restrict__ T1, cpx<T>* __restrict__ alpha, cpx<T>* __restrict__ T2, SpecParams sp,
+              double* alpha0_shadow) {
+  constexpr int N = 32 * E, NHH = N / 2 + 1, LD = 4 * BC + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* buf = tw + kNmax;
+  load_tw_full(tw);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int B = N * NHH;
+  const size_t S = (size_t)N * B;
+  const int b0 = blockIdx.x * BC;
+  const int nb = min(BC, B - b0);
+  constexpr bool needs_beta = (MODE == kModeStep || MODE == kModeDensity);
+  if (needs_beta) {
+    for (int t = threadIdx.x; t < N * BC; t += blockDim.x) {
+      const int j = t / BC, c = t - j * BC;
+      buf[j * LD + c] = c < nb ? T1[(size_t)j * B + b0 + c] : cpx<T>{T(0), T(0)};
+    }
+    __syncthreads();
+    for (int c = wib; c < nb; c += 8) {
+      cpx<T> v[E];
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = buf[(lane + 32 * m) * LD + c];
+      warp_fft<T, E, -1>(v, lane, tw);
+#pragma unroll
+      for (int k1 = 0; k1 < E; ++k1) buf[out_index(k1, E, lane) * LD + c] = v[k1];
+    }
+  }
+  __syncthreads();
+  const T two_pi_L = (T)(2.0 * M_PI / sp.L);
+  const T inv_L3 = (T)sp.inv_L3;
+  const T tau_eps = (T)(sp.tau / sp.eps), eps_tau = (T)(sp.eps / sp.tau), k2 = (T)sp.k2, tau = (T)sp.tau;
+  const T filt = sp.H0 > 0 ? (T)(-2.0 * M_PI * M_PI / (sp.H0 * sp.H0)) : T(0);
+  for (int t = threadIdx.x; t < N * BC; t += blockDim.x) {
+    const int j = t / BC, c = t - j * BC;
+    const int m = b0 + c;
+    cpx<T> o1{T(0), T(0)}, o2{T(0), T(0)}, o3{T(0), T(0)};
+    if (c < nb) {
+      const int ky = m / NHH, kz = m - ky * NHH;
+      const int qx = j < N / 2 ? j : j - N;
+      const int qy = ky < N / 2 ? ky : ky - N;
+      const int qz = kz < N / 2 ? kz : kz - N;
+      const T q2 = (T)(qx * qx + qy * qy + qz * qz);
+      const T Phi = sp.H0 > 0 ? t_exp(filt * q2) : T(1);
+      const size_t gi = (size_t)j * B + m;
+      if (MODE == kModeStep || MODE == kModeGradOnly) {
+        const cpx<T> a = alpha[gi];
+        if (MODE == kModeStep) {
+          cpx<T> beta = buf[j * LD + c];
+          beta.x *= inv_L3;
+          beta.y *= inv_L3;
+          const T lam = two_pi_L * two_pi_L * q2 + k2;
+          cpx<T> an;
+          if (sp.propagator == 0) {
+            const T kappa = T(1) / (T(1) + tau_eps * lam);
+            const T src = T(1) / (lam + eps_tau);
+            an = cpx<T>{kappa * a.x + src * beta.x, kappa * a.y + src * beta.y};
+          } else {
+            const T kappa = t_exp(-tau_eps * lam);
+            an = cpx<T>{kappa * (a.x + tau * beta.x), kappa * (a.y + tau * beta.y)};
+          }
+          alpha[gi] = an;
+          if (m == 0 && j == 0 && alpha0_shadow) {
+            const double lam0 = sp.k2;
+            double s = *alpha0_shadow;
+            if (sp.propagator == 0) s = s / (1.0 + sp.tau / sp.eps * lam0) + sp.beta0 / (lam0 + sp.eps / sp.tau);
+            else s = exp(-sp.tau / sp.eps * lam0) * (s + sp.tau * sp.beta0);
+            *alpha0_shadow = s;
+          }
+        }
+        const T yx = two_pi_L * (T)qx * Phi, yy = two_pi_L * (T)qy * Phi, yz = two_pi_L * (T)qz * Phi;
+        if (qx != -N / 2) o1 = cpx<T>{-yx * a.y, yx * a.x};
+        if (qy != -N / 2) o2 = cpx<T>{-yy * a.y, yy * a.x};
+        if (qz != -N / 2) o3 = cpx<T>{-yz * a.y, yz * a.x};
+      } else if (MODE == kModeDensity) {
+        const cpx<T> beta = buf[j * LD + c];
+        o1 = cpx<T>{beta.x * inv_L3 * Phi, beta.y * inv_L3 * Phi};
+      } else {
+        o1 = alpha[gi];
+      }
+    }
+    buf[j * LD + BC + c] = o1;
+    buf[j * LD + 2 * BC + c] = o2;
+    buf[j * LD + 3 * BC + c] = o3;
+  }
+  __syncthreads();
+  constexpr int nout = (MODE == kModeStep || MODE == kModeGradOnly) ? 3 : 1;
+  for (int col = wib; col < nout * BC; col += 8) {
+    const int c = BC + col;
+    if (col % BC >= nb) continue;
+    cpx<T> v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = buf[(lane + 32 * m) * LD + c];
+    warp_fft<T, E, +1>(v, lane, tw);
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) buf[out_index(k1, E, lane) * LD + c] = v[k1];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < N * BC; t += blockDim.x) {
+    const int j = t / BC, c = t - j * BC;
+    if (c < nb) {
+#pragma unroll
+      for (int d = 0; d < nout; ++d) T2[d * S + (size_t)j * B + b0 + c] = buf[j * LD + (d + 1) * BC + c];
+    }
+  }
+}
+
+// Rows c2r: each warp takes a row pair of every component, rebuilds the
+// full pencil Z = A + i B from the Hermitian halves, inverse-transforms it,
+// and writes (gx, gy, gz, 0) nodes (NCOMP == 3) or a plain grid (NCOMP == 1).
+template <typename T, int E, int NCOMP>
+__global__ void __launch_bounds__(256)
+kw_rows_c2r(const cpx<T>* __restrict__ in, size_t comp_stride, T* __restrict__ out, int rows, double* max_acc) {
+  constexpr int N = 32 * E, NH = N / 2 + 1;
+  constexpr int NOUT = NCOMP == 3 ? 4 : 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* zb_all = tw + kNmax;                                   // [8][N]
+  T* ob_all = reinterpret_cast<T*>(zb_all + 8 * N);             // [8][2][N][NOUT]
+  load_tw_full(tw);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  cpx<T>* zb = zb_all + wib * N;
+  T* ob = ob_all + wib * 2 * N * NOUT;
+  const int nwarps = gridDim.x * 8;
+  double mx = -INFINITY;
+  for (int pr = blockIdx.x * 8 + wib; pr < rows / 2; pr += nwarps) {
+    for (int d = 0; d < NCOMP; ++d) {
+      const cpx<T>* ra = in + d * comp_stride + (size_t)(2 * pr) * NH;
+      const cpx<T>* rb = ra + NH;
+      for (int k = lane; k < NH; k += 32) {
+        cpx<T> A = ra[k], Bv = rb[k];
+        if (k == 0 || k == N / 2) {
+          A.y = T(0);
+          Bv.y = T(0);
+        }
+        zb[k] = cpx<T>{A.x - Bv.y, A.y + Bv.x};
+        if (k > 0 && k < N / 2) zb[N - k] = cpx<T>{A.x + Bv.y, -A.y + Bv.x};   // conj A + i conj B
+      }
+      __syncwarp();
+      cpx<T> v[E];
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = zb[lane + 32 * m];
+      __syncwarp();
+      warp_fft<T, E, +1>(v, lane, tw);
+#pragma unroll
+      for (int k1 = 0; k1 < E; ++k1) {
+        const int j = out_index(k1, E, lane);
+        ob[(0 * N + j) * NOUT + d] = v[k1].x;
+        ob[(1 * N + j) * NOUT + d] = v[k1].y;
+      }
+    }
+    __syncwarp();
+    T* oa = out + (size_t)(2 * pr) * N * NOUT;
+    if (NOUT == 4) {
+      for (int t = lane; t < 2 * N; t += 32) {
+        const T* sv = ob + t * 4;
+        if constexpr (sizeof(T) == 4) {
+          reinterpret_cast<float4*>(oa)[t] = make_float4(sv[0], sv[1], sv[2], 0.f);
+        } else {
+          reinterpret_cast<double2*>(oa)[2 * t] = make_double2(sv[0], sv[1]);
+          reinterpret_cast<double2*>(oa)[2 * t + 1] = make_double2(sv[2], 0.0);
+        }
+      }
+    } else {
+      for (int t = lane; t < 2 * N; t += 32) {
+        const T v = ob[t];
+        oa[t] = v;
+        mx = fmax(mx, (double)v);
+      }
+    }
+    __syncwarp();
+  }
+  if (NOUT == 1 && max_acc) {
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+      long long b = __double_as_longlong(mx);
+      if (b < 0) b ^= 0x7fffffffffffffffLL;
+      atomicMax(reinterpret_cast<long long*>(max_acc), b);
+    }
+  }
+}
+
+static int warp_blocks(int rows) {
+  int b = (rows / 2 + 7) / 8;
+  return b > 152 * 8 ? 152 * 8 : (b < 1 ? 1 : b);
+}
+
+template <typename T, int E>
+static cudaError_t warp_rows_r2c(const void* in, int in_kind, double in_scale, bool zero_input, cpx<T>* out, int rows,
+                                 double* mass_acc, cudaStream_t s) {
+  if (in_kind == 0)
+    kw_rows_r2c<T, E, T><<<warp_blocks(rows), 256, 0, s>>>((T*)in, in_scale, zero_input ? 1 : 0, out, rows, mass_acc);
+  else
+    kw_rows_r2c<T, E, unsigned long long><<<warp_blocks(rows), 256, 0, s>>>((unsigned long long*)in, in_scale,
+                                                                           zero_input ? 1 : 0, out, rows, mass_acc);
+  return cudaGetLastError();
+}
+
+template <typename T, int E, int DIR>
+static cudaError_t warp_cols(cpx<T>* data, int A, int B, int ncomp, size_t comp_stride, double scale, cudaStream_t s) {
+  constexpr int BC = 16;
+  const size_t smem = (kNmax + (size_t)32 * E * (BC + 1)) * sizeof(cpx<T>);
+  auto k = kw_cols<T, E, DIR, BC>;
+  cudaError_t e = set_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((B + BC - 1) / BC, A, ncomp);
+  k<<<grid, 256, smem, s>>>(data, B, comp_stride, (T)scale);
+  return cudaGetLastError();
+}
+
+template <typename T, int E, int MODE>
+static cudaError_t warp_spectral(const cpx<T>* T1, cpx<T>* alpha, cpx<T>* T2, SpecParams sp, double* shadow,
+                                 cudaStream_t s) {
+  constexpr int N = 32 * E;
+  constexpr int BC = (sizeof(T) == 8 && E == 8) ? 4 : ((sizeof(T) == 8 || E == 8) ? 8 : 16);
+  const int B = N * (N / 2 + 1);
+  const size_t smem = (kNmax + (size_t)N * (4 * BC + 1)) * sizeof(cpx<T>);
+  auto k = kw_spectral_x<T, E, MODE, BC>;
+  cudaError_t e = set_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  k<<<(B + BC - 1) / BC, 256, smem, s>>>(T1, alpha, T2, sp, shadow);
+  return cudaGetLastError();
+}
+
+template <typename T, int E, int NCOMP>
+static cudaError_t warp_rows_c2r(const cpx<T>* in, size_t comp_stride, T* out, int rows, double* max_acc,
+                                 cudaStream_t s) {
+  constexpr int N = 32 * E;
+  constexpr int NOUT = NCOMP == 3 ? 4 : 1;
+  const size_t smem = (kNmax + (size_t)8 * N) * sizeof(cpx<T>) + (size_t)8 * 2 * N * NOUT * sizeof(T);
+  auto k = kw_rows_c2r<T, E, NCOMP>;
+  cudaError_t e = set_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  k<<<warp_blocks(rows), 256, smem, s>>>(in, comp_stride, out, rows, max_acc);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
@@ -386,6 +805,9 @@ static int rows_per_pair_block(int H, size_t elem, bool with_out4) {
 template <typename T>
 cudaError_t launch_rows_r2c(const void* in, int in_kind, double in_scale, bool zero_input, cpx<T>* out,
                             int H, int rows, double* mass_acc, cudaStream_t s) {
+  if (H == 64) return warp_rows_r2c<T, 2>(in, in_kind, in_scale, zero_input, out, rows, mass_acc, s);
+  if (H == 128) return warp_rows_r2c<T, 4>(in, in_kind, in_scale, zero_input, out, rows, mass_acc, s);
+  if (H == 256) return warp_rows_r2c<T, 8>(in, in_kind, in_scale, zero_input, out, rows, mass_acc, s);
   const int lgH = ilog2(H);
   const int RP = rows_per_pair_block(H, sizeof(T), false);
   const size_t smem = (kNmax / 2 + (size_t)RP * (H + 1)) * sizeof(cpx<T>);
@@ -415,6 +837,12 @@ static int col_chunk(int H, int slots) {
 template <typename T>
 cudaError_t launch_cols(cpx<T>* data, int H, int A, int B, int ncomp, size_t comp_stride, int dir, double scale,
                         cudaStream_t s) {
+  if (H == 64) return dir < 0 ? warp_cols<T, 2, -1>(data, A, B, ncomp, comp_stride, scale, s)
+                              : warp_cols<T, 2, +1>(data, A, B, ncomp, comp_stride, scale, s);
+  if (H == 128) return dir < 0 ? warp_cols<T, 4, -1>(data, A, B, ncomp, comp_stride, scale, s)
+                               : warp_cols<T, 4, +1>(data, A, B, ncomp, comp_stride, scale, s);
+  if (H == 256) return dir < 0 ? warp_cols<T, 8, -1>(data, A, B, ncomp, comp_stride, scale, s)
+                               : warp_cols<T, 8, +1>(data, A, B, ncomp, comp_stride, scale, s);
   const int lgH = ilog2(H);
   int BC = col_chunk<T>(H, 1);
   if (BC > 16) BC = 16;
@@ -450,9 +878,24 @@ static cudaError_t spectral_mode(const cpx<T>* T1, cpx<T>* alpha, cpx<T>* T2, in
   return cudaGetLastError();
 }
 
+template <typename T, int E>
+static cudaError_t warp_spectral_mode(const cpx<T>* T1, cpx<T>* alpha, cpx<T>* T2, SpecParams sp, int mode,
+                                      double* shadow, cudaStream_t s) {
+  switch (mode) {
+    case kModeStep: return warp_spectral<T, E, kModeStep>(T1, alpha, T2, sp, shadow, s);
+    case kModeDensity: return warp_spectral<T, E, kModeDensity>(T1, alpha, T2, sp, nullptr, s);
+    case kModeField: return warp_spectral<T, E, kModeField>(T1, alpha, T2, sp, nullptr, s);
+    case kModeGradOnly: return warp_spectral<T, E, kModeGradOnly>(T1, alpha, T2, sp, nullptr, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 template <typename T>
 cudaError_t launch_spectral_x(const cpx<T>* T1, cpx<T>* alpha, cpx<T>* T2, int H, SpecParams sp, int mode,
                               double* alpha0_shadow, cudaStream_t s) {
+  if (H == 64) return warp_spectral_mode<T, 2>(T1, alpha, T2, sp, mode, alpha0_shadow, s);
+  if (H == 128) return warp_spectral_mode<T, 4>(T1, alpha, T2, sp, mode, alpha0_shadow, s);
+  if (H == 256) return warp_spectral_mode<T, 8>(T1, alpha, T2, sp, mode, alpha0_shadow, s);
   switch (mode) {
     case kModeStep: return spectral_mode<T, kModeStep>(T1, alpha, T2, H, sp, alpha0_shadow, s);
     case kModeDensity: return spectral_mode<T, kModeDensity>(T1, alpha, T2, H, sp, nullptr, s);
@@ -465,6 +908,12 @@ cudaError_t launch_spectral_x(const cpx<T>* T1, cpx<T>* alpha, cpx<T>* T2, int H
 template <typename T>
 cudaError_t launch_rows_c2r(const cpx<T>* in, int ncomp, size_t comp_stride, T* out, int H, int rows,
                             double* max_acc, cudaStream_t s) {
+  if (H == 64) return ncomp == 3 ? warp_rows_c2r<T, 2, 3>(in, comp_stride, out, rows, nullptr, s)
+                                 : warp_rows_c2r<T, 2, 1>(in, comp_stride, out, rows, max_acc, s);
+  if (H == 128) return ncomp == 3 ? warp_rows_c2r<T, 4, 3>(in, comp_stride, out, rows, nullptr, s)
+                                  : warp_rows_c2r<T, 4, 1>(in, comp_stride, out, rows, max_acc, s);
+  if (H == 256) return ncomp == 3 ? warp_rows_c2r<T, 8, 3>(in, comp_stride, out, rows, nullptr, s)
+                                  : warp_rows_c2r<T, 8, 1>(in, comp_stride, out, rows, max_acc, s);
   const int lgH = ilog2(H);
   const int RP = rows_per_pair_block(H, sizeof(T), true);
   const int NOUT = ncomp == 3 ? 4 : 1;
