@@ -236,6 +236,28 @@ int sipf_forward_ft_dev(int precision, int32_t H, double L, const void* grid,
 int sipf_inverse_ft_dev(int precision, int32_t H, void* spec, void* grid,
                         void* stream);
 
+/* The inverse transform of sipf_inverse_ft_dev for callers that cannot
+ * allocate device memory -- for example code running inside another
+ * library's callback, a server with a fixed memory budget, or any path where
+ * the implicit device synchronisation of cudaMalloc/cudaFree is not allowed.
+ * The paper has no counterpart: this is a property of the library only.
+ *   - Unlike sipf_inverse_ft_dev, `spec` is left unchanged: the transform runs
+ *     in a work space built into the library (a static device array of
+ *     64*64*33 complex doubles, about 2.1 MB, held on every GPU that loads the
+ *     library until the process exits).  H*H*(H/2+1) complex values must fit
+ *     in it: H <= 64 in either precision; larger H returns SIPF_EINVAL.
+ *   - Nothing is allocated; the spectrum is copied device to device into the
+ *     work space, then transformed as in sipf_inverse_ft_dev.
+ *   - The first call on a device looks up the work space's device address
+ *     (and uploads the twiddle table if no other entry point did); make that
+ *     first call before any stream capture.
+ *   - All calls share the one work space, which keeps the last call's
+ *     contents.  Calls whose work overlaps on the GPU (different streams, or
+ *     different host threads without ordering) race and give wrong results;
+ *     order them on one stream. */
+int sipf_inverse_ft_noalloc_dev(int precision, int32_t H, const void* spec, void* grid,
+                                void* stream);
+
 #ifdef __cplusplus
 }
 #endif

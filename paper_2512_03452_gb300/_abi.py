@@ -97,6 +97,7 @@ _SIGS = {
                                        ctypes.c_double, _P, ctypes.c_int32, ctypes.c_int32, _P, _P]),
     "sipf_forward_ft_dev": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, ctypes.c_double, _P, _P, _P]),
     "sipf_inverse_ft_dev": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, _P, _P, _P]),
+    "sipf_inverse_ft_noalloc_dev": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, _P, _P, _P]),
 }
 
 
@@ -256,3 +257,10 @@ def sipf_forward_ft_dev(precision, H, L, grid, spec, stream=0) -> None:
 
 def sipf_inverse_ft_dev(precision, H, spec, grid, stream=0) -> None:
     _check(load().sipf_inverse_ft_dev(precision, H, _P(spec), _P(grid), _P(stream)), "sipf_inverse_ft_dev")
+
+
+def sipf_inverse_ft_noalloc_dev(precision, H, spec, grid, stream=0) -> None:
+    """Inverse transform with the library's built-in work space (no device
+    allocation; `spec` is left unchanged; H <= 64)."""
+    _check(load().sipf_inverse_ft_noalloc_dev(precision, H, _P(spec), _P(grid), _P(stream)),
+           "sipf_inverse_ft_noalloc_dev")

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <cstdio>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -859,3 +860,65 @@ int sipf_inverse_ft_dev(int precision, int32_t H, void* spec, void* grid, void* 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Inverse transform that allocates nothing.
+//
+// Its work space is the file-scope array below, sized for one half spectrum
+// of H = 64 in double precision; every GPU that loads the library holds these
+// bytes until the process exits.  Host code must not use the array's name as
+// a device address: the device address is looked up once per device with
+// cudaGetSymbolAddress (with that device current) and cached.
+// ---------------------------------------------------------------------------
+static constexpr size_t kNoAllocMaxH = 64;
+static constexpr size_t kNoAllocScratchBytes = kNoAllocMaxH * kNoAllocMaxH * (kNoAllocMaxH / 2 + 1) * 2 * sizeof(double);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  SIPF_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(SIPF_EINVAL, "device index beyond the supported range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    SIPF_CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return SIPF_OK;
+}
+}  // namespace
+
+extern "C" int sipf_inverse_ft_noalloc_dev(int precision, int32_t H, const void* spec, void* grid, void* stream) {
+  if (precision != 32 && precision != 64) return fail(SIPF_EINVAL, "precision");
+  if (!is_pow2(H) || H < 8 || H > kNmax || !grid || !spec) return fail(SIPF_EINVAL, "inverse_ft_noalloc args");
+  const size_t nh = (size_t)H / 2 + 1;
+  const size_t bytes = (size_t)H * H * nh * 2 * (precision == 64 ? 8 : 4);
+  if (bytes > kNoAllocScratchBytes)
+    return fail(SIPF_EINVAL, "sipf_inverse_ft_noalloc_dev: the spectrum (" + std::to_string(bytes) +
+                                 " bytes) exceeds the built-in work space of " + std::to_string(kNoAllocScratchBytes) +
+                                 " bytes (H <= 64)");
+  SIPF_CK(ensure_device_tables());
+  void* work = nullptr;
+  int r = noalloc_scratch(&work);
+  if (r) return r;
+  cudaStream_t s = (cudaStream_t)stream;
+  SIPF_CK(cudaMemcpyAsync(work, spec, bytes, cudaMemcpyDeviceToDevice, s));
+  if (precision == 64) {
+    cpx<double>* o = (cpx<double>*)work;
+    SIPF_CK(launch_cols<double>(o, H, 1, H * (int)nh, 1, 0, +1, 1.0, s));
+    SIPF_CK(launch_cols<double>(o, H, H, (int)nh, 1, 0, +1, 1.0, s));
+    SIPF_CK(launch_rows_c2r<double>(o, 1, 0, (double*)grid, H, H * H, nullptr, s));
+  } else {
+    cpx<float>* o = (cpx<float>*)work;
+    SIPF_CK(launch_cols<float>(o, H, 1, H * (int)nh, 1, 0, +1, 1.0, s));
+    SIPF_CK(launch_cols<float>(o, H, H, (int)nh, 1, 0, +1, 1.0, s));
+    SIPF_CK(launch_rows_c2r<float>(o, 1, 0, (float*)grid, H, H * H, nullptr, s));
+  }
+  return SIPF_OK;
+}
