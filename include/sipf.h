@@ -191,8 +191,11 @@ int sipf_timing_read(sipf_ctx* ctx, sipf_timing* out);
 /* Kernels launched by the context since sipf_init (host-side count). */
 int64_t sipf_kernel_launches(const sipf_ctx* ctx);
 
-/* Wait for the context's stream; returns SIPF_ENONFINITE if a kernel saw a
- * non-finite position since the last call (the flag is then cleared). */
+/* Wait for the context's stream and report the kernels' sticky error flags
+ * since the last call (then cleared): SIPF_ENONFINITE for a non-finite
+ * position, SIPF_ETIMEOUT for a bounded wait on a staging copy that ran out,
+ * SIPF_ENOMEM if the overflow bin of the particle layout was full (a particle
+ * was dropped). */
 int sipf_sync(sipf_ctx* ctx);
 
 /* Free everything the context owns.  NULL is a no-op. */

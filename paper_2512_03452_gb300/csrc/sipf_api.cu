@@ -708,6 +708,7 @@ int sipf_sync(sipf_ctx* c) {
   if (flag) {
     SIPF_CK(cudaMemset(c->err, 0, sizeof(int)));
     if (flag & 1) return fail(SIPF_ENONFINITE, "a particle position became non-finite");
+    if (flag & 4) return fail(SIPF_ETIMEOUT, "a bounded wait for a staging copy ran out");
     return fail(SIPF_ENOMEM, "the overflow bin of the particle layout was full");
   }
   return SIPF_OK;
