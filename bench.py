@@ -250,6 +250,8 @@ def run_ours(args, world, rank, local):
            "d2h_bytes_per_step": 12 * P_FULL, "steps": Ke,
            "path": "sipf_upload_soa + sipf_step + sipf_download_soa, pinned host SoA float32"}
 
+    batch = None if args.no_batch else run_batch_leg(world, dev, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ns = 200_000
@@ -278,8 +280,64 @@ def run_ours(args, world, rank, local):
             "fp64": {"value": world * P_FULL * K64 / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64 / K64,
                      "steps": K64},
             "diagnostics": {k: diag[k] for k in ("mass", "peak", "m2", "ring_radius", "step")},
+            "batch": batch,
         }
         print(json.dumps(line), flush=True)
+
+
+def run_batch_leg(world, dev, stream, n_runs=256, steps=64, warmup=32):
+    """The batched form on an ensemble of uneven runs (P log-uniform in
+    [1e4, 1e6], H in {32, 64}, FP32): replayed 32-step graphs, the same steps
+    issued directly, and the same runs as separate single-run contexts stepped
+    one after another."""
+    import numpy as np
+    import torch
+
+    from paper_2512_03452_gb300 import Batch, Simulation, _abi, params_from_workload, workloads
+
+    ws = workloads.ensemble(n_runs)
+    params = [params_from_workload(w, precision=32) for w in ws]
+    X0s = [workloads.sample_positions(w) for w in ws]
+    total_p = sum(w.P for w in ws)
+
+    def timed(fn, k):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            fn(k)
+            b.record(stream)
+        b.synchronize()
+        return dist_max(a.elapsed_time(b), world, dev)
+
+    out = {"workload": f"ensemble of {n_runs} runs, P log-uniform 1e4..1e6, H in {{32, 64}}, FP32",
+           "runs": n_runs, "particles": total_p, "steps": steps, "unit": UNIT}
+    with Batch(params, X0s, stream=stream.cuda_stream) as b:
+        b.step(warmup)
+        b.sync()
+        k0 = _abi.sipf_batch_kernel_launches(b.handle)
+        ms = timed(b.step, steps)
+        out["gpu_launches_per_step"] = (_abi.sipf_batch_kernel_launches(b.handle) - k0) / steps
+        b.use_graph(False)
+        ms_direct = timed(b.step, steps)
+        b.sync()
+    out["value"] = world * total_p * steps / (ms * 1e-3)
+    out["ms_per_step"] = ms / steps
+    out["direct_issue_ms_per_step"] = ms_direct / steps
+    sims = [Simulation(p, X, stream=stream.cuda_stream) for p, X in zip(params, X0s)]
+    try:
+        def seq(k):
+            for _ in range(k):
+                for sim in sims:
+                    sim.step(1)
+        seq(2)
+        torch.cuda.synchronize()
+        ms_seq = timed(seq, steps // 4)
+    finally:
+        for sim in sims:
+            sim.close()
+    out["sequential_single_runs_ms_per_step"] = ms_seq / (steps // 4)
+    out["speedup_vs_sequential"] = out["sequential_single_runs_ms_per_step"] / out["ms_per_step"]
+    return out
 
 
 # ----------------------------------------------------------------- reference arm
@@ -323,6 +381,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble leg")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     world, rank, local = dist_init(args)

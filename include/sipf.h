@@ -204,6 +204,57 @@ void sipf_destroy(sipf_ctx* ctx);
 const char* sipf_strerror(int code);
 const char* sipf_last_error(void);
 
+/* ---- batched runs --------------------------------------------------------
+ * Many independent runs of Algorithm 4 (an ensemble over seeds, chi, P, H,
+ * ... as in the parameter studies of Sec. 5) advanced together: per step the
+ * field solve is launched once per distinct grid size H (runs of equal H in
+ * one launch of each FFT kernel) and every particle pass once for all runs,
+ * whose work items are drawn from one shared counter.  Steps are recorded
+ * in a CUDA graph of 32 steps and replayed.  Each run computes exactly what
+ * a sipf_ctx with the same parameters and X0 computes (bit for bit in
+ * deterministic deposit mode; up to the order of floating-point atomic
+ * additions otherwise).
+ */
+typedef struct sipf_batch sipf_batch;
+
+/* Create nruns runs: run r has parameters params[r] and initial positions
+ * X0[r] (host, params[r].P x 3 row-major float64).  All runs must share
+ * precision and deposit_mode, have H >= 32 and resort_every 0 or 16;
+ * 1 <= nruns <= 4096.
+ * stream: a cudaStream_t (not the legacy default stream, which cannot be
+ * captured) or NULL for a stream the batch creates.  On failure nothing is
+ * left allocated and *out is NULL; SIPF_EINVAL names the offending run. */
+int sipf_batch_init(int32_t nruns, const sipf_params* params, const double* const* X0,
+                    void* stream, sipf_batch** out);
+
+/* Advance every run by nsteps >= 0 steps (asynchronous on the batch's
+ * stream).  The step index n is shared by all runs and kept on the device. */
+int sipf_batch_step(sipf_batch* b, int64_t nsteps);
+
+/* enable = 0: issue every step's launches directly instead of replaying the
+ * recorded 32-step graph (same results; for timing the graph's benefit). */
+int sipf_batch_use_graph(sipf_batch* b, int enable);
+
+/* Step index n of all runs; -1 for NULL. */
+int64_t sipf_batch_current_step(const sipf_batch* b);
+
+/* Library kernels launched since sipf_batch_init, counting every kernel of
+ * a replayed graph (host-side count); -1 for NULL. */
+int64_t sipf_batch_kernel_launches(const sipf_batch* b);
+
+/* Per-run read-back, as sipf_positions / sipf_diagnostics / sipf_spectrum
+ * for run `run` (0 <= run < nruns).  Synchronise. */
+int sipf_batch_positions(sipf_batch* b, int32_t run, double* out);
+int sipf_batch_diagnostics(sipf_batch* b, int32_t run, sipf_diag* out);
+int sipf_batch_spectrum(sipf_batch* b, int32_t run, double* out);
+
+/* Wait for the batch's stream; report the first run's sticky kernel error
+ * flags as sipf_sync does. */
+int sipf_batch_sync(sipf_batch* b);
+
+/* Free every run and the batch.  NULL is a no-op. */
+void sipf_batch_destroy(sipf_batch* b);
+
 /* ---- stateless operators on caller-owned device memory ------------------
  * precision: 32 or 64 (element type float / double of every real array).
  * All are asynchronous on `stream` (cudaStream_t or NULL for the default).

@@ -13,7 +13,7 @@ from . import _abi
 from ._abi import (DEPOSIT_ATOMIC, DEPOSIT_DETERMINISTIC, PROP_EXP, PROP_IMPLICIT, SPLIT_HALF,
                    SPLIT_PLAIN, SipfError)
 
-__all__ = ["Simulation", "make_params", "SipfError", "SPLIT_HALF", "SPLIT_PLAIN",
+__all__ = ["Simulation", "Batch", "make_params", "SipfError", "SPLIT_HALF", "SPLIT_PLAIN",
            "DEPOSIT_ATOMIC", "DEPOSIT_DETERMINISTIC", "PROP_IMPLICIT", "PROP_EXP"]
 
 
@@ -100,6 +100,66 @@ class Simulation:
         if self.ctx:
             _abi.sipf_destroy(self.ctx)
             self.ctx = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent runs advanced together (one launch per kernel for all runs,
+    steps replayed from a CUDA graph).  Run r behaves like
+    Simulation(params[r], X0s[r])."""
+
+    def __init__(self, params, X0s, stream: int | None = None):
+        self.params = list(params)
+        self.P = [int(p.P) for p in self.params]
+        self.H = [int(p.H) for p in self.params]
+        self.handle = _abi.sipf_batch_init(self.params, X0s, stream)
+
+    def __len__(self):
+        return len(self.params)
+
+    def step(self, n: int = 1):
+        _abi.sipf_batch_step(self.handle, n)
+
+    def use_graph(self, enable: bool):
+        _abi.sipf_batch_use_graph(self.handle, int(enable))
+
+    @property
+    def n(self) -> int:
+        return _abi.sipf_batch_current_step(self.handle)
+
+    def sync(self):
+        _abi.sipf_batch_sync(self.handle)
+
+    def positions(self, run: int) -> np.ndarray:
+        out = np.empty((self.P[run], 3), dtype=np.float64)
+        _abi.sipf_batch_positions(self.handle, run, out)
+        return out
+
+    def spectrum(self, run: int) -> np.ndarray:
+        H = self.H[run]
+        out = np.empty((H, H, H // 2 + 1, 2), dtype=np.float64)
+        _abi.sipf_batch_spectrum(self.handle, run, out)
+        return out[..., 0] + 1j * out[..., 1]
+
+    def diagnostics(self, run: int) -> dict:
+        d = _abi.sipf_batch_diagnostics(self.handle, run)
+        return {name: getattr(d, name) for name, _ in d._fields_}
+
+    def close(self):
+        if self.handle:
+            _abi.sipf_batch_destroy(self.handle)
+            self.handle = 0
 
     def __enter__(self):
         return self

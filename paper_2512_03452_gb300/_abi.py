@@ -98,6 +98,17 @@ _SIGS = {
     "sipf_forward_ft_dev": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, ctypes.c_double, _P, _P, _P]),
     "sipf_inverse_ft_dev": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, _P, _P, _P]),
     "sipf_inverse_ft_noalloc_dev": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, _P, _P, _P]),
+    "sipf_batch_init": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(sipf_params), ctypes.POINTER(_D), _P,
+                                       ctypes.POINTER(_P)]),
+    "sipf_batch_step": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "sipf_batch_use_graph": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sipf_batch_current_step": (ctypes.c_int64, [_P]),
+    "sipf_batch_kernel_launches": (ctypes.c_int64, [_P]),
+    "sipf_batch_positions": (ctypes.c_int, [_P, ctypes.c_int32, _D]),
+    "sipf_batch_diagnostics": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(sipf_diag)]),
+    "sipf_batch_spectrum": (ctypes.c_int, [_P, ctypes.c_int32, _D]),
+    "sipf_batch_sync": (ctypes.c_int, [_P]),
+    "sipf_batch_destroy": (None, [_P]),
 }
 
 
@@ -264,3 +275,57 @@ def sipf_inverse_ft_noalloc_dev(precision, H, spec, grid, stream=0) -> None:
     allocation; `spec` is left unchanged; H <= 64)."""
     _check(load().sipf_inverse_ft_noalloc_dev(precision, H, _P(spec), _P(grid), _P(stream)),
            "sipf_inverse_ft_noalloc_dev")
+
+
+# ---- batched runs --------------------------------------------------------------
+def sipf_batch_init(params, X0s, stream: int | None = None) -> int:
+    """params: sequence of sipf_params; X0s: matching (P_r, 3) float64 arrays.
+    Returns the batch handle."""
+    import numpy as np
+    n = len(params)
+    if len(X0s) != n:
+        raise ValueError("one X0 per run")
+    arr = (sipf_params * n)(*params)
+    keep = [np.ascontiguousarray(X, dtype=np.float64) for X in X0s]
+    ptrs = (_D * n)(*[_dptr(X) for X in keep])
+    h = _P()
+    _check(load().sipf_batch_init(n, arr, ptrs, _P(stream or 0), ctypes.byref(h)), "sipf_batch_init")
+    return h.value
+
+
+def sipf_batch_step(b: int, nsteps: int) -> None:
+    _check(load().sipf_batch_step(_P(b), int(nsteps)), "sipf_batch_step")
+
+
+def sipf_batch_use_graph(b: int, enable: int) -> None:
+    _check(load().sipf_batch_use_graph(_P(b), int(enable)), "sipf_batch_use_graph")
+
+
+def sipf_batch_current_step(b: int) -> int:
+    return int(load().sipf_batch_current_step(_P(b)))
+
+
+def sipf_batch_kernel_launches(b: int) -> int:
+    return int(load().sipf_batch_kernel_launches(_P(b)))
+
+
+def sipf_batch_positions(b: int, run: int, out) -> None:
+    _check(load().sipf_batch_positions(_P(b), int(run), _dptr(out)), "sipf_batch_positions")
+
+
+def sipf_batch_diagnostics(b: int, run: int) -> sipf_diag:
+    d = sipf_diag()
+    _check(load().sipf_batch_diagnostics(_P(b), int(run), ctypes.byref(d)), "sipf_batch_diagnostics")
+    return d
+
+
+def sipf_batch_spectrum(b: int, run: int, out) -> None:
+    _check(load().sipf_batch_spectrum(_P(b), int(run), _dptr(out)), "sipf_batch_spectrum")
+
+
+def sipf_batch_sync(b: int) -> None:
+    _check(load().sipf_batch_sync(_P(b)), "sipf_batch_sync")
+
+
+def sipf_batch_destroy(b: int) -> None:
+    load().sipf_batch_destroy(_P(b))

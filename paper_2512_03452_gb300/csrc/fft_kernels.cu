@@ -443,20 +443,21 @@ template <typename T> __device__ __forceinline__ void load_tw_full(cpx<T>* tw) {
   for (int i = threadIdx.x; i < kNmax; i += blockDim.x) tw[i] = cpx<T>{(T)g_twiddle[i].x, (T)g_twiddle[i].y};
 }
 
+// Kernel bodies take their arrays and block coordinates explicitly so the same
+// code serves one run (the __global__ wrappers below) and a batch of runs
+// (the *_batch kernels, one run per block row).
+
 // Rows r2c: each warp takes row pairs (two real rows as one complex pencil).
 template <typename T, int E, typename Tin>
-__global__ void __launch_bounds__(256)
-kw_rows_r2c(Tin* __restrict__ in, double in_scale, int zero_input, cpx<T>* __restrict__ out, int rows,
-            double* mass_acc) {
+__device__ __forceinline__ void rows_r2c_body(Tin* __restrict__ in, double in_scale, int zero_input,
+                                              cpx<T>* __restrict__ out, int rows, double* mass_acc, int bx, int gx,
+                                              const cpx<T>* tw, cpx<T> (*zball)[32 * E]) {
   constexpr int N = 32 * E, NH = N / 2 + 1;
-  __shared__ cpx<T> tw[kNmax];
-  __shared__ cpx<T> zb[8][N];
-  load_tw_full(tw);
-  __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int nwarps = gridDim.x * 8;
+  cpx<T>* zb = zball[wib];
+  const int nwarps = gx * 8;
   double msum = 0.0;
-  for (int pr = blockIdx.x * 8 + wib; pr < rows / 2; pr += nwarps) {
+  for (int pr = bx * 8 + wib; pr < rows / 2; pr += nwarps) {
     const size_t ra = (size_t)(2 * pr) * N, rb = ra + N;
     cpx<T> v[E];
 #pragma unroll
@@ -484,12 +485,12 @@ kw_rows_r2c(Tin* __restrict__ in, double in_scale, int zero_input, cpx<T>* __res
     }
     warp_fft<T, E, -1>(v, lane, tw);
 #pragma unroll
-    for (int k1 = 0; k1 < E; ++k1) zb[wib][out_index(k1, E, lane)] = v[k1];
+    for (int k1 = 0; k1 < E; ++k1) zb[out_index(k1, E, lane)] = v[k1];
     __syncwarp();
     cpx<T>* oa = out + (size_t)(2 * pr) * NH;
     for (int k = lane; k < NH; k += 32) {
-      const cpx<T> zk = zb[wib][k];
-      const cpx<T> zm = cconj(zb[wib][(N - k) & (N - 1)]);
+      const cpx<T> zk = zb[k];
+      const cpx<T> zm = cconj(zb[(N - k) & (N - 1)]);
       const cpx<T> d = csub(zk, zm);
       oa[k] = cpx<T>{(zk.x + zm.x) * T(0.5), (zk.y + zm.y) * T(0.5)};
       oa[NH + k] = cpx<T>{d.y * T(0.5), -d.x * T(0.5)};
@@ -502,19 +503,24 @@ kw_rows_r2c(Tin* __restrict__ in, double in_scale, int zero_input, cpx<T>* __res
   }
 }
 
+template <typename T, int E, typename Tin>
+__global__ void __launch_bounds__(256)
+kw_rows_r2c(Tin* __restrict__ in, double in_scale, int zero_input, cpx<T>* __restrict__ out, int rows,
+            double* mass_acc) {
+  __shared__ cpx<T> tw[kNmax];
+  __shared__ cpx<T> zb[8][32 * E];
+  load_tw_full(tw);
+  __syncthreads();
+  rows_r2c_body<T, E, Tin>(in, in_scale, zero_input, out, rows, mass_acc, blockIdx.x, gridDim.x, tw, zb);
+}
+
 // c2c along the middle axis of [A][H][B]: a block stages an H x BC tile
 // (coalesced row segments), warps transform its columns from shared memory.
 template <typename T, int E, int DIR, int BC>
-__global__ void __launch_bounds__(256)
-kw_cols(cpx<T>* __restrict__ data, int B, size_t comp_stride, T scale) {
+__device__ __forceinline__ void cols_body(cpx<T>* __restrict__ base, int B, T scale, int b0, const cpx<T>* tw,
+                                          cpx<T>* buf) {
   constexpr int N = 32 * E, LD = BC + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* buf = tw + kNmax;
-  load_tw_full(tw);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  cpx<T>* base = data + blockIdx.z * comp_stride + (size_t)blockIdx.y * N * B;
-  const int b0 = blockIdx.x * BC;
   const int nb = min(BC, B - b0);
   for (int t = threadIdx.x; t < N * BC; t += blockDim.x) {
     const int j = t / BC, c = t - j * BC;
@@ -539,21 +545,26 @@ kw_cols(cpx<T>* __restrict__ data, int B, size_t comp_stride, T scale) {
   }
 }
 
+template <typename T, int E, int DIR, int BC>
+__global__ void __launch_bounds__(256)
+kw_cols(cpx<T>* __restrict__ data, int B, size_t comp_stride, T scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+  load_tw_full(tw);
+  cpx<T>* base = data + blockIdx.z * comp_stride + (size_t)blockIdx.y * (32 * E) * B;
+  cols_body<T, E, DIR, BC>(base, B, scale, blockIdx.x * BC, tw, tw + kNmax);
+}
+
 // x-axis pass fused with the spectral work (as k_spectral_x), warp FFTs.
 // Shared tile: [N][4 BC + 1]; slot 0 = beta, slots 1..3 the outputs.
 template <typename T, int E, int MODE, int BC>
-__global__ void __launch_bounds__(256)
-kw_spectral_x(const cpx<T>* __restrict__ T1, cpx<T>* __restrict__ alpha, cpx<T>* __restrict__ T2, SpecParams sp,
-              double* alpha0_shadow) {
+__device__ __forceinline__ void spectral_body(const cpx<T>* __restrict__ T1, cpx<T>* __restrict__ alpha,
+                                              cpx<T>* __restrict__ T2, const SpecParams& sp, double* alpha0_shadow,
+                                              int b0, const cpx<T>* tw, cpx<T>* buf) {
   constexpr int N = 32 * E, NHH = N / 2 + 1, LD = 4 * BC + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* buf = tw + kNmax;
-  load_tw_full(tw);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int B = N * NHH;
   const size_t S = (size_t)N * B;
-  const int b0 = blockIdx.x * BC;
   const int nb = min(BC, B - b0);
   constexpr bool needs_beta = (MODE == kModeStep || MODE == kModeDensity);
   if (needs_beta) {
@@ -650,26 +661,31 @@ kw_spectral_x(const cpx<T>* __restrict__ T1, cpx<T>* __restrict__ alpha, cpx<T>*
   }
 }
 
+template <typename T, int E, int MODE, int BC>
+__global__ void __launch_bounds__(256)
+kw_spectral_x(const cpx<T>* __restrict__ T1, cpx<T>* __restrict__ alpha, cpx<T>* __restrict__ T2, SpecParams sp,
+              double* alpha0_shadow) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+  load_tw_full(tw);
+  spectral_body<T, E, MODE, BC>(T1, alpha, T2, sp, alpha0_shadow, blockIdx.x * BC, tw, tw + kNmax);
+}
+
 // Rows c2r: each warp takes a row pair of every component, rebuilds the
 // full pencil Z = A + i B from the Hermitian halves, inverse-transforms it,
 // and writes (gx, gy, gz, 0) nodes (NCOMP == 3) or a plain grid (NCOMP == 1).
 template <typename T, int E, int NCOMP>
-__global__ void __launch_bounds__(256)
-kw_rows_c2r(const cpx<T>* __restrict__ in, size_t comp_stride, T* __restrict__ out, int rows, double* max_acc) {
+__device__ __forceinline__ void rows_c2r_body(const cpx<T>* __restrict__ in, size_t comp_stride, T* __restrict__ out,
+                                              int rows, double* max_acc, int bx, int gx, const cpx<T>* tw,
+                                              cpx<T>* zb_all, T* ob_all) {
   constexpr int N = 32 * E, NH = N / 2 + 1;
   constexpr int NOUT = NCOMP == 3 ? 4 : 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* zb_all = tw + kNmax;                                   // [8][N]
-  T* ob_all = reinterpret_cast<T*>(zb_all + 8 * N);             // [8][2][N][NOUT]
-  load_tw_full(tw);
-  __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   cpx<T>* zb = zb_all + wib * N;
   T* ob = ob_all + wib * 2 * N * NOUT;
-  const int nwarps = gridDim.x * 8;
+  const int nwarps = gx * 8;
   double mx = -INFINITY;
-  for (int pr = blockIdx.x * 8 + wib; pr < rows / 2; pr += nwarps) {
+  for (int pr = bx * 8 + wib; pr < rows / 2; pr += nwarps) {
     for (int d = 0; d < NCOMP; ++d) {
       const cpx<T>* ra = in + d * comp_stride + (size_t)(2 * pr) * NH;
       const cpx<T>* rb = ra + NH;
@@ -724,6 +740,75 @@ kw_rows_c2r(const cpx<T>* __restrict__ in, size_t comp_stride, T* __restrict__ o
       atomicMax(reinterpret_cast<long long*>(max_acc), b);
     }
   }
+}
+
+template <typename T, int E, int NCOMP>
+__global__ void __launch_bounds__(256)
+kw_rows_c2r(const cpx<T>* __restrict__ in, size_t comp_stride, T* __restrict__ out, int rows, double* max_acc) {
+  constexpr int N = 32 * E;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* zb_all = tw + kNmax;
+  T* ob_all = reinterpret_cast<T*>(zb_all + 8 * N);
+  load_tw_full(tw);
+  __syncthreads();
+  rows_c2r_body<T, E, NCOMP>(in, comp_stride, out, rows, max_acc, blockIdx.x, gridDim.x, tw, zb_all, ob_all);
+}
+
+// ---------------------------------------------------------------------------
+// Batched step kernels: runs of one grid size H, one run per block row (y or
+// z), arrays and parameters from a device table.
+// ---------------------------------------------------------------------------
+template <typename T, int E>
+__global__ void __launch_bounds__(256) kwb_rows_r2c(const FftRun<T>* __restrict__ runs) {
+  __shared__ cpx<T> tw[kNmax];
+  __shared__ cpx<T> zb[8][32 * E];
+  load_tw_full(tw);
+  __syncthreads();
+  const FftRun<T>& r = runs[blockIdx.y];
+  constexpr int N = 32 * E;
+  if (r.phi_fixed)
+    rows_r2c_body<T, E, unsigned long long>((unsigned long long*)r.phi, r.in_scale, 1, r.T1, N * N, nullptr,
+                                            blockIdx.x, gridDim.x, tw, zb);
+  else
+    rows_r2c_body<T, E, T>((T*)r.phi, 1.0, 1, r.T1, N * N, nullptr, blockIdx.x, gridDim.x, tw, zb);
+}
+
+// which = 0: forward y pass of T1; 1: inverse y pass of the three T2 components
+template <typename T, int E, int DIR, int BC>
+__global__ void __launch_bounds__(256) kwb_cols(const FftRun<T>* __restrict__ runs, int ncomp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+  load_tw_full(tw);
+  constexpr int N = 32 * E, NHH = N / 2 + 1;
+  const int run = blockIdx.z / ncomp, comp = blockIdx.z - run * ncomp;
+  const FftRun<T>& r = runs[run];
+  const size_t S = (size_t)N * N * NHH;
+  cpx<T>* data = DIR < 0 ? r.T1 : r.T2 + comp * S;
+  cols_body<T, E, DIR, BC>(data + (size_t)blockIdx.y * N * NHH, NHH, T(1), blockIdx.x * BC, tw, tw + kNmax);
+}
+
+template <typename T, int E, int BC>
+__global__ void __launch_bounds__(256) kwb_spectral_x(const FftRun<T>* __restrict__ runs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+  load_tw_full(tw);
+  const FftRun<T>& r = runs[blockIdx.y];
+  spectral_body<T, E, kModeStep, BC>(r.T1, r.alpha, r.T2, r.sp, r.shadow, blockIdx.x * BC, tw, tw + kNmax);
+}
+
+template <typename T, int E>
+__global__ void __launch_bounds__(256) kwb_rows_c2r(const FftRun<T>* __restrict__ runs) {
+  constexpr int N = 32 * E;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* zb_all = tw + kNmax;
+  T* ob_all = reinterpret_cast<T*>(zb_all + 8 * N);
+  load_tw_full(tw);
+  __syncthreads();
+  const FftRun<T>& r = runs[blockIdx.y];
+  const size_t S = (size_t)N * N * (N / 2 + 1);
+  rows_c2r_body<T, E, 3>(r.T2, S, r.grad, N * N, nullptr, blockIdx.x, gridDim.x, tw, zb_all, ob_all);
 }
 
 static int warp_blocks(int rows) {
@@ -805,6 +890,7 @@ static int rows_per_pair_block(int H, size_t elem, bool with_out4) {
 template <typename T>
 cudaError_t launch_rows_r2c(const void* in, int in_kind, double in_scale, bool zero_input, cpx<T>* out,
                             int H, int rows, double* mass_acc, cudaStream_t s) {
+  if (H == 32) return warp_rows_r2c<T, 1>(in, in_kind, in_scale, zero_input, out, rows, mass_acc, s);
   if (H == 64) return warp_rows_r2c<T, 2>(in, in_kind, in_scale, zero_input, out, rows, mass_acc, s);
   if (H == 128) return warp_rows_r2c<T, 4>(in, in_kind, in_scale, zero_input, out, rows, mass_acc, s);
   if (H == 256) return warp_rows_r2c<T, 8>(in, in_kind, in_scale, zero_input, out, rows, mass_acc, s);
@@ -837,6 +923,8 @@ static int col_chunk(int H, int slots) {
 template <typename T>
 cudaError_t launch_cols(cpx<T>* data, int H, int A, int B, int ncomp, size_t comp_stride, int dir, double scale,
                         cudaStream_t s) {
+  if (H == 32) return dir < 0 ? warp_cols<T, 1, -1>(data, A, B, ncomp, comp_stride, scale, s)
+                              : warp_cols<T, 1, +1>(data, A, B, ncomp, comp_stride, scale, s);
   if (H == 64) return dir < 0 ? warp_cols<T, 2, -1>(data, A, B, ncomp, comp_stride, scale, s)
                               : warp_cols<T, 2, +1>(data, A, B, ncomp, comp_stride, scale, s);
   if (H == 128) return dir < 0 ? warp_cols<T, 4, -1>(data, A, B, ncomp, comp_stride, scale, s)
@@ -893,6 +981,7 @@ static cudaError_t warp_spectral_mode(const cpx<T>* T1, cpx<T>* alpha, cpx<T>* T
 template <typename T>
 cudaError_t launch_spectral_x(const cpx<T>* T1, cpx<T>* alpha, cpx<T>* T2, int H, SpecParams sp, int mode,
                               double* alpha0_shadow, cudaStream_t s) {
+  if (H == 32) return warp_spectral_mode<T, 1>(T1, alpha, T2, sp, mode, alpha0_shadow, s);
   if (H == 64) return warp_spectral_mode<T, 2>(T1, alpha, T2, sp, mode, alpha0_shadow, s);
   if (H == 128) return warp_spectral_mode<T, 4>(T1, alpha, T2, sp, mode, alpha0_shadow, s);
   if (H == 256) return warp_spectral_mode<T, 8>(T1, alpha, T2, sp, mode, alpha0_shadow, s);
@@ -908,6 +997,8 @@ cudaError_t launch_spectral_x(const cpx<T>* T1, cpx<T>* alpha, cpx<T>* T2, int H
 template <typename T>
 cudaError_t launch_rows_c2r(const cpx<T>* in, int ncomp, size_t comp_stride, T* out, int H, int rows,
                             double* max_acc, cudaStream_t s) {
+  if (H == 32) return ncomp == 3 ? warp_rows_c2r<T, 1, 3>(in, comp_stride, out, rows, nullptr, s)
+                                 : warp_rows_c2r<T, 1, 1>(in, comp_stride, out, rows, max_acc, s);
   if (H == 64) return ncomp == 3 ? warp_rows_c2r<T, 2, 3>(in, comp_stride, out, rows, nullptr, s)
                                  : warp_rows_c2r<T, 2, 1>(in, comp_stride, out, rows, max_acc, s);
   if (H == 128) return ncomp == 3 ? warp_rows_c2r<T, 4, 3>(in, comp_stride, out, rows, nullptr, s)
@@ -932,13 +1023,59 @@ cudaError_t launch_rows_c2r(const cpx<T>* in, int ncomp, size_t comp_stride, T* 
   return cudaGetLastError();
 }
 
+template <typename T, int E>
+static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, cudaStream_t s) {
+  constexpr int N = 32 * E, NHH = N / 2 + 1;
+  constexpr int BC = 16;
+  constexpr int SBC = (sizeof(T) == 8 && E == 8) ? 4 : ((sizeof(T) == 8 || E == 8) ? 8 : 16);
+  cudaError_t e;
+  const int rblocks = max(1, min(152 * 8 / max(nruns, 1), (N * N / 2 + 7) / 8));
+  const size_t smc = (kNmax + (size_t)N * (BC + 1)) * sizeof(cpx<T>);
+  if (stages & kFieldForward) {
+    kwb_rows_r2c<T, E><<<dim3(rblocks, nruns), 256, 0, s>>>(runs);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = set_smem(kwb_cols<T, E, -1, BC>, smc)) != cudaSuccess) return e;
+    kwb_cols<T, E, -1, BC><<<dim3((NHH + BC - 1) / BC, N, nruns), 256, smc, s>>>(runs, 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (stages & kFieldSpectral) {
+    const size_t sms = (kNmax + (size_t)N * (4 * SBC + 1)) * sizeof(cpx<T>);
+    if ((e = set_smem(kwb_spectral_x<T, E, SBC>, sms)) != cudaSuccess) return e;
+    kwb_spectral_x<T, E, SBC><<<dim3((N * NHH + SBC - 1) / SBC, nruns), 256, sms, s>>>(runs);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (stages & kFieldInverse) {
+    if ((e = set_smem(kwb_cols<T, E, +1, BC>, smc)) != cudaSuccess) return e;
+    kwb_cols<T, E, +1, BC><<<dim3((NHH + BC - 1) / BC, N, nruns * 3), 256, smc, s>>>(runs, 3);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t smr = (kNmax + (size_t)8 * N) * sizeof(cpx<T>) + (size_t)8 * 2 * N * 4 * sizeof(T);
+    if ((e = set_smem(kwb_rows_c2r<T, E>, smr)) != cudaSuccess) return e;
+    kwb_rows_c2r<T, E><<<dim3(rblocks, nruns), 256, smr, s>>>(runs);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_field_batch(const FftRun<T>* runs, int nruns, int H, int stages, cudaStream_t s) {
+  if (nruns <= 0) return cudaSuccess;
+  switch (H) {
+    case 32: return field_batch_e<T, 1>(runs, nruns, stages, s);
+    case 64: return field_batch_e<T, 2>(runs, nruns, stages, s);
+    case 128: return field_batch_e<T, 4>(runs, nruns, stages, s);
+    case 256: return field_batch_e<T, 8>(runs, nruns, stages, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 #define SIPF_INST(T)                                                                                          \
   template cudaError_t launch_rows_r2c<T>(const void*, int, double, bool, cpx<T>*, int, int, double*,        \
                                           cudaStream_t);                                                    \
   template cudaError_t launch_cols<T>(cpx<T>*, int, int, int, int, size_t, int, double, cudaStream_t);       \
   template cudaError_t launch_spectral_x<T>(const cpx<T>*, cpx<T>*, cpx<T>*, int, SpecParams, int, double*,  \
                                             cudaStream_t);                                                  \
-  template cudaError_t launch_rows_c2r<T>(const cpx<T>*, int, size_t, T*, int, int, double*, cudaStream_t);
+  template cudaError_t launch_rows_c2r<T>(const cpx<T>*, int, size_t, T*, int, int, double*, cudaStream_t);     \
+  template cudaError_t launch_field_batch<T>(const FftRun<T>*, int, int, int, cudaStream_t);
 SIPF_INST(float)
 SIPF_INST(double)
 #undef SIPF_INST

@@ -113,6 +113,16 @@ __device__ __forceinline__ int tile_of(int cx, int cy, int cz, int shift, int nt
   return (((cx >> shift) * ntx) + (cy >> shift)) * ntx + (cz >> shift);
 }
 
+// Find the run of global work item c: largest r with prefix[r] <= c.
+__device__ __forceinline__ int find_run(const long long* prefix, int nruns, long long c) {
+  int lo = 0, hi = nruns - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 // ---------------------------------------------------------------------------
 // The binned particle kernel.  Template flags:
 //   MOVE:    advance X^{n-1} -> X^n (Algorithm 4, particle loop)
@@ -133,6 +143,176 @@ constexpr int kWinSlots = kWin * kWin * kWin;
 constexpr int kReplicas = 4;                  // window copies (lane mod 4)
 constexpr int kChunk = 4096;                  // particles per work item
 
+// One work item of k_binned (deposit and/or re-bin without a move).
+template <typename T, bool FIXED, bool MOVE, bool DEPOSIT, bool REBIN, bool WHOLE>
+__device__ __forceinline__ void binned_chunk(const BinArgs<T>& a, const ChunkDesc& cur,
+                                             typename WinType<T>::type* win) {
+  using A = typename WinType<T>::type;
+  const int H = a.g.H, mask = a.g.mask;
+  const int wslots = WHOLE ? H * H * H : kWinSlots;
+  const int lane = threadIdx.x & 31;
+  // lanes of a warp that land in the same cell add into different copies
+  A* const my_win = win + (lane & (kReplicas - 1)) * wslots;
+  const int bin = cur.bin, len = cur.len;
+  const long long start = cur.start;
+  // window origin (node coordinates of slot (0,0,0))
+  bool has_win = DEPOSIT && (WHOLE || bin < a.NT);
+  int ox = 0, oy = 0, oz = 0;
+  if (!WHOLE && bin < a.NT) {
+    const int tz = bin % a.ntx, ty = (bin / a.ntx) % a.ntx, tx = bin / (a.ntx * a.ntx);
+    ox = tx * kTileE - kMargin - 1;
+    oy = ty * kTileE - kMargin - 1;
+    oz = tz * kTileE - kMargin - 1;
+  }
+  // window scale 2^K
+  const int K = FIXED ? a.fix_k : WinType<T>::bits - ceil_log2(len + 1);
+  const T wwin = pow2<T>(K);
+  const int iters = (len + blockDim.x - 1) / blockDim.x;
+  // next particle's data is loaded one iteration ahead
+  T px = T(0), py = T(0), pz = T(0);
+  uint32_t pid = 0;
+  if ((int)threadIdx.x < len) {
+    px = a.sx[start + threadIdx.x];
+    py = a.sy[start + threadIdx.x];
+    pz = a.sz[start + threadIdx.x];
+    pid = a.sid[start + threadIdx.x];
+  }
+  for (int it = 0; it < iters; ++it) {
+    const int i = it * blockDim.x + threadIdx.x;
+    const bool valid = i < len;
+    T x = px, y = py, z = pz;
+    const uint32_t id = pid;
+    if (i + (int)blockDim.x < len) {
+      const long long s = start + i + blockDim.x;
+      px = a.sx[s];
+      py = a.sy[s];
+      pz = a.sz[s];
+      pid = a.sid[s];
+    }
+    if (MOVE && valid) {
+      T nz[6];
+      normals6(a.seed, (uint64_t)id, a.n, nz);
+      if (a.split == 0) {
+        // Z = X + W^- + chi tau I*(grad c)(X + W^-),  X^n = Z + W^+
+        const T yx = x + a.s_noise * nz[0], yy = y + a.s_noise * nz[1], yz = z + a.s_noise * nz[2];
+        const V3<T> gr = gather_grad(a.grad4, a.g2p, yx, yy, yz, a.g);
+        x = wrap_coord((yx + a.chitau * gr.x) + a.s_noise * nz[3], a.g);
+        y = wrap_coord((yy + a.chitau * gr.y) + a.s_noise * nz[4], a.g);
+        z = wrap_coord((yz + a.chitau * gr.z) + a.s_noise * nz[5], a.g);
+      } else {
+        // X^n = X + chi tau I*(grad c)(X) + W,  W ~ N(0, 2 mu tau I)
+        const V3<T> gr = gather_grad(a.grad4, a.g2p, x, y, z, a.g);
+        x = wrap_coord((x + a.chitau * gr.x) + a.s_noise * nz[0], a.g);
+        y = wrap_coord((y + a.chitau * gr.y) + a.s_noise * nz[1], a.g);
+        z = wrap_coord((z + a.chitau * gr.z) + a.s_noise * nz[2], a.g);
+      }
+      if (!(t_finite(x) && t_finite(y) && t_finite(z))) atomicOr(a.err, 1);
+    }
+    int cx = 0, cy = 0, cz = 0;
+    T lx = T(0), ly = T(0), lz = T(0);
+    cell_lambda(x, a.g, cx, lx);
+    cell_lambda(y, a.g, cy, ly);
+    cell_lambda(z, a.g, cz, lz);
+    // reserve the destination slot first: the atomic's round trip overlaps the deposit
+    int t = 0, rank = 0, leader = 0, b0 = 0;
+    if (REBIN) {
+      t = tile_of(cx & mask, cy & mask, cz & mask, a.tile_shift, a.ntx);
+      const unsigned key = valid ? (unsigned)t : 0xFFFFFFFFu;
+      const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+      leader = __ffs(peers) - 1;
+      rank = __popc(peers & ((1u << lane) - 1u));
+      if (valid && lane == leader) b0 = atomicAdd(a.dst_cursor + t, __popc(peers));
+    }
+    if (DEPOSIT && valid) {
+      bool fits = has_win;
+      int sx = 0, sy = 0, sz = 0;
+      if (!WHOLE && fits) {
+        sx = (cx - 1 - ox) & mask;
+        sy = (cy - 1 - oy) & mask;
+        sz = (cz - 1 - oz) & mask;
+        fits = sx <= kWin - 4 && sy <= kWin - 4 && sz <= kWin - 4;
+      }
+      if (fits) {
+        int ix[4], iy[4], iz[4];
+        if (WHOLE) {
+          axis_layers_global(cx, mask, H * H, ix);
+          axis_layers_global(cy, mask, H, iy);
+          axis_layers_global(cz, mask, 1, iz);
+          stencil_visit<T>(a.p2g, ix, iy, iz, lx, ly, lz, wwin,
+                           [&](int idx, T f) { win_add(my_win + idx, WinType<T>::round(f)); });
+        } else {
+          // base slot plus compile-time offsets of the 4x4x4 box
+          A* wb = my_win + ((sx * kWin) + sy) * kWin + sz;
+#pragma unroll
+          for (int o = 0; o < 4; ++o) {
+            ix[o] = o * (kWin * kWin);
+            iy[o] = o * kWin;
+            iz[o] = o;
+          }
+          stencil_visit<T>(a.p2g, ix, iy, iz, lx, ly, lz, wwin,
+                           [&](int idx, T f) { win_add(wb + idx, WinType<T>::round(f)); });
+        }
+      } else if (FIXED) {
+        unsigned long long* grid = static_cast<unsigned long long*>(a.phi);
+        stencil_visit_global<T>(a.p2g, cx, cy, cz, lx, ly, lz, wwin, a.g, [&](int idx, T f) {
+          atomicAdd(grid + idx, (unsigned long long)(long long)WinType<T>::round(f));
+        });
+      } else {
+        T* grid = static_cast<T*>(a.phi);
+        stencil_visit_global<T>(a.p2g, cx, cy, cz, lx, ly, lz, a.wmass, a.g,
+                                [&](int idx, T f) { atomicAdd(grid + idx, f); });
+      }
+    }
+    if (REBIN) {
+      b0 = __shfl_sync(0xFFFFFFFFu, b0, leader);
+      if (valid) {
+        long long slot;
+        const int r = b0 + rank;
+        if (r < a.dst_cap[t]) {
+          slot = a.dst_base[t] + r;
+        } else {
+          const int o = atomicAdd(a.dst_cursor + a.NT, 1);
+          slot = o < a.dst_cap[a.NT] ? a.dst_base[a.NT] + o : -1;
+        }
+        if (slot >= 0) {
+          a.dx[slot] = x;
+          a.dy[slot] = y;
+          a.dz[slot] = z;
+          a.did[slot] = id;
+        } else {
+          atomicOr(a.err, 2);   // overflow bin full: the particle is lost
+        }
+      }
+    }
+  }
+  if (DEPOSIT && has_win) {
+    __syncthreads();
+    // add the window to the grid: consecutive threads walk consecutive slots
+    // along the fastest axis, so the reductions of a warp hit contiguous nodes
+    const T unit = a.wmass / wwin;   // M0/P * 2^-K
+    for (int sidx = threadIdx.x; sidx < wslots; sidx += blockDim.x) {
+      A v = win[sidx];
+      win[sidx] = A(0);
+#pragma unroll
+      for (int r = 1; r < kReplicas; ++r) {
+        v += win[r * wslots + sidx];
+        win[r * wslots + sidx] = A(0);
+      }
+      if (v != A(0)) {
+        int gi;
+        if (WHOLE) {
+          gi = sidx;
+        } else {
+          const int c = sidx % kWin, b = (sidx / kWin) % kWin, aa = sidx / (kWin * kWin);
+          gi = (((ox + aa) & mask) * H + ((oy + b) & mask)) * H + ((oz + c) & mask);
+        }
+        if (FIXED) atomicAdd(static_cast<unsigned long long*>(a.phi) + gi, (unsigned long long)(long long)v);
+        else atomicAdd(static_cast<T*>(a.phi) + gi, (T)v * unit);
+      }
+    }
+  }
+}
+
 template <typename T, bool FIXED, bool MOVE, bool DEPOSIT, bool REBIN, bool WHOLE>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
 k_binned(BinArgs<T> a) {
@@ -141,11 +321,7 @@ k_binned(BinArgs<T> a) {
   A* win = reinterpret_cast<A*>(smem_raw);
   __shared__ ChunkDesc s_desc[2];
   const long long nchunks = a.chunk_start[a.NT + 1];
-  const int H = a.g.H, mask = a.g.mask;
-  const int wslots = WHOLE ? H * H * H : kWinSlots;
-  const int lane = threadIdx.x & 31;
-  // lanes of a warp that land in the same cell add into different copies
-  A* const my_win = win + (lane & (kReplicas - 1)) * wslots;
+  const int wslots = WHOLE ? a.g.H * a.g.H * a.g.H : kWinSlots;
   if (DEPOSIT)
     for (int i = threadIdx.x; i < kReplicas * wslots; i += blockDim.x) win[i] = A(0);
   // work items are taken from a global counter; the next one is fetched
@@ -163,165 +339,53 @@ k_binned(BinArgs<T> a) {
       const long long c = (long long)atomicAdd(a.work, 1ULL);
       if (c < nchunks) nxt = a.chunks[c];
     }
-    const int bin = cur.bin, len = cur.len;
-    const long long start = cur.start;
-    // window origin (node coordinates of slot (0,0,0))
-    bool has_win = DEPOSIT && (WHOLE || bin < a.NT);
-    int ox = 0, oy = 0, oz = 0;
-    if (!WHOLE && bin < a.NT) {
-      const int tz = bin % a.ntx, ty = (bin / a.ntx) % a.ntx, tx = bin / (a.ntx * a.ntx);
-      ox = tx * kTileE - kMargin - 1;
-      oy = ty * kTileE - kMargin - 1;
-      oz = tz * kTileE - kMargin - 1;
-    }
-    // window scale 2^K
-    const int K = FIXED ? a.fix_k : WinType<T>::bits - ceil_log2(len + 1);
-    const T wwin = pow2<T>(K);
-    const int iters = (len + blockDim.x - 1) / blockDim.x;
-    // next particle's data is loaded one iteration ahead
-    T px = T(0), py = T(0), pz = T(0);
-    uint32_t pid = 0;
-    if ((int)threadIdx.x < len) {
-      px = a.sx[start + threadIdx.x];
-      py = a.sy[start + threadIdx.x];
-      pz = a.sz[start + threadIdx.x];
-      pid = a.sid[start + threadIdx.x];
-    }
-    for (int it = 0; it < iters; ++it) {
-      const int i = it * blockDim.x + threadIdx.x;
-      const bool valid = i < len;
-      T x = px, y = py, z = pz;
-      const uint32_t id = pid;
-      if (i + (int)blockDim.x < len) {
-        const long long s = start + i + blockDim.x;
-        px = a.sx[s];
-        py = a.sy[s];
-        pz = a.sz[s];
-        pid = a.sid[s];
-      }
-      if (MOVE && valid) {
-        T nz[6];
-        normals6(a.seed, (uint64_t)id, a.n, nz);
-        if (a.split == 0) {
-          // Z = X + W^- + chi tau I*(grad c)(X + W^-),  X^n = Z + W^+
-          const T yx = x + a.s_noise * nz[0], yy = y + a.s_noise * nz[1], yz = z + a.s_noise * nz[2];
-          const V3<T> gr = gather_grad(a.grad4, a.g2p, yx, yy, yz, a.g);
-          x = wrap_coord((yx + a.chitau * gr.x) + a.s_noise * nz[3], a.g);
-          y = wrap_coord((yy + a.chitau * gr.y) + a.s_noise * nz[4], a.g);
-          z = wrap_coord((yz + a.chitau * gr.z) + a.s_noise * nz[5], a.g);
-        } else {
-          // X^n = X + chi tau I*(grad c)(X) + W,  W ~ N(0, 2 mu tau I)
-          const V3<T> gr = gather_grad(a.grad4, a.g2p, x, y, z, a.g);
-          x = wrap_coord((x + a.chitau * gr.x) + a.s_noise * nz[0], a.g);
-          y = wrap_coord((y + a.chitau * gr.y) + a.s_noise * nz[1], a.g);
-          z = wrap_coord((z + a.chitau * gr.z) + a.s_noise * nz[2], a.g);
-        }
-        if (!(t_finite(x) && t_finite(y) && t_finite(z))) atomicOr(a.err, 1);
-      }
-      int cx = 0, cy = 0, cz = 0;
-      T lx = T(0), ly = T(0), lz = T(0);
-      cell_lambda(x, a.g, cx, lx);
-      cell_lambda(y, a.g, cy, ly);
-      cell_lambda(z, a.g, cz, lz);
-      // reserve the destination slot first: the atomic's round trip overlaps the deposit
-      int t = 0, rank = 0, leader = 0, b0 = 0;
-      if (REBIN) {
-        t = tile_of(cx & mask, cy & mask, cz & mask, a.tile_shift, a.ntx);
-        const unsigned key = valid ? (unsigned)t : 0xFFFFFFFFu;
-        const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
-        leader = __ffs(peers) - 1;
-        rank = __popc(peers & ((1u << lane) - 1u));
-        if (valid && lane == leader) b0 = atomicAdd(a.dst_cursor + t, __popc(peers));
-      }
-      if (DEPOSIT && valid) {
-        bool fits = has_win;
-        int sx = 0, sy = 0, sz = 0;
-        if (!WHOLE && fits) {
-          sx = (cx - 1 - ox) & mask;
-          sy = (cy - 1 - oy) & mask;
-          sz = (cz - 1 - oz) & mask;
-          fits = sx <= kWin - 4 && sy <= kWin - 4 && sz <= kWin - 4;
-        }
-        if (fits) {
-          int ix[4], iy[4], iz[4];
-          if (WHOLE) {
-            axis_layers_global(cx, mask, H * H, ix);
-            axis_layers_global(cy, mask, H, iy);
-            axis_layers_global(cz, mask, 1, iz);
-            stencil_visit<T>(a.p2g, ix, iy, iz, lx, ly, lz, wwin,
-                             [&](int idx, T f) { win_add(my_win + idx, WinType<T>::round(f)); });
-          } else {
-            // base slot plus compile-time offsets of the 4x4x4 box
-            A* wb = my_win + ((sx * kWin) + sy) * kWin + sz;
-#pragma unroll
-            for (int o = 0; o < 4; ++o) {
-              ix[o] = o * (kWin * kWin);
-              iy[o] = o * kWin;
-              iz[o] = o;
-            }
-            stencil_visit<T>(a.p2g, ix, iy, iz, lx, ly, lz, wwin,
-                             [&](int idx, T f) { win_add(wb + idx, WinType<T>::round(f)); });
-          }
-        } else if (FIXED) {
-          unsigned long long* grid = static_cast<unsigned long long*>(a.phi);
-          stencil_visit_global<T>(a.p2g, cx, cy, cz, lx, ly, lz, wwin, a.g, [&](int idx, T f) {
-            atomicAdd(grid + idx, (unsigned long long)(long long)WinType<T>::round(f));
-          });
-        } else {
-          T* grid = static_cast<T*>(a.phi);
-          stencil_visit_global<T>(a.p2g, cx, cy, cz, lx, ly, lz, a.wmass, a.g,
-                                  [&](int idx, T f) { atomicAdd(grid + idx, f); });
-        }
-      }
-      if (REBIN) {
-        b0 = __shfl_sync(0xFFFFFFFFu, b0, leader);
-        if (valid) {
-          long long slot;
-          const int r = b0 + rank;
-          if (r < a.dst_cap[t]) {
-            slot = a.dst_base[t] + r;
-          } else {
-            const int o = atomicAdd(a.dst_cursor + a.NT, 1);
-            slot = o < a.dst_cap[a.NT] ? a.dst_base[a.NT] + o : -1;
-          }
-          if (slot >= 0) {
-            a.dx[slot] = x;
-            a.dy[slot] = y;
-            a.dz[slot] = z;
-            a.did[slot] = id;
-          } else {
-            atomicOr(a.err, 2);   // overflow bin full: the particle is lost
-          }
-        }
-      }
-    }
-    if (DEPOSIT && has_win) {
-      __syncthreads();
-      // add the window to the grid: consecutive threads walk consecutive slots
-      // along the fastest axis, so the reductions of a warp hit contiguous nodes
-      const T unit = a.wmass / wwin;   // M0/P * 2^-K
-      for (int sidx = threadIdx.x; sidx < wslots; sidx += blockDim.x) {
-        A v = win[sidx];
-        win[sidx] = A(0);
-#pragma unroll
-        for (int r = 1; r < kReplicas; ++r) {
-          v += win[r * wslots + sidx];
-          win[r * wslots + sidx] = A(0);
-        }
-        if (v != A(0)) {
-          int gi;
-          if (WHOLE) {
-            gi = sidx;
-          } else {
-            const int c = sidx % kWin, b = (sidx / kWin) % kWin, aa = sidx / (kWin * kWin);
-            gi = (((ox + aa) & mask) * H + ((oy + b) & mask)) * H + ((oz + c) & mask);
-          }
-          if (FIXED) atomicAdd(static_cast<unsigned long long*>(a.phi) + gi, (unsigned long long)(long long)v);
-          else atomicAdd(static_cast<T*>(a.phi) + gi, (T)v * unit);
-        }
-      }
-    }
+    binned_chunk<T, FIXED, MOVE, DEPOSIT, REBIN, WHOLE>(a, cur, win);
     if (threadIdx.x == 0) s_desc[buf ^ 1] = nxt;
+    __syncthreads();
+  }
+}
+
+// Batched deposit over the bins of all runs (tile windows, H >= 32).
+template <typename T, bool FIXED>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
+k_deposit_batch(const BinArgs<T>* __restrict__ table, const long long* __restrict__ prefix, int nruns,
+                unsigned long long* work) {
+  using A = typename WinType<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  A* win = reinterpret_cast<A*>(smem_raw);
+  __shared__ ChunkDesc s_desc[2];
+  __shared__ int s_run[2];
+  const long long total = prefix[nruns];
+  for (int i = threadIdx.x; i < kReplicas * kWinSlots; i += blockDim.x) win[i] = A(0);
+  if (threadIdx.x == 0) {
+    const long long c = (long long)atomicAdd(work, 1ULL);
+    if (c < total) {
+      const int r = find_run(prefix, nruns, c);
+      s_run[0] = r;
+      s_desc[0] = table[r].chunks[c - prefix[r]];
+    } else {
+      s_desc[0] = ChunkDesc{0, 0, 0};
+    }
+  }
+  __syncthreads();
+  for (int buf = 0;; buf ^= 1) {
+    const ChunkDesc cur = s_desc[buf];
+    if (cur.len == 0) break;
+    const int run = s_run[buf];
+    ChunkDesc nxt{0, 0, 0};
+    int nrun = 0;
+    if (threadIdx.x == 0) {
+      const long long c = (long long)atomicAdd(work, 1ULL);
+      if (c < total) {
+        nrun = find_run(prefix, nruns, c);
+        nxt = table[nrun].chunks[c - prefix[nrun]];
+      }
+    }
+    binned_chunk<T, FIXED, false, true, false, false>(table[run], cur, win);
+    if (threadIdx.x == 0) {
+      s_desc[buf ^ 1] = nxt;
+      s_run[buf ^ 1] = nrun;
+    }
     __syncthreads();
   }
 }
@@ -343,75 +407,66 @@ constexpr int kNbr = 125;   // 5^3 destination tiles around the source tile
 template <typename T> struct MoveRound { static constexpr int n = sizeof(T) == 4 ? 2048 : 1024; };
 
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
-k_move(BinArgs<T> a) {
+struct MoveSmem {
+  static constexpr int R = MoveRound<T>::n;
+  ChunkDesc desc[2];
+  int run[2];
+  __align__(16) T x[R];
+  __align__(16) T y[R];
+  __align__(16) T z[R];
+  __align__(16) uint32_t id[R];
+  int meta[R];        // neighbour slot (0..124) | rank << 7, or -1 - tile for far moves
+  int cnt[kNbr], base[kNbr], tile[kNbr];
+  __align__(8) uint64_t bar;
+  int abort;
+};
+
+// One work item of the move + re-bin pass (see above).  n: step index of the
+// move (noise counter).  MOVE = false only re-bins (capacity rebuilds).
+template <typename T, bool MOVE>
+__device__ __forceinline__ void move_chunk(const BinArgs<T>& a, const ChunkDesc& cur, uint32_t n, MoveSmem<T>& sm,
+                                           uint32_t& phase) {
   constexpr int R = MoveRound<T>::n;
   constexpr int PER = R / 256;
-  __shared__ ChunkDesc s_desc[2];
-  __shared__ __align__(16) T s_x[R];
-  __shared__ __align__(16) T s_y[R];
-  __shared__ __align__(16) T s_z[R];
-  __shared__ __align__(16) uint32_t s_id[R];
-  __shared__ int s_meta[R];        // neighbour slot (0..124) | rank << 7, or -1 - tile for far moves
-  __shared__ int s_cnt[kNbr], s_base[kNbr], s_tile[kNbr];
-  __shared__ __align__(8) uint64_t s_bar;
-  __shared__ int s_abort;
-  const long long nchunks = a.chunk_start[a.NT + 1];
   const int mask = a.g.mask, ntx = a.ntx, tmask = a.ntx - 1;   // tiles per axis: a power of two
-  if (threadIdx.x == 0) {
-    mbar_init(&s_bar, 1);
-    s_abort = 0;
-    const long long c = (long long)atomicAdd(a.work, 1ULL);
-    s_desc[0] = c < nchunks ? a.chunks[c] : ChunkDesc{0, 0, 0};
+  const bool in_tile = cur.bin < a.NT;
+  const int stz = cur.bin & tmask, sty = (cur.bin / ntx) & tmask, stx = cur.bin / (ntx * ntx);
+  // destination tile of each neighbour slot (periodic)
+  for (int k = threadIdx.x; k < kNbr; k += blockDim.x) {
+    const int dx = k / 25 - 2, dy = (k / 5) % 5 - 2, dz = k % 5 - 2;
+    sm.tile[k] = ((((stx + dx) & tmask) * ntx) + ((sty + dy) & tmask)) * ntx + ((stz + dz) & tmask);
   }
-  __syncthreads();
-  uint32_t phase = 0;
-  for (int buf = 0;; buf ^= 1) {
-    const ChunkDesc cur = s_desc[buf];
-    if (cur.len == 0 || s_abort) break;
-    ChunkDesc nxt{0, 0, 0};
+  for (int r0 = 0; r0 < cur.len; r0 += R) {
+    const int cnt = min(R, cur.len - r0);
+    // stage the round's particles with TMA (bins start on 4-slot boundaries
+    // and have capacity rounded up to 4, so the rounded copy stays inside)
     if (threadIdx.x == 0) {
-      const long long c = (long long)atomicAdd(a.work, 1ULL);
-      if (c < nchunks) nxt = a.chunks[c];
+      const long long s0 = cur.start + r0;
+      const uint32_t n4 = (uint32_t)((cnt + 3) & ~3);
+      fence_proxy_async_smem();
+      mbar_expect_tx(&sm.bar, n4 * (3 * (uint32_t)sizeof(T) + 4));
+      tma_load_1d(sm.x, a.sx + s0, n4 * sizeof(T), &sm.bar);
+      tma_load_1d(sm.y, a.sy + s0, n4 * sizeof(T), &sm.bar);
+      tma_load_1d(sm.z, a.sz + s0, n4 * sizeof(T), &sm.bar);
+      tma_load_1d(sm.id, a.sid + s0, n4 * 4, &sm.bar);
     }
-    const bool in_tile = cur.bin < a.NT;
-    const int stz = cur.bin & tmask, sty = (cur.bin / ntx) & tmask, stx = cur.bin / (ntx * ntx);
-    // destination tile of each neighbour slot (periodic)
-    for (int k = threadIdx.x; k < kNbr; k += blockDim.x) {
-      const int dx = k / 25 - 2, dy = (k / 5) % 5 - 2, dz = k % 5 - 2;
-      s_tile[k] = ((((stx + dx) & tmask) * ntx) + ((sty + dy) & tmask)) * ntx + ((stz + dz) & tmask);
+    for (int k = threadIdx.x; k < kNbr; k += blockDim.x) sm.cnt[k] = 0;
+    if (!mbar_wait(&sm.bar, phase, 1u << 26)) {
+      atomicOr(a.err, 4);   // staging copy did not complete
+      sm.abort = 1;
     }
-    for (int r0 = 0; r0 < cur.len; r0 += R) {
-      const int n = min(R, cur.len - r0);
-      // stage the round's particles with TMA (bins start on 4-slot boundaries
-      // and have capacity rounded up to 4, so the rounded copy stays inside)
-      if (threadIdx.x == 0) {
-        const long long s0 = cur.start + r0;
-        const uint32_t n4 = (uint32_t)((n + 3) & ~3);
-        fence_proxy_async_smem();
-        mbar_expect_tx(&s_bar, n4 * (3 * (uint32_t)sizeof(T) + 4));
-        tma_load_1d(s_x, a.sx + s0, n4 * sizeof(T), &s_bar);
-        tma_load_1d(s_y, a.sy + s0, n4 * sizeof(T), &s_bar);
-        tma_load_1d(s_z, a.sz + s0, n4 * sizeof(T), &s_bar);
-        tma_load_1d(s_id, a.sid + s0, n4 * 4, &s_bar);
-      }
-      for (int k = threadIdx.x; k < kNbr; k += blockDim.x) s_cnt[k] = 0;
-      if (!mbar_wait(&s_bar, phase, 1u << 26)) {
-        atomicOr(a.err, 4);   // staging copy did not complete
-        s_abort = 1;
-      }
-      phase ^= 1;
-      __syncthreads();
-      if (s_abort) break;
-      // 1. move and stage
+    phase ^= 1;
+    __syncthreads();
+    if (sm.abort) return;
+    // 1. move and stage
 #pragma unroll 1
-      for (int k = 0; k < PER; ++k) {
-        const int i = k * 256 + threadIdx.x;
-        if (i >= n) break;
-        T x = s_x[i], y = s_y[i], z = s_z[i];
-        const uint32_t id = s_id[i];
+    for (int k = 0; k < PER; ++k) {
+      const int i = k * 256 + threadIdx.x;
+      if (i >= cnt) break;
+      T x = sm.x[i], y = sm.y[i], z = sm.z[i];
+      if (MOVE) {
         T nz[6];
-        normals6(a.seed, (uint64_t)id, a.n, nz);
+        normals6(a.seed, (uint64_t)sm.id[i], n, nz);
         if (a.split == 0) {
           // Z = X + W^- + chi tau I*(grad c)(X + W^-),  X^n = Z + W^+
           const T yx = x + a.s_noise * nz[0], yy = y + a.s_noise * nz[1], yz = z + a.s_noise * nz[2];
@@ -427,67 +482,138 @@ k_move(BinArgs<T> a) {
           z = wrap_coord((z + a.chitau * gr.z) + a.s_noise * nz[2], a.g);
         }
         if (!(t_finite(x) && t_finite(y) && t_finite(z))) atomicOr(a.err, 1);
-        int cx, cy, cz;
-        T l;
-        cell_lambda(x, a.g, cx, l);
-        cell_lambda(y, a.g, cy, l);
-        cell_lambda(z, a.g, cz, l);
-        const int ux = (cx & mask) >> a.tile_shift, uy = (cy & mask) >> a.tile_shift, uz = (cz & mask) >> a.tile_shift;
-        // destination relative to the source tile, minimum image in tile units
-        const int half = ntx >> 1;
-        const int dx = ((ux - stx + half) & tmask) - half;
-        const int dy = ((uy - sty + half) & tmask) - half;
-        const int dz = ((uz - stz + half) & tmask) - half;
-        int meta;
-        if (in_tile && dx >= -2 && dx <= 2 && dy >= -2 && dy <= 2 && dz >= -2 && dz <= 2) {
-          const int nb = ((dx + 2) * 5 + (dy + 2)) * 5 + (dz + 2);
-          meta = nb | (atomicAdd(s_cnt + nb, 1) << 7);
-        } else {
-          meta = -1 - ((ux * ntx + uy) * ntx + uz);
-        }
-        s_x[i] = x;
-        s_y[i] = y;
-        s_z[i] = z;
-        s_meta[i] = meta;
       }
-      __syncthreads();
-      // 2. one reservation per destination tile
-      for (int k = threadIdx.x; k < kNbr; k += blockDim.x) {
-        const int c = s_cnt[k];
-        if (c) s_base[k] = atomicAdd(a.dst_cursor + s_tile[k], c);
+      int cx, cy, cz;
+      T l;
+      cell_lambda(x, a.g, cx, l);
+      cell_lambda(y, a.g, cy, l);
+      cell_lambda(z, a.g, cz, l);
+      const int ux = (cx & mask) >> a.tile_shift, uy = (cy & mask) >> a.tile_shift, uz = (cz & mask) >> a.tile_shift;
+      // destination relative to the source tile, minimum image in tile units
+      const int half = ntx >> 1;
+      const int dx = ((ux - stx + half) & tmask) - half;
+      const int dy = ((uy - sty + half) & tmask) - half;
+      const int dz = ((uz - stz + half) & tmask) - half;
+      int meta;
+      if (in_tile && dx >= -2 && dx <= 2 && dy >= -2 && dy <= 2 && dz >= -2 && dz <= 2) {
+        const int nb = ((dx + 2) * 5 + (dy + 2)) * 5 + (dz + 2);
+        meta = nb | (atomicAdd(sm.cnt + nb, 1) << 7);
+      } else {
+        meta = -1 - ((ux * ntx + uy) * ntx + uz);
       }
-      __syncthreads();
-      // 3. write out
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int meta = s_meta[i];
-        int t, r;
-        if (meta >= 0) {
-          const int k = meta & 127;
-          t = s_tile[k];
-          r = s_base[k] + (meta >> 7);
-        } else {
-          t = -1 - meta;
-          r = atomicAdd(a.dst_cursor + t, 1);
-        }
-        long long slot;
-        if (r < a.dst_cap[t]) {
-          slot = a.dst_base[t] + r;
-        } else {
-          const int o = atomicAdd(a.dst_cursor + a.NT, 1);
-          slot = o < a.dst_cap[a.NT] ? a.dst_base[a.NT] + o : -1;
-        }
-        if (slot >= 0) {
-          a.dx[slot] = s_x[i];
-          a.dy[slot] = s_y[i];
-          a.dz[slot] = s_z[i];
-          a.did[slot] = s_id[i];
-        } else {
-          atomicOr(a.err, 2);   // overflow bin full: the particle is lost
-        }
-      }
-      __syncthreads();
+      sm.x[i] = x;
+      sm.y[i] = y;
+      sm.z[i] = z;
+      sm.meta[i] = meta;
     }
-    if (threadIdx.x == 0) s_desc[buf ^ 1] = nxt;
+    __syncthreads();
+    // 2. one reservation per destination tile
+    for (int k = threadIdx.x; k < kNbr; k += blockDim.x) {
+      const int c = sm.cnt[k];
+      if (c) sm.base[k] = atomicAdd(a.dst_cursor + sm.tile[k], c);
+    }
+    __syncthreads();
+    // 3. write out
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      const int meta = sm.meta[i];
+      int t, r;
+      if (meta >= 0) {
+        const int k = meta & 127;
+        t = sm.tile[k];
+        r = sm.base[k] + (meta >> 7);
+      } else {
+        t = -1 - meta;
+        r = atomicAdd(a.dst_cursor + t, 1);
+      }
+      long long slot;
+      if (r < a.dst_cap[t]) {
+        slot = a.dst_base[t] + r;
+      } else {
+        const int o = atomicAdd(a.dst_cursor + a.NT, 1);
+        slot = o < a.dst_cap[a.NT] ? a.dst_base[a.NT] + o : -1;
+      }
+      if (slot >= 0) {
+        a.dx[slot] = sm.x[i];
+        a.dy[slot] = sm.y[i];
+        a.dz[slot] = sm.z[i];
+        a.did[slot] = sm.id[i];
+      } else {
+        atomicOr(a.err, 2);   // overflow bin full: the particle is lost
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+k_move(BinArgs<T> a) {
+  __shared__ MoveSmem<T> sm;
+  const long long nchunks = a.chunk_start[a.NT + 1];
+  if (threadIdx.x == 0) {
+    mbar_init(&sm.bar, 1);
+    sm.abort = 0;
+    const long long c = (long long)atomicAdd(a.work, 1ULL);
+    sm.desc[0] = c < nchunks ? a.chunks[c] : ChunkDesc{0, 0, 0};
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  for (int buf = 0;; buf ^= 1) {
+    const ChunkDesc cur = sm.desc[buf];
+    if (cur.len == 0 || sm.abort) break;
+    ChunkDesc nxt{0, 0, 0};
+    if (threadIdx.x == 0) {
+      const long long c = (long long)atomicAdd(a.work, 1ULL);
+      if (c < nchunks) nxt = a.chunks[c];
+    }
+    move_chunk<T, true>(a, cur, a.n, sm, phase);
+    if (threadIdx.x == 0) sm.desc[buf ^ 1] = nxt;
+    __syncthreads();
+  }
+}
+
+
+// Batched move (MOVE) or re-bin (!MOVE): work items of all runs from one
+// counter; run r's arguments at table[r]; the step index from device memory.
+template <typename T, bool MOVE>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+k_move_batch(const BinArgs<T>* __restrict__ table, const long long* __restrict__ prefix, int nruns,
+             unsigned long long* work, const uint32_t* step) {
+  __shared__ MoveSmem<T> sm;
+  const long long total = prefix[nruns];
+  const uint32_t n = *step + 1;
+  if (threadIdx.x == 0) {
+    mbar_init(&sm.bar, 1);
+    sm.abort = 0;
+    const long long c = (long long)atomicAdd(work, 1ULL);
+    if (c < total) {
+      const int r = find_run(prefix, nruns, c);
+      sm.run[0] = r;
+      sm.desc[0] = table[r].chunks[c - prefix[r]];
+    } else {
+      sm.desc[0] = ChunkDesc{0, 0, 0};
+    }
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  for (int buf = 0;; buf ^= 1) {
+    const ChunkDesc cur = sm.desc[buf];
+    if (cur.len == 0 || sm.abort) break;
+    const int run = sm.run[buf];
+    ChunkDesc nxt{0, 0, 0};
+    int nrun = 0;
+    if (threadIdx.x == 0) {
+      const long long c = (long long)atomicAdd(work, 1ULL);
+      if (c < total) {
+        nrun = find_run(prefix, nruns, c);
+        nxt = table[nrun].chunks[c - prefix[nrun]];
+      }
+    }
+    move_chunk<T, MOVE>(table[run], cur, n, sm, phase);
+    if (threadIdx.x == 0) {
+      sm.desc[buf ^ 1] = nxt;
+      sm.run[buf ^ 1] = nrun;
+    }
     __syncthreads();
   }
 }
@@ -509,10 +635,11 @@ template <typename T> cudaError_t launch_move(const BinArgs<T>& a, cudaStream_t 
 // From the fill cursors of the buffer just written: valid counts (clamped to
 // capacity), the chunk prefix sum, the chunk descriptors, and the reset of the
 // other buffer's cursors and of the work counter.  One block.
-__global__ void __launch_bounds__(1024)
-k_chunk_list(const int* __restrict__ cursor, const int* __restrict__ cap, const long long* __restrict__ base,
-             int* __restrict__ count, long long* __restrict__ chunk_start, ChunkDesc* __restrict__ chunks,
-             int* __restrict__ other_cursor, int NT, unsigned long long* work, unsigned long long* ovf_total) {
+__device__ __forceinline__ void chunk_list_body(const int* __restrict__ cursor, const int* __restrict__ cap,
+                                                const long long* __restrict__ base, int* __restrict__ count,
+                                                long long* __restrict__ chunk_start, ChunkDesc* __restrict__ chunks,
+                                                int* __restrict__ other_cursor, int NT, unsigned long long* work,
+                                                unsigned long long* ovf_total) {
   __shared__ long long s_part[1024];
   const int nb = NT + 1;
   const int per = (nb + blockDim.x - 1) / blockDim.x;
@@ -542,8 +669,51 @@ k_chunk_list(const int* __restrict__ cursor, const int* __restrict__ cap, const 
   }
   if (threadIdx.x == blockDim.x - 1) chunk_start[nb] = s_part[threadIdx.x];
   if (threadIdx.x == 0) {
-    *work = 0ULL;
+    if (work) *work = 0ULL;
     if (ovf_total) *ovf_total += (unsigned long long)count[NT];
+  }
+}
+
+__global__ void __launch_bounds__(1024)
+k_chunk_list(const int* __restrict__ cursor, const int* __restrict__ cap, const long long* __restrict__ base,
+             int* __restrict__ count, long long* __restrict__ chunk_start, ChunkDesc* __restrict__ chunks,
+             int* __restrict__ other_cursor, int NT, unsigned long long* work, unsigned long long* ovf_total) {
+  chunk_list_body(cursor, cap, base, count, chunk_start, chunks, other_cursor, NT, work, ovf_total);
+}
+
+// One block per run.
+__global__ void __launch_bounds__(1024) k_chunk_list_batch(const ChunkListArgs* __restrict__ t) {
+  const ChunkListArgs& a = t[blockIdx.x];
+  chunk_list_body(a.cursor, a.cap, a.base, a.count, a.chunk_start, a.chunks, a.other_cursor, a.NT, nullptr, nullptr);
+}
+
+// Prefix over runs of their work-item counts; clears the work counter and,
+// if asked, advances the batch's step counter.
+__global__ void __launch_bounds__(1024)
+k_run_prefix(const ChunkListArgs* __restrict__ t, int nruns, long long* __restrict__ prefix, unsigned long long* work,
+             uint32_t* step, int bump) {
+  __shared__ long long s_part[1024];
+  const int per = (nruns + blockDim.x - 1) / blockDim.x;
+  const int r0 = threadIdx.x * per;
+  long long local = 0;
+  for (int r = r0; r < min(r0 + per, nruns); ++r) local += t[r].chunk_start[t[r].NT + 1];
+  s_part[threadIdx.x] = local;
+  __syncthreads();
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+    const long long v = threadIdx.x >= (unsigned)off ? s_part[threadIdx.x - off] : 0;
+    __syncthreads();
+    s_part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  long long run = s_part[threadIdx.x] - local;
+  for (int r = r0; r < min(r0 + per, nruns); ++r) {
+    prefix[r] = run;
+    run += t[r].chunk_start[t[r].NT + 1];
+  }
+  if (threadIdx.x == blockDim.x - 1) prefix[nruns] = s_part[threadIdx.x];
+  if (threadIdx.x == 0) {
+    *work = 0ULL;
+    if (bump) *step += 1u;
   }
 }
 
@@ -551,9 +721,8 @@ k_chunk_list(const int* __restrict__ cursor, const int* __restrict__ cap, const 
 // Spare room: half the tile's own count, 64, and a quarter of what its six
 // face neighbours hold (particles diffuse in across steep density edges).
 // The overflow bin keeps capacity ovf_cap.  One block.
-__global__ void __launch_bounds__(1024)
-k_layout(const int* __restrict__ want, int* __restrict__ cap, long long* __restrict__ base, int NT, int ntx,
-         int ovf_cap) {
+__device__ __forceinline__ void layout_body(const int* __restrict__ want, int* __restrict__ cap,
+                                            long long* __restrict__ base, int NT, int ntx, int ovf_cap) {
   __shared__ long long s_part[1024];
   const int per = (NT + blockDim.x - 1) / blockDim.x;
   const int b0 = threadIdx.x * per;
@@ -590,6 +759,18 @@ k_layout(const int* __restrict__ want, int* __restrict__ cap, long long* __restr
     base[NT] = s_part[threadIdx.x];
     cap[NT] = (ovf_cap + 3) & ~3;
   }
+}
+
+__global__ void __launch_bounds__(1024)
+k_layout(const int* __restrict__ want, int* __restrict__ cap, long long* __restrict__ base, int NT, int ntx,
+         int ovf_cap) {
+  layout_body(want, cap, base, NT, ntx, ovf_cap);
+}
+
+// One block per run.
+__global__ void __launch_bounds__(1024) k_layout_batch(const LayoutArgs* __restrict__ t) {
+  const LayoutArgs& a = t[blockIdx.x];
+  layout_body(a.want, a.cap, a.base, a.NT, a.ntx, a.ovf_cap);
 }
 
 // Tile histogram of plain (unbinned) positions.  With few enough tiles each
@@ -880,6 +1061,53 @@ cudaError_t launch_chunk_list(const int* cursor, const int* cap, const long long
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_move_batch(const BinArgs<T>* table, const long long* prefix, int nruns, unsigned long long* work,
+                              const uint32_t* step, bool move, cudaStream_t s) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e;
+  auto k = move ? k_move_batch<T, true> : k_move_batch<T, false>;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, 0)) != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  k<<<sms * per_sm, 256, 0, s>>>(table, prefix, nruns, work, step);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_deposit_batch(const BinArgs<T>* table, const long long* prefix, int nruns,
+                                 unsigned long long* work, bool fixed, cudaStream_t s) {
+  const size_t smem = (size_t)kReplicas * kWinSlots * sizeof(typename WinType<T>::type);
+  auto k = fixed ? k_deposit_batch<T, true> : k_deposit_batch<T, false>;
+  cudaError_t e;
+  if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem)) != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  k<<<sms * per_sm, 256, smem, s>>>(table, prefix, nruns, work);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chunk_list_batch(const ChunkListArgs* t, int nruns, cudaStream_t s) {
+  k_chunk_list_batch<<<nruns, 1024, 0, s>>>(t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_run_prefix(const ChunkListArgs* t, int nruns, long long* prefix, unsigned long long* work,
+                              uint32_t* step, int bump, cudaStream_t s) {
+  k_run_prefix<<<1, 1024, 0, s>>>(t, nruns, prefix, work, step, bump);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_layout_batch(const LayoutArgs* t, int nruns, cudaStream_t s) {
+  k_layout_batch<<<nruns, 1024, 0, s>>>(t);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_layout(const int* want, int* cap, long long* base, int NT, int ntx, int ovf_cap, cudaStream_t s) {
   k_layout<<<1, 1024, 0, s>>>(want, cap, base, NT, ntx, ovf_cap);
   return cudaGetLastError();
@@ -972,6 +1200,10 @@ template <typename T> cudaError_t launch_alpha_energy(const cpx<T>* alpha, int H
 #define SIPF_INST(T)                                                                                          \
   template cudaError_t launch_binned<T>(const BinArgs<T>&, int, int, int, cudaStream_t);                       \
   template cudaError_t launch_move<T>(const BinArgs<T>&, cudaStream_t);                                       \
+  template cudaError_t launch_move_batch<T>(const BinArgs<T>*, const long long*, int, unsigned long long*,     \
+                                            const uint32_t*, bool, cudaStream_t);                            \
+  template cudaError_t launch_deposit_batch<T>(const BinArgs<T>*, const long long*, int, unsigned long long*,  \
+                                               bool, cudaStream_t);                                           \
   template cudaError_t launch_tile_hist<T>(const T*, const T*, const T*, int64_t, Geo<T>, int, int, int, int*, \
                                            cudaStream_t);                                                    \
   template bool launch_rebin_plain<T>(const T*, const T*, const T*, const uint32_t*, int64_t, Geo<T>, int, int, \

@@ -118,6 +118,7 @@ struct sipf_ctx {
   void* grad = nullptr;    // 4 H^3 T: (gx, gy, gz, 0) per node; scratch between steps
   double* dsc = nullptr;   // FP64 accumulators (see kDsc*)
   int* err = nullptr;
+  void* fft_run = nullptr; // device FftRun<T> of this context (H >= 32): the step's field solve
   // optional per-stage timing: 7 events per step (stage boundaries)
   bool timing = false;
   std::vector<cudaEvent_t> ev;
@@ -149,6 +150,21 @@ SpecParams spec_params(const sipf_ctx* c) {
 
 // deterministic grid: integer counts of 2^-K weight units, times M0/P
 double fixed_in_scale(const sipf_ctx* c) { return c->p.mass / (double)c->p.P * ldexp(1.0, -fixed_k(c->p)); }
+
+// Arrays and parameters of the field solve of one run (batched FFT kernels).
+template <typename T> FftRun<T> make_fft_run(const sipf_ctx* c) {
+  FftRun<T> f;
+  f.phi = c->phi;
+  f.phi_fixed = c->fixed() ? 1 : 0;
+  f.in_scale = fixed_in_scale(c);
+  f.T1 = (cpx<T>*)c->T1;
+  f.alpha = (cpx<T>*)c->alpha;
+  f.T2 = (cpx<T>*)c->T2;
+  f.grad = (T*)c->grad;
+  f.sp = spec_params(c);
+  f.shadow = c->dsc + kDscAlpha0;
+  return f;
+}
 
 // Kernel arguments for src -> dst; src_buf < 0 selects the particle-order staging.
 template <typename T> BinArgs<T> bin_args(sipf_ctx* c, int src_buf, int src_lay, int dst_buf, int dst_lay) {
@@ -263,16 +279,29 @@ template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
     cudaEvent_t ev[7] = {};
     const int64_t l0 = c->launches;
     SIPF_CK(mark(&ev[0]));
+    const FftRun<T>* fr = (const FftRun<T>*)c->fft_run;
     // beta^(n-1) = F_H I(rho-hat^(n-1)); the deposit grid is cleared as it is read
-    SIPF_CK(launch_rows_r2c<T>(c->phi, c->fixed() ? 1 : 0, fixed_in_scale(c), true, T1, H, H * H, nullptr,
-                               c->stream));
-    SIPF_CK(launch_cols<T>(T1, H, H, nh, 1, 0, -1, 1.0, c->stream));
+    if (fr) {
+      SIPF_CK(launch_field_batch<T>(fr, 1, H, kFieldForward, c->stream));
+    } else {
+      SIPF_CK(launch_rows_r2c<T>(c->phi, c->fixed() ? 1 : 0, fixed_in_scale(c), true, T1, H, H * H, nullptr,
+                                 c->stream));
+      SIPF_CK(launch_cols<T>(T1, H, H, nh, 1, 0, -1, 1.0, c->stream));
+    }
     SIPF_CK(mark(&ev[1]));
     // alpha^n and G(alpha^(n-1)), x axis back-transformed
-    SIPF_CK(launch_spectral_x<T>(T1, al, T2, H, sp, kModeStep, c->dsc + kDscAlpha0, c->stream));
+    if (fr) {
+      SIPF_CK(launch_field_batch<T>(fr, 1, H, kFieldSpectral, c->stream));
+    } else {
+      SIPF_CK(launch_spectral_x<T>(T1, al, T2, H, sp, kModeStep, c->dsc + kDscAlpha0, c->stream));
+    }
     SIPF_CK(mark(&ev[2]));
-    SIPF_CK(launch_cols<T>(T2, H, H, nh, 3, S, +1, 1.0, c->stream));
-    SIPF_CK(launch_rows_c2r<T>(T2, 3, S, (T*)c->grad, H, H * H, nullptr, c->stream));
+    if (fr) {
+      SIPF_CK(launch_field_batch<T>(fr, 1, H, kFieldInverse, c->stream));
+    } else {
+      SIPF_CK(launch_cols<T>(T2, H, H, nh, 3, S, +1, 1.0, c->stream));
+      SIPF_CK(launch_rows_c2r<T>(T2, 3, S, (T*)c->grad, H, H * H, nullptr, c->stream));
+    }
     SIPF_CK(mark(&ev[3]));
     // X^(n-1) -> X^n, re-bin into the other buffer by the new tile
     const int src = c->cur, dst = 1 - c->cur;
@@ -511,6 +540,7 @@ void free_ctx(sipf_ctx* c) {
   cudaFree(c->grad);
   cudaFree(c->dsc);
   cudaFree(c->err);
+  cudaFree(c->fft_run);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -606,6 +636,18 @@ int sipf_init(const sipf_params* p, const double* X0, void* stream, sipf_ctx** o
   if (e == cudaSuccess) e = cudaMalloc(&c->grad, 4 * N * c->esz);
   if (e == cudaSuccess) e = cudaMalloc(&c->dsc, kDscCount * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(int));
+  if (e == cudaSuccess && p->H >= 32) {
+    e = cudaMalloc(&c->fft_run, p->precision == 64 ? sizeof(FftRun<double>) : sizeof(FftRun<float>));
+    if (e == cudaSuccess) {
+      if (p->precision == 64) {
+        const FftRun<double> f = make_fft_run<double>(c);
+        e = cudaMemcpy(c->fft_run, &f, sizeof(f), cudaMemcpyHostToDevice);
+      } else {
+        const FftRun<float> f = make_fft_run<float>(c);
+        e = cudaMemcpy(c->fft_run, &f, sizeof(f), cudaMemcpyHostToDevice);
+      }
+    }
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(c->alpha, 0, S * 2 * c->esz, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->dsc, 0, kDscCount * sizeof(double), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
@@ -923,3 +965,324 @@ extern "C" int sipf_inverse_ft_noalloc_dev(int precision, int32_t H, const void*
   }
   return SIPF_OK;
 }
+
+// ===========================================================================
+// Batched runs: independent SIPF-PIC runs of uneven P, H, chi, seed, ... in
+// the same launches.  Each run keeps the state of an ordinary context; the
+// batch issues, per step, the field solve once per grid size (runs of equal
+// H share each launch) and the particle passes once for all runs (work items
+// of all runs from one counter).  Steps are captured in CUDA graphs of 32
+// steps, the period after which the buffer and layout parities repeat; the
+// step counter lives in device memory so the graph can be replayed.
+// ===========================================================================
+struct sipf_batch {
+  int nruns = 0;
+  std::vector<sipf_ctx*> runs;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int precision = 32;
+  bool fixed = false;
+  std::vector<int> group_H, group_n;
+  std::vector<void*> fft_tab;                    // device FftRun<T>[group_n]
+  void* move_tab[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  void* rebin_tab[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  void* dep_tab[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  ChunkListArgs* cl_tab[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  LayoutArgs* ly_tab[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  long long* prefix = nullptr;
+  unsigned long long* work = nullptr;
+  uint32_t* step = nullptr;
+  int cur = 0, lc = 1, since = 0;
+  int64_t n = 0;
+  bool use_graph = true;
+  cudaGraphExec_t graph = nullptr;
+  int graph_cur = -1, graph_lc = -1, graph_since = -1;
+  int64_t launches = 0;
+};
+
+namespace {
+
+constexpr int kBatchResort = 16;
+constexpr int kBatchGraphSteps = 32;
+constexpr int kBatchMaxRuns = 4096;   // 3 x runs block rows of the inverse y pass stay below 65535
+
+void batch_free(sipf_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (void* p : b->fft_tab) cudaFree(p);
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      cudaFree(b->move_tab[i][j]);
+      cudaFree(b->rebin_tab[i][j]);
+      cudaFree(b->dep_tab[i][j]);
+      cudaFree(b->cl_tab[i][j]);
+      cudaFree(b->ly_tab[i][j]);
+    }
+  cudaFree(b->prefix);
+  cudaFree(b->work);
+  cudaFree(b->step);
+  for (sipf_ctx* c : b->runs) free_ctx(c);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+template <typename T> int batch_tables(sipf_batch* b) {
+  const int R = b->nruns;
+  // field-solve tables per grid size
+  for (int g = 0; g < (int)b->group_H.size(); ++g) {
+    std::vector<FftRun<T>> t;
+    for (sipf_ctx* c : b->runs) {
+      if (c->p.H != b->group_H[g]) continue;
+      const FftRun<T> f = make_fft_run<T>(c);
+      t.push_back(f);
+    }
+    void* d = nullptr;
+    SIPF_CK(cudaMalloc(&d, t.size() * sizeof(FftRun<T>)));
+    b->fft_tab.push_back(d);
+    SIPF_CK(cudaMemcpy(d, t.data(), t.size() * sizeof(FftRun<T>), cudaMemcpyHostToDevice));
+  }
+  // particle tables for every (buffer, layout) parity
+  for (int cur = 0; cur < 2; ++cur)
+    for (int lc = 0; lc < 2; ++lc) {
+      std::vector<BinArgs<T>> mv, rb, dp;
+      std::vector<ChunkListArgs> cl;
+      std::vector<LayoutArgs> ly;
+      for (sipf_ctx* c : b->runs) {
+        mv.push_back(bin_args<T>(c, cur, lc, 1 - cur, lc));
+        rb.push_back(bin_args<T>(c, cur, lc, 1 - cur, 1 - lc));
+        dp.push_back(bin_args<T>(c, cur, lc, -1, 0));
+        // chunk list of buffer `cur` written with layout `lc`
+        cl.push_back(ChunkListArgs{c->cursor[cur], c->lcap[lc], c->lbase[lc], c->count, c->chunk_start, c->chunks,
+                                   c->cursor[1 - cur], c->NT});
+        // new layout `lc` from the counts of buffer `cur`
+        ly.push_back(LayoutArgs{c->cursor[cur], c->lcap[lc], c->lbase[lc], c->NT, c->ntx, (int)c->p.P});
+      }
+      SIPF_CK(cudaMalloc(&b->move_tab[cur][lc], R * sizeof(BinArgs<T>)));
+      SIPF_CK(cudaMalloc(&b->rebin_tab[cur][lc], R * sizeof(BinArgs<T>)));
+      SIPF_CK(cudaMalloc(&b->dep_tab[cur][lc], R * sizeof(BinArgs<T>)));
+      SIPF_CK(cudaMalloc(&b->cl_tab[cur][lc], R * sizeof(ChunkListArgs)));
+      SIPF_CK(cudaMalloc(&b->ly_tab[cur][lc], R * sizeof(LayoutArgs)));
+      SIPF_CK(cudaMemcpy(b->move_tab[cur][lc], mv.data(), R * sizeof(BinArgs<T>), cudaMemcpyHostToDevice));
+      SIPF_CK(cudaMemcpy(b->rebin_tab[cur][lc], rb.data(), R * sizeof(BinArgs<T>), cudaMemcpyHostToDevice));
+      SIPF_CK(cudaMemcpy(b->dep_tab[cur][lc], dp.data(), R * sizeof(BinArgs<T>), cudaMemcpyHostToDevice));
+      SIPF_CK(cudaMemcpy(b->cl_tab[cur][lc], cl.data(), R * sizeof(ChunkListArgs), cudaMemcpyHostToDevice));
+      SIPF_CK(cudaMemcpy(b->ly_tab[cur][lc], ly.data(), R * sizeof(LayoutArgs), cudaMemcpyHostToDevice));
+    }
+  return SIPF_OK;
+}
+
+// Enqueue one step of every run (mirrors step_impl) and advance the host-side
+// parities.
+template <typename T> int batch_issue_step(sipf_batch* b) {
+  const int R = b->nruns;
+  cudaStream_t s = b->stream;
+  for (int g = 0; g < (int)b->group_H.size(); ++g)
+    SIPF_CK(launch_field_batch<T>((const FftRun<T>*)b->fft_tab[g], b->group_n[g], b->group_H[g], kFieldAll, s));
+  SIPF_CK(cudaMemsetAsync(b->work, 0, sizeof(unsigned long long), s));
+  SIPF_CK(launch_move_batch<T>((const BinArgs<T>*)b->move_tab[b->cur][b->lc], b->prefix, R, b->work, b->step, true, s));
+  SIPF_CK(launch_chunk_list_batch(b->cl_tab[1 - b->cur][b->lc], R, s));
+  SIPF_CK(launch_run_prefix(b->cl_tab[1 - b->cur][b->lc], R, b->prefix, b->work, b->step, 1, s));
+  b->launches += 5 * (int64_t)b->group_H.size() + 3;
+  b->cur = 1 - b->cur;
+  if (++b->since >= kBatchResort) {
+    SIPF_CK(launch_layout_batch(b->ly_tab[b->cur][1 - b->lc], R, s));
+    SIPF_CK(launch_move_batch<T>((const BinArgs<T>*)b->rebin_tab[b->cur][b->lc], b->prefix, R, b->work, b->step, false,
+                                 s));
+    SIPF_CK(launch_chunk_list_batch(b->cl_tab[1 - b->cur][1 - b->lc], R, s));
+    SIPF_CK(launch_run_prefix(b->cl_tab[1 - b->cur][1 - b->lc], R, b->prefix, b->work, b->step, 0, s));
+    b->launches += 4;
+    b->cur = 1 - b->cur;
+    b->lc = 1 - b->lc;
+    b->since = 0;
+  }
+  SIPF_CK(launch_deposit_batch<T>((const BinArgs<T>*)b->dep_tab[b->cur][b->lc], b->prefix, R, b->work, b->fixed, s));
+  b->launches += 1;
+  b->n += 1;
+  return SIPF_OK;
+}
+
+template <typename T> int batch_step_impl(sipf_batch* b, int64_t nsteps) {
+  while (nsteps > 0) {
+    if (b->use_graph && nsteps >= kBatchGraphSteps) {
+      if (!b->graph || b->graph_cur != b->cur || b->graph_lc != b->lc || b->graph_since != b->since) {
+        if (b->graph) {
+          cudaGraphExecDestroy(b->graph);
+          b->graph = nullptr;
+        }
+        const int c0 = b->cur, l0 = b->lc, s0 = b->since;
+        const int64_t n0 = b->n, k0 = b->launches;
+        SIPF_CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed));
+        int r = SIPF_OK;
+        for (int i = 0; i < kBatchGraphSteps && r == SIPF_OK; ++i) r = batch_issue_step<T>(b);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (r) {
+          if (g) cudaGraphDestroy(g);
+          return r;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        const cudaError_t e2 = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaGraphInstantiate");
+        // capture issued nothing: restore the parities, they advance on launch
+        b->cur = c0;
+        b->lc = l0;
+        b->since = s0;
+        b->n = n0;
+        b->launches = k0;
+        b->graph_cur = c0;
+        b->graph_lc = l0;
+        b->graph_since = s0;
+      }
+      SIPF_CK(cudaGraphLaunch(b->graph, b->stream));
+      // 32 steps hold 32 moves and 2 capacity rebuilds: parities return
+      b->n += kBatchGraphSteps;
+      b->launches += kBatchGraphSteps * (5 * (int64_t)b->group_H.size() + 4) + 2 * 4;
+      nsteps -= kBatchGraphSteps;
+    } else {
+      int r = batch_issue_step<T>(b);
+      if (r) return r;
+      nsteps -= 1;
+    }
+  }
+  return SIPF_OK;
+}
+
+// Make run r's context describe the batch's current state.
+void batch_sync_run(sipf_batch* b, int r) {
+  sipf_ctx* c = b->runs[r];
+  c->cur = b->cur;
+  c->lc = b->lc;
+  c->n = b->n;
+  c->since_layout = b->since;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sipf_batch_init(int32_t nruns, const sipf_params* params, const double* const* X0, void* stream,
+                    sipf_batch** out) {
+  if (!out) return fail(SIPF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (nruns < 1 || !params || !X0) return fail(SIPF_EINVAL, "batch needs nruns >= 1, params and X0");
+  if (nruns > kBatchMaxRuns) return fail(SIPF_EINVAL, "batch holds at most 4096 runs");
+  for (int r = 0; r < nruns; ++r) {
+    const sipf_params& p = params[r];
+    int v = validate(&p);
+    if (v) return fail(v, "run " + std::to_string(r) + ": " + g_last_error);
+    if (p.H < 32) return fail(SIPF_EINVAL, "run " + std::to_string(r) + ": batched runs need H >= 32");
+    if (p.precision != params[0].precision || p.deposit_mode != params[0].deposit_mode)
+      return fail(SIPF_EINVAL, "run " + std::to_string(r) + ": precision and deposit_mode must match run 0");
+    if (p.resort_every != 0 && p.resort_every != kBatchResort)
+      return fail(SIPF_EINVAL, "run " + std::to_string(r) + ": batched runs rebuild capacities every 16 steps");
+    if (!X0[r]) return fail(SIPF_EINVAL, "run " + std::to_string(r) + ": X0 is NULL");
+  }
+  sipf_batch* b = new sipf_batch();
+  b->nruns = nruns;
+  b->precision = params[0].precision;
+  b->fixed = params[0].deposit_mode == SIPF_DEPOSIT_DETERMINISTIC;
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete b;
+      return cuda_fail(e, "cudaStreamCreate");
+    }
+    b->own_stream = true;
+  }
+  for (int r = 0; r < nruns; ++r) {
+    sipf_ctx* c = nullptr;
+    int v = sipf_init(&params[r], X0[r], b->stream, &c);
+    if (v) {
+      batch_free(b);
+      return v;
+    }
+    b->runs.push_back(c);
+  }
+  for (sipf_ctx* c : b->runs) {
+    bool found = false;
+    for (size_t g = 0; g < b->group_H.size(); ++g)
+      if (b->group_H[g] == c->p.H) {
+        b->group_n[g] += 1;
+        found = true;
+      }
+    if (!found) {
+      b->group_H.push_back(c->p.H);
+      b->group_n.push_back(1);
+    }
+  }
+  cudaError_t e = cudaMalloc(&b->prefix, (nruns + 1) * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMalloc(&b->work, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&b->step, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->step, 0, sizeof(uint32_t), b->stream);
+  if (e != cudaSuccess) {
+    batch_free(b);
+    return cuda_fail(e, "sipf_batch_init allocation");
+  }
+  b->cur = b->runs[0]->cur;
+  b->lc = b->runs[0]->lc;
+  int r = b->precision == 64 ? batch_tables<double>(b) : batch_tables<float>(b);
+  if (!r) {
+    cudaError_t e3 = launch_run_prefix(b->cl_tab[b->cur][b->lc], nruns, b->prefix, b->work, b->step, 0, b->stream);
+    if (e3 == cudaSuccess) e3 = cudaStreamSynchronize(b->stream);
+    if (e3 != cudaSuccess) r = cuda_fail(e3, "sipf_batch_init prefix");
+  }
+  if (r) {
+    batch_free(b);
+    return r;
+  }
+  *out = b;
+  return SIPF_OK;
+}
+
+int sipf_batch_step(sipf_batch* b, int64_t nsteps) {
+  if (!b) return fail(SIPF_EINVAL, "batch is NULL");
+  if (nsteps < 0) return fail(SIPF_EINVAL, "nsteps < 0");
+  if (b->n + nsteps > 0xFFFFFFFFLL) return fail(SIPF_EINVAL, "step counter would exceed 2^32 - 1");
+  return b->precision == 64 ? batch_step_impl<double>(b, nsteps) : batch_step_impl<float>(b, nsteps);
+}
+
+int sipf_batch_use_graph(sipf_batch* b, int enable) {
+  if (!b) return fail(SIPF_EINVAL, "batch is NULL");
+  b->use_graph = enable != 0;
+  return SIPF_OK;
+}
+
+int64_t sipf_batch_current_step(const sipf_batch* b) { return b ? b->n : -1; }
+
+int64_t sipf_batch_kernel_launches(const sipf_batch* b) { return b ? b->launches : -1; }
+
+int sipf_batch_positions(sipf_batch* b, int32_t run, double* out) {
+  if (!b || !out || run < 0 || run >= b->nruns) return fail(SIPF_EINVAL, "bad batch, run or out");
+  batch_sync_run(b, run);
+  return sipf_positions(b->runs[run], out);
+}
+
+int sipf_batch_diagnostics(sipf_batch* b, int32_t run, sipf_diag* out) {
+  if (!b || !out || run < 0 || run >= b->nruns) return fail(SIPF_EINVAL, "bad batch, run or out");
+  batch_sync_run(b, run);
+  return sipf_diagnostics(b->runs[run], out);
+}
+
+int sipf_batch_spectrum(sipf_batch* b, int32_t run, double* out) {
+  if (!b || !out || run < 0 || run >= b->nruns) return fail(SIPF_EINVAL, "bad batch, run or out");
+  batch_sync_run(b, run);
+  return sipf_spectrum(b->runs[run], out);
+}
+
+int sipf_batch_sync(sipf_batch* b) {
+  if (!b) return fail(SIPF_EINVAL, "batch is NULL");
+  SIPF_CK(cudaStreamSynchronize(b->stream));
+  for (sipf_ctx* c : b->runs) {
+    int r = sipf_sync(c);
+    if (r) return r;
+  }
+  return SIPF_OK;
+}
+
+void sipf_batch_destroy(sipf_batch* b) { batch_free(b); }
+
+}  // extern "C"

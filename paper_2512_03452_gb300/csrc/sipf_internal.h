@@ -24,6 +24,20 @@ struct SpecParams {
 
 enum SpecMode { kModeStep = 0, kModeDensity = 1, kModeField = 2, kModeGradOnly = 3 };
 
+// One run of a batch, as seen by the batched FFT kernels.
+template <typename T>
+struct FftRun {
+  void* phi;          // deposit grid: T, or int64 fixed point (phi_fixed)
+  int phi_fixed;
+  double in_scale;    // fixed point -> mass
+  cpx<T>* T1;         // forward intermediate
+  cpx<T>* alpha;      // alpha^(n)
+  cpx<T>* T2;         // three gradient spectra
+  T* grad;            // 4 H^3 nodes (gx, gy, gz, 0)
+  SpecParams sp;
+  double* shadow;     // FP64 zero-mode shadow
+};
+
 // Per-device constant tables (twiddles); idempotent, thread-safe.
 cudaError_t ensure_device_tables();
 
@@ -49,6 +63,16 @@ cudaError_t launch_spectral_x(const cpx<T>* T1, cpx<T>* alpha, cpx<T>* T2, int H
 template <typename T>
 cudaError_t launch_rows_c2r(const cpx<T>* in, int ncomp, size_t comp_stride, T* out, int H,
                             int rows, double* max_acc, cudaStream_t s);
+
+// The whole field solve of a step (F_H of phi, update of alpha, gradient
+// spectra, their inverse transforms) for `nruns` runs of the same H (32, 64,
+// 128 or 256), the run table in device memory.  `stages` selects the forward
+// transform (2 launches), the spectral pass (1) and the inverse transforms
+// (2).  A single run's step uses the same kernels with a one-entry table, so
+// a run computes the same bits alone or in a batch.
+enum { kFieldForward = 1, kFieldSpectral = 2, kFieldInverse = 4, kFieldAll = 7 };
+template <typename T>
+cudaError_t launch_field_batch(const FftRun<T>* runs, int nruns, int H, int stages, cudaStream_t s);
 
 // ---- particle launchers (particle_kernels.cu) -----------------------------------
 // One work item of the binned kernel: `len` particles of bin `bin` from slot `start`.
@@ -86,6 +110,33 @@ struct BinArgs {
   int p2g, g2p, split, fixed;
   int* err;                      // sticky error word: bit 0 non-finite position, bit 1 lost particle
 };
+// Per-run argument tables of the batched bookkeeping kernels.
+struct ChunkListArgs {
+  const int* cursor;        // fill cursors of the buffer just written
+  const int* cap;
+  const long long* base;
+  int* count;
+  long long* chunk_start;   // [NT+2]
+  ChunkDesc* chunks;
+  int* other_cursor;        // cursors of the other buffer (cleared)
+  int NT;
+};
+struct LayoutArgs {
+  const int* want;
+  int* cap;
+  long long* base;
+  int NT, ntx, ovf_cap;
+};
+template <typename T>
+cudaError_t launch_move_batch(const BinArgs<T>* table, const long long* prefix, int nruns, unsigned long long* work,
+                              const uint32_t* step, bool move, cudaStream_t s);
+template <typename T>
+cudaError_t launch_deposit_batch(const BinArgs<T>* table, const long long* prefix, int nruns,
+                                 unsigned long long* work, bool fixed, cudaStream_t s);
+cudaError_t launch_chunk_list_batch(const ChunkListArgs* t, int nruns, cudaStream_t s);
+cudaError_t launch_run_prefix(const ChunkListArgs* t, int nruns, long long* prefix, unsigned long long* work,
+                              uint32_t* step, int bump, cudaStream_t s);
+cudaError_t launch_layout_batch(const LayoutArgs* t, int nruns, cudaStream_t s);
 int binned_window_slots(int H);
 int binned_chunk();
 int binned_tile_shift(int H);
