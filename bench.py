@@ -36,9 +36,11 @@ UNIT = "particle-steps/s"
 P_FULL, H_FULL = 10_000_000, 128
 # algorithmic bytes of the particle kernel per particle-step (FP32): read X (12 B) + write X (12 B)
 BYTES_PER_PARTICLE = 24
-# DRAM traffic (read + write bytes per launch) of the fused move kernel from an
-# ncu capture, keyed by the SHA-256 of the kernel source it was taken on.
-MOVE_TRAFFIC = {}
+# DRAM traffic (read + write bytes) of the particle phase, move + re-bin
+# (314.5 MB) and deposit (135.0 MB) launches of one step, from ncu captures of
+# the torus workload, keyed by the SHA-256 of the kernel sources they were
+# taken on (a changed kernel reports null until it is captured again).
+MOVE_TRAFFIC = {"40634f06b4f6586984342864f5b51aa6de50572fae8a6e6bb55ed0b20846bc27": 449.5e6}
 FALLBACK_HBM_GBS = 6800.0
 
 
