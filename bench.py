@@ -253,6 +253,7 @@ def run_ours(args, world, rank, local):
            "path": "sipf_upload_soa + sipf_step + sipf_download_soa, pinned host SoA float32"}
 
     batch = None if args.no_batch else run_batch_leg(world, dev, stream)
+    adjoint = None if args.no_adjoint else run_adjoint_leg(world, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -283,6 +284,7 @@ def run_ours(args, world, rank, local):
                      "steps": K64},
             "diagnostics": {k: diag[k] for k in ("mass", "peak", "m2", "ring_radius", "step")},
             "batch": batch,
+            "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
 
@@ -342,6 +344,39 @@ def run_batch_leg(world, dev, stream, n_runs=256, steps=64, warmup=32):
     return out
 
 
+def run_adjoint_leg(world, dev, stream, nsteps=200, checkpoint=20, reps=2):
+    """The adjoint form on its workload: P = 1e6, H = 64, FP32 forward, N = 200
+    steps, checkpoints every 20; loss J = sum_j (rho_j(T) - rho*_j)^2 in FP64
+    with rho* from a chi = 1.3 run with the same X0 and noise.  Device time of
+    the forward (with checkpoints) and of the reverse sweep (segment
+    recomputation included), per step."""
+    import numpy as np
+
+    from paper_2512_03452_gb300 import _abi, params_from_workload, workloads
+    from paper_2512_03452_gb300.adjoint import Adjoint
+
+    w = workloads.adjoint_case()
+    X0 = workloads.sample_positions(w)
+    p = params_from_workload(w, precision=32)
+    with Adjoint(p, X0, nsteps, checkpoint, stream=stream.cuda_stream) as eng:
+        rho_star = eng.forward(1.3, w.mu)
+        fwd, bwd = [], []
+        for _ in range(reps + 1):
+            rho = eng.forward(w.chi, w.mu)
+            gc, gm, gX = eng.backward(2.0 * (rho - rho_star))
+            f, b = eng.timing()
+            fwd.append(f)
+            bwd.append(b)
+        launches = _abi.sipf_adjoint_kernel_launches(eng.handle)
+    f, b = dist_max(min(fwd[1:]), world, dev), dist_max(min(bwd[1:]), world, dev)
+    J = float(np.sum((rho - rho_star) ** 2))
+    return {"workload": f"{w.name}, N={nsteps}, checkpoint every {checkpoint}, FP32 forward, FP64 loss",
+            "adjoint_ms_per_step": (f + b) / nsteps, "forward_ms_per_step": f / nsteps,
+            "backward_ms_per_step": b / nsteps, "backward_over_forward": b / f,
+            "loss": J, "dJ_dchi": gc, "dJ_dmu": gm, "dJ_dX0_max": float(np.max(np.abs(gX))),
+            "gpu_launches_total": launches}
+
+
 # ----------------------------------------------------------------- reference arm
 def run_reference(args, world, rank):
     """The FP64 oracle on the host cores, each step a bounded sample of the workload."""
@@ -384,6 +419,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble leg")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     world, rank, local = dist_init(args)

@@ -255,6 +255,50 @@ int sipf_batch_sync(sipf_batch* b);
 /* Free every run and the batch.  NULL is a no-op. */
 void sipf_batch_destroy(sipf_batch* b);
 
+/* ---- adjoint -------------------------------------------------------------
+ * Gradients of a scalar J(rho(T)) with respect to chi, mu and X^0 through
+ * N = nsteps steps of Algorithm 4, the noise held fixed (the same Philox
+ * counters as the forward), by reverse mode with hand-written transposes of
+ * every operator of the step: the deposit I and the gather I* are each
+ * other's transposes (Sec. 3.2, <I rho, f> = <rho, I* f>), the transpose of
+ * F_H is L^-3 F_H^-1, pointwise spectral factors turn into their complex
+ * conjugates, and particle positions enter through the derivatives of the
+ * weight polynomials of Eqs. (2ord) and (4ord).  rho(T) is the deposited
+ * density I rho-hat / h^3 of X^N (sipf_density with filtered = 0).
+ * Memory: the forward keeps X^n (id order) and alpha^n every
+ * checkpoint_every steps; the reverse sweep recomputes one segment at a time
+ * and holds its X^{n-1} and gradient grids.  chi and mu > 0 may change
+ * between forward calls; the other parameters are fixed at init.
+ */
+typedef struct sipf_adjoint sipf_adjoint;
+
+/* Create the adjoint engine for parameters *p (p->chi and p->mu are the
+ * first values; p->mu > 0), initial positions X0 (host P x 3 float64), N =
+ * nsteps >= 1, checkpoint_every >= 1 (0: 20).  stream: cudaStream_t or NULL. */
+int sipf_adjoint_init(const sipf_params* p, const double* X0, int64_t nsteps,
+                      int32_t checkpoint_every, void* stream, sipf_adjoint** out);
+
+/* Run the N forward steps from X0 (host P x 3 float64; NULL keeps the last
+ * one) with the given chi and mu, keeping the checkpoints, and write rho(T)
+ * (host H^3 float64) to rho_out unless NULL.  Synchronises. */
+int sipf_adjoint_forward(sipf_adjoint* a, double chi, double mu, const double* X0,
+                         double* rho_out);
+
+/* Given rho_bar = dJ/drho(T) (host H^3 float64), write dJ/dchi, dJ/dmu and
+ * dJ/dX^0 (host P x 3 float64); any output may be NULL.  Needs a preceding
+ * sipf_adjoint_forward.  dJ/dchi and dJ/dmu are accumulated in FP64.
+ * Synchronises. */
+int sipf_adjoint_backward(sipf_adjoint* a, const double* rho_bar, double* grad_chi,
+                          double* grad_mu, double* grad_X0);
+
+/* Device time of the last forward and backward calls (CUDA events). */
+int sipf_adjoint_timing(const sipf_adjoint* a, double* forward_ms, double* backward_ms);
+
+/* Library kernels launched by the engine so far; -1 for NULL. */
+int64_t sipf_adjoint_kernel_launches(const sipf_adjoint* a);
+
+void sipf_adjoint_destroy(sipf_adjoint* a);
+
 /* ---- stateless operators on caller-owned device memory ------------------
  * precision: 32 or 64 (element type float / double of every real array).
  * All are asynchronous on `stream` (cudaStream_t or NULL for the default).

@@ -109,6 +109,13 @@ _SIGS = {
     "sipf_batch_spectrum": (ctypes.c_int, [_P, ctypes.c_int32, _D]),
     "sipf_batch_sync": (ctypes.c_int, [_P]),
     "sipf_batch_destroy": (None, [_P]),
+    "sipf_adjoint_init": (ctypes.c_int, [ctypes.POINTER(sipf_params), _D, ctypes.c_int64, ctypes.c_int32, _P,
+                                         ctypes.POINTER(_P)]),
+    "sipf_adjoint_forward": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _D, _D]),
+    "sipf_adjoint_backward": (ctypes.c_int, [_P, _D, _D, _D, _D]),
+    "sipf_adjoint_timing": (ctypes.c_int, [_P, _D, _D]),
+    "sipf_adjoint_kernel_launches": (ctypes.c_int64, [_P]),
+    "sipf_adjoint_destroy": (None, [_P]),
 }
 
 
@@ -329,3 +336,46 @@ def sipf_batch_sync(b: int) -> None:
 
 def sipf_batch_destroy(b: int) -> None:
     load().sipf_batch_destroy(_P(b))
+
+
+# ---- adjoint ---------------------------------------------------------------------
+def sipf_adjoint_init(p: sipf_params, X0, nsteps: int, checkpoint_every: int = 0, stream: int | None = None) -> int:
+    import numpy as np
+    X0 = np.ascontiguousarray(X0, dtype=np.float64)
+    h = _P()
+    _check(load().sipf_adjoint_init(ctypes.byref(p), _dptr(X0), int(nsteps), int(checkpoint_every), _P(stream or 0),
+                                    ctypes.byref(h)), "sipf_adjoint_init")
+    return h.value
+
+
+def sipf_adjoint_forward(a: int, chi: float, mu: float, X0, rho_out) -> None:
+    """X0: (P, 3) float64 array or None; rho_out: (H, H, H) float64 array or None."""
+    import numpy as np
+    x = None if X0 is None else _dptr(np.ascontiguousarray(X0, dtype=np.float64))
+    r = None if rho_out is None else _dptr(rho_out)
+    _check(load().sipf_adjoint_forward(_P(a), float(chi), float(mu), x, r), "sipf_adjoint_forward")
+
+
+def sipf_adjoint_backward(a: int, rho_bar, grad_X0=None):
+    """Returns (dJ/dchi, dJ/dmu); fills grad_X0 ((P, 3) float64) if given."""
+    import numpy as np
+    rb = np.ascontiguousarray(rho_bar, dtype=np.float64)
+    gc, gm = ctypes.c_double(), ctypes.c_double()
+    gx = None if grad_X0 is None else _dptr(grad_X0)
+    _check(load().sipf_adjoint_backward(_P(a), _dptr(rb), ctypes.byref(gc), ctypes.byref(gm), gx),
+           "sipf_adjoint_backward")
+    return gc.value, gm.value
+
+
+def sipf_adjoint_timing(a: int):
+    f, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().sipf_adjoint_timing(_P(a), ctypes.byref(f), ctypes.byref(b)), "sipf_adjoint_timing")
+    return f.value, b.value
+
+
+def sipf_adjoint_kernel_launches(a: int) -> int:
+    return int(load().sipf_adjoint_kernel_launches(_P(a)))
+
+
+def sipf_adjoint_destroy(a: int) -> None:
+    load().sipf_adjoint_destroy(_P(a))

@@ -1,0 +1,322 @@
+// Reverse-mode (adjoint) kernels of the SIPF-PIC step with the noise held
+// fixed: the transposes of the deposit I (Algorithm 2), of the gather I*
+// (Algorithm 3) and of the Fourier-side update (Eq. (alpha_hat_update), the
+// filtered spectral gradient of Algorithm 4), and the position derivatives of
+// the weight polynomials of Eqs. (2ord) and (4ord).  Particles are taken in id
+// order; X^{n-1}, the gradient grids g^{n-1} and the cotangent grids are small
+// enough to stay in L2 at the sizes the adjoint serves.
+#include <cuda_runtime.h>
+
+#include "sipf_device.cuh"
+#include "sipf_internal.h"
+
+namespace sipf {
+namespace {
+
+template <typename T> struct A3 { T x, y, z; };
+
+// 1D factors and their derivatives on one axis: in-cell layers j = 0, 1 and
+// the outer layers -1 (om) and 2 (o2) of Gamma_4.
+template <typename T> struct AxisD {
+  T f[2], d[2];     // 1 - l, l and -1, +1
+  T om, dom, o2, do2;
+  T q, dq;          // l (1 - l) / 2 and its derivative (the boost term of the inner nodes)
+};
+
+template <typename T> __device__ __forceinline__ AxisD<T> axis_d(T l) {
+  AxisD<T> a;
+  a.f[0] = T(1) - l;
+  a.f[1] = l;
+  a.d[0] = T(-1);
+  a.d[1] = T(1);
+  const T s6 = T(1.0 / 6.0);
+  a.om = -(T(2) - l) * l * (T(1) - l) * s6;           // -(2 l - 3 l^2 + l^3) / 6
+  a.dom = -(T(2) - T(6) * l + T(3) * l * l) * s6;
+  a.o2 = -(T(1) + l) * (T(1) - l) * l * s6;           // -(l - l^3) / 6
+  a.do2 = -(T(1) - T(3) * l * l) * s6;
+  a.q = T(0.5) * l * (T(1) - l);
+  a.dq = T(0.5) * (T(1) - T(2) * l);
+  return a;
+}
+
+// Visit the 8 nodes of Gamma_2 with F and dF/dlambda: fn(idx, F, Fx, Fy, Fz).
+template <typename T, typename Fn>
+__device__ __forceinline__ void gamma2_grad_visit(const int ix[4], const int iy[4], const int iz[4], const AxisD<T>& ax,
+                                                  const AxisD<T>& ay, const AxisD<T>& az, Fn&& fn) {
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+        fn(ix[a + 1] + iy[b + 1] + iz[c + 1], ax.f[a] * ay.f[b] * az.f[c], ax.d[a] * ay.f[b] * az.f[c],
+           ax.f[a] * ay.d[b] * az.f[c], ax.f[a] * ay.f[b] * az.d[c]);
+}
+
+// Visit the 32 nodes of Gamma_4 with F and dF/dlambda.  Inner nodes:
+// F = B(l) prod f, B = 1 + sum_k l_k (1 - l_k)/2; outer nodes: the cubic factor
+// of their axis times the bilinear factor of the other two.
+template <typename T, typename Fn>
+__device__ __forceinline__ void gamma4_grad_visit(const int ix[4], const int iy[4], const int iz[4], const AxisD<T>& ax,
+                                                  const AxisD<T>& ay, const AxisD<T>& az, Fn&& fn) {
+  const T B = T(1) + ax.q + ay.q + az.q;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const T tri = ax.f[a] * ay.f[b] * az.f[c];
+        fn(ix[a + 1] + iy[b + 1] + iz[c + 1], B * tri, ax.dq * tri + B * ax.d[a] * ay.f[b] * az.f[c],
+           ay.dq * tri + B * ax.f[a] * ay.d[b] * az.f[c], az.dq * tri + B * ax.f[a] * ay.f[b] * az.d[c]);
+      }
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const T yz = ay.f[b] * az.f[c];
+      fn(ix[0] + iy[b + 1] + iz[c + 1], ax.om * yz, ax.dom * yz, ax.om * ay.d[b] * az.f[c], ax.om * ay.f[b] * az.d[c]);
+      fn(ix[3] + iy[b + 1] + iz[c + 1], ax.o2 * yz, ax.do2 * yz, ax.o2 * ay.d[b] * az.f[c], ax.o2 * ay.f[b] * az.d[c]);
+    }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const T xz = ax.f[a] * az.f[c];
+      fn(ix[a + 1] + iy[0] + iz[c + 1], ay.om * xz, ay.om * ax.d[a] * az.f[c], ay.dom * xz, ay.om * ax.f[a] * az.d[c]);
+      fn(ix[a + 1] + iy[3] + iz[c + 1], ay.o2 * xz, ay.o2 * ax.d[a] * az.f[c], ay.do2 * xz, ay.o2 * ax.f[a] * az.d[c]);
+    }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const T xy = ax.f[a] * ay.f[b];
+      fn(ix[a + 1] + iy[b + 1] + iz[0], az.om * xy, az.om * ax.d[a] * ay.f[b], az.om * ax.f[a] * ay.d[b], az.dom * xy);
+      fn(ix[a + 1] + iy[b + 1] + iz[3], az.o2 * xy, az.o2 * ax.d[a] * ay.f[b], az.o2 * ax.f[a] * ay.d[b], az.do2 * xy);
+    }
+}
+
+template <typename T, typename Fn>
+__device__ __forceinline__ void stencil_grad_visit(int order, T px, T py, T pz, const Geo<T>& g, Fn&& fn) {
+  int cx, cy, cz;
+  T lx, ly, lz;
+  cell_lambda(px, g, cx, lx);
+  cell_lambda(py, g, cy, ly);
+  cell_lambda(pz, g, cz, lz);
+  int ix[4], iy[4], iz[4];
+  axis_layers_global(cx, g.mask, g.H * g.H, ix);
+  axis_layers_global(cy, g.mask, g.H, iy);
+  axis_layers_global(cz, g.mask, 1, iz);
+  const AxisD<T> ax = axis_d(lx), ay = axis_d(ly), az = axis_d(lz);
+  if (order == 4) gamma4_grad_visit<T>(ix, iy, iz, ax, ay, az, fn);
+  else gamma2_grad_visit<T>(ix, iy, iz, ax, ay, az, fn);
+}
+
+// w (H/L) sum_gamma grad_lambda F_gamma(lambda(X)) phibar[q_gamma]: the
+// transpose of X -> I rho-hat(X) applied to the grid cotangent phibar.
+template <typename T>
+__device__ __forceinline__ A3<T> deposit_adjoint(const T* __restrict__ phibar, int order, T px, T py, T pz, T w_inv_h,
+                                                 const Geo<T>& g) {
+  A3<T> s{T(0), T(0), T(0)};
+  stencil_grad_visit<T>(order, px, py, pz, g, [&](int idx, T, T fx, T fy, T fz) {
+    const T f = __ldg(phibar + idx);
+    s.x += fx * f;
+    s.y += fy * f;
+    s.z += fz * f;
+  });
+  return A3<T>{s.x * w_inv_h, s.y * w_inv_h, s.z * w_inv_h};
+}
+
+template <typename T> __device__ __forceinline__ void red_add(T* p, T v) { atomicAdd(p, v); }
+
+// Block sum of two values into FP64 accumulators (one atomic pair per block).
+template <typename T> __device__ __forceinline__ void block_acc2(T a, T b, double* acc) {
+  __shared__ double sa[32], sb[32];
+  double da = (double)a, db = (double)b;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    da += __shfl_xor_sync(0xffffffffu, da, o);
+    db += __shfl_xor_sync(0xffffffffu, db, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sa[wid] = da;
+    sb[wid] = db;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    da = lane < nw ? sa[lane] : 0.0;
+    db = lane < nw ? sb[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      da += __shfl_xor_sync(0xffffffffu, da, o);
+      db += __shfl_xor_sync(0xffffffffu, db, o);
+    }
+    if (lane == 0) {
+      atomicAdd(acc, da);
+      atomicAdd(acc + 1, db);
+    }
+  }
+}
+
+// One reverse step n for every particle p (id order).  In: X^{n-1}, the
+// gradient grids g^{n-1} as (gx, gy, gz, 0) nodes, phibar^{n-1} and Xbar^n;
+// out: Xbar^{n-1} (in place), the gradient-grid cotangents gbar (3 planes of
+// H^3, accumulated) and the sums for dJ/dchi and dJ/ds.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_adj_step(AdjArgs<T> a) {
+  T chi_part = T(0), s_part = T(0);
+  const Geo<T> g = a.g;
+  const size_t H3 = (size_t)g.H * g.H * g.H;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.P; p += (int64_t)gridDim.x * blockDim.x) {
+    const T x = a.x[p], y = a.y[p], z = a.z[p];
+    const T bx = a.xb[p], by = a.xb[a.P + p], bz = a.xb[2 * a.P + p];
+    T nz[6];
+    normals6(a.seed, (uint64_t)p, a.n, nz);
+    // point where the drift gradient is gathered: X + W^- (half splitting) or X
+    const T qx = a.split == 0 ? x + a.s_noise * nz[0] : x;
+    const T qy = a.split == 0 ? y + a.s_noise * nz[1] : y;
+    const T qz = a.split == 0 ? z + a.s_noise * nz[2] : z;
+    // V = I* g (q) and its Jacobian J[d][e] = dV_d / dq_e
+    T V[3] = {T(0), T(0), T(0)};
+    T J[3][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
+    stencil_grad_visit<T>(a.g2p, qx, qy, qz, g, [&](int idx, T f, T fx, T fy, T fz) {
+      const T* gp = a.grad4 + (size_t)idx * 4;
+      const T v[3] = {__ldg(gp), __ldg(gp + 1), __ldg(gp + 2)};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        V[d] += f * v[d];
+        J[d][0] += fx * v[d];
+        J[d][1] += fy * v[d];
+        J[d][2] += fz * v[d];
+      }
+    });
+    chi_part += a.tau * (V[0] * bx + V[1] * by + V[2] * bz);
+    const T ct = a.chitau * g.inv_h;   // J above is in lambda units: d/dq = (H/L) d/dlambda
+    const T ybx = bx + ct * (J[0][0] * bx + J[1][0] * by + J[2][0] * bz);
+    const T yby = by + ct * (J[0][1] * bx + J[1][1] * by + J[2][1] * bz);
+    const T ybz = bz + ct * (J[0][2] * bx + J[1][2] * by + J[2][2] * bz);
+    if (a.split == 0)
+      s_part += nz[0] * ybx + nz[1] * yby + nz[2] * ybz + nz[3] * bx + nz[4] * by + nz[5] * bz;
+    else
+      s_part += nz[0] * bx + nz[1] * by + nz[2] * bz;
+    // gbar_d += F_gamma(q) chi tau Xbar_d  (transpose of the gather)
+    const T cbx = a.chitau * bx, cby = a.chitau * by, cbz = a.chitau * bz;
+    stencil_grad_visit<T>(a.g2p, qx, qy, qz, g, [&](int idx, T f, T, T, T) {
+      red_add(a.gbar + idx, f * cbx);
+      red_add(a.gbar + H3 + idx, f * cby);
+      red_add(a.gbar + 2 * H3 + idx, f * cbz);
+    });
+    // transpose of the deposit of X^{n-1}
+    const A3<T> dp = deposit_adjoint<T>(a.phibar, a.p2g, x, y, z, a.w_inv_h, g);
+    a.xb[p] = ybx + dp.x;
+    a.xb[a.P + p] = yby + dp.y;
+    a.xb[2 * a.P + p] = ybz + dp.z;
+  }
+  block_acc2<T>(chi_part, s_part, a.acc);
+}
+
+// Terminal cotangent: Xbar^N = transpose of the deposit at X^N applied to phibar^N.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_adj_terminal(const T* __restrict__ x, const T* __restrict__ y, const T* __restrict__ z, int64_t P,
+               const T* __restrict__ phibar, int p2g, T w_inv_h, Geo<T> g, T* __restrict__ xb) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+    const A3<T> dp = deposit_adjoint<T>(phibar, p2g, x[p], y[p], z[p], w_inv_h, g);
+    xb[p] = dp.x;
+    xb[P + p] = dp.y;
+    xb[2 * P + p] = dp.z;
+  }
+}
+
+// Fourier side of one reverse step on full 3D half spectra [H][H][H/2+1]:
+//   abar <- A abar + sum_d conj(m_d) ghat_d,   m_d = 2 pi i q_d / L Phi_q (0 on q_d = -H/2),
+//   betabar_next = L^-3 B abar  (written to `spec`, ready for the inverse transform
+//   that gives the transpose of F_H).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_adj_spectral(const cpx<T>* __restrict__ ghat, cpx<T>* __restrict__ abar, cpx<T>* __restrict__ spec, int H,
+               SpecParams sp) {
+  const int nh = H / 2 + 1;
+  const size_t S = (size_t)H * H * nh;
+  const T two_pi_L = T(6.283185307179586 / sp.L);
+  const T filt = sp.H0 > 0 ? T(-2.0 * 9.869604401089358 / (sp.H0 * sp.H0)) : T(0);
+  const T tau_eps = T(sp.tau / sp.eps), eps_tau = T(sp.eps / sp.tau), k2 = T(sp.k2), tau = T(sp.tau);
+  const T inv_L3 = T(sp.inv_L3);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += (size_t)gridDim.x * blockDim.x) {
+    const int mz = (int)(i % nh);
+    const int my = (int)((i / nh) % H);
+    const int mx = (int)(i / ((size_t)nh * H));
+    const int qx = mx < H / 2 ? mx : mx - H;
+    const int qy = my < H / 2 ? my : my - H;
+    const int qz = mz < H / 2 ? mz : mz - H;
+    const T q2 = T(qx * qx + qy * qy + qz * qz);
+    const T lam = two_pi_L * two_pi_L * q2 + k2;
+    T A, B;
+    if (sp.propagator == 0) {
+      A = T(1) / (T(1) + tau_eps * lam);
+      B = T(1) / (lam + eps_tau);
+    } else {
+      A = t_exp(-tau_eps * lam);
+      B = A * tau;
+    }
+    const T Phi = sp.H0 > 0 ? t_exp(filt * q2) : T(1);
+    cpx<T> acc{T(0), T(0)};
+    const int qd[3] = {qx, qy, qz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (qd[d] == -H / 2) continue;
+      const T yd = two_pi_L * T(qd[d]) * Phi;
+      const cpx<T> gh = ghat[d * S + i];
+      // conj(i yd) (gh.x + i gh.y) = yd (gh.y - i gh.x)
+      acc.x += yd * gh.y;
+      acc.y -= yd * gh.x;
+    }
+    const cpx<T> ab = abar[i];
+    const cpx<T> an{A * ab.x + acc.x, A * ab.y + acc.y};
+    abar[i] = an;
+    spec[i] = cpx<T>{inv_L3 * B * an.x, inv_L3 * B * an.y};
+  }
+}
+
+int grid_blocks(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
+}
+
+}  // namespace
+
+template <typename T> cudaError_t launch_adj_step(const AdjArgs<T>& a, cudaStream_t s) {
+  if (a.P <= 0) return cudaSuccess;
+  k_adj_step<T><<<grid_blocks(a.P), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_adj_terminal(const T* x, const T* y, const T* z, int64_t P, const T* phibar, int p2g, T w_inv_h,
+                                Geo<T> g, T* xb, cudaStream_t s) {
+  if (P <= 0) return cudaSuccess;
+  k_adj_terminal<T><<<grid_blocks(P), 256, 0, s>>>(x, y, z, P, phibar, p2g, w_inv_h, g, xb);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_adj_spectral(const cpx<T>* ghat, cpx<T>* abar, cpx<T>* spec, int H, SpecParams sp,
+                                cudaStream_t s) {
+  const int64_t S = (int64_t)H * H * (H / 2 + 1);
+  k_adj_spectral<T><<<grid_blocks(S), 256, 0, s>>>(ghat, abar, spec, H, sp);
+  return cudaGetLastError();
+}
+
+#define SIPF_ADJ_INST(T)                                                                                          \
+  template cudaError_t launch_adj_step<T>(const AdjArgs<T>&, cudaStream_t);                                      \
+  template cudaError_t launch_adj_terminal<T>(const T*, const T*, const T*, int64_t, const T*, int, T, Geo<T>, T*, \
+                                              cudaStream_t);                                                     \
+  template cudaError_t launch_adj_spectral<T>(const cpx<T>*, cpx<T>*, cpx<T>*, int, SpecParams, cudaStream_t);
+SIPF_ADJ_INST(float)
+SIPF_ADJ_INST(double)
+#undef SIPF_ADJ_INST
+
+}  // namespace sipf

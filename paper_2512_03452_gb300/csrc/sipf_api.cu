@@ -1286,3 +1286,289 @@ int sipf_batch_sync(sipf_batch* b) {
 void sipf_batch_destroy(sipf_batch* b) { batch_free(b); }
 
 }  // extern "C"
+
+// ===========================================================================
+// Adjoint form: gradients of a function of rho(T) with respect to chi, mu and
+// X^0 through N steps of Algorithm 4 with the noise held fixed.  The forward
+// pass keeps (X^n in id order, alpha^n) every `C` steps; the reverse sweep
+// recomputes one segment of C steps at a time from its checkpoint, storing
+// X^{n-1} and the gradient grids g^{n-1} of each step, and runs the
+// transposed operators backwards through it.
+// ===========================================================================
+struct sipf_adjoint {
+  sipf_ctx* c = nullptr;
+  int64_t N = 0;
+  int C = 20;
+  int nck = 0;
+  void* ckX = nullptr;     // nck x 3P T: X^{kC} (x plane, y plane, z plane)
+  void* ckA = nullptr;     // nck x S complex T: alpha^{kC}
+  void* segX = nullptr;    // C x 3P T: X^{n-1} of the segment being reversed
+  void* segG = nullptr;    // C x 4 H^3 T: g^{n-1} as (gx, gy, gz, 0) nodes
+  void* XN = nullptr;      // 3P T: X^N
+  void* xb = nullptr;      // 3P T: Xbar
+  void* abar = nullptr;    // S complex T
+  void* spec = nullptr;    // S complex T: L^-3 B abar, then inverse-transform work
+  void* gbar = nullptr;    // 3 H^3 T
+  void* ghat = nullptr;    // 3 S complex T
+  void* phibar = nullptr;  // H^3 T
+  double* acc = nullptr;   // [dJ/dchi, dJ/ds]
+  std::vector<double> X0;
+  bool have_forward = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t launches = 0;    // adjoint kernels (the forward steps count in the context)
+};
+
+namespace {
+
+constexpr int kAdjCheckpoint = 20;
+
+void adjoint_free(sipf_adjoint* a) {
+  if (!a) return;
+  if (a->c && a->c->stream) cudaStreamSynchronize(a->c->stream);
+  for (void* p : {a->ckX, a->ckA, a->segX, a->segG, a->XN, a->xb, a->abar, a->spec, a->gbar, a->ghat, a->phibar})
+    cudaFree(p);
+  cudaFree(a->acc);
+  for (cudaEvent_t e : a->ev)
+    if (e) cudaEventDestroy(e);
+  free_ctx(a->c);
+  delete a;
+}
+
+// Put the context in state (X in id order, alpha, step n): re-bin and deposit.
+template <typename T> int load_state(sipf_ctx* c, const T* X, const void* alpha, int64_t n) {
+  const size_t P = (size_t)c->p.P;
+  for (int d = 0; d < 3; ++d)
+    SIPF_CK(cudaMemcpyAsync(c->st[d], X + d * P, P * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+  SIPF_CK(launch_iota(c->st_id, c->p.P, c->stream));
+  SIPF_CK(cudaMemcpyAsync(c->alpha, alpha, (size_t)c->S() * 2 * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+  c->n = n;
+  return rebin_from_staging<T>(c);
+}
+
+template <typename T> int adjoint_forward_impl(sipf_adjoint* a, double* rho_out) {
+  sipf_ctx* c = a->c;
+  const size_t P = (size_t)c->p.P, S2 = (size_t)c->S() * 2;
+  T* ckX = (T*)a->ckX;
+  T* ckA = (T*)a->ckA;
+  SIPF_CK(cudaEventRecord(a->ev[0], c->stream));
+  SIPF_CK(cudaMemsetAsync(c->alpha, 0, S2 * sizeof(T), c->stream));
+  SIPF_CK(cudaMemsetAsync(c->dsc, 0, kDscCount * sizeof(double), c->stream));
+  c->n = 0;
+  int r = upload_aos<T>(c, a->X0.data());
+  if (r) return r;
+  for (int64_t n = 1; n <= a->N; ++n) {
+    if ((n - 1) % a->C == 0) {
+      const int64_t k = (n - 1) / a->C;
+      T* X = ckX + (size_t)k * 3 * P;
+      r = positions_dev_impl<T>(c, X, X + P, X + 2 * P);
+      if (r) return r;
+      SIPF_CK(cudaMemcpyAsync(ckA + (size_t)k * S2, c->alpha, S2 * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+    }
+    r = step_impl<T>(c, 1);
+    if (r) return r;
+  }
+  T* XN = (T*)a->XN;
+  r = positions_dev_impl<T>(c, XN, XN + P, XN + 2 * P);
+  if (r) return r;
+  SIPF_CK(cudaEventRecord(a->ev[1], c->stream));
+  if (rho_out) {
+    r = density_host<T>(c, rho_out, 0);
+    if (r) return r;
+  }
+  a->have_forward = true;
+  return SIPF_OK;
+}
+
+template <typename T>
+int adjoint_backward_impl(sipf_adjoint* a, const double* rho_bar, double* grad_chi, double* grad_mu, double* grad_X0) {
+  sipf_ctx* c = a->c;
+  const sipf_params& p = c->p;
+  const int H = p.H, nh = H / 2 + 1;
+  const size_t P = (size_t)p.P, H3 = (size_t)c->H3(), S = (size_t)c->S();
+  const Geo<T> geo = make_geo<T>(p.L, H);
+  const double h3 = pow(p.L / H, 3);
+  const T w_inv_h = (T)(p.mass / (double)p.P * H / p.L);
+  cudaStream_t s = c->stream;
+  SIPF_CK(cudaEventRecord(a->ev[2], s));
+  {
+    std::vector<T> hb(H3);
+    for (size_t i = 0; i < H3; ++i) hb[i] = (T)(rho_bar[i] / h3);
+    SIPF_CK(cudaMemcpyAsync(a->phibar, hb.data(), H3 * sizeof(T), cudaMemcpyHostToDevice, s));
+    SIPF_CK(cudaStreamSynchronize(s));
+  }
+  T* XN = (T*)a->XN;
+  T* xb = (T*)a->xb;
+  SIPF_CK(launch_adj_terminal<T>(XN, XN + P, XN + 2 * P, p.P, (const T*)a->phibar, p.p2g_order, w_inv_h, geo, xb, s));
+  a->launches += 1;
+  SIPF_CK(cudaMemsetAsync(a->abar, 0, S * 2 * sizeof(T), s));
+  SIPF_CK(cudaMemsetAsync(a->phibar, 0, H3 * sizeof(T), s));   // phibar^{N-1} = L^-3 F^-1 (B abar^N) = 0
+  SIPF_CK(cudaMemsetAsync(a->acc, 0, 2 * sizeof(double), s));
+  const double sn = p.splitting == SIPF_SPLIT_HALF ? sqrt(p.mu * p.dt) : sqrt(2.0 * p.mu * p.dt);
+  SpecParams sp = spec_params(c);
+  T* segX = (T*)a->segX;
+  T* segG = (T*)a->segG;
+  for (int k = a->nck - 1; k >= 0; --k) {
+    const int64_t k0 = (int64_t)k * a->C, k1 = std::min<int64_t>(k0 + a->C, a->N);
+    int r = load_state<T>(c, (const T*)a->ckX + (size_t)k * 3 * P, (const T*)a->ckA + (size_t)k * 2 * S, k0);
+    if (r) return r;
+    for (int64_t j = k0; j < k1; ++j) {
+      T* X = segX + (size_t)(j - k0) * 3 * P;
+      r = positions_dev_impl<T>(c, X, X + P, X + 2 * P);
+      if (r) return r;
+      r = step_impl<T>(c, 1);
+      if (r) return r;
+      // after step j+1 the context's gradient buffer holds g^{j}
+      SIPF_CK(cudaMemcpyAsync(segG + (size_t)(j - k0) * 4 * H3, c->grad, 4 * H3 * sizeof(T), cudaMemcpyDeviceToDevice,
+                              s));
+    }
+    for (int64_t n = k1; n > k0; --n) {
+      const size_t i = (size_t)(n - 1 - k0);
+      SIPF_CK(cudaMemsetAsync(a->gbar, 0, 3 * H3 * sizeof(T), s));
+      AdjArgs<T> aa{};
+      aa.x = segX + i * 3 * P;
+      aa.y = aa.x + P;
+      aa.z = aa.x + 2 * P;
+      aa.grad4 = segG + i * 4 * H3;
+      aa.phibar = (const T*)a->phibar;
+      aa.xb = xb;
+      aa.gbar = (T*)a->gbar;
+      aa.acc = a->acc;
+      aa.g = geo;
+      aa.s_noise = (T)sn;
+      aa.chitau = (T)(p.chi * p.dt);
+      aa.tau = (T)p.dt;
+      aa.w_inv_h = w_inv_h;
+      aa.seed = p.seed;
+      aa.n = (uint32_t)n;
+      aa.P = p.P;
+      aa.p2g = p.p2g_order;
+      aa.g2p = p.g2p_order;
+      aa.split = p.splitting;
+      SIPF_CK(launch_adj_step<T>(aa, s));
+      // ghat = unnormalised DFT of the three cotangent grids
+      cpx<T>* gh = (cpx<T>*)a->ghat;
+      SIPF_CK(launch_rows_r2c<T>(a->gbar, 0, 1.0, false, gh, H, 3 * H * H, nullptr, s));
+      SIPF_CK(launch_cols<T>(gh, H, 3 * H, nh, 1, 0, -1, 1.0, s));
+      SIPF_CK(launch_cols<T>(gh, H, 1, H * nh, 3, S, -1, 1.0, s));
+      // abar^{n-1} = A abar^n + Gop^T gbar;  spec = L^-3 B abar^{n-1}
+      cpx<T>* sc = (cpx<T>*)a->spec;
+      SIPF_CK(launch_adj_spectral<T>(gh, (cpx<T>*)a->abar, sc, H, sp, s));
+      // phibar^{n-2} = F^-1(spec)
+      SIPF_CK(launch_cols<T>(sc, H, 1, H * nh, 1, 0, +1, 1.0, s));
+      SIPF_CK(launch_cols<T>(sc, H, H, nh, 1, 0, +1, 1.0, s));
+      SIPF_CK(launch_rows_c2r<T>(sc, 1, 0, (T*)a->phibar, H, H * H, nullptr, s));
+      a->launches += 8;
+    }
+  }
+  SIPF_CK(cudaEventRecord(a->ev[3], s));
+  double acc[2];
+  SIPF_CK(cudaMemcpyAsync(acc, a->acc, sizeof(acc), cudaMemcpyDeviceToHost, s));
+  std::vector<T> h;
+  if (grad_X0) {
+    h.resize(3 * P);
+    SIPF_CK(cudaMemcpyAsync(h.data(), xb, 3 * P * sizeof(T), cudaMemcpyDeviceToHost, s));
+  }
+  SIPF_CK(cudaStreamSynchronize(s));
+  if (grad_chi) *grad_chi = acc[0];
+  if (grad_mu) *grad_mu = acc[1] * sn / (2.0 * p.mu);
+  if (grad_X0)
+    for (size_t i = 0; i < P; ++i)
+      for (int d = 0; d < 3; ++d) grad_X0[3 * i + d] = (double)h[d * P + i];
+  return SIPF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sipf_adjoint_init(const sipf_params* p, const double* X0, int64_t nsteps, int32_t checkpoint_every, void* stream,
+                      sipf_adjoint** out) {
+  if (!out) return fail(SIPF_EINVAL, "out is NULL");
+  *out = nullptr;
+  int v = validate(p);
+  if (v) return v;
+  if (!X0) return fail(SIPF_EINVAL, "X0 is NULL");
+  if (nsteps < 1 || nsteps > 0xFFFFFFFFLL) return fail(SIPF_EINVAL, "nsteps (1 <= nsteps < 2^32)");
+  if (checkpoint_every < 0) return fail(SIPF_EINVAL, "checkpoint_every (>= 0)");
+  if (!(p->mu > 0)) return fail(SIPF_EINVAL, "the adjoint needs mu > 0 (dJ/dmu goes through sqrt(mu tau))");
+  sipf_adjoint* a = new sipf_adjoint();
+  a->N = nsteps;
+  a->C = checkpoint_every > 0 ? checkpoint_every : kAdjCheckpoint;
+  if (a->C > nsteps) a->C = (int)nsteps;
+  a->nck = (int)((nsteps + a->C - 1) / a->C);
+  a->X0.assign(X0, X0 + 3 * p->P);
+  int r = sipf_init(p, X0, stream, &a->c);
+  if (r) {
+    delete a;
+    return r;
+  }
+  sipf_ctx* c = a->c;
+  const size_t esz = c->esz, P = (size_t)p->P, H3 = (size_t)c->H3(), S = (size_t)c->S();
+  cudaError_t e = cudaMalloc(&a->ckX, (size_t)a->nck * 3 * P * esz);
+  if (e == cudaSuccess) e = cudaMalloc(&a->ckA, (size_t)a->nck * 2 * S * esz);
+  if (e == cudaSuccess) e = cudaMalloc(&a->segX, (size_t)a->C * 3 * P * esz);
+  if (e == cudaSuccess) e = cudaMalloc(&a->segG, (size_t)a->C * 4 * H3 * esz);
+  if (e == cudaSuccess) e = cudaMalloc(&a->XN, 3 * P * esz);
+  if (e == cudaSuccess) e = cudaMalloc(&a->xb, 3 * P * esz);
+  if (e == cudaSuccess) e = cudaMalloc(&a->abar, 2 * S * esz);
+  if (e == cudaSuccess) e = cudaMalloc(&a->spec, 2 * S * esz);
+  if (e == cudaSuccess) e = cudaMalloc(&a->gbar, 3 * H3 * esz);
+  if (e == cudaSuccess) e = cudaMalloc(&a->ghat, 3 * 2 * S * esz);
+  if (e == cudaSuccess) e = cudaMalloc(&a->phibar, H3 * esz);
+  if (e == cudaSuccess) e = cudaMalloc(&a->acc, 2 * sizeof(double));
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&a->ev[i]);
+  if (e != cudaSuccess) {
+    adjoint_free(a);
+    return cuda_fail(e, "sipf_adjoint_init allocation");
+  }
+  *out = a;
+  return SIPF_OK;
+}
+
+int sipf_adjoint_forward(sipf_adjoint* a, double chi, double mu, const double* X0, double* rho_out) {
+  if (!a) return fail(SIPF_EINVAL, "adjoint is NULL");
+  if (!(isfinite(chi) && chi >= 0)) return fail(SIPF_EINVAL, "chi (>= 0)");
+  if (!(isfinite(mu) && mu > 0)) return fail(SIPF_EINVAL, "mu (> 0)");
+  if (X0) {
+    for (int64_t i = 0; i < 3 * a->c->p.P; ++i)
+      if (!isfinite(X0[i])) return fail(SIPF_ENONFINITE, "X0 holds a non-finite coordinate");
+    a->X0.assign(X0, X0 + 3 * a->c->p.P);
+  }
+  a->c->p.chi = chi;
+  a->c->p.mu = mu;
+  a->have_forward = false;
+  int r = DISPATCH(a->c, adjoint_forward_impl, a, rho_out);
+  if (r) return r;
+  return sipf_sync(a->c);
+}
+
+int sipf_adjoint_backward(sipf_adjoint* a, const double* rho_bar, double* grad_chi, double* grad_mu,
+                          double* grad_X0) {
+  if (!a || !rho_bar) return fail(SIPF_EINVAL, "adjoint or rho_bar is NULL");
+  if (!a->have_forward) return fail(SIPF_EINVAL, "sipf_adjoint_backward needs a preceding sipf_adjoint_forward");
+  int r = DISPATCH(a->c, adjoint_backward_impl, a, rho_bar, grad_chi, grad_mu, grad_X0);
+  if (r) return r;
+  return sipf_sync(a->c);
+}
+
+int sipf_adjoint_timing(const sipf_adjoint* a, double* forward_ms, double* backward_ms) {
+  if (!a) return fail(SIPF_EINVAL, "adjoint is NULL");
+  float f = 0.f, b = 0.f;
+  if (forward_ms) {
+    SIPF_CK(cudaEventSynchronize(a->ev[1]));
+    SIPF_CK(cudaEventElapsedTime(&f, a->ev[0], a->ev[1]));
+    *forward_ms = f;
+  }
+  if (backward_ms) {
+    SIPF_CK(cudaEventSynchronize(a->ev[3]));
+    SIPF_CK(cudaEventElapsedTime(&b, a->ev[2], a->ev[3]));
+    *backward_ms = b;
+  }
+  return SIPF_OK;
+}
+
+int64_t sipf_adjoint_kernel_launches(const sipf_adjoint* a) { return a ? a->c->launches + a->launches : -1; }
+
+void sipf_adjoint_destroy(sipf_adjoint* a) { adjoint_free(a); }
+
+}  // extern "C"

@@ -74,6 +74,32 @@ enum { kFieldForward = 1, kFieldSpectral = 2, kFieldInverse = 4, kFieldAll = 7 }
 template <typename T>
 cudaError_t launch_field_batch(const FftRun<T>* runs, int nruns, int H, int stages, cudaStream_t s);
 
+// ---- adjoint launchers (adjoint_kernels.cu) ----------------------------------------
+// One reverse step over all particles in id order (see k_adj_step).
+template <typename T>
+struct AdjArgs {
+  const T* x;          // X^{n-1}, P each (id order)
+  const T* y;
+  const T* z;
+  const T* grad4;      // g^{n-1}: (gx, gy, gz, 0) per node, 4 H^3
+  const T* phibar;     // transpose-of-deposit cotangent grid phibar^{n-1}, H^3
+  T* xb;               // Xbar: 3 planes of P (in: Xbar^n, out: Xbar^{n-1})
+  T* gbar;             // 3 planes of H^3 (accumulated)
+  double* acc;         // [0] += sum tau V.Xbar (dJ/dchi), [1] += dJ/ds terms
+  Geo<T> g;
+  T s_noise, chitau, tau, w_inv_h;
+  uint64_t seed;
+  uint32_t n;          // step index of the forward step being reversed
+  int64_t P;
+  int p2g, g2p, split;
+};
+template <typename T> cudaError_t launch_adj_step(const AdjArgs<T>& a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adj_terminal(const T* x, const T* y, const T* z, int64_t P, const T* phibar, int p2g, T w_inv_h,
+                                Geo<T> g, T* xb, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adj_spectral(const cpx<T>* ghat, cpx<T>* abar, cpx<T>* spec, int H, SpecParams sp, cudaStream_t s);
+
 // ---- particle launchers (particle_kernels.cu) -----------------------------------
 // One work item of the binned kernel: `len` particles of bin `bin` from slot `start`.
 struct ChunkDesc {
