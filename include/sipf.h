@@ -260,11 +260,12 @@ void sipf_batch_destroy(sipf_batch* b);
  * N = nsteps steps of Algorithm 4, the noise held fixed (the same Philox
  * counters as the forward), by reverse mode with hand-written transposes of
  * every operator of the step: the deposit I and the gather I* are each
- * other's transposes (Sec. 3.2, <I rho, f> = <rho, I* f>), the transpose of
- * F_H is L^-3 F_H^-1, pointwise spectral factors turn into their complex
- * conjugates, and particle positions enter through the derivatives of the
- * weight polynomials of Eqs. (2ord) and (4ord).  rho(T) is the deposited
- * density I rho-hat / h^3 of X^N (sipf_density with filtered = 0).
+ * other's transposes (<I rho, f> = <rho, I* f>, the relation stated after
+ * Def. grid2particle in Sec. 3.1), the transpose of F_H is L^-3 F_H^-1,
+ * pointwise spectral factors turn into their complex conjugates, and
+ * particle positions enter through the derivatives of the weight
+ * polynomials of Eqs. (2ord) and (4ord).  rho(T) is the deposited density
+ * I rho-hat / h^3 of X^N (sipf_density with filtered = 0).
  * Memory: the forward keeps X^n (id order) and alpha^n every
  * checkpoint_every steps; the reverse sweep recomputes one segment at a time
  * and holds its X^{n-1} and gradient grids.  chi and mu > 0 may change

@@ -22,7 +22,7 @@ L^-3 F_H^-1, the transpose of F_H^-1 (complex-to-real) is the unnormalised
 forward DFT, a pointwise factor m_q turns into conj(m_q).  Every spectrum in
 the chain is Hermitian, so the half layout carries it without weights.  The
 deposit I and the gather I* are transposes of each other (the relation
-<I rho, f> = <rho, I* f> of Sec. 3.2); the particle-position derivatives come
+<I rho, f> = <rho, I* f> stated after Def. grid2particle, Sec. 3.1); the particle-position derivatives come
 from the derivatives of the weight polynomials of Eqs. (2ord) and (4ord).
 """
 from __future__ import annotations

@@ -41,7 +41,7 @@ def test_weight_derivatives_sum_to_zero(order):
 
 
 def test_deposit_and_gather_are_transposes():
-    """<I w, f> = <w, I* f> (Sec. 3.2) and the position derivative of <I w, f>."""
+    """<I w, f> = <w, I* f> (the relation after Def. grid2particle, Sec. 3.1) and the position derivative of <I w, f>."""
     rng = np.random.default_rng(1)
     H, L, P = 8, 1.3, 50
     X = rng.uniform(-L / 2, L / 2, size=(P, 3))
