@@ -252,6 +252,7 @@ def run_ours(args, world, rank, local):
            "d2h_bytes_per_step": 12 * P_FULL, "steps": Ke,
            "path": "sipf_upload_soa + sipf_step + sipf_download_soa, pinned host SoA float32"}
 
+    extra = None if args.no_extra else run_extra_legs(world, dev, stream, X0)
     batch = None if args.no_batch else run_batch_leg(world, dev, stream)
     adjoint = None if args.no_adjoint else run_adjoint_leg(world, dev, stream)
 
@@ -285,8 +286,66 @@ def run_ours(args, world, rank, local):
             "diagnostics": {k: diag[k] for k in ("mass", "peak", "m2", "ring_radius", "step")},
             "batch": batch,
             "adjoint": adjoint,
+            "sweep": extra,
         }
         print(json.dumps(line), flush=True)
+
+
+def run_extra_legs(world, dev, stream, X0_128, steps=50, warmup=5):
+    """The ring workload at H = 64 and 256 (same particles), the deterministic
+    deposit at H = 128, cuFFT (torch.fft) doing the field solve's transforms
+    at H = 128 for comparison, and this GPU's FP64 FMA rate (the FP64 form's
+    arithmetic bound)."""
+    import torch
+
+    from paper_2512_03452_gb300 import Simulation, _abi, params_from_workload, workloads
+
+    out = {}
+
+    def timed_sim(w, steps, **kw):
+        sim = Simulation(params_from_workload(w, **kw), X0_128, stream=stream.cuda_stream)
+        sim.step(warmup)
+        sim.sync()
+        _abi.sipf_timing_enable(sim.ctx, 1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            sim.step(steps)
+            b.record(stream)
+        b.synchronize()
+        ms = dist_max(a.elapsed_time(b), world, dev)
+        t = _abi.sipf_timing_read(sim.ctx)
+        sim.close()
+        stages = {k: getattr(t, k) / max(t.steps, 1) for k in
+                  ("forward_ms", "spectral_ms", "inverse_ms", "move_ms", "bookkeeping_ms", "deposit_ms")}
+        return {"value": world * w.P * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+                "steps": steps, "stages_ms_per_step": stages}
+
+    for H in (64, 256):
+        out[f"H{H}"] = timed_sim(workloads.torus_ring(H=H, P=P_FULL), steps, precision=32)
+    out["H128_deterministic_deposit"] = timed_sim(workloads.torus_ring(H=H_FULL, P=P_FULL), steps, precision=32,
+                                                  deposit_mode=1)
+    # cuFFT via torch.fft: r2c of the deposit, and three c2r of gradient spectra
+    H = H_FULL
+    g = torch.randn((H, H, H), device=dev, dtype=torch.float32)
+    G = torch.fft.rfftn(g)
+    G3 = torch.stack([G, G, G])
+    for _ in range(3):
+        torch.fft.rfftn(g)
+        torch.fft.irfftn(G3, s=(H, H, H))
+    reps = 50
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        torch.fft.rfftn(g)
+        torch.fft.irfftn(G3, s=(H, H, H))
+    b.record()
+    b.synchronize()
+    out["cufft_H128_ms"] = {"forward_plus_3_inverse": a.elapsed_time(b) / reps,
+                            "note": "torch.fft (cuFFT): rfftn of one H^3 grid + irfftn of three spectra, "
+                                    "transforms only (no spectral update, no filter, no interleaved output)"}
+    out["fp64_fma_gflops"] = _abi.sipf_measure_fp64_fma(stream.cuda_stream)
+    return out
 
 
 def run_batch_leg(world, dev, stream, n_runs=256, steps=64, warmup=32):
@@ -318,6 +377,7 @@ def run_batch_leg(world, dev, stream, n_runs=256, steps=64, warmup=32):
     with Batch(params, X0s, stream=stream.cuda_stream) as b:
         b.step(warmup)
         b.sync()
+        out["autotune"] = b.autotune(3)
         k0 = _abi.sipf_batch_kernel_launches(b.handle)
         ms = timed(b.step, steps)
         out["gpu_launches_per_step"] = (_abi.sipf_batch_kernel_launches(b.handle) - k0) / steps
@@ -420,6 +480,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
+    ap.add_argument("--no-extra", action="store_true", help="skip the H sweep, deterministic, cuFFT and FP64 legs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     world, rank, local = dist_init(args)

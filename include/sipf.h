@@ -231,6 +231,30 @@ int sipf_batch_init(int32_t nruns, const sipf_params* params, const double* cons
  * stream).  The step index n is shared by all runs and kept on the device. */
 int sipf_batch_step(sipf_batch* b, int64_t nsteps);
 
+/* Launch shapes chosen by sipf_batch_autotune, per distinct grid size H
+ * (groups in order of first appearance) and for the particle passes. */
+typedef struct sipf_batch_tuning {
+  int32_t ngroups;
+  int32_t H[4];
+  int32_t cols_tile[4];           /* pencils per block of the y passes: 8, 16, 32   */
+  int32_t xpass_tile[4];          /* pencils per block of the fused x pass: 4, 8, 16 */
+  int32_t rows_blocks_per_sm[4];  /* blocks per SM shared by the row passes          */
+  int32_t move_blocks_per_sm;     /* move + re-bin blocks per SM (0: occupancy limit) */
+  int32_t deposit_blocks_per_sm;  /* deposit blocks per SM (0: occupancy limit)       */
+  double field_ms[4];             /* best device ms per step of each group's field solve */
+  double move_ms;                 /* best device ms per step: move, chunk lists, run prefix */
+  double deposit_ms;              /* best device ms per step: deposit                   */
+  int64_t steps_used;             /* steps the runs advanced while tuning               */
+} sipf_batch_tuning;
+
+/* Autotuner of the batch's tile and block shapes: coordinate descent over the
+ * candidates above, each timed with CUDA events on steps_per_trial (>= 2)
+ * real steps of the batch (the first step of a trial is not timed).  Shapes
+ * do not change results, so the runs advance by out->steps_used steps (about
+ * steps_per_trial x (9 per group + 9)).  Later steps use the chosen shapes;
+ * out may be NULL.  Synchronises. */
+int sipf_batch_autotune(sipf_batch* b, int32_t steps_per_trial, sipf_batch_tuning* out);
+
 /* enable = 0: issue every step's launches directly instead of replaying the
  * recorded 32-step graph (same results; for timing the graph's benefit). */
 int sipf_batch_use_graph(sipf_batch* b, int enable);
@@ -299,6 +323,11 @@ int sipf_adjoint_timing(const sipf_adjoint* a, double* forward_ms, double* backw
 int64_t sipf_adjoint_kernel_launches(const sipf_adjoint* a);
 
 void sipf_adjoint_destroy(sipf_adjoint* a);
+
+/* Measure this GPU's FP64 fused multiply-add throughput (GFLOP/s, 2 per FMA)
+ * with a throughput-bound kernel of independent FMA chains on `stream`;
+ * the FP64 form's arithmetic bound.  Synchronises. */
+int sipf_measure_fp64_fma(void* stream, double* gflops);
 
 /* ---- stateless operators on caller-owned device memory ------------------
  * precision: 32 or 64 (element type float / double of every real array).

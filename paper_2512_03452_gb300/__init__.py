@@ -134,6 +134,17 @@ class Batch:
     def use_graph(self, enable: bool):
         _abi.sipf_batch_use_graph(self.handle, int(enable))
 
+    def autotune(self, steps_per_trial: int = 3) -> dict:
+        """Choose tile and block shapes by timing real steps (the runs advance by
+        the returned steps_used); returns the choices and best times."""
+        t = _abi.sipf_batch_autotune(self.handle, steps_per_trial)
+        g = t.ngroups
+        return {"groups": [{"H": t.H[i], "cols_tile": t.cols_tile[i], "xpass_tile": t.xpass_tile[i],
+                            "rows_blocks_per_sm": t.rows_blocks_per_sm[i], "field_ms": t.field_ms[i]}
+                           for i in range(g)],
+                "move_blocks_per_sm": t.move_blocks_per_sm, "deposit_blocks_per_sm": t.deposit_blocks_per_sm,
+                "move_ms": t.move_ms, "deposit_ms": t.deposit_ms, "steps_used": t.steps_used}
+
     @property
     def n(self) -> int:
         return _abi.sipf_batch_current_step(self.handle)

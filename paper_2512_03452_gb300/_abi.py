@@ -55,6 +55,14 @@ class sipf_timing(ctypes.Structure):
     ]
 
 
+class sipf_batch_tuning(ctypes.Structure):
+    _fields_ = [("ngroups", ctypes.c_int32), ("H", ctypes.c_int32 * 4), ("cols_tile", ctypes.c_int32 * 4),
+                ("xpass_tile", ctypes.c_int32 * 4), ("rows_blocks_per_sm", ctypes.c_int32 * 4),
+                ("move_blocks_per_sm", ctypes.c_int32), ("deposit_blocks_per_sm", ctypes.c_int32),
+                ("field_ms", ctypes.c_double * 4), ("move_ms", ctypes.c_double), ("deposit_ms", ctypes.c_double),
+                ("steps_used", ctypes.c_int64)]
+
+
 class SipfError(RuntimeError):
     def __init__(self, code: int, where: str, msg: str):
         super().__init__(f"{where} failed ({code}: {msg})")
@@ -102,6 +110,7 @@ _SIGS = {
                                        ctypes.POINTER(_P)]),
     "sipf_batch_step": (ctypes.c_int, [_P, ctypes.c_int64]),
     "sipf_batch_use_graph": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sipf_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(sipf_batch_tuning)]),
     "sipf_batch_current_step": (ctypes.c_int64, [_P]),
     "sipf_batch_kernel_launches": (ctypes.c_int64, [_P]),
     "sipf_batch_positions": (ctypes.c_int, [_P, ctypes.c_int32, _D]),
@@ -116,6 +125,7 @@ _SIGS = {
     "sipf_adjoint_timing": (ctypes.c_int, [_P, _D, _D]),
     "sipf_adjoint_kernel_launches": (ctypes.c_int64, [_P]),
     "sipf_adjoint_destroy": (None, [_P]),
+    "sipf_measure_fp64_fma": (ctypes.c_int, [_P, _D]),
 }
 
 
@@ -304,6 +314,12 @@ def sipf_batch_step(b: int, nsteps: int) -> None:
     _check(load().sipf_batch_step(_P(b), int(nsteps)), "sipf_batch_step")
 
 
+def sipf_batch_autotune(b: int, steps_per_trial: int = 3) -> sipf_batch_tuning:
+    t = sipf_batch_tuning()
+    _check(load().sipf_batch_autotune(_P(b), int(steps_per_trial), ctypes.byref(t)), "sipf_batch_autotune")
+    return t
+
+
 def sipf_batch_use_graph(b: int, enable: int) -> None:
     _check(load().sipf_batch_use_graph(_P(b), int(enable)), "sipf_batch_use_graph")
 
@@ -379,3 +395,9 @@ def sipf_adjoint_kernel_launches(a: int) -> int:
 
 def sipf_adjoint_destroy(a: int) -> None:
     load().sipf_adjoint_destroy(_P(a))
+
+
+def sipf_measure_fp64_fma(stream: int = 0) -> float:
+    g = ctypes.c_double()
+    _check(load().sipf_measure_fp64_fma(_P(stream), ctypes.byref(g)), "sipf_measure_fp64_fma")
+    return g.value

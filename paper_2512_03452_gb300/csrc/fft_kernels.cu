@@ -1023,31 +1023,77 @@ cudaError_t launch_rows_c2r(const cpx<T>* in, int ncomp, size_t comp_stride, T* 
   return cudaGetLastError();
 }
 
-template <typename T, int E>
-static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, cudaStream_t s) {
+constexpr size_t kMaxSmem = 227 * 1024;
+
+template <typename T, int E, int BC>
+static size_t cols_smem() {
+  return (kNmax + (size_t)32 * E * (BC + 1)) * sizeof(cpx<T>);
+}
+template <typename T, int E, int SBC>
+static size_t spectral_smem() {
+  return (kNmax + (size_t)32 * E * (4 * SBC + 1)) * sizeof(cpx<T>);
+}
+
+template <typename T, int E, int DIR, int BC>
+static cudaError_t kwb_cols_launch(const FftRun<T>* runs, int nruns, int ncomp, cudaStream_t s) {
   constexpr int N = 32 * E, NHH = N / 2 + 1;
-  constexpr int BC = 16;
-  constexpr int SBC = (sizeof(T) == 8 && E == 8) ? 4 : ((sizeof(T) == 8 || E == 8) ? 8 : 16);
+  const size_t smc = cols_smem<T, E, BC>();
+  if (smc > kMaxSmem) return cudaErrorInvalidValue;
   cudaError_t e;
-  const int rblocks = max(1, min(152 * 8 / max(nruns, 1), (N * N / 2 + 7) / 8));
-  const size_t smc = (kNmax + (size_t)N * (BC + 1)) * sizeof(cpx<T>);
+  if ((e = set_smem(kwb_cols<T, E, DIR, BC>, smc)) != cudaSuccess) return e;
+  kwb_cols<T, E, DIR, BC><<<dim3((NHH + BC - 1) / BC, N, nruns * ncomp), 256, smc, s>>>(runs, ncomp);
+  return cudaGetLastError();
+}
+
+template <typename T, int E, int DIR>
+static cudaError_t kwb_cols_bc(const FftRun<T>* runs, int nruns, int ncomp, int bc, cudaStream_t s) {
+  switch (bc) {
+    case 8: return kwb_cols_launch<T, E, DIR, 8>(runs, nruns, ncomp, s);
+    case 32: return kwb_cols_launch<T, E, DIR, 32>(runs, nruns, ncomp, s);
+    default: return kwb_cols_launch<T, E, DIR, 16>(runs, nruns, ncomp, s);
+  }
+}
+
+template <typename T, int E, int SBC>
+static cudaError_t kwb_spectral_launch(const FftRun<T>* runs, int nruns, cudaStream_t s) {
+  constexpr int N = 32 * E, NHH = N / 2 + 1;
+  const size_t sms = spectral_smem<T, E, SBC>();
+  if (sms > kMaxSmem) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if ((e = set_smem(kwb_spectral_x<T, E, SBC>, sms)) != cudaSuccess) return e;
+  kwb_spectral_x<T, E, SBC><<<dim3((N * NHH + SBC - 1) / SBC, nruns), 256, sms, s>>>(runs);
+  return cudaGetLastError();
+}
+
+// Default x-pass tile: as wide as shared memory comfortably allows.
+template <typename T, int E> static int default_sbc() {
+  return (sizeof(T) == 8 && E == 8) ? 4 : ((sizeof(T) == 8 || E == 8) ? 8 : 16);
+}
+
+template <typename T, int E>
+static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, const FieldTune& tune,
+                                 cudaStream_t s) {
+  constexpr int N = 32 * E;
+  cudaError_t e;
+  const int rows_budget = 152 * (tune.rows_per_sm > 0 ? tune.rows_per_sm : 8);
+  const int rblocks = max(1, min(rows_budget / max(nruns, 1), (N * N / 2 + 7) / 8));
+  const int bc = tune.bc > 0 ? tune.bc : 16;
+  const int sbc = tune.sbc > 0 ? tune.sbc : default_sbc<T, E>();
   if (stages & kFieldForward) {
     kwb_rows_r2c<T, E><<<dim3(rblocks, nruns), 256, 0, s>>>(runs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = set_smem(kwb_cols<T, E, -1, BC>, smc)) != cudaSuccess) return e;
-    kwb_cols<T, E, -1, BC><<<dim3((NHH + BC - 1) / BC, N, nruns), 256, smc, s>>>(runs, 1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = kwb_cols_bc<T, E, -1>(runs, nruns, 1, bc, s)) != cudaSuccess) return e;
   }
   if (stages & kFieldSpectral) {
-    const size_t sms = (kNmax + (size_t)N * (4 * SBC + 1)) * sizeof(cpx<T>);
-    if ((e = set_smem(kwb_spectral_x<T, E, SBC>, sms)) != cudaSuccess) return e;
-    kwb_spectral_x<T, E, SBC><<<dim3((N * NHH + SBC - 1) / SBC, nruns), 256, sms, s>>>(runs);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    switch (sbc) {
+      case 4: e = kwb_spectral_launch<T, E, 4>(runs, nruns, s); break;
+      case 8: e = kwb_spectral_launch<T, E, 8>(runs, nruns, s); break;
+      default: e = kwb_spectral_launch<T, E, 16>(runs, nruns, s); break;
+    }
+    if (e != cudaSuccess) return e;
   }
   if (stages & kFieldInverse) {
-    if ((e = set_smem(kwb_cols<T, E, +1, BC>, smc)) != cudaSuccess) return e;
-    kwb_cols<T, E, +1, BC><<<dim3((NHH + BC - 1) / BC, N, nruns * 3), 256, smc, s>>>(runs, 3);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = kwb_cols_bc<T, E, +1>(runs, nruns, 3, bc, s)) != cudaSuccess) return e;
     const size_t smr = (kNmax + (size_t)8 * N) * sizeof(cpx<T>) + (size_t)8 * 2 * N * 4 * sizeof(T);
     if ((e = set_smem(kwb_rows_c2r<T, E>, smr)) != cudaSuccess) return e;
     kwb_rows_c2r<T, E><<<dim3(rblocks, nruns), 256, smr, s>>>(runs);
@@ -1056,14 +1102,33 @@ static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, c
   return cudaSuccess;
 }
 
+template <typename T, int E> static bool field_tune_valid_e(const FieldTune& t) {
+  const int bc = t.bc > 0 ? t.bc : 16, sbc = t.sbc > 0 ? t.sbc : default_sbc<T, E>();
+  size_t c = bc == 8 ? cols_smem<T, E, 8>() : bc == 32 ? cols_smem<T, E, 32>() : cols_smem<T, E, 16>();
+  size_t x = sbc == 4 ? spectral_smem<T, E, 4>() : sbc == 8 ? spectral_smem<T, E, 8>() : spectral_smem<T, E, 16>();
+  return (bc == 8 || bc == 16 || bc == 32) && (sbc == 4 || sbc == 8 || sbc == 16) && c <= kMaxSmem &&
+         x <= kMaxSmem && t.rows_per_sm >= 0 && t.rows_per_sm <= 32;
+}
+
+template <typename T> bool field_tune_valid(int H, const FieldTune& t) {
+  switch (H) {
+    case 32: return field_tune_valid_e<T, 1>(t);
+    case 64: return field_tune_valid_e<T, 2>(t);
+    case 128: return field_tune_valid_e<T, 4>(t);
+    case 256: return field_tune_valid_e<T, 8>(t);
+  }
+  return false;
+}
+
 template <typename T>
-cudaError_t launch_field_batch(const FftRun<T>* runs, int nruns, int H, int stages, cudaStream_t s) {
+cudaError_t launch_field_batch(const FftRun<T>* runs, int nruns, int H, int stages, cudaStream_t s,
+                               const FieldTune& tune) {
   if (nruns <= 0) return cudaSuccess;
   switch (H) {
-    case 32: return field_batch_e<T, 1>(runs, nruns, stages, s);
-    case 64: return field_batch_e<T, 2>(runs, nruns, stages, s);
-    case 128: return field_batch_e<T, 4>(runs, nruns, stages, s);
-    case 256: return field_batch_e<T, 8>(runs, nruns, stages, s);
+    case 32: return field_batch_e<T, 1>(runs, nruns, stages, tune, s);
+    case 64: return field_batch_e<T, 2>(runs, nruns, stages, tune, s);
+    case 128: return field_batch_e<T, 4>(runs, nruns, stages, tune, s);
+    case 256: return field_batch_e<T, 8>(runs, nruns, stages, tune, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -1075,7 +1140,8 @@ cudaError_t launch_field_batch(const FftRun<T>* runs, int nruns, int H, int stag
   template cudaError_t launch_spectral_x<T>(const cpx<T>*, cpx<T>*, cpx<T>*, int, SpecParams, int, double*,  \
                                             cudaStream_t);                                                  \
   template cudaError_t launch_rows_c2r<T>(const cpx<T>*, int, size_t, T*, int, int, double*, cudaStream_t);     \
-  template cudaError_t launch_field_batch<T>(const FftRun<T>*, int, int, int, cudaStream_t);
+  template cudaError_t launch_field_batch<T>(const FftRun<T>*, int, int, int, cudaStream_t, const FieldTune&); \
+  template bool field_tune_valid<T>(int, const FieldTune&);
 SIPF_INST(float)
 SIPF_INST(double)
 #undef SIPF_INST

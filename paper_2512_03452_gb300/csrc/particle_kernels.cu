@@ -143,6 +143,37 @@ constexpr int kWinSlots = kWin * kWin * kWin;
 constexpr int kReplicas = 4;                  // window copies (lane mod 4)
 constexpr int kChunk = 4096;                  // particles per work item
 
+// Add the shared window (all replicas) to the grid and clear it: consecutive
+// threads walk consecutive slots along the fastest axis, so the reductions of
+// a warp hit contiguous nodes.  (ox, oy, oz): node of slot (0,0,0).
+template <typename T, bool FIXED, bool WHOLE>
+__device__ __forceinline__ void window_flush(const BinArgs<T>& a, typename WinType<T>::type* win, int wslots, int ox,
+                                             int oy, int oz, T wwin) {
+  using A = typename WinType<T>::type;
+  const int H = a.g.H, mask = a.g.mask;
+  const T unit = a.wmass / wwin;   // M0/P * 2^-K
+  for (int sidx = threadIdx.x; sidx < wslots; sidx += blockDim.x) {
+    A v = win[sidx];
+    win[sidx] = A(0);
+#pragma unroll
+    for (int r = 1; r < kReplicas; ++r) {
+      v += win[r * wslots + sidx];
+      win[r * wslots + sidx] = A(0);
+    }
+    if (v != A(0)) {
+      int gi;
+      if (WHOLE) {
+        gi = sidx;
+      } else {
+        const int c = sidx % kWin, b = (sidx / kWin) % kWin, aa = sidx / (kWin * kWin);
+        gi = (((ox + aa) & mask) * H + ((oy + b) & mask)) * H + ((oz + c) & mask);
+      }
+      if (FIXED) atomicAdd(static_cast<unsigned long long*>(a.phi) + gi, (unsigned long long)(long long)v);
+      else atomicAdd(static_cast<T*>(a.phi) + gi, (T)v * unit);
+    }
+  }
+}
+
 // One work item of k_binned (deposit and/or re-bin without a move).
 template <typename T, bool FIXED, bool MOVE, bool DEPOSIT, bool REBIN, bool WHOLE>
 __device__ __forceinline__ void binned_chunk(const BinArgs<T>& a, const ChunkDesc& cur,
@@ -287,29 +318,7 @@ __device__ __forceinline__ void binned_chunk(const BinArgs<T>& a, const ChunkDes
   }
   if (DEPOSIT && has_win) {
     __syncthreads();
-    // add the window to the grid: consecutive threads walk consecutive slots
-    // along the fastest axis, so the reductions of a warp hit contiguous nodes
-    const T unit = a.wmass / wwin;   // M0/P * 2^-K
-    for (int sidx = threadIdx.x; sidx < wslots; sidx += blockDim.x) {
-      A v = win[sidx];
-      win[sidx] = A(0);
-#pragma unroll
-      for (int r = 1; r < kReplicas; ++r) {
-        v += win[r * wslots + sidx];
-        win[r * wslots + sidx] = A(0);
-      }
-      if (v != A(0)) {
-        int gi;
-        if (WHOLE) {
-          gi = sidx;
-        } else {
-          const int c = sidx % kWin, b = (sidx / kWin) % kWin, aa = sidx / (kWin * kWin);
-          gi = (((ox + aa) & mask) * H + ((oy + b) & mask)) * H + ((oz + c) & mask);
-        }
-        if (FIXED) atomicAdd(static_cast<unsigned long long*>(a.phi) + gi, (unsigned long long)(long long)v);
-        else atomicAdd(static_cast<T*>(a.phi) + gi, (T)v * unit);
-      }
-    }
+    window_flush<T, FIXED, WHOLE>(a, win, wslots, ox, oy, oz, wwin);
   }
 }
 
@@ -416,7 +425,8 @@ struct MoveSmem {
   __align__(16) T z[R];
   __align__(16) uint32_t id[R];
   int meta[R];        // neighbour slot (0..124) | rank << 7, or -1 - tile for far moves
-  int cnt[kNbr], base[kNbr], tile[kNbr];
+  int cnt[kNbr], base[kNbr], tile[kNbr], cap[kNbr];
+  long long gbase[kNbr];   // first slot of each destination bin
   __align__(8) uint64_t bar;
   int abort;
 };
@@ -507,27 +517,36 @@ __device__ __forceinline__ void move_chunk(const BinArgs<T>& a, const ChunkDesc&
       sm.meta[i] = meta;
     }
     __syncthreads();
-    // 2. one reservation per destination tile
+    // 2. one reservation per destination tile (with its capacity and first slot)
     for (int k = threadIdx.x; k < kNbr; k += blockDim.x) {
       const int c = sm.cnt[k];
-      if (c) sm.base[k] = atomicAdd(a.dst_cursor + sm.tile[k], c);
+      if (c) {
+        const int t = sm.tile[k];
+        sm.base[k] = atomicAdd(a.dst_cursor + t, c);
+        sm.cap[k] = a.dst_cap[t];
+        sm.gbase[k] = a.dst_base[t];
+      }
     }
     __syncthreads();
     // 3. write out
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
       const int meta = sm.meta[i];
-      int t, r;
+      int r, cap;
+      long long gb;
       if (meta >= 0) {
         const int k = meta & 127;
-        t = sm.tile[k];
         r = sm.base[k] + (meta >> 7);
+        cap = sm.cap[k];
+        gb = sm.gbase[k];
       } else {
-        t = -1 - meta;
+        const int t = -1 - meta;
         r = atomicAdd(a.dst_cursor + t, 1);
+        cap = a.dst_cap[t];
+        gb = a.dst_base[t];
       }
       long long slot;
-      if (r < a.dst_cap[t]) {
-        slot = a.dst_base[t] + r;
+      if (r < cap) {
+        slot = gb + r;
       } else {
         const int o = atomicAdd(a.dst_cursor + a.NT, 1);
         slot = o < a.dst_cap[a.NT] ? a.dst_base[a.NT] + o : -1;
@@ -626,6 +645,30 @@ template <typename T> cudaError_t launch_move(const BinArgs<T>& a, cudaStream_t 
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_move<T>, 256, 0)) != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   k_move<T><<<sms * per_sm, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 FMA throughput probe (the FP64 form's ALU bound): eight independent
+// dependency chains per thread, `iters` fused multiply-adds each; the result
+// is stored only if it is never reached, so nothing is optimised away.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_fp64_fma(int iters, double a, double b, double* sink) {
+  double v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = (double)(threadIdx.x + k) * 1e-9;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = fma(v[k], a, b);
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t += v[k];
+  if (t == 12345.678) *sink = t;
+}
+
+cudaError_t launch_fp64_fma(int blocks, int iters, double* sink, cudaStream_t s) {
+  k_fp64_fma<<<blocks, 256, 0, s>>>(iters, 0.999999, 1e-7, sink);
   return cudaGetLastError();
 }
 
@@ -1063,13 +1106,14 @@ cudaError_t launch_chunk_list(const int* cursor, const int* cap, const long long
 
 template <typename T>
 cudaError_t launch_move_batch(const BinArgs<T>* table, const long long* prefix, int nruns, unsigned long long* work,
-                              const uint32_t* step, bool move, cudaStream_t s) {
+                              const uint32_t* step, bool move, cudaStream_t s, int blocks_per_sm) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e;
   auto k = move ? k_move_batch<T, true> : k_move_batch<T, false>;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, 0)) != cudaSuccess) return e;
+  if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
   if (per_sm < 1) per_sm = 1;
   k<<<sms * per_sm, 256, 0, s>>>(table, prefix, nruns, work, step);
   return cudaGetLastError();
@@ -1077,7 +1121,7 @@ cudaError_t launch_move_batch(const BinArgs<T>* table, const long long* prefix, 
 
 template <typename T>
 cudaError_t launch_deposit_batch(const BinArgs<T>* table, const long long* prefix, int nruns,
-                                 unsigned long long* work, bool fixed, cudaStream_t s) {
+                                 unsigned long long* work, bool fixed, cudaStream_t s, int blocks_per_sm) {
   const size_t smem = (size_t)kReplicas * kWinSlots * sizeof(typename WinType<T>::type);
   auto k = fixed ? k_deposit_batch<T, true> : k_deposit_batch<T, false>;
   cudaError_t e;
@@ -1087,6 +1131,7 @@ cudaError_t launch_deposit_batch(const BinArgs<T>* table, const long long* prefi
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem)) != cudaSuccess) return e;
+  if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
   if (per_sm < 1) per_sm = 1;
   k<<<sms * per_sm, 256, smem, s>>>(table, prefix, nruns, work);
   return cudaGetLastError();
@@ -1201,9 +1246,9 @@ template <typename T> cudaError_t launch_alpha_energy(const cpx<T>* alpha, int H
   template cudaError_t launch_binned<T>(const BinArgs<T>&, int, int, int, cudaStream_t);                       \
   template cudaError_t launch_move<T>(const BinArgs<T>&, cudaStream_t);                                       \
   template cudaError_t launch_move_batch<T>(const BinArgs<T>*, const long long*, int, unsigned long long*,     \
-                                            const uint32_t*, bool, cudaStream_t);                            \
+                                            const uint32_t*, bool, cudaStream_t, int);                       \
   template cudaError_t launch_deposit_batch<T>(const BinArgs<T>*, const long long*, int, unsigned long long*,  \
-                                               bool, cudaStream_t);                                           \
+                                               bool, cudaStream_t, int);                                      \
   template cudaError_t launch_tile_hist<T>(const T*, const T*, const T*, int64_t, Geo<T>, int, int, int, int*, \
                                            cudaStream_t);                                                    \
   template bool launch_rebin_plain<T>(const T*, const T*, const T*, const uint32_t*, int64_t, Geo<T>, int, int, \

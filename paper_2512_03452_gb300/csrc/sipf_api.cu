@@ -998,6 +998,11 @@ struct sipf_batch {
   cudaGraphExec_t graph = nullptr;
   int graph_cur = -1, graph_lc = -1, graph_since = -1;
   int64_t launches = 0;
+  // launch shapes (autotuned) and per-phase events of the last issued step
+  std::vector<FieldTune> field_tune;
+  int move_bps = 0, dep_bps = 0;
+  bool record_phases = false;
+  std::vector<cudaEvent_t> ev;   // 2 per group, then move pair, deposit pair
 };
 
 namespace {
@@ -1022,6 +1027,7 @@ void batch_free(sipf_batch* b) {
   cudaFree(b->prefix);
   cudaFree(b->work);
   cudaFree(b->step);
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
   for (sipf_ctx* c : b->runs) free_ctx(c);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -1077,18 +1083,27 @@ template <typename T> int batch_tables(sipf_batch* b) {
 template <typename T> int batch_issue_step(sipf_batch* b) {
   const int R = b->nruns;
   cudaStream_t s = b->stream;
-  for (int g = 0; g < (int)b->group_H.size(); ++g)
-    SIPF_CK(launch_field_batch<T>((const FftRun<T>*)b->fft_tab[g], b->group_n[g], b->group_H[g], kFieldAll, s));
+  const int G = (int)b->group_H.size();
+  auto mark = [&](int i) -> cudaError_t { return b->record_phases ? cudaEventRecord(b->ev[i], s) : cudaSuccess; };
+  for (int g = 0; g < G; ++g) {
+    SIPF_CK(mark(2 * g));
+    SIPF_CK(launch_field_batch<T>((const FftRun<T>*)b->fft_tab[g], b->group_n[g], b->group_H[g], kFieldAll, s,
+                                  b->field_tune[g]));
+    SIPF_CK(mark(2 * g + 1));
+  }
+  SIPF_CK(mark(2 * G));
   SIPF_CK(cudaMemsetAsync(b->work, 0, sizeof(unsigned long long), s));
-  SIPF_CK(launch_move_batch<T>((const BinArgs<T>*)b->move_tab[b->cur][b->lc], b->prefix, R, b->work, b->step, true, s));
+  SIPF_CK(launch_move_batch<T>((const BinArgs<T>*)b->move_tab[b->cur][b->lc], b->prefix, R, b->work, b->step, true, s,
+                               b->move_bps));
   SIPF_CK(launch_chunk_list_batch(b->cl_tab[1 - b->cur][b->lc], R, s));
   SIPF_CK(launch_run_prefix(b->cl_tab[1 - b->cur][b->lc], R, b->prefix, b->work, b->step, 1, s));
+  SIPF_CK(mark(2 * G + 1));
   b->launches += 5 * (int64_t)b->group_H.size() + 3;
   b->cur = 1 - b->cur;
   if (++b->since >= kBatchResort) {
     SIPF_CK(launch_layout_batch(b->ly_tab[b->cur][1 - b->lc], R, s));
     SIPF_CK(launch_move_batch<T>((const BinArgs<T>*)b->rebin_tab[b->cur][b->lc], b->prefix, R, b->work, b->step, false,
-                                 s));
+                                 s, b->move_bps));
     SIPF_CK(launch_chunk_list_batch(b->cl_tab[1 - b->cur][1 - b->lc], R, s));
     SIPF_CK(launch_run_prefix(b->cl_tab[1 - b->cur][1 - b->lc], R, b->prefix, b->work, b->step, 0, s));
     b->launches += 4;
@@ -1096,7 +1111,10 @@ template <typename T> int batch_issue_step(sipf_batch* b) {
     b->lc = 1 - b->lc;
     b->since = 0;
   }
-  SIPF_CK(launch_deposit_batch<T>((const BinArgs<T>*)b->dep_tab[b->cur][b->lc], b->prefix, R, b->work, b->fixed, s));
+  SIPF_CK(mark(2 * G + 2));
+  SIPF_CK(launch_deposit_batch<T>((const BinArgs<T>*)b->dep_tab[b->cur][b->lc], b->prefix, R, b->work, b->fixed, s,
+                                  b->dep_bps));
+  SIPF_CK(mark(2 * G + 3));
   b->launches += 1;
   b->n += 1;
   return SIPF_OK;
@@ -1145,6 +1163,104 @@ template <typename T> int batch_step_impl(sipf_batch* b, int64_t nsteps) {
       if (r) return r;
       nsteps -= 1;
     }
+  }
+  return SIPF_OK;
+}
+
+// Autotuner: coordinate descent over the launch shapes, each candidate timed
+// on real steps of the batch (the first step of a trial warms the shapes, the
+// fastest of the others counts).  Shapes do not change results, so the runs
+// simply advance by the steps spent here.
+template <typename T> int batch_autotune_impl(sipf_batch* b, int trial, sipf_batch_tuning* out) {
+  const int G = (int)b->group_H.size();
+  const int64_t n0 = b->n;
+  b->record_phases = true;
+  auto measure = [&](int e0, int e1, float* ms) -> int {
+    float best = 3.0e38f;
+    for (int i = 0; i < trial; ++i) {
+      int r = batch_issue_step<T>(b);
+      if (r) return r;
+      if (i == 0) continue;
+      SIPF_CK(cudaEventSynchronize(b->ev[e1]));
+      float t = 0.f;
+      SIPF_CK(cudaEventElapsedTime(&t, b->ev[e0], b->ev[e1]));
+      best = std::min(best, t);
+    }
+    *ms = best;
+    return SIPF_OK;
+  };
+  std::vector<float> field_ms(G, 0.f);
+  for (int g = 0; g < G; ++g) {
+    FieldTune best_t = b->field_tune[g];
+    float best = 3.0e38f;
+    for (int dim = 0; dim < 3; ++dim) {
+      static const int cand[3][3] = {{8, 16, 32}, {4, 8, 16}, {4, 8, 16}};
+      for (int ci = 0; ci < 3; ++ci) {
+        FieldTune t = best_t;
+        (dim == 0 ? t.bc : dim == 1 ? t.sbc : t.rows_per_sm) = cand[dim][ci];
+        if (!field_tune_valid<T>(b->group_H[g], t)) continue;
+        b->field_tune[g] = t;
+        float ms = 0.f;
+        int r = measure(2 * g, 2 * g + 1, &ms);
+        if (r) return r;
+        if (ms < best) {
+          best = ms;
+          best_t = t;
+        }
+      }
+      b->field_tune[g] = best_t;
+    }
+    field_ms[g] = best;
+  }
+  float move_ms = 3.0e38f, dep_ms = 3.0e38f;
+  {
+    int best_c = b->move_bps;
+    for (int c : {1, 2, 3, 0}) {
+      b->move_bps = c;
+      float ms = 0.f;
+      int r = measure(2 * G, 2 * G + 1, &ms);
+      if (r) return r;
+      if (ms < move_ms) {
+        move_ms = ms;
+        best_c = c;
+      }
+    }
+    b->move_bps = best_c;
+  }
+  {
+    int best_c = b->dep_bps;
+    for (int c : {1, 2, 3, 4, 0}) {
+      b->dep_bps = c;
+      float ms = 0.f;
+      int r = measure(2 * G + 2, 2 * G + 3, &ms);
+      if (r) return r;
+      if (ms < dep_ms) {
+        dep_ms = ms;
+        best_c = c;
+      }
+    }
+    b->dep_bps = best_c;
+  }
+  b->record_phases = false;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  if (out) {
+    memset(out, 0, sizeof(*out));
+    out->ngroups = G;
+    for (int g = 0; g < G && g < 4; ++g) {
+      out->H[g] = b->group_H[g];
+      out->cols_tile[g] = b->field_tune[g].bc;
+      out->xpass_tile[g] = b->field_tune[g].sbc;
+      out->rows_blocks_per_sm[g] = b->field_tune[g].rows_per_sm;
+      out->field_ms[g] = field_ms[g];
+    }
+    out->move_blocks_per_sm = b->move_bps;
+    out->deposit_blocks_per_sm = b->dep_bps;
+    out->move_ms = move_ms;
+    out->deposit_ms = dep_ms;
+    out->steps_used = b->n - n0;
   }
   return SIPF_OK;
 }
@@ -1214,7 +1330,13 @@ int sipf_batch_init(int32_t nruns, const sipf_params* params, const double* cons
       b->group_n.push_back(1);
     }
   }
+  b->field_tune.assign(b->group_H.size(), FieldTune{});
   cudaError_t e = cudaMalloc(&b->prefix, (nruns + 1) * sizeof(long long));
+  for (size_t i = 0; i < 2 * b->group_H.size() + 4 && e == cudaSuccess; ++i) {
+    cudaEvent_t ev = nullptr;
+    e = cudaEventCreate(&ev);
+    if (e == cudaSuccess) b->ev.push_back(ev);
+  }
   if (e == cudaSuccess) e = cudaMalloc(&b->work, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&b->step, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemsetAsync(b->step, 0, sizeof(uint32_t), b->stream);
@@ -1243,6 +1365,17 @@ int sipf_batch_step(sipf_batch* b, int64_t nsteps) {
   if (nsteps < 0) return fail(SIPF_EINVAL, "nsteps < 0");
   if (b->n + nsteps > 0xFFFFFFFFLL) return fail(SIPF_EINVAL, "step counter would exceed 2^32 - 1");
   return b->precision == 64 ? batch_step_impl<double>(b, nsteps) : batch_step_impl<float>(b, nsteps);
+}
+
+int sipf_batch_autotune(sipf_batch* b, int32_t steps_per_trial, sipf_batch_tuning* out) {
+  if (!b) return fail(SIPF_EINVAL, "batch is NULL");
+  if (steps_per_trial < 2) return fail(SIPF_EINVAL, "steps_per_trial (>= 2)");
+  const int64_t most = (int64_t)steps_per_trial * (9 * (int64_t)b->group_H.size() + 9);
+  if (b->n + most > 0xFFFFFFFFLL) return fail(SIPF_EINVAL, "step counter would exceed 2^32 - 1");
+  int r = b->precision == 64 ? batch_autotune_impl<double>(b, steps_per_trial, out)
+                             : batch_autotune_impl<float>(b, steps_per_trial, out);
+  b->record_phases = false;
+  return r;
 }
 
 int sipf_batch_use_graph(sipf_batch* b, int enable) {
@@ -1564,6 +1697,33 @@ int sipf_adjoint_timing(const sipf_adjoint* a, double* forward_ms, double* backw
     SIPF_CK(cudaEventElapsedTime(&b, a->ev[2], a->ev[3]));
     *backward_ms = b;
   }
+  return SIPF_OK;
+}
+
+int sipf_measure_fp64_fma(void* stream, double* gflops) {
+  if (!gflops) return fail(SIPF_EINVAL, "gflops is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  SIPF_CK(cudaGetDevice(&dev));
+  SIPF_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  double* sink = nullptr;
+  SIPF_CK(cudaMalloc(&sink, sizeof(double)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int blocks = sms * 8, iters = 1 << 14;
+  if (e == cudaSuccess) e = launch_fp64_fma(blocks, 64, sink, s);   // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  if (e == cudaSuccess) e = launch_fp64_fma(blocks, iters, sink, s);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (e != cudaSuccess) return cuda_fail(e, "sipf_measure_fp64_fma");
+  *gflops = 2.0 * blocks * 256.0 * 8.0 * iters / (ms * 1e-3) / 1e9;
   return SIPF_OK;
 }
 

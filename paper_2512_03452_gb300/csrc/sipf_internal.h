@@ -71,8 +71,20 @@ cudaError_t launch_rows_c2r(const cpx<T>* in, int ncomp, size_t comp_stride, T* 
 // (2).  A single run's step uses the same kernels with a one-entry table, so
 // a run computes the same bits alone or in a batch.
 enum { kFieldForward = 1, kFieldSpectral = 2, kFieldInverse = 4, kFieldAll = 7 };
+// Launch shapes of the field solve (0: default): the column tile of the y
+// passes (8, 16 or 32 pencils per block), the column tile of the fused x pass
+// (4, 8 or 16) and the blocks per SM given to the row passes.  Results do not
+// depend on them.
+struct FieldTune {
+  int bc = 0, sbc = 0, rows_per_sm = 0;
+};
 template <typename T>
-cudaError_t launch_field_batch(const FftRun<T>* runs, int nruns, int H, int stages, cudaStream_t s);
+cudaError_t launch_field_batch(const FftRun<T>* runs, int nruns, int H, int stages, cudaStream_t s,
+                               const FieldTune& tune = FieldTune{});
+template <typename T> bool field_tune_valid(int H, const FieldTune& t);
+
+// FP64 FMA throughput probe: blocks x 256 threads x 8 chains x iters FMAs.
+cudaError_t launch_fp64_fma(int blocks, int iters, double* sink, cudaStream_t s);
 
 // ---- adjoint launchers (adjoint_kernels.cu) ----------------------------------------
 // One reverse step over all particles in id order (see k_adj_step).
@@ -155,10 +167,10 @@ struct LayoutArgs {
 };
 template <typename T>
 cudaError_t launch_move_batch(const BinArgs<T>* table, const long long* prefix, int nruns, unsigned long long* work,
-                              const uint32_t* step, bool move, cudaStream_t s);
+                              const uint32_t* step, bool move, cudaStream_t s, int blocks_per_sm = 0);
 template <typename T>
 cudaError_t launch_deposit_batch(const BinArgs<T>* table, const long long* prefix, int nruns,
-                                 unsigned long long* work, bool fixed, cudaStream_t s);
+                                 unsigned long long* work, bool fixed, cudaStream_t s, int blocks_per_sm = 0);
 cudaError_t launch_chunk_list_batch(const ChunkListArgs* t, int nruns, cudaStream_t s);
 cudaError_t launch_run_prefix(const ChunkListArgs* t, int nruns, long long* prefix, unsigned long long* work,
                               uint32_t* step, int bump, cudaStream_t s);

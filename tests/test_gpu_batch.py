@@ -138,3 +138,24 @@ def test_batch_rejects_bad_parameter_sets():
     det = [params[0], params_from_workload(workloads.Workload("d", P=100, H=32), precision=32, deposit_mode=1)]
     with pytest.raises(_abi.SipfError):
         Batch(det, [X0s[0], workloads.sample_positions(workloads.Workload("d", P=100, H=32))])
+
+
+def test_autotune_changes_shapes_not_results():
+    """Deterministic deposit: a batch that autotunes and one that does not give
+    the same bits after the same number of steps."""
+    _, params, X0s = _runs(32, mode=1, n=4, seed=12)
+    with Batch(params, X0s) as a:
+        t = a.autotune(2)
+        assert t["steps_used"] > 0 and len(t["groups"]) == 2
+        for g in t["groups"]:
+            assert g["cols_tile"] in (8, 16, 32) and g["xpass_tile"] in (4, 8, 16) and g["field_ms"] > 0
+        a.step(40)
+        a.sync()
+        n = a.n
+        got = [(a.positions(r), a.spectrum(r)) for r in range(len(params))]
+    with Batch(params, X0s) as b:
+        b.step(n)
+        b.sync()
+        for r in range(len(params)):
+            assert np.array_equal(b.positions(r), got[r][0]), r
+            assert np.array_equal(b.spectrum(r), got[r][1]), r
