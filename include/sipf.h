@@ -239,6 +239,8 @@ typedef struct sipf_batch_tuning {
   int32_t cols_tile[4];           /* pencils per block of the y passes: 8, 16, 32   */
   int32_t xpass_tile[4];          /* pencils per block of the fused x pass: 4, 8, 16 */
   int32_t rows_blocks_per_sm[4];  /* blocks per SM shared by the row passes          */
+  int32_t plane_kernels[4];       /* 1: both inner axes in one plane kernel per
+                                     direction; 0: separate pencil passes        */
   int32_t move_blocks_per_sm;     /* move + re-bin blocks per SM (0: occupancy limit) */
   int32_t deposit_blocks_per_sm;  /* deposit blocks per SM (0: occupancy limit)       */
   double field_ms[4];             /* best device ms per step of each group's field solve */
@@ -251,9 +253,15 @@ typedef struct sipf_batch_tuning {
  * candidates above, each timed with CUDA events on steps_per_trial (>= 2)
  * real steps of the batch (the first step of a trial is not timed).  Shapes
  * do not change results, so the runs advance by out->steps_used steps (about
- * steps_per_trial x (9 per group + 9)).  Later steps use the chosen shapes;
+ * steps_per_trial x (11 per group + 9)).  Later steps use the chosen shapes;
  * out may be NULL.  Synchronises. */
 int sipf_batch_autotune(sipf_batch* b, int32_t steps_per_trial, sipf_batch_tuning* out);
+
+/* Apply a tuning (for example one saved from sipf_batch_autotune on the same
+ * kind of batch): groups must list the batch's H values in the same order;
+ * 0 in a shape field means the default.  SIPF_EINVAL for shapes the kernels
+ * do not support (shared memory). */
+int sipf_batch_set_tuning(sipf_batch* b, const sipf_batch_tuning* t);
 
 /* enable = 0: issue every step's launches directly instead of replaying the
  * recorded 32-step graph (same results; for timing the graph's benefit). */

@@ -140,7 +140,8 @@ class Batch:
         t = _abi.sipf_batch_autotune(self.handle, steps_per_trial)
         g = t.ngroups
         return {"groups": [{"H": t.H[i], "cols_tile": t.cols_tile[i], "xpass_tile": t.xpass_tile[i],
-                            "rows_blocks_per_sm": t.rows_blocks_per_sm[i], "field_ms": t.field_ms[i]}
+                            "rows_blocks_per_sm": t.rows_blocks_per_sm[i], "plane_kernels": t.plane_kernels[i],
+                            "field_ms": t.field_ms[i]}
                            for i in range(g)],
                 "move_blocks_per_sm": t.move_blocks_per_sm, "deposit_blocks_per_sm": t.deposit_blocks_per_sm,
                 "move_ms": t.move_ms, "deposit_ms": t.deposit_ms, "steps_used": t.steps_used}

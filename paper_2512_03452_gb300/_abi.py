@@ -58,6 +58,7 @@ class sipf_timing(ctypes.Structure):
 class sipf_batch_tuning(ctypes.Structure):
     _fields_ = [("ngroups", ctypes.c_int32), ("H", ctypes.c_int32 * 4), ("cols_tile", ctypes.c_int32 * 4),
                 ("xpass_tile", ctypes.c_int32 * 4), ("rows_blocks_per_sm", ctypes.c_int32 * 4),
+                ("plane_kernels", ctypes.c_int32 * 4),
                 ("move_blocks_per_sm", ctypes.c_int32), ("deposit_blocks_per_sm", ctypes.c_int32),
                 ("field_ms", ctypes.c_double * 4), ("move_ms", ctypes.c_double), ("deposit_ms", ctypes.c_double),
                 ("steps_used", ctypes.c_int64)]
@@ -111,6 +112,7 @@ _SIGS = {
     "sipf_batch_step": (ctypes.c_int, [_P, ctypes.c_int64]),
     "sipf_batch_use_graph": (ctypes.c_int, [_P, ctypes.c_int]),
     "sipf_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(sipf_batch_tuning)]),
+    "sipf_batch_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(sipf_batch_tuning)]),
     "sipf_batch_current_step": (ctypes.c_int64, [_P]),
     "sipf_batch_kernel_launches": (ctypes.c_int64, [_P]),
     "sipf_batch_positions": (ctypes.c_int, [_P, ctypes.c_int32, _D]),
@@ -318,6 +320,10 @@ def sipf_batch_autotune(b: int, steps_per_trial: int = 3) -> sipf_batch_tuning:
     t = sipf_batch_tuning()
     _check(load().sipf_batch_autotune(_P(b), int(steps_per_trial), ctypes.byref(t)), "sipf_batch_autotune")
     return t
+
+
+def sipf_batch_set_tuning(b: int, t: sipf_batch_tuning) -> None:
+    _check(load().sipf_batch_set_tuning(_P(b), ctypes.byref(t)), "sipf_batch_set_tuning")
 
 
 def sipf_batch_use_graph(b: int, enable: int) -> None:

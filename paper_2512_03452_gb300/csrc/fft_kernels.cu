@@ -811,6 +811,163 @@ __global__ void __launch_bounds__(256) kwb_rows_c2r(const FftRun<T>* __restrict_
   rows_c2r_body<T, E, 3>(r.T2, S, r.grad, N * N, nullptr, blockIdx.x, gridDim.x, tw, zb_all, ob_all);
 }
 
+// ---------------------------------------------------------------------------
+// Plane kernels (H <= 128): one block holds a whole x-plane of the half
+// spectrum, H x (H/2+1) complex values, in shared memory and does both inner
+// axes there, so the y pass costs no extra trip through L2.
+//   forward: r2c of the plane's rows (two real rows per complex warp FFT, the
+//            deposit grid cleared as it is read), then the y-axis FFT of every
+//            column, then one coalesced write of the plane;
+//   inverse: one component's plane, y-axis inverse of every column, then c2r
+//            of row pairs, written into that component's slot of the
+//            interleaved (gx, gy, gz, -) nodes.
+// ---------------------------------------------------------------------------
+template <typename T, int E> constexpr size_t plane_smem_bytes() {
+  return ((size_t)32 * E * (16 * E + 1) + (size_t)8 * 32 * E + kNmax) * sizeof(cpx<T>);
+}
+
+template <typename T, int E, typename Tin>
+__device__ __forceinline__ void plane_fwd_body(Tin* __restrict__ in, double in_scale, cpx<T>* __restrict__ out,
+                                               const cpx<T>* tw, cpx<T>* P, cpx<T>* zball) {
+  constexpr int N = 32 * E, NH = N / 2 + 1;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  cpx<T>* zb = zball + wib * N;
+  // 1. rows: two real rows as one complex pencil, split into their half spectra
+  for (int pr = wib; pr < N / 2; pr += 8) {
+    const size_t ra = (size_t)(2 * pr) * N, rb = ra + N;
+    cpx<T> v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      T a, b;
+      if constexpr (sizeof(Tin) == 8 && !std::is_floating_point<Tin>::value) {
+        a = (T)((double)(long long)in[ra + lane + 32 * m] * in_scale);
+        b = (T)((double)(long long)in[rb + lane + 32 * m] * in_scale);
+      } else {
+        a = (T)in[ra + lane + 32 * m];
+        b = (T)in[rb + lane + 32 * m];
+      }
+      v[m] = cpx<T>{a, b};
+    }
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      in[ra + lane + 32 * m] = Tin(0);
+      in[rb + lane + 32 * m] = Tin(0);
+    }
+    warp_fft<T, E, -1>(v, lane, tw);
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) zb[out_index(k1, E, lane)] = v[k1];
+    __syncwarp();
+    cpx<T>* pa = P + (size_t)(2 * pr) * NH;
+    for (int k = lane; k < NH; k += 32) {
+      const cpx<T> zk = zb[k];
+      const cpx<T> zm = cconj(zb[(N - k) & (N - 1)]);
+      const cpx<T> d = csub(zk, zm);
+      pa[k] = cpx<T>{(zk.x + zm.x) * T(0.5), (zk.y + zm.y) * T(0.5)};
+      pa[NH + k] = cpx<T>{d.y * T(0.5), -d.x * T(0.5)};
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // 2. y axis: one column per warp
+  for (int c = wib; c < NH; c += 8) {
+    cpx<T> v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = P[(lane + 32 * m) * NH + c];
+    warp_fft<T, E, -1>(v, lane, tw);
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) P[out_index(k1, E, lane) * NH + c] = v[k1];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < N * NH; t += blockDim.x) out[t] = P[t];
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void plane_inv_body(const cpx<T>* __restrict__ in, T* __restrict__ out, int x, int d,
+                                               const cpx<T>* tw, cpx<T>* P, cpx<T>* zball) {
+  constexpr int N = 32 * E, NH = N / 2 + 1;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  cpx<T>* zb = zball + wib * N;
+  for (int t = threadIdx.x; t < N * NH; t += blockDim.x) P[t] = in[t];
+  __syncthreads();
+  // 1. y axis inverse: one column per warp
+  for (int c = wib; c < NH; c += 8) {
+    cpx<T> v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = P[(lane + 32 * m) * NH + c];
+    warp_fft<T, E, +1>(v, lane, tw);
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) P[out_index(k1, E, lane) * NH + c] = v[k1];
+  }
+  __syncthreads();
+  // 2. rows: two Hermitian half rows A, B as the pencil A + i B; the inverse
+  //    transform's real part is row A, its imaginary part row B
+  for (int pr = wib; pr < N / 2; pr += 8) {
+    cpx<T>* pa = P + (size_t)(2 * pr) * NH;
+    const cpx<T>* pb = pa + NH;
+    for (int k = lane; k < NH; k += 32) {
+      cpx<T> A = pa[k], Bv = pb[k];
+      if (k == 0 || k == N / 2) {
+        A.y = T(0);
+        Bv.y = T(0);
+      }
+      zb[k] = cpx<T>{A.x - Bv.y, A.y + Bv.x};
+      if (k > 0 && k < N / 2) zb[N - k] = cpx<T>{A.x + Bv.y, -A.y + Bv.x};   // conj A + i conj B
+    }
+    __syncwarp();
+    cpx<T> v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = zb[lane + 32 * m];
+    __syncwarp();
+    warp_fft<T, E, +1>(v, lane, tw);
+    // stage the two output rows in the two plane rows just consumed
+    T* ob = reinterpret_cast<T*>(pa);
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) {
+      const int j = out_index(k1, E, lane);
+      ob[j] = v[k1].x;
+      ob[N + j] = v[k1].y;
+    }
+    __syncwarp();
+    T* orow = out + ((size_t)x * N + 2 * pr) * N * 4 + d;
+    for (int t = lane; t < 2 * N; t += 32) orow[(size_t)t * 4] = ob[t];
+    __syncwarp();
+  }
+}
+
+template <typename T, int E>
+__global__ void __launch_bounds__(256) kwp_fwd(const FftRun<T>* __restrict__ runs) {
+  constexpr int N = 32 * E, NH = N / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* zb = tw + kNmax;
+  cpx<T>* P = zb + 8 * N;
+  load_tw_full(tw);
+  __syncthreads();
+  const FftRun<T>& r = runs[blockIdx.y];
+  const int x = blockIdx.x;
+  cpx<T>* out = r.T1 + (size_t)x * N * NH;
+  if (r.phi_fixed)
+    plane_fwd_body<T, E, unsigned long long>(static_cast<unsigned long long*>(r.phi) + (size_t)x * N * N, r.in_scale,
+                                             out, tw, P, zb);
+  else
+    plane_fwd_body<T, E, T>(static_cast<T*>(r.phi) + (size_t)x * N * N, 1.0, out, tw, P, zb);
+}
+
+template <typename T, int E>
+__global__ void __launch_bounds__(256) kwp_inv(const FftRun<T>* __restrict__ runs) {
+  constexpr int N = 32 * E, NH = N / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* zb = tw + kNmax;
+  cpx<T>* P = zb + 8 * N;
+  load_tw_full(tw);
+  __syncthreads();
+  const FftRun<T>& r = runs[blockIdx.z];
+  const int x = blockIdx.x, d = blockIdx.y;
+  const size_t S = (size_t)N * N * NH;
+  plane_inv_body<T, E>(r.T2 + d * S + (size_t)x * N * NH, r.grad, x, d, tw, P, zb);
+}
+
 static int warp_blocks(int rows) {
   int b = (rows / 2 + 7) / 8;
   return b > 152 * 8 ? 152 * 8 : (b < 1 ? 1 : b);
@@ -1079,10 +1236,18 @@ static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, c
   const int rblocks = max(1, min(rows_budget / max(nruns, 1), (N * N / 2 + 7) / 8));
   const int bc = tune.bc > 0 ? tune.bc : 16;
   const int sbc = tune.sbc > 0 ? tune.sbc : default_sbc<T, E>();
+  constexpr size_t psm = plane_smem_bytes<T, E>();
+  const bool planes = tune.plane_mode == 0 && E <= 4 && psm <= kMaxSmem;
   if (stages & kFieldForward) {
-    kwb_rows_r2c<T, E><<<dim3(rblocks, nruns), 256, 0, s>>>(runs);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = kwb_cols_bc<T, E, -1>(runs, nruns, 1, bc, s)) != cudaSuccess) return e;
+    if (planes) {
+      if ((e = set_smem(kwp_fwd<T, E>, psm)) != cudaSuccess) return e;
+      kwp_fwd<T, E><<<dim3(N, nruns), 256, psm, s>>>(runs);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else {
+      kwb_rows_r2c<T, E><<<dim3(rblocks, nruns), 256, 0, s>>>(runs);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = kwb_cols_bc<T, E, -1>(runs, nruns, 1, bc, s)) != cudaSuccess) return e;
+    }
   }
   if (stages & kFieldSpectral) {
     switch (sbc) {
@@ -1092,7 +1257,11 @@ static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, c
     }
     if (e != cudaSuccess) return e;
   }
-  if (stages & kFieldInverse) {
+  if ((stages & kFieldInverse) && planes) {
+    if ((e = set_smem(kwp_inv<T, E>, psm)) != cudaSuccess) return e;
+    kwp_inv<T, E><<<dim3(N, 3, nruns), 256, psm, s>>>(runs);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else if (stages & kFieldInverse) {
     if ((e = kwb_cols_bc<T, E, +1>(runs, nruns, 3, bc, s)) != cudaSuccess) return e;
     const size_t smr = (kNmax + (size_t)8 * N) * sizeof(cpx<T>) + (size_t)8 * 2 * N * 4 * sizeof(T);
     if ((e = set_smem(kwb_rows_c2r<T, E>, smr)) != cudaSuccess) return e;
@@ -1107,7 +1276,21 @@ template <typename T, int E> static bool field_tune_valid_e(const FieldTune& t) 
   size_t c = bc == 8 ? cols_smem<T, E, 8>() : bc == 32 ? cols_smem<T, E, 32>() : cols_smem<T, E, 16>();
   size_t x = sbc == 4 ? spectral_smem<T, E, 4>() : sbc == 8 ? spectral_smem<T, E, 8>() : spectral_smem<T, E, 16>();
   return (bc == 8 || bc == 16 || bc == 32) && (sbc == 4 || sbc == 8 || sbc == 16) && c <= kMaxSmem &&
-         x <= kMaxSmem && t.rows_per_sm >= 0 && t.rows_per_sm <= 32;
+         x <= kMaxSmem && t.rows_per_sm >= 0 && t.rows_per_sm <= 32 && (t.plane_mode == 0 || t.plane_mode == 1);
+}
+
+template <typename T> FieldTune field_tune_default(int H) {
+  FieldTune t;
+  t.bc = 16;
+  t.rows_per_sm = 8;
+  t.plane_mode = 0;
+  switch (H) {
+    case 32: t.sbc = default_sbc<T, 1>(); break;
+    case 64: t.sbc = default_sbc<T, 2>(); break;
+    case 128: t.sbc = default_sbc<T, 4>(); break;
+    default: t.sbc = default_sbc<T, 8>(); break;
+  }
+  return t;
 }
 
 template <typename T> bool field_tune_valid(int H, const FieldTune& t) {
@@ -1141,7 +1324,8 @@ cudaError_t launch_field_batch(const FftRun<T>* runs, int nruns, int H, int stag
                                             cudaStream_t);                                                  \
   template cudaError_t launch_rows_c2r<T>(const cpx<T>*, int, size_t, T*, int, int, double*, cudaStream_t);     \
   template cudaError_t launch_field_batch<T>(const FftRun<T>*, int, int, int, cudaStream_t, const FieldTune&); \
-  template bool field_tune_valid<T>(int, const FieldTune&);
+  template bool field_tune_valid<T>(int, const FieldTune&);                                                   \
+  template FieldTune field_tune_default<T>(int);
 SIPF_INST(float)
 SIPF_INST(double)
 #undef SIPF_INST

@@ -677,57 +677,103 @@ cudaError_t launch_fp64_fma(int blocks, int iters, double* sink, cudaStream_t s)
 // ---------------------------------------------------------------------------
 // From the fill cursors of the buffer just written: valid counts (clamped to
 // capacity), the chunk prefix sum, the chunk descriptors, and the reset of the
-// other buffer's cursors and of the work counter.  One block.
-__device__ __forceinline__ void chunk_list_body(const int* __restrict__ cursor, const int* __restrict__ cap,
-                                                const long long* __restrict__ base, int* __restrict__ count,
-                                                long long* __restrict__ chunk_start, ChunkDesc* __restrict__ chunks,
-                                                int* __restrict__ other_cursor, int NT, unsigned long long* work,
-                                                unsigned long long* ovf_total) {
-  __shared__ long long s_part[1024];
-  const int nb = NT + 1;
-  const int per = (nb + blockDim.x - 1) / blockDim.x;
-  const int b0 = threadIdx.x * per;
-  long long local = 0;
-  for (int b = b0; b < min(b0 + per, nb); ++b) {
-    const int c = min(cursor[b], cap[b]);
-    count[b] = c;
-    local += (c + kChunk - 1) / kChunk;
-    other_cursor[b] = 0;
+// other buffer's cursors and of the work counter.  Two passes over blocks of
+// kCLBlock bins: count (block-local exclusive prefix of chunks and the block
+// total), then emit (block offset from the totals of the blocks before it,
+// the descriptors, the grand total).
+// ---------------------------------------------------------------------------
+constexpr int kCLBlock = 1024;
+
+__device__ __forceinline__ long long block_exclusive_scan_ll(long long v, long long& total) {
+  __shared__ long long s_w[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  long long incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
   }
-  s_part[threadIdx.x] = local;
+  if (lane == 31) s_w[wid] = incl;
   __syncthreads();
-  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-    const long long v = threadIdx.x >= (unsigned)off ? s_part[threadIdx.x - off] : 0;
-    __syncthreads();
-    s_part[threadIdx.x] += v;
-    __syncthreads();
+  if (wid == 0) {
+    long long w = lane < nw ? s_w[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    s_w[lane] = w;   // inclusive prefix of warp totals
   }
-  long long run = s_part[threadIdx.x] - local;   // exclusive prefix
-  for (int b = b0; b < min(b0 + per, nb); ++b) {
-    chunk_start[b] = run;
-    const int c = count[b];
-    for (int j = 0; j * kChunk < c; ++j)
-      chunks[run + j] = ChunkDesc{base[b] + (long long)j * kChunk, b, min(kChunk, c - j * kChunk)};
-    run += (c + kChunk - 1) / kChunk;
+  __syncthreads();
+  total = s_w[nw - 1];
+  const long long ex = (wid > 0 ? s_w[wid - 1] : 0) + incl - v;
+  __syncthreads();
+  return ex;
+}
+
+__device__ __forceinline__ void chunk_count_body(const ChunkListArgs& a, int blk) {
+  const int nb = a.NT + 1;
+  const int b = blk * kCLBlock + threadIdx.x;
+  long long ch = 0;
+  if (b < nb) {
+    const int c = min(a.cursor[b], a.cap[b]);
+    a.count[b] = c;
+    ch = (c + kChunk - 1) / kChunk;
+    a.other_cursor[b] = 0;
   }
-  if (threadIdx.x == blockDim.x - 1) chunk_start[nb] = s_part[threadIdx.x];
+  long long total;
+  const long long ex = block_exclusive_scan_ll(ch, total);
+  if (b < nb) a.chunk_start[b] = ex;
+  if (threadIdx.x == 0) a.part[blk] = total;
+}
+
+__device__ __forceinline__ void chunk_emit_body(const ChunkListArgs& a, int blk, int nblk, unsigned long long* work,
+                                                unsigned long long* ovf_total) {
+  __shared__ long long s_off;
   if (threadIdx.x == 0) {
+    long long o = 0;
+    for (int i = 0; i < blk; ++i) o += a.part[i];
+    s_off = o;
+  }
+  __syncthreads();
+  const long long off = s_off;
+  const int nb = a.NT + 1;
+  const int b = blk * kCLBlock + threadIdx.x;
+  if (b < nb) {
+    const long long st = a.chunk_start[b] + off;
+    a.chunk_start[b] = st;
+    const int c = a.count[b];
+    const long long bb = a.base[b];
+    for (int j = 0; j * kChunk < c; ++j) a.chunks[st + j] = ChunkDesc{bb + (long long)j * kChunk, b, min(kChunk, c - j * kChunk)};
+  }
+  if (blk == nblk - 1 && threadIdx.x == 0) {
+    a.chunk_start[nb] = off + a.part[blk];
     if (work) *work = 0ULL;
-    if (ovf_total) *ovf_total += (unsigned long long)count[NT];
+    if (ovf_total) *ovf_total += (unsigned long long)a.count[a.NT];
   }
 }
 
-__global__ void __launch_bounds__(1024)
-k_chunk_list(const int* __restrict__ cursor, const int* __restrict__ cap, const long long* __restrict__ base,
-             int* __restrict__ count, long long* __restrict__ chunk_start, ChunkDesc* __restrict__ chunks,
-             int* __restrict__ other_cursor, int NT, unsigned long long* work, unsigned long long* ovf_total) {
-  chunk_list_body(cursor, cap, base, count, chunk_start, chunks, other_cursor, NT, work, ovf_total);
+__device__ __forceinline__ int chunk_list_blocks_dev(int NT) { return (NT + 1 + kCLBlock - 1) / kCLBlock; }
+
+__global__ void __launch_bounds__(kCLBlock) k_chunk_count(ChunkListArgs a) { chunk_count_body(a, blockIdx.x); }
+
+__global__ void __launch_bounds__(kCLBlock)
+k_chunk_emit(ChunkListArgs a, unsigned long long* work, unsigned long long* ovf_total) {
+  chunk_emit_body(a, blockIdx.x, gridDim.x, work, ovf_total);
 }
 
-// One block per run.
-__global__ void __launch_bounds__(1024) k_chunk_list_batch(const ChunkListArgs* __restrict__ t) {
-  const ChunkListArgs& a = t[blockIdx.x];
-  chunk_list_body(a.cursor, a.cap, a.base, a.count, a.chunk_start, a.chunks, a.other_cursor, a.NT, nullptr, nullptr);
+// Batched: grid (blocks of the largest run, runs).
+__global__ void __launch_bounds__(kCLBlock) k_chunk_count_batch(const ChunkListArgs* __restrict__ t) {
+  const ChunkListArgs a = t[blockIdx.y];
+  if ((int)blockIdx.x >= chunk_list_blocks_dev(a.NT)) return;
+  chunk_count_body(a, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kCLBlock) k_chunk_emit_batch(const ChunkListArgs* __restrict__ t) {
+  const ChunkListArgs a = t[blockIdx.y];
+  const int nblk = chunk_list_blocks_dev(a.NT);
+  if ((int)blockIdx.x >= nblk) return;
+  chunk_emit_body(a, blockIdx.x, nblk, nullptr, nullptr);
 }
 
 // Prefix over runs of their work-item counts; clears the work counter and,
@@ -1097,10 +1143,15 @@ cudaError_t launch_binned(const BinArgs<T>& a, int move, int deposit, int rebin,
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_chunk_list(const int* cursor, const int* cap, const long long* base, int* count,
-                              long long* chunk_start, ChunkDesc* chunks, int* other_cursor, int NT,
-                              unsigned long long* work, unsigned long long* ovf_total, cudaStream_t s) {
-  k_chunk_list<<<1, 1024, 0, s>>>(cursor, cap, base, count, chunk_start, chunks, other_cursor, NT, work, ovf_total);
+int chunk_list_blocks(int NT) { return (NT + 1 + kCLBlock - 1) / kCLBlock; }
+
+cudaError_t launch_chunk_list(const ChunkListArgs& a, unsigned long long* work, unsigned long long* ovf_total,
+                              cudaStream_t s) {
+  const int nblk = chunk_list_blocks(a.NT);
+  k_chunk_count<<<nblk, kCLBlock, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_chunk_emit<<<nblk, kCLBlock, 0, s>>>(a, work, ovf_total);
   return cudaGetLastError();
 }
 
@@ -1137,8 +1188,12 @@ cudaError_t launch_deposit_batch(const BinArgs<T>* table, const long long* prefi
   return cudaGetLastError();
 }
 
-cudaError_t launch_chunk_list_batch(const ChunkListArgs* t, int nruns, cudaStream_t s) {
-  k_chunk_list_batch<<<nruns, 1024, 0, s>>>(t);
+cudaError_t launch_chunk_list_batch(const ChunkListArgs* t, int nruns, int max_NT, cudaStream_t s) {
+  const dim3 grid(chunk_list_blocks(max_NT), nruns);
+  k_chunk_count_batch<<<grid, kCLBlock, 0, s>>>(t);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_chunk_emit_batch<<<grid, kCLBlock, 0, s>>>(t);
   return cudaGetLastError();
 }
 

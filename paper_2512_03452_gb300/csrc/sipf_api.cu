@@ -99,6 +99,7 @@ struct sipf_ctx {
   int* count = nullptr;
   long long* chunk_start = nullptr;
   ChunkDesc* chunks = nullptr;
+  long long* part = nullptr;    // per-block chunk totals of the chunk-list passes
   unsigned long long* work = nullptr;
   unsigned long long* ovf = nullptr;   // particles found in the overflow bin while timing
   int* hist = nullptr;
@@ -216,6 +217,12 @@ template <typename T> BinArgs<T> bin_args(sipf_ctx* c, int src_buf, int src_lay,
   return a;
 }
 
+// Chunk-list arguments: bins of (cursor, cap, base) into the context's chunk
+// arrays; `other` are the cursors to clear for the next pass.
+ChunkListArgs cl_args(sipf_ctx* c, const int* cursor, const int* cap, const long long* base, int* other) {
+  return ChunkListArgs{cursor, cap, base, c->count, c->chunk_start, c->chunks, other, c->NT, c->part};
+}
+
 // Deposit the current bins into phi (initialisation of Algorithm 4 and after
 // positions are replaced).
 template <typename T> int deposit_current(sipf_ctx* c) {
@@ -236,8 +243,8 @@ template <typename T> int rebin_from_staging(sipf_ctx* c) {
                               make_geo<T>(c->p.L, c->p.H), c->shift, c->ntx, c->NT, c->hist, c->stream));
   SIPF_CK(launch_layout(c->hist, c->lcap[L], c->lbase[L], c->NT, c->ntx, (int)c->p.P, c->stream));
   // chunk list of the staging (one bin holding all P particles); clears the destination cursors
-  SIPF_CK(launch_chunk_list(c->st_count, c->st_cap, c->st_base, c->count, c->chunk_start, c->chunks, c->cursor[d],
-                            c->NT, c->work, nullptr, c->stream));
+  SIPF_CK(launch_chunk_list(cl_args(c, c->st_count, c->st_cap, c->st_base, c->cursor[d]), c->work, nullptr,
+                            c->stream));
   cudaError_t e = cudaSuccess;
   if (!launch_rebin_plain<T>((const T*)c->st[0], (const T*)c->st[1], (const T*)c->st[2], c->st_id, c->p.P,
                              make_geo<T>(c->p.L, c->p.H), c->shift, c->ntx, c->NT, (T*)c->bx[d][0], (T*)c->bx[d][1],
@@ -247,8 +254,8 @@ template <typename T> int rebin_from_staging(sipf_ctx* c) {
     e = launch_binned<T>(bin_args<T>(c, -1, 0, d, L), 0, 0, 1, c->stream);
   }
   SIPF_CK(e);
-  SIPF_CK(launch_chunk_list(c->cursor[d], c->lcap[L], c->lbase[L], c->count, c->chunk_start, c->chunks,
-                            c->cursor[1 - d], c->NT, c->work, nullptr, c->stream));
+  SIPF_CK(launch_chunk_list(cl_args(c, c->cursor[d], c->lcap[L], c->lbase[L], c->cursor[1 - d]), c->work, nullptr,
+                            c->stream));
   c->cur = d;
   c->lc = L;
   c->since_layout = 0;
@@ -308,9 +315,9 @@ template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
     SIPF_CK(cudaMemsetAsync(c->work, 0, sizeof(unsigned long long), c->stream));
     SIPF_CK(launch_move<T>(bin_args<T>(c, src, c->lc, dst, c->lc), c->stream));
     SIPF_CK(mark(&ev[4]));
-    SIPF_CK(launch_chunk_list(c->cursor[dst], c->lcap[c->lc], c->lbase[c->lc], c->count, c->chunk_start, c->chunks,
-                              c->cursor[src], c->NT, c->work, c->timing ? c->ovf : nullptr, c->stream));
-    c->launches += 7;
+    SIPF_CK(launch_chunk_list(cl_args(c, c->cursor[dst], c->lcap[c->lc], c->lbase[c->lc], c->cursor[src]), c->work,
+                              c->timing ? c->ovf : nullptr, c->stream));
+    c->launches += 8;
     c->cur = dst;
     c->n += 1;
     if (++c->since_layout >= c->resort()) {
@@ -319,9 +326,9 @@ template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
       SIPF_CK(launch_layout(c->cursor[c->cur], c->lcap[L], c->lbase[L], c->NT, c->ntx, (int)c->p.P, c->stream));
       SIPF_CK(cudaMemsetAsync(c->work, 0, sizeof(unsigned long long), c->stream));
       SIPF_CK(launch_binned<T>(bin_args<T>(c, c->cur, c->lc, d2, L), 0, 0, 1, c->stream));
-      SIPF_CK(launch_chunk_list(c->cursor[d2], c->lcap[L], c->lbase[L], c->count, c->chunk_start, c->chunks,
-                                c->cursor[c->cur], c->NT, c->work, nullptr, c->stream));
-      c->launches += 3;
+      SIPF_CK(launch_chunk_list(cl_args(c, c->cursor[d2], c->lcap[L], c->lbase[L], c->cursor[c->cur]), c->work, nullptr,
+                                c->stream));
+      c->launches += 4;
       c->cur = d2;
       c->lc = L;
       c->since_layout = 0;
@@ -530,6 +537,7 @@ void free_ctx(sipf_ctx* c) {
   cudaFree(c->count);
   cudaFree(c->chunk_start);
   cudaFree(c->chunks);
+  cudaFree(c->part);
   cudaFree(c->work);
   cudaFree(c->ovf);
   cudaFree(c->hist);
@@ -625,6 +633,7 @@ int sipf_init(const sipf_params* p, const double* X0, void* stream, sipf_ctx** o
   if (e == cudaSuccess) e = cudaMalloc(&c->count, nb * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&c->chunk_start, (nb + 1) * sizeof(long long));
   if (e == cudaSuccess) e = cudaMalloc(&c->chunks, (size_t)c->max_chunks() * sizeof(ChunkDesc));
+  if (e == cudaSuccess) e = cudaMalloc(&c->part, (size_t)chunk_list_blocks(c->NT) * sizeof(long long));
   if (e == cudaSuccess) e = cudaMalloc(&c->work, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&c->ovf, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ovf, 0, sizeof(unsigned long long), c->stream);
@@ -998,6 +1007,7 @@ struct sipf_batch {
   cudaGraphExec_t graph = nullptr;
   int graph_cur = -1, graph_lc = -1, graph_since = -1;
   int64_t launches = 0;
+  int max_NT = 1;   // most tiles of any run (grid of the batched chunk-list passes)
   // launch shapes (autotuned) and per-phase events of the last issued step
   std::vector<FieldTune> field_tune;
   int move_bps = 0, dep_bps = 0;
@@ -1059,8 +1069,7 @@ template <typename T> int batch_tables(sipf_batch* b) {
         rb.push_back(bin_args<T>(c, cur, lc, 1 - cur, 1 - lc));
         dp.push_back(bin_args<T>(c, cur, lc, -1, 0));
         // chunk list of buffer `cur` written with layout `lc`
-        cl.push_back(ChunkListArgs{c->cursor[cur], c->lcap[lc], c->lbase[lc], c->count, c->chunk_start, c->chunks,
-                                   c->cursor[1 - cur], c->NT});
+        cl.push_back(cl_args(c, c->cursor[cur], c->lcap[lc], c->lbase[lc], c->cursor[1 - cur]));
         // new layout `lc` from the counts of buffer `cur`
         ly.push_back(LayoutArgs{c->cursor[cur], c->lcap[lc], c->lbase[lc], c->NT, c->ntx, (int)c->p.P});
       }
@@ -1095,18 +1104,18 @@ template <typename T> int batch_issue_step(sipf_batch* b) {
   SIPF_CK(cudaMemsetAsync(b->work, 0, sizeof(unsigned long long), s));
   SIPF_CK(launch_move_batch<T>((const BinArgs<T>*)b->move_tab[b->cur][b->lc], b->prefix, R, b->work, b->step, true, s,
                                b->move_bps));
-  SIPF_CK(launch_chunk_list_batch(b->cl_tab[1 - b->cur][b->lc], R, s));
+  SIPF_CK(launch_chunk_list_batch(b->cl_tab[1 - b->cur][b->lc], R, b->max_NT, s));
   SIPF_CK(launch_run_prefix(b->cl_tab[1 - b->cur][b->lc], R, b->prefix, b->work, b->step, 1, s));
   SIPF_CK(mark(2 * G + 1));
-  b->launches += 5 * (int64_t)b->group_H.size() + 3;
+  b->launches += 5 * (int64_t)b->group_H.size() + 4;
   b->cur = 1 - b->cur;
   if (++b->since >= kBatchResort) {
     SIPF_CK(launch_layout_batch(b->ly_tab[b->cur][1 - b->lc], R, s));
     SIPF_CK(launch_move_batch<T>((const BinArgs<T>*)b->rebin_tab[b->cur][b->lc], b->prefix, R, b->work, b->step, false,
                                  s, b->move_bps));
-    SIPF_CK(launch_chunk_list_batch(b->cl_tab[1 - b->cur][1 - b->lc], R, s));
+    SIPF_CK(launch_chunk_list_batch(b->cl_tab[1 - b->cur][1 - b->lc], R, b->max_NT, s));
     SIPF_CK(launch_run_prefix(b->cl_tab[1 - b->cur][1 - b->lc], R, b->prefix, b->work, b->step, 0, s));
-    b->launches += 4;
+    b->launches += 5;
     b->cur = 1 - b->cur;
     b->lc = 1 - b->lc;
     b->since = 0;
@@ -1156,7 +1165,7 @@ template <typename T> int batch_step_impl(sipf_batch* b, int64_t nsteps) {
       SIPF_CK(cudaGraphLaunch(b->graph, b->stream));
       // 32 steps hold 32 moves and 2 capacity rebuilds: parities return
       b->n += kBatchGraphSteps;
-      b->launches += kBatchGraphSteps * (5 * (int64_t)b->group_H.size() + 4) + 2 * 4;
+      b->launches += kBatchGraphSteps * (5 * (int64_t)b->group_H.size() + 5) + 2 * 5;
       nsteps -= kBatchGraphSteps;
     } else {
       int r = batch_issue_step<T>(b);
@@ -1191,13 +1200,15 @@ template <typename T> int batch_autotune_impl(sipf_batch* b, int trial, sipf_bat
   };
   std::vector<float> field_ms(G, 0.f);
   for (int g = 0; g < G; ++g) {
-    FieldTune best_t = b->field_tune[g];
+    FieldTune best_t = field_tune_default<T>(b->group_H[g]);
     float best = 3.0e38f;
-    for (int dim = 0; dim < 3; ++dim) {
-      static const int cand[3][3] = {{8, 16, 32}, {4, 8, 16}, {4, 8, 16}};
-      for (int ci = 0; ci < 3; ++ci) {
+    // plane kernels or pencil passes first, then the x-pass tile, then the
+    // pencil-pass shapes (which only matter if pencils won)
+    static const std::vector<int> cand[4] = {{0, 1}, {4, 8, 16}, {8, 16, 32}, {4, 8, 16}};
+    for (int dim = 0; dim < 4; ++dim) {
+      for (int v : cand[dim]) {
         FieldTune t = best_t;
-        (dim == 0 ? t.bc : dim == 1 ? t.sbc : t.rows_per_sm) = cand[dim][ci];
+        (dim == 0 ? t.plane_mode : dim == 1 ? t.sbc : dim == 2 ? t.bc : t.rows_per_sm) = v;
         if (!field_tune_valid<T>(b->group_H[g], t)) continue;
         b->field_tune[g] = t;
         float ms = 0.f;
@@ -1254,6 +1265,7 @@ template <typename T> int batch_autotune_impl(sipf_batch* b, int trial, sipf_bat
       out->cols_tile[g] = b->field_tune[g].bc;
       out->xpass_tile[g] = b->field_tune[g].sbc;
       out->rows_blocks_per_sm[g] = b->field_tune[g].rows_per_sm;
+      out->plane_kernels[g] = b->field_tune[g].plane_mode == 0 ? 1 : 0;
       out->field_ms[g] = field_ms[g];
     }
     out->move_blocks_per_sm = b->move_bps;
@@ -1331,6 +1343,7 @@ int sipf_batch_init(int32_t nruns, const sipf_params* params, const double* cons
     }
   }
   b->field_tune.assign(b->group_H.size(), FieldTune{});
+  for (sipf_ctx* c : b->runs) b->max_NT = std::max(b->max_NT, c->NT);
   cudaError_t e = cudaMalloc(&b->prefix, (nruns + 1) * sizeof(long long));
   for (size_t i = 0; i < 2 * b->group_H.size() + 4 && e == cudaSuccess; ++i) {
     cudaEvent_t ev = nullptr;
@@ -1370,12 +1383,40 @@ int sipf_batch_step(sipf_batch* b, int64_t nsteps) {
 int sipf_batch_autotune(sipf_batch* b, int32_t steps_per_trial, sipf_batch_tuning* out) {
   if (!b) return fail(SIPF_EINVAL, "batch is NULL");
   if (steps_per_trial < 2) return fail(SIPF_EINVAL, "steps_per_trial (>= 2)");
-  const int64_t most = (int64_t)steps_per_trial * (9 * (int64_t)b->group_H.size() + 9);
+  const int64_t most = (int64_t)steps_per_trial * (11 * (int64_t)b->group_H.size() + 9);
   if (b->n + most > 0xFFFFFFFFLL) return fail(SIPF_EINVAL, "step counter would exceed 2^32 - 1");
   int r = b->precision == 64 ? batch_autotune_impl<double>(b, steps_per_trial, out)
                              : batch_autotune_impl<float>(b, steps_per_trial, out);
   b->record_phases = false;
   return r;
+}
+
+int sipf_batch_set_tuning(sipf_batch* b, const sipf_batch_tuning* t) {
+  if (!b || !t) return fail(SIPF_EINVAL, "batch or tuning is NULL");
+  if (t->ngroups != (int)b->group_H.size()) return fail(SIPF_EINVAL, "tuning has a different number of H groups");
+  std::vector<FieldTune> ft(b->group_H.size());
+  for (size_t g = 0; g < ft.size(); ++g) {
+    if (t->H[g] != b->group_H[g]) return fail(SIPF_EINVAL, "tuning groups are in a different H order");
+    ft[g].bc = t->cols_tile[g];
+    ft[g].sbc = t->xpass_tile[g];
+    ft[g].rows_per_sm = t->rows_blocks_per_sm[g];
+    ft[g].plane_mode = t->plane_kernels[g] ? 0 : 1;
+    const bool ok = b->precision == 64 ? field_tune_valid<double>(b->group_H[g], ft[g])
+                                       : field_tune_valid<float>(b->group_H[g], ft[g]);
+    if (!ok) return fail(SIPF_EINVAL, "tuning group " + std::to_string(g) + " has an unsupported tile shape");
+  }
+  if (t->move_blocks_per_sm < 0 || t->move_blocks_per_sm > 32 || t->deposit_blocks_per_sm < 0 ||
+      t->deposit_blocks_per_sm > 32)
+    return fail(SIPF_EINVAL, "blocks per SM (0..32)");
+  b->field_tune = ft;
+  b->move_bps = t->move_blocks_per_sm;
+  b->dep_bps = t->deposit_blocks_per_sm;
+  if (b->graph) {
+    SIPF_CK(cudaStreamSynchronize(b->stream));
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return SIPF_OK;
 }
 
 int sipf_batch_use_graph(sipf_batch* b, int enable) {

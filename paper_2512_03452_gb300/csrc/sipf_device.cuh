@@ -19,8 +19,16 @@ __device__ __forceinline__ bool t_finite(double v) { return isfinite(v); }
 
 template <typename T> __device__ __forceinline__ cpx<T> cadd(cpx<T> a, cpx<T> b) { return {a.x + b.x, a.y + b.y}; }
 template <typename T> __device__ __forceinline__ cpx<T> csub(cpx<T> a, cpx<T> b) { return {a.x - b.x, a.y - b.y}; }
+// Complex product with its roundings spelled out (one product rounded, the
+// other fused into it), so every kernel that inlines it, whatever the
+// compiler's contraction choices around it, gives the same bits: the FFT
+// kernels of a run and of a batch, or of two launch shapes, agree exactly.
+__device__ __forceinline__ float t_mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double t_mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float t_fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double t_fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 template <typename T> __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
-  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+  return {t_fma_rn(a.x, b.x, -t_mul_rn(a.y, b.y)), t_fma_rn(a.x, b.y, t_mul_rn(a.y, b.x))};
 }
 template <typename T> __device__ __forceinline__ cpx<T> cconj(cpx<T> a) { return {a.x, -a.y}; }
 

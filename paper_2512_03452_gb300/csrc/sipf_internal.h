@@ -73,15 +73,18 @@ cudaError_t launch_rows_c2r(const cpx<T>* in, int ncomp, size_t comp_stride, T* 
 enum { kFieldForward = 1, kFieldSpectral = 2, kFieldInverse = 4, kFieldAll = 7 };
 // Launch shapes of the field solve (0: default): the column tile of the y
 // passes (8, 16 or 32 pencils per block), the column tile of the fused x pass
-// (4, 8 or 16) and the blocks per SM given to the row passes.  Results do not
-// depend on them.
+// (4, 8 or 16), the blocks per SM given to the row passes, and whether the two
+// inner axes run as one plane kernel per direction or as separate pencil
+// passes.  Results agree to rounding; they do not depend on the tile shapes.
 struct FieldTune {
   int bc = 0, sbc = 0, rows_per_sm = 0;
+  int plane_mode = 0;   // 0: plane kernels for the inner axes where they fit (H <= 128), 1: pencil passes
 };
 template <typename T>
 cudaError_t launch_field_batch(const FftRun<T>* runs, int nruns, int H, int stages, cudaStream_t s,
                                const FieldTune& tune = FieldTune{});
 template <typename T> bool field_tune_valid(int H, const FieldTune& t);
+template <typename T> FieldTune field_tune_default(int H);   // the shapes used when a field is 0
 
 // FP64 FMA throughput probe: blocks x 256 threads x 8 chains x iters FMAs.
 cudaError_t launch_fp64_fma(int blocks, int iters, double* sink, cudaStream_t s);
@@ -158,6 +161,7 @@ struct ChunkListArgs {
   ChunkDesc* chunks;
   int* other_cursor;        // cursors of the other buffer (cleared)
   int NT;
+  long long* part;          // chunk totals of the blocks of kCLBlock bins (chunk_list_blocks(NT))
 };
 struct LayoutArgs {
   const int* want;
@@ -171,7 +175,7 @@ cudaError_t launch_move_batch(const BinArgs<T>* table, const long long* prefix, 
 template <typename T>
 cudaError_t launch_deposit_batch(const BinArgs<T>* table, const long long* prefix, int nruns,
                                  unsigned long long* work, bool fixed, cudaStream_t s, int blocks_per_sm = 0);
-cudaError_t launch_chunk_list_batch(const ChunkListArgs* t, int nruns, cudaStream_t s);
+cudaError_t launch_chunk_list_batch(const ChunkListArgs* t, int nruns, int max_NT, cudaStream_t s);
 cudaError_t launch_run_prefix(const ChunkListArgs* t, int nruns, long long* prefix, unsigned long long* work,
                               uint32_t* step, int bump, cudaStream_t s);
 cudaError_t launch_layout_batch(const LayoutArgs* t, int nruns, cudaStream_t s);
@@ -184,9 +188,11 @@ template <typename T> cudaError_t launch_move(const BinArgs<T>& a, cudaStream_t 
 // From fill cursors: clamped counts, chunk prefix sums and chunk descriptors
 // (slots from `base`); clears other_cursor and the work counter.  ovf_total
 // (nullable) accumulates the number of particles in the overflow bin.
-cudaError_t launch_chunk_list(const int* cursor, const int* cap, const long long* base, int* count,
-                              long long* chunk_start, ChunkDesc* chunks, int* other_cursor, int NT,
-                              unsigned long long* work, unsigned long long* ovf_total, cudaStream_t s);
+// Chunk list of one buffer: two launches (count, emit); clears *work and adds
+// the overflow-bin count to *ovf_total when those are non-NULL.
+int chunk_list_blocks(int NT);
+cudaError_t launch_chunk_list(const ChunkListArgs& a, unsigned long long* work, unsigned long long* ovf_total,
+                              cudaStream_t s);
 cudaError_t launch_layout(const int* want, int* cap, long long* base, int NT, int ntx, int ovf_cap, cudaStream_t s);
 template <typename T>
 cudaError_t launch_tile_hist(const T* x, const T* y, const T* z, int64_t P, Geo<T> g, int shift, int ntx, int NT,

@@ -123,7 +123,7 @@ def test_batch_launches_do_not_grow_with_runs():
             counts.append(_abi.sipf_batch_kernel_launches(b.handle) - k0)
     # both batches hold H = 32 and H = 64 runs: same launches per step
     assert counts[0] == counts[1]
-    assert counts[0] == 32 * (2 * 5 + 4) + 2 * 4
+    assert counts[0] == 32 * (2 * 5 + 5) + 2 * 5
 
 
 def test_batch_rejects_bad_parameter_sets():
@@ -159,3 +159,49 @@ def test_autotune_changes_shapes_not_results():
         for r in range(len(params)):
             assert np.array_equal(b.positions(r), got[r][0]), r
             assert np.array_equal(b.spectrum(r), got[r][1]), r
+
+
+def _tuning(H, **kw):
+    t = _abi.sipf_batch_tuning()
+    t.ngroups = len(H)
+    for g, h in enumerate(H):
+        t.H[g] = h
+        t.plane_kernels[g] = 1
+    for k, v in kw.items():
+        if k in ("move_blocks_per_sm", "deposit_blocks_per_sm"):
+            setattr(t, k, v)
+        else:
+            g, name = k.split("_", 1)
+            getattr(t, name)[int(g[1:])] = v
+    return t
+
+
+@pytest.mark.parametrize("shape", [dict(g1_plane_kernels=0), dict(g0_plane_kernels=0, g0_cols_tile=32),
+                                   dict(g1_plane_kernels=0, g1_cols_tile=8, g1_rows_blocks_per_sm=4),
+                                   dict(g1_xpass_tile=4), dict(move_blocks_per_sm=1, deposit_blocks_per_sm=1)])
+def test_launch_shapes_give_identical_bits(shape):
+    """Plane or pencil FFT kernels, tile widths and grid sizes: the same bits
+    (deterministic deposit; the lone-particle run amplifies any difference)."""
+    _, params, X0s = _runs(32, mode=1, n=4, seed=12)
+
+    def run(t):
+        with Batch(params, X0s) as b:
+            if t is not None:
+                _abi.sipf_batch_set_tuning(b.handle, t)
+            b.step(60)
+            b.sync()
+            return [(b.positions(r), b.spectrum(r)) for r in range(len(params))]
+
+    ref, got = run(None), run(_tuning([32, 64], **shape))
+    for r in range(len(params)):
+        assert np.array_equal(got[r][0], ref[r][0]), r
+        assert np.array_equal(got[r][1], ref[r][1]), r
+
+
+def test_set_tuning_rejects_bad_shapes():
+    _, params, X0s = _runs(32, mode=0, n=2, seed=1)
+    with Batch(params, X0s) as b:
+        with pytest.raises(_abi.SipfError):
+            _abi.sipf_batch_set_tuning(b.handle, _tuning([32, 64], g0_cols_tile=12))
+        with pytest.raises(_abi.SipfError):
+            _abi.sipf_batch_set_tuning(b.handle, _tuning([64, 32]))
