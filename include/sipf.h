@@ -241,6 +241,8 @@ typedef struct sipf_batch_tuning {
   int32_t rows_blocks_per_sm[4];  /* blocks per SM shared by the row passes          */
   int32_t plane_kernels[4];       /* 1: both inner axes in one plane kernel per
                                      direction; 0: separate pencil passes        */
+  int32_t plane_warps[4];         /* warps per block of the plane kernels: 8, 16, 32 */
+  int32_t xpass_warps[4];         /* warps per block of the fused x pass: 8, 16      */
   int32_t move_blocks_per_sm;     /* move + re-bin blocks per SM (0: occupancy limit) */
   int32_t deposit_blocks_per_sm;  /* deposit blocks per SM (0: occupancy limit)       */
   double field_ms[4];             /* best device ms per step of each group's field solve */
@@ -253,7 +255,7 @@ typedef struct sipf_batch_tuning {
  * candidates above, each timed with CUDA events on steps_per_trial (>= 2)
  * real steps of the batch (the first step of a trial is not timed).  Shapes
  * do not change results, so the runs advance by out->steps_used steps (about
- * steps_per_trial x (11 per group + 9)).  Later steps use the chosen shapes;
+ * steps_per_trial x (16 per group + 9)).  Later steps use the chosen shapes;
  * out may be NULL.  Synchronises. */
 int sipf_batch_autotune(sipf_batch* b, int32_t steps_per_trial, sipf_batch_tuning* out);
 

@@ -527,7 +527,7 @@ __device__ __forceinline__ void cols_body(cpx<T>* __restrict__ base, int B, T sc
     buf[j * LD + c] = c < nb ? base[(size_t)j * B + b0 + c] : cpx<T>{T(0), T(0)};
   }
   __syncthreads();
-  for (int c = wib; c < nb; c += 8) {
+  for (int c = wib; c < nb; c += (int)(blockDim.x >> 5)) {
     cpx<T> v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = buf[(lane + 32 * m) * LD + c];
@@ -573,7 +573,7 @@ __device__ __forceinline__ void spectral_body(const cpx<T>* __restrict__ T1, cpx
       buf[j * LD + c] = c < nb ? T1[(size_t)j * B + b0 + c] : cpx<T>{T(0), T(0)};
     }
     __syncthreads();
-    for (int c = wib; c < nb; c += 8) {
+    for (int c = wib; c < nb; c += (int)(blockDim.x >> 5)) {
       cpx<T> v[E];
 #pragma unroll
       for (int m = 0; m < E; ++m) v[m] = buf[(lane + 32 * m) * LD + c];
@@ -641,7 +641,7 @@ __device__ __forceinline__ void spectral_body(const cpx<T>* __restrict__ T1, cpx
   }
   __syncthreads();
   constexpr int nout = (MODE == kModeStep || MODE == kModeGradOnly) ? 3 : 1;
-  for (int col = wib; col < nout * BC; col += 8) {
+  for (int col = wib; col < nout * BC; col += (int)(blockDim.x >> 5)) {
     const int c = BC + col;
     if (col % BC >= nb) continue;
     cpx<T> v[E];
@@ -789,7 +789,7 @@ __global__ void __launch_bounds__(256) kwb_cols(const FftRun<T>* __restrict__ ru
 }
 
 template <typename T, int E, int BC>
-__global__ void __launch_bounds__(256) kwb_spectral_x(const FftRun<T>* __restrict__ runs) {
+__global__ void __launch_bounds__(512) kwb_spectral_x(const FftRun<T>* __restrict__ runs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
   load_tw_full(tw);
@@ -822,8 +822,11 @@ __global__ void __launch_bounds__(256) kwb_rows_c2r(const FftRun<T>* __restrict_
 //            of row pairs, written into that component's slot of the
 //            interleaved (gx, gy, gz, -) nodes.
 // ---------------------------------------------------------------------------
-template <typename T, int E> constexpr size_t plane_smem_bytes() {
-  return ((size_t)32 * E * (16 * E + 1) + (size_t)8 * 32 * E + kNmax) * sizeof(cpx<T>);
+constexpr int kDefaultPlaneWarps = 8;      // warps per block of the plane kernels
+constexpr int kDefaultSpectralWarps = 8;   // warps per block of the fused x pass
+
+template <typename T, int E> constexpr size_t plane_smem_bytes(int nw) {
+  return ((size_t)32 * E * (16 * E + 1) + (size_t)nw * 32 * E + kNmax) * sizeof(cpx<T>);
 }
 
 template <typename T, int E, typename Tin>
@@ -833,7 +836,7 @@ __device__ __forceinline__ void plane_fwd_body(Tin* __restrict__ in, double in_s
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   cpx<T>* zb = zball + wib * N;
   // 1. rows: two real rows as one complex pencil, split into their half spectra
-  for (int pr = wib; pr < N / 2; pr += 8) {
+  for (int pr = wib; pr < N / 2; pr += (int)(blockDim.x >> 5)) {
     const size_t ra = (size_t)(2 * pr) * N, rb = ra + N;
     cpx<T> v[E];
 #pragma unroll
@@ -869,7 +872,7 @@ __device__ __forceinline__ void plane_fwd_body(Tin* __restrict__ in, double in_s
   }
   __syncthreads();
   // 2. y axis: one column per warp
-  for (int c = wib; c < NH; c += 8) {
+  for (int c = wib; c < NH; c += (int)(blockDim.x >> 5)) {
     cpx<T> v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = P[(lane + 32 * m) * NH + c];
@@ -890,7 +893,7 @@ __device__ __forceinline__ void plane_inv_body(const cpx<T>* __restrict__ in, T*
   for (int t = threadIdx.x; t < N * NH; t += blockDim.x) P[t] = in[t];
   __syncthreads();
   // 1. y axis inverse: one column per warp
-  for (int c = wib; c < NH; c += 8) {
+  for (int c = wib; c < NH; c += (int)(blockDim.x >> 5)) {
     cpx<T> v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = P[(lane + 32 * m) * NH + c];
@@ -901,7 +904,7 @@ __device__ __forceinline__ void plane_inv_body(const cpx<T>* __restrict__ in, T*
   __syncthreads();
   // 2. rows: two Hermitian half rows A, B as the pencil A + i B; the inverse
   //    transform's real part is row A, its imaginary part row B
-  for (int pr = wib; pr < N / 2; pr += 8) {
+  for (int pr = wib; pr < N / 2; pr += (int)(blockDim.x >> 5)) {
     cpx<T>* pa = P + (size_t)(2 * pr) * NH;
     const cpx<T>* pb = pa + NH;
     for (int k = lane; k < NH; k += 32) {
@@ -935,12 +938,12 @@ __device__ __forceinline__ void plane_inv_body(const cpx<T>* __restrict__ in, T*
 }
 
 template <typename T, int E>
-__global__ void __launch_bounds__(256) kwp_fwd(const FftRun<T>* __restrict__ runs) {
+__global__ void __launch_bounds__(1024) kwp_fwd(const FftRun<T>* __restrict__ runs) {
   constexpr int N = 32 * E, NH = N / 2 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* zb = tw + kNmax;
-  cpx<T>* P = zb + 8 * N;
+  cpx<T>* P = zb + (blockDim.x >> 5) * N;
   load_tw_full(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.y];
@@ -954,12 +957,12 @@ __global__ void __launch_bounds__(256) kwp_fwd(const FftRun<T>* __restrict__ run
 }
 
 template <typename T, int E>
-__global__ void __launch_bounds__(256) kwp_inv(const FftRun<T>* __restrict__ runs) {
+__global__ void __launch_bounds__(1024) kwp_inv(const FftRun<T>* __restrict__ runs) {
   constexpr int N = 32 * E, NH = N / 2 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* zb = tw + kNmax;
-  cpx<T>* P = zb + 8 * N;
+  cpx<T>* P = zb + (blockDim.x >> 5) * N;
   load_tw_full(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.z];
@@ -1212,13 +1215,13 @@ static cudaError_t kwb_cols_bc(const FftRun<T>* runs, int nruns, int ncomp, int 
 }
 
 template <typename T, int E, int SBC>
-static cudaError_t kwb_spectral_launch(const FftRun<T>* runs, int nruns, cudaStream_t s) {
+static cudaError_t kwb_spectral_launch(const FftRun<T>* runs, int nruns, int nw, cudaStream_t s) {
   constexpr int N = 32 * E, NHH = N / 2 + 1;
   const size_t sms = spectral_smem<T, E, SBC>();
   if (sms > kMaxSmem) return cudaErrorInvalidValue;
   cudaError_t e;
   if ((e = set_smem(kwb_spectral_x<T, E, SBC>, sms)) != cudaSuccess) return e;
-  kwb_spectral_x<T, E, SBC><<<dim3((N * NHH + SBC - 1) / SBC, nruns), 256, sms, s>>>(runs);
+  kwb_spectral_x<T, E, SBC><<<dim3((N * NHH + SBC - 1) / SBC, nruns), 32 * nw, sms, s>>>(runs);
   return cudaGetLastError();
 }
 
@@ -1236,12 +1239,14 @@ static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, c
   const int rblocks = max(1, min(rows_budget / max(nruns, 1), (N * N / 2 + 7) / 8));
   const int bc = tune.bc > 0 ? tune.bc : 16;
   const int sbc = tune.sbc > 0 ? tune.sbc : default_sbc<T, E>();
-  constexpr size_t psm = plane_smem_bytes<T, E>();
+  const int pnw = tune.plane_nw > 0 ? tune.plane_nw : kDefaultPlaneWarps;
+  const int snw = tune.spec_nw > 0 ? tune.spec_nw : kDefaultSpectralWarps;
+  const size_t psm = plane_smem_bytes<T, E>(pnw);
   const bool planes = tune.plane_mode == 0 && E <= 4 && psm <= kMaxSmem;
   if (stages & kFieldForward) {
     if (planes) {
       if ((e = set_smem(kwp_fwd<T, E>, psm)) != cudaSuccess) return e;
-      kwp_fwd<T, E><<<dim3(N, nruns), 256, psm, s>>>(runs);
+      kwp_fwd<T, E><<<dim3(N, nruns), 32 * pnw, psm, s>>>(runs);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     } else {
       kwb_rows_r2c<T, E><<<dim3(rblocks, nruns), 256, 0, s>>>(runs);
@@ -1251,15 +1256,15 @@ static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, c
   }
   if (stages & kFieldSpectral) {
     switch (sbc) {
-      case 4: e = kwb_spectral_launch<T, E, 4>(runs, nruns, s); break;
-      case 8: e = kwb_spectral_launch<T, E, 8>(runs, nruns, s); break;
-      default: e = kwb_spectral_launch<T, E, 16>(runs, nruns, s); break;
+      case 4: e = kwb_spectral_launch<T, E, 4>(runs, nruns, snw, s); break;
+      case 8: e = kwb_spectral_launch<T, E, 8>(runs, nruns, snw, s); break;
+      default: e = kwb_spectral_launch<T, E, 16>(runs, nruns, snw, s); break;
     }
     if (e != cudaSuccess) return e;
   }
   if ((stages & kFieldInverse) && planes) {
     if ((e = set_smem(kwp_inv<T, E>, psm)) != cudaSuccess) return e;
-    kwp_inv<T, E><<<dim3(N, 3, nruns), 256, psm, s>>>(runs);
+    kwp_inv<T, E><<<dim3(N, 3, nruns), 32 * pnw, psm, s>>>(runs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   } else if (stages & kFieldInverse) {
     if ((e = kwb_cols_bc<T, E, +1>(runs, nruns, 3, bc, s)) != cudaSuccess) return e;
@@ -1275,8 +1280,12 @@ template <typename T, int E> static bool field_tune_valid_e(const FieldTune& t) 
   const int bc = t.bc > 0 ? t.bc : 16, sbc = t.sbc > 0 ? t.sbc : default_sbc<T, E>();
   size_t c = bc == 8 ? cols_smem<T, E, 8>() : bc == 32 ? cols_smem<T, E, 32>() : cols_smem<T, E, 16>();
   size_t x = sbc == 4 ? spectral_smem<T, E, 4>() : sbc == 8 ? spectral_smem<T, E, 8>() : spectral_smem<T, E, 16>();
+  const bool pnw_ok = t.plane_nw == 0 || t.plane_nw == 8 || t.plane_nw == 16 || t.plane_nw == 32;
+  const bool snw_ok = t.spec_nw == 0 || t.spec_nw == 8 || t.spec_nw == 16;
+  const int pnw = t.plane_nw > 0 ? t.plane_nw : kDefaultPlaneWarps;
   return (bc == 8 || bc == 16 || bc == 32) && (sbc == 4 || sbc == 8 || sbc == 16) && c <= kMaxSmem &&
-         x <= kMaxSmem && t.rows_per_sm >= 0 && t.rows_per_sm <= 32 && (t.plane_mode == 0 || t.plane_mode == 1);
+         x <= kMaxSmem && t.rows_per_sm >= 0 && t.rows_per_sm <= 32 && (t.plane_mode == 0 || t.plane_mode == 1) &&
+         pnw_ok && snw_ok && (t.plane_mode == 1 || E > 4 || plane_smem_bytes<T, E>(pnw) <= kMaxSmem);
 }
 
 template <typename T> FieldTune field_tune_default(int H) {
@@ -1284,6 +1293,8 @@ template <typename T> FieldTune field_tune_default(int H) {
   t.bc = 16;
   t.rows_per_sm = 8;
   t.plane_mode = 0;
+  t.plane_nw = kDefaultPlaneWarps;
+  t.spec_nw = kDefaultSpectralWarps;
   switch (H) {
     case 32: t.sbc = default_sbc<T, 1>(); break;
     case 64: t.sbc = default_sbc<T, 2>(); break;

@@ -79,6 +79,8 @@ enum { kFieldForward = 1, kFieldSpectral = 2, kFieldInverse = 4, kFieldAll = 7 }
 struct FieldTune {
   int bc = 0, sbc = 0, rows_per_sm = 0;
   int plane_mode = 0;   // 0: plane kernels for the inner axes where they fit (H <= 128), 1: pencil passes
+  int plane_nw = 0;     // warps per block of the plane kernels (8, 16, 32)
+  int spec_nw = 0;      // warps per block of the fused x pass (8, 16)
 };
 template <typename T>
 cudaError_t launch_field_batch(const FftRun<T>* runs, int nruns, int H, int stages, cudaStream_t s,
