@@ -37,10 +37,10 @@ P_FULL, H_FULL = 10_000_000, 128
 # algorithmic bytes of the particle kernel per particle-step (FP32): read X (12 B) + write X (12 B)
 BYTES_PER_PARTICLE = 24
 # DRAM traffic (read + write bytes) of the particle phase, move + re-bin
-# (314.5 MB) and deposit (135.0 MB) launches of one step, from ncu captures of
+# (314.4 MB) and deposit (134.5 MB) launches of one step, from ncu captures of
 # the torus workload, keyed by the SHA-256 of the kernel sources they were
 # taken on (a changed kernel reports null until it is captured again).
-MOVE_TRAFFIC = {"40634f06b4f6586984342864f5b51aa6de50572fae8a6e6bb55ed0b20846bc27": 449.5e6}
+MOVE_TRAFFIC = {"4aeb88cc48fbf2bf54ad4267affe99e198673082a837a44903dbd2a872459db1": 448.9e6}
 FALLBACK_HBM_GBS = 6800.0
 
 
