@@ -1232,7 +1232,9 @@ template <typename T, int E> static int default_sbc() {
 
 template <typename T, int E>
 static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, const FieldTune& tune,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, int* launched) {
+  int dummy = 0;
+  int& nk = launched ? *launched : dummy;
   constexpr int N = 32 * E;
   cudaError_t e;
   const int rows_budget = 152 * (tune.rows_per_sm > 0 ? tune.rows_per_sm : 8);
@@ -1248,10 +1250,12 @@ static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, c
       if ((e = set_smem(kwp_fwd<T, E>, psm)) != cudaSuccess) return e;
       kwp_fwd<T, E><<<dim3(N, nruns), 32 * pnw, psm, s>>>(runs);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      nk += 1;
     } else {
       kwb_rows_r2c<T, E><<<dim3(rblocks, nruns), 256, 0, s>>>(runs);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       if ((e = kwb_cols_bc<T, E, -1>(runs, nruns, 1, bc, s)) != cudaSuccess) return e;
+      nk += 2;
     }
   }
   if (stages & kFieldSpectral) {
@@ -1261,17 +1265,20 @@ static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, c
       default: e = kwb_spectral_launch<T, E, 16>(runs, nruns, snw, s); break;
     }
     if (e != cudaSuccess) return e;
+    nk += 1;
   }
   if ((stages & kFieldInverse) && planes) {
     if ((e = set_smem(kwp_inv<T, E>, psm)) != cudaSuccess) return e;
     kwp_inv<T, E><<<dim3(N, 3, nruns), 32 * pnw, psm, s>>>(runs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    nk += 1;
   } else if (stages & kFieldInverse) {
     if ((e = kwb_cols_bc<T, E, +1>(runs, nruns, 3, bc, s)) != cudaSuccess) return e;
     const size_t smr = (kNmax + (size_t)8 * N) * sizeof(cpx<T>) + (size_t)8 * 2 * N * 4 * sizeof(T);
     if ((e = set_smem(kwb_rows_c2r<T, E>, smr)) != cudaSuccess) return e;
     kwb_rows_c2r<T, E><<<dim3(rblocks, nruns), 256, smr, s>>>(runs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    nk += 2;
   }
   return cudaSuccess;
 }
@@ -1316,13 +1323,13 @@ template <typename T> bool field_tune_valid(int H, const FieldTune& t) {
 
 template <typename T>
 cudaError_t launch_field_batch(const FftRun<T>* runs, int nruns, int H, int stages, cudaStream_t s,
-                               const FieldTune& tune) {
+                               const FieldTune& tune, int* launched) {
   if (nruns <= 0) return cudaSuccess;
   switch (H) {
-    case 32: return field_batch_e<T, 1>(runs, nruns, stages, tune, s);
-    case 64: return field_batch_e<T, 2>(runs, nruns, stages, tune, s);
-    case 128: return field_batch_e<T, 4>(runs, nruns, stages, tune, s);
-    case 256: return field_batch_e<T, 8>(runs, nruns, stages, tune, s);
+    case 32: return field_batch_e<T, 1>(runs, nruns, stages, tune, s, launched);
+    case 64: return field_batch_e<T, 2>(runs, nruns, stages, tune, s, launched);
+    case 128: return field_batch_e<T, 4>(runs, nruns, stages, tune, s, launched);
+    case 256: return field_batch_e<T, 8>(runs, nruns, stages, tune, s, launched);
   }
   return cudaErrorInvalidValue;
 }
@@ -1334,7 +1341,7 @@ cudaError_t launch_field_batch(const FftRun<T>* runs, int nruns, int H, int stag
   template cudaError_t launch_spectral_x<T>(const cpx<T>*, cpx<T>*, cpx<T>*, int, SpecParams, int, double*,  \
                                             cudaStream_t);                                                  \
   template cudaError_t launch_rows_c2r<T>(const cpx<T>*, int, size_t, T*, int, int, double*, cudaStream_t);     \
-  template cudaError_t launch_field_batch<T>(const FftRun<T>*, int, int, int, cudaStream_t, const FieldTune&); \
+  template cudaError_t launch_field_batch<T>(const FftRun<T>*, int, int, int, cudaStream_t, const FieldTune&, int*); \
   template bool field_tune_valid<T>(int, const FieldTune&);                                                   \
   template FieldTune field_tune_default<T>(int);
 SIPF_INST(float)

@@ -287,9 +287,10 @@ template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
     const int64_t l0 = c->launches;
     SIPF_CK(mark(&ev[0]));
     const FftRun<T>* fr = (const FftRun<T>*)c->fft_run;
+    int fk = 0;   // field-solve kernels launched this step
     // beta^(n-1) = F_H I(rho-hat^(n-1)); the deposit grid is cleared as it is read
     if (fr) {
-      SIPF_CK(launch_field_batch<T>(fr, 1, H, kFieldForward, c->stream));
+      SIPF_CK(launch_field_batch<T>(fr, 1, H, kFieldForward, c->stream, FieldTune{}, &fk));
     } else {
       SIPF_CK(launch_rows_r2c<T>(c->phi, c->fixed() ? 1 : 0, fixed_in_scale(c), true, T1, H, H * H, nullptr,
                                  c->stream));
@@ -298,13 +299,13 @@ template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
     SIPF_CK(mark(&ev[1]));
     // alpha^n and G(alpha^(n-1)), x axis back-transformed
     if (fr) {
-      SIPF_CK(launch_field_batch<T>(fr, 1, H, kFieldSpectral, c->stream));
+      SIPF_CK(launch_field_batch<T>(fr, 1, H, kFieldSpectral, c->stream, FieldTune{}, &fk));
     } else {
       SIPF_CK(launch_spectral_x<T>(T1, al, T2, H, sp, kModeStep, c->dsc + kDscAlpha0, c->stream));
     }
     SIPF_CK(mark(&ev[2]));
     if (fr) {
-      SIPF_CK(launch_field_batch<T>(fr, 1, H, kFieldInverse, c->stream));
+      SIPF_CK(launch_field_batch<T>(fr, 1, H, kFieldInverse, c->stream, FieldTune{}, &fk));
     } else {
       SIPF_CK(launch_cols<T>(T2, H, H, nh, 3, S, +1, 1.0, c->stream));
       SIPF_CK(launch_rows_c2r<T>(T2, 3, S, (T*)c->grad, H, H * H, nullptr, c->stream));
@@ -317,7 +318,7 @@ template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
     SIPF_CK(mark(&ev[4]));
     SIPF_CK(launch_chunk_list(cl_args(c, c->cursor[dst], c->lcap[c->lc], c->lbase[c->lc], c->cursor[src]), c->work,
                               c->timing ? c->ovf : nullptr, c->stream));
-    c->launches += 8;
+    c->launches += (fr ? fk : 5) + 3;
     c->cur = dst;
     c->n += 1;
     if (++c->since_layout >= c->resort()) {
@@ -1008,6 +1009,7 @@ struct sipf_batch {
   int graph_cur = -1, graph_lc = -1, graph_since = -1;
   int64_t launches = 0;
   int max_NT = 1;   // most tiles of any run (grid of the batched chunk-list passes)
+  int field_kernels = 0;   // field-solve kernels of the last issued step
   // launch shapes (autotuned) and per-phase events of the last issued step
   std::vector<FieldTune> field_tune;
   int move_bps = 0, dep_bps = 0;
@@ -1093,11 +1095,12 @@ template <typename T> int batch_issue_step(sipf_batch* b) {
   const int R = b->nruns;
   cudaStream_t s = b->stream;
   const int G = (int)b->group_H.size();
+  int fk = 0;   // field-solve kernels launched this step
   auto mark = [&](int i) -> cudaError_t { return b->record_phases ? cudaEventRecord(b->ev[i], s) : cudaSuccess; };
   for (int g = 0; g < G; ++g) {
     SIPF_CK(mark(2 * g));
     SIPF_CK(launch_field_batch<T>((const FftRun<T>*)b->fft_tab[g], b->group_n[g], b->group_H[g], kFieldAll, s,
-                                  b->field_tune[g]));
+                                  b->field_tune[g], &fk));
     SIPF_CK(mark(2 * g + 1));
   }
   SIPF_CK(mark(2 * G));
@@ -1107,7 +1110,8 @@ template <typename T> int batch_issue_step(sipf_batch* b) {
   SIPF_CK(launch_chunk_list_batch(b->cl_tab[1 - b->cur][b->lc], R, b->max_NT, s));
   SIPF_CK(launch_run_prefix(b->cl_tab[1 - b->cur][b->lc], R, b->prefix, b->work, b->step, 1, s));
   SIPF_CK(mark(2 * G + 1));
-  b->launches += 5 * (int64_t)b->group_H.size() + 4;
+  b->launches += fk + 4;
+  b->field_kernels = fk;
   b->cur = 1 - b->cur;
   if (++b->since >= kBatchResort) {
     SIPF_CK(launch_layout_batch(b->ly_tab[b->cur][1 - b->lc], R, s));
@@ -1165,7 +1169,7 @@ template <typename T> int batch_step_impl(sipf_batch* b, int64_t nsteps) {
       SIPF_CK(cudaGraphLaunch(b->graph, b->stream));
       // 32 steps hold 32 moves and 2 capacity rebuilds: parities return
       b->n += kBatchGraphSteps;
-      b->launches += kBatchGraphSteps * (5 * (int64_t)b->group_H.size() + 5) + 2 * 5;
+      b->launches += kBatchGraphSteps * ((int64_t)b->field_kernels + 5) + 2 * 5;
       nsteps -= kBatchGraphSteps;
     } else {
       int r = batch_issue_step<T>(b);

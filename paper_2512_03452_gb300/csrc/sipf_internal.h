@@ -84,7 +84,7 @@ struct FieldTune {
 };
 template <typename T>
 cudaError_t launch_field_batch(const FftRun<T>* runs, int nruns, int H, int stages, cudaStream_t s,
-                               const FieldTune& tune = FieldTune{});
+                               const FieldTune& tune = FieldTune{}, int* launched = nullptr);   // += kernels launched
 template <typename T> bool field_tune_valid(int H, const FieldTune& t);
 template <typename T> FieldTune field_tune_default(int H);   // the shapes used when a field is 0
 
