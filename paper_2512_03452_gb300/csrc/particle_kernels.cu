@@ -975,6 +975,46 @@ k_unbin(BinArgs<T> a, T* __restrict__ ox, T* __restrict__ oy, T* __restrict__ oz
   }
 }
 
+// Gather back to particle order in two coalesced-friendly passes: each
+// particle's (x, y, z) goes to its id's slot of a 4-wide scratch array (one
+// 16- or 32-byte store instead of three scattered 4- or 8-byte ones), then
+// the scratch is transposed into the three output arrays.
+template <typename T> struct Vec4Store;
+template <> struct Vec4Store<float> {
+  static __device__ __forceinline__ void put(float* dst, float x, float y, float z) {
+    *reinterpret_cast<float4*>(dst) = make_float4(x, y, z, 0.f);
+  }
+};
+template <> struct Vec4Store<double> {
+  static __device__ __forceinline__ void put(double* dst, double x, double y, double z) {
+    reinterpret_cast<double2*>(dst)[0] = make_double2(x, y);
+    reinterpret_cast<double2*>(dst)[1] = make_double2(z, 0.0);
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_unbin_aos(BinArgs<T> a, T* __restrict__ aos) {
+  const long long c = blockIdx.x;
+  if (c >= a.chunk_start[a.NT + 1]) return;
+  const ChunkDesc d = a.chunks[c];
+  for (int i = threadIdx.x; i < d.len; i += blockDim.x) {
+    const long long s = d.start + i;
+    Vec4Store<T>::put(aos + (size_t)a.sid[s] * 4, a.sx[s], a.sy[s], a.sz[s]);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_aos4_to_soa(const T* __restrict__ aos, int64_t P, T* __restrict__ ox, T* __restrict__ oy, T* __restrict__ oz) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
+    const T* v = aos + (size_t)p * 4;
+    ox[p] = v[0];
+    oy[p] = v[1];
+    oz[p] = v[2];
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_iota(uint32_t* id, int64_t P) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -1240,8 +1280,17 @@ bool launch_rebin_plain(const T* x, const T* y, const T* z, const uint32_t* id, 
 }
 
 template <typename T>
-cudaError_t launch_unbin(const BinArgs<T>& a, int64_t max_chunks, T* x, T* y, T* z, cudaStream_t s) {
-  k_unbin<T><<<(unsigned)max_chunks, 256, 0, s>>>(a, x, y, z);
+cudaError_t launch_unbin(const BinArgs<T>& a, int64_t max_chunks, T* x, T* y, T* z, T* aos_scratch, int64_t P,
+                         cudaStream_t s) {
+  if (!aos_scratch) {
+    k_unbin<T><<<(unsigned)max_chunks, 256, 0, s>>>(a, x, y, z);
+    return cudaGetLastError();
+  }
+  k_unbin_aos<T><<<(unsigned)max_chunks, 256, 0, s>>>(a, aos_scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t b = (P + 255) / 256;
+  k_aos4_to_soa<T><<<(unsigned)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b)), 256, 0, s>>>(aos_scratch, P, x, y, z);
   return cudaGetLastError();
 }
 
@@ -1309,7 +1358,7 @@ template <typename T> cudaError_t launch_alpha_energy(const cpx<T>* alpha, int H
   template bool launch_rebin_plain<T>(const T*, const T*, const T*, const uint32_t*, int64_t, Geo<T>, int, int, \
                                       int, T*, T*, T*, uint32_t*, const long long*, const int*, int*, int*,    \
                                       cudaStream_t, cudaError_t*);                                            \
-  template cudaError_t launch_unbin<T>(const BinArgs<T>&, int64_t, T*, T*, T*, cudaStream_t);                 \
+  template cudaError_t launch_unbin<T>(const BinArgs<T>&, int64_t, T*, T*, T*, T*, int64_t, cudaStream_t);    \
   template cudaError_t launch_deposit<T>(const T*, const T*, const T*, int64_t, Geo<T>, T, T*, int,           \
                                          cudaStream_t);                                                      \
   template cudaError_t launch_gather<T>(const T*, const T*, const T*, int64_t, Geo<T>, const T*, int, int,   \

@@ -264,7 +264,10 @@ template <typename T> int rebin_from_staging(sipf_ctx* c) {
 
 // Particle order -> staging arrays (or caller-owned device arrays).
 template <typename T> int unbin_to(sipf_ctx* c, T* x, T* y, T* z) {
-  SIPF_CK(launch_unbin<T>(bin_args<T>(c, c->cur, c->lc, -1, 0), c->max_chunks(), x, y, z, c->stream));
+  // the other bin buffer is free between steps (the next move overwrites it):
+  // its x array (cap_total >= 4P elements) is the 4-wide scratch
+  SIPF_CK(launch_unbin<T>(bin_args<T>(c, c->cur, c->lc, -1, 0), c->max_chunks(), x, y, z,
+                          (T*)c->bx[1 - c->cur][0], c->p.P, c->stream));
   return SIPF_OK;
 }
 

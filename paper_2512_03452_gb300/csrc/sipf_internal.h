@@ -206,7 +206,10 @@ bool launch_rebin_plain(const T* x, const T* y, const T* z, const uint32_t* id, 
                         int ntx, int NT, T* dx, T* dy, T* dz, uint32_t* did, const long long* dst_base,
                         const int* dst_cap, int* dst_cursor, int* err, cudaStream_t s, cudaError_t* e);
 template <typename T>
-cudaError_t launch_unbin(const BinArgs<T>& a, int64_t max_chunks, T* x, T* y, T* z, cudaStream_t s);
+// Particle order from the bins; with aos_scratch (4 P elements) through a
+// 4-wide scratch array and a transpose, else by three scattered stores.
+cudaError_t launch_unbin(const BinArgs<T>& a, int64_t max_chunks, T* x, T* y, T* z, T* aos_scratch, int64_t P,
+                         cudaStream_t s);
 cudaError_t launch_iota(uint32_t* id, int64_t P, cudaStream_t s);
 template <typename T>
 cudaError_t launch_deposit(const T* x, const T* y, const T* z, int64_t P, Geo<T> g, T w, T* phi, int order,
