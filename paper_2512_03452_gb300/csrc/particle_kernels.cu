@@ -730,24 +730,38 @@ __device__ __forceinline__ void chunk_count_body(const ChunkListArgs& a, int blk
 __device__ __forceinline__ void chunk_emit_body(const ChunkListArgs& a, int blk, int nblk, unsigned long long* work,
                                                 unsigned long long* ovf_total) {
   __shared__ long long s_off;
+  __shared__ long long s_ls[kCLBlock];   // block-local first chunk of each bin
   if (threadIdx.x == 0) {
     long long o = 0;
     for (int i = 0; i < blk; ++i) o += a.part[i];
     s_off = o;
   }
+  const long long total = a.part[blk];
   __syncthreads();
   const long long off = s_off;
   const int nb = a.NT + 1;
   const int b = blk * kCLBlock + threadIdx.x;
   if (b < nb) {
-    const long long st = a.chunk_start[b] + off;
-    a.chunk_start[b] = st;
-    const int c = a.count[b];
-    const long long bb = a.base[b];
-    for (int j = 0; j * kChunk < c; ++j) a.chunks[st + j] = ChunkDesc{bb + (long long)j * kChunk, b, min(kChunk, c - j * kChunk)};
+    const long long ls = a.chunk_start[b];
+    a.chunk_start[b] = ls + off;
+    s_ls[threadIdx.x] = ls;
+  } else {
+    s_ls[threadIdx.x] = total;
+  }
+  __syncthreads();
+  // descriptors: one per thread, each finding its bin (the last bin whose first chunk is <= q)
+  for (long long q = threadIdx.x; q < total; q += blockDim.x) {
+    int i = 0;
+#pragma unroll
+    for (int step = kCLBlock / 2; step > 0; step >>= 1)
+      if (s_ls[i + step] <= q) i += step;
+    const int bin = blk * kCLBlock + i;
+    const int j = (int)(q - s_ls[i]);
+    const int c = a.count[bin];
+    a.chunks[off + q] = ChunkDesc{a.base[bin] + (long long)j * kChunk, bin, min(kChunk, c - j * kChunk)};
   }
   if (blk == nblk - 1 && threadIdx.x == 0) {
-    a.chunk_start[nb] = off + a.part[blk];
+    a.chunk_start[nb] = off + total;
     if (work) *work = 0ULL;
     if (ovf_total) *ovf_total += (unsigned long long)a.count[a.NT];
   }
