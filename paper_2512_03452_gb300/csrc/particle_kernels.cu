@@ -140,7 +140,13 @@ constexpr int kTileE = 1 << kTileShift;
 constexpr int kMargin = 0;                    // deposits read bins of the current positions
 constexpr int kWin = kTileE + 2 * kMargin + 3;  // 11 nodes per axis (tile + stencil halo)
 constexpr int kWinSlots = kWin * kWin * kWin;
-constexpr int kReplicas = 4;                  // window copies (lane mod 4)
+constexpr int kReplicas = 4;                  // whole-grid window copies (lane mod 4), one after another
+// Tile windows keep kTileReps copies interleaved word by word (slot s, copy r
+// at s * kTileReps + r; lane mod kTileReps picks the copy), so the lanes of a
+// warp that share a copy hit banks that differ unless their slots agree mod
+// 32 / kTileReps: far fewer bank conflicts than copies stored one after
+// another, whose random slots spread over all 32 banks at random.
+constexpr int kTileReps = 8;
 constexpr int kChunk = 4096;                  // particles per work item
 
 // Add the shared window (all replicas) to the grid and clear it: consecutive
@@ -153,12 +159,19 @@ __device__ __forceinline__ void window_flush(const BinArgs<T>& a, typename WinTy
   const int H = a.g.H, mask = a.g.mask;
   const T unit = a.wmass / wwin;   // M0/P * 2^-K
   for (int sidx = threadIdx.x; sidx < wslots; sidx += blockDim.x) {
-    A v = win[sidx];
-    win[sidx] = A(0);
+    A v = A(0);
+    if (WHOLE) {
 #pragma unroll
-    for (int r = 1; r < kReplicas; ++r) {
-      v += win[r * wslots + sidx];
-      win[r * wslots + sidx] = A(0);
+      for (int r = 0; r < kReplicas; ++r) {
+        v += win[r * wslots + sidx];
+        win[r * wslots + sidx] = A(0);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < kTileReps; ++r) {
+        v += win[sidx * kTileReps + r];
+        win[sidx * kTileReps + r] = A(0);
+      }
     }
     if (v != A(0)) {
       int gi;
@@ -272,13 +285,13 @@ __device__ __forceinline__ void binned_chunk(const BinArgs<T>& a, const ChunkDes
           stencil_visit<T>(a.p2g, ix, iy, iz, lx, ly, lz, wwin,
                            [&](int idx, T f) { win_add(my_win + idx, WinType<T>::round(f)); });
         } else {
-          // base slot plus compile-time offsets of the 4x4x4 box
-          A* wb = my_win + ((sx * kWin) + sy) * kWin + sz;
+          // base slot plus compile-time offsets of the 4x4x4 box (interleaved copies)
+          A* wb = win + (((sx * kWin) + sy) * kWin + sz) * kTileReps + (lane & (kTileReps - 1));
 #pragma unroll
           for (int o = 0; o < 4; ++o) {
-            ix[o] = o * (kWin * kWin);
-            iy[o] = o * kWin;
-            iz[o] = o;
+            ix[o] = o * (kWin * kWin * kTileReps);
+            iy[o] = o * (kWin * kTileReps);
+            iz[o] = o * kTileReps;
           }
           stencil_visit<T>(a.p2g, ix, iy, iz, lx, ly, lz, wwin,
                            [&](int idx, T f) { win_add(wb + idx, WinType<T>::round(f)); });
@@ -332,7 +345,7 @@ k_binned(BinArgs<T> a) {
   const long long nchunks = a.chunk_start[a.NT + 1];
   const int wslots = WHOLE ? a.g.H * a.g.H * a.g.H : kWinSlots;
   if (DEPOSIT)
-    for (int i = threadIdx.x; i < kReplicas * wslots; i += blockDim.x) win[i] = A(0);
+    for (int i = threadIdx.x; i < (WHOLE ? kReplicas : kTileReps) * wslots; i += blockDim.x) win[i] = A(0);
   // work items are taken from a global counter; the next one is fetched
   // while the current one is processed
   if (threadIdx.x == 0) {
@@ -365,7 +378,7 @@ k_deposit_batch(const BinArgs<T>* __restrict__ table, const long long* __restric
   __shared__ ChunkDesc s_desc[2];
   __shared__ int s_run[2];
   const long long total = prefix[nruns];
-  for (int i = threadIdx.x; i < kReplicas * kWinSlots; i += blockDim.x) win[i] = A(0);
+  for (int i = threadIdx.x; i < kTileReps * kWinSlots; i += blockDim.x) win[i] = A(0);
   if (threadIdx.x == 0) {
     const long long c = (long long)atomicAdd(work, 1ULL);
     if (c < total) {
@@ -1160,7 +1173,7 @@ __global__ void __launch_bounds__(256) k_alpha_energy(const cpx<T>* __restrict__
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
-int binned_window_slots(int H) { return kReplicas * (H <= 16 ? H * H * H : kWinSlots); }
+int binned_window_slots(int H) { return H <= 16 ? kReplicas * H * H * H : kTileReps * kWinSlots; }
 int binned_chunk() { return kChunk; }
 int binned_tile_shift(int H) { return H <= 16 ? 30 : kTileShift; }
 
@@ -1227,7 +1240,7 @@ cudaError_t launch_move_batch(const BinArgs<T>* table, const long long* prefix, 
 template <typename T>
 cudaError_t launch_deposit_batch(const BinArgs<T>* table, const long long* prefix, int nruns,
                                  unsigned long long* work, bool fixed, cudaStream_t s, int blocks_per_sm) {
-  const size_t smem = (size_t)kReplicas * kWinSlots * sizeof(typename WinType<T>::type);
+  const size_t smem = (size_t)kTileReps * kWinSlots * sizeof(typename WinType<T>::type);
   auto k = fixed ? k_deposit_batch<T, true> : k_deposit_batch<T, false>;
   cudaError_t e;
   if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
