@@ -37,10 +37,10 @@ P_FULL, H_FULL = 10_000_000, 128
 # algorithmic bytes of the particle kernel per particle-step (FP32): read X (12 B) + write X (12 B)
 BYTES_PER_PARTICLE = 24
 # DRAM traffic (read + write bytes) of the particle phase, move + re-bin
-# (314.4 MB) and deposit (134.5 MB) launches of one step, from ncu captures of
+# (314.4 MB) and deposit (134.7 MB) launches of one step, from ncu captures of
 # the torus workload, keyed by the SHA-256 of the kernel sources they were
 # taken on (a changed kernel reports null until it is captured again).
-MOVE_TRAFFIC = {"33fe6e4a34b02057b7bfb6eeb1193c2bacd01e10e170ad65e2f7d91613c60eba": 448.9e6}
+MOVE_TRAFFIC = {"e1d74287d6d04a5fe5958c30225cafbff0b9494a050c60d01650c6c806ac274c": 449.1e6}
 FALLBACK_HBM_GBS = 6800.0
 
 

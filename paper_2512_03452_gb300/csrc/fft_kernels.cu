@@ -439,6 +439,14 @@ __device__ __forceinline__ void warp_fft(cpx<T> (&v)[E], int lane, const cpx<T>*
 
 __device__ __forceinline__ int out_index(int k1, int E, int lane) { return k1 + E * (int)(__brev((unsigned)lane) >> 27); }
 
+// Shared scratch of the warp FFTs carries one padding slot per 32 elements
+// (pencils) or per 32 rows (tiles): a warp's outputs, stored in bit-reversed
+// order with index stride E, then fall into distinct banks (2 wavefronts per
+// 8-byte warp store instead of 2E) while natural-order loads stay at 2.
+__device__ __forceinline__ int zpad(int i) { return i + (i >> 5); }
+__device__ __forceinline__ int tpad(int j, int LD, int c) { return j * LD + (j >> 5) + c; }
+constexpr int padded_len(int n) { return n + n / 32; }
+
 template <typename T> __device__ __forceinline__ void load_tw_full(cpx<T>* tw) {
   for (int i = threadIdx.x; i < kNmax; i += blockDim.x) tw[i] = cpx<T>{(T)g_twiddle[i].x, (T)g_twiddle[i].y};
 }
@@ -451,7 +459,7 @@ template <typename T> __device__ __forceinline__ void load_tw_full(cpx<T>* tw) {
 template <typename T, int E, typename Tin>
 __device__ __forceinline__ void rows_r2c_body(Tin* __restrict__ in, double in_scale, int zero_input,
                                               cpx<T>* __restrict__ out, int rows, double* mass_acc, int bx, int gx,
-                                              const cpx<T>* tw, cpx<T> (*zball)[32 * E]) {
+                                              const cpx<T>* tw, cpx<T> (*zball)[33 * E]) {
   constexpr int N = 32 * E, NH = N / 2 + 1;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   cpx<T>* zb = zball[wib];
@@ -485,12 +493,12 @@ __device__ __forceinline__ void rows_r2c_body(Tin* __restrict__ in, double in_sc
     }
     warp_fft<T, E, -1>(v, lane, tw);
 #pragma unroll
-    for (int k1 = 0; k1 < E; ++k1) zb[out_index(k1, E, lane)] = v[k1];
+    for (int k1 = 0; k1 < E; ++k1) zb[zpad(out_index(k1, E, lane))] = v[k1];
     __syncwarp();
     cpx<T>* oa = out + (size_t)(2 * pr) * NH;
     for (int k = lane; k < NH; k += 32) {
-      const cpx<T> zk = zb[k];
-      const cpx<T> zm = cconj(zb[(N - k) & (N - 1)]);
+      const cpx<T> zk = zb[zpad(k)];
+      const cpx<T> zm = cconj(zb[zpad((N - k) & (N - 1))]);
       const cpx<T> d = csub(zk, zm);
       oa[k] = cpx<T>{(zk.x + zm.x) * T(0.5), (zk.y + zm.y) * T(0.5)};
       oa[NH + k] = cpx<T>{d.y * T(0.5), -d.x * T(0.5)};
@@ -508,7 +516,7 @@ __global__ void __launch_bounds__(256)
 kw_rows_r2c(Tin* __restrict__ in, double in_scale, int zero_input, cpx<T>* __restrict__ out, int rows,
             double* mass_acc) {
   __shared__ cpx<T> tw[kNmax];
-  __shared__ cpx<T> zb[8][32 * E];
+  __shared__ cpx<T> zb[8][33 * E];
   load_tw_full(tw);
   __syncthreads();
   rows_r2c_body<T, E, Tin>(in, in_scale, zero_input, out, rows, mass_acc, blockIdx.x, gridDim.x, tw, zb);
@@ -524,22 +532,22 @@ __device__ __forceinline__ void cols_body(cpx<T>* __restrict__ base, int B, T sc
   const int nb = min(BC, B - b0);
   for (int t = threadIdx.x; t < N * BC; t += blockDim.x) {
     const int j = t / BC, c = t - j * BC;
-    buf[j * LD + c] = c < nb ? base[(size_t)j * B + b0 + c] : cpx<T>{T(0), T(0)};
+    buf[tpad(j, LD, c)] = c < nb ? base[(size_t)j * B + b0 + c] : cpx<T>{T(0), T(0)};
   }
   __syncthreads();
   for (int c = wib; c < nb; c += (int)(blockDim.x >> 5)) {
     cpx<T> v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = buf[(lane + 32 * m) * LD + c];
+    for (int m = 0; m < E; ++m) v[m] = buf[tpad(lane + 32 * m, LD, c)];
     warp_fft<T, E, DIR>(v, lane, tw);
 #pragma unroll
-    for (int k1 = 0; k1 < E; ++k1) buf[out_index(k1, E, lane) * LD + c] = v[k1];
+    for (int k1 = 0; k1 < E; ++k1) buf[tpad(out_index(k1, E, lane), LD, c)] = v[k1];
   }
   __syncthreads();
   for (int t = threadIdx.x; t < N * BC; t += blockDim.x) {
     const int j = t / BC, c = t - j * BC;
     if (c < nb) {
-      const cpx<T> v = buf[j * LD + c];
+      const cpx<T> v = buf[tpad(j, LD, c)];
       base[(size_t)j * B + b0 + c] = cpx<T>{v.x * scale, v.y * scale};
     }
   }
@@ -570,16 +578,16 @@ __device__ __forceinline__ void spectral_body(const cpx<T>* __restrict__ T1, cpx
   if (needs_beta) {
     for (int t = threadIdx.x; t < N * BC; t += blockDim.x) {
       const int j = t / BC, c = t - j * BC;
-      buf[j * LD + c] = c < nb ? T1[(size_t)j * B + b0 + c] : cpx<T>{T(0), T(0)};
+      buf[tpad(j, LD, c)] = c < nb ? T1[(size_t)j * B + b0 + c] : cpx<T>{T(0), T(0)};
     }
     __syncthreads();
     for (int c = wib; c < nb; c += (int)(blockDim.x >> 5)) {
       cpx<T> v[E];
 #pragma unroll
-      for (int m = 0; m < E; ++m) v[m] = buf[(lane + 32 * m) * LD + c];
+      for (int m = 0; m < E; ++m) v[m] = buf[tpad(lane + 32 * m, LD, c)];
       warp_fft<T, E, -1>(v, lane, tw);
 #pragma unroll
-      for (int k1 = 0; k1 < E; ++k1) buf[out_index(k1, E, lane) * LD + c] = v[k1];
+      for (int k1 = 0; k1 < E; ++k1) buf[tpad(out_index(k1, E, lane), LD, c)] = v[k1];
     }
   }
   __syncthreads();
@@ -602,7 +610,7 @@ __device__ __forceinline__ void spectral_body(const cpx<T>* __restrict__ T1, cpx
       if (MODE == kModeStep || MODE == kModeGradOnly) {
         const cpx<T> a = alpha[gi];
         if (MODE == kModeStep) {
-          cpx<T> beta = buf[j * LD + c];
+          cpx<T> beta = buf[tpad(j, LD, c)];
           beta.x *= inv_L3;
           beta.y *= inv_L3;
           const T lam = two_pi_L * two_pi_L * q2 + k2;
@@ -629,15 +637,15 @@ __device__ __forceinline__ void spectral_body(const cpx<T>* __restrict__ T1, cpx
         if (qy != -N / 2) o2 = cpx<T>{-yy * a.y, yy * a.x};
         if (qz != -N / 2) o3 = cpx<T>{-yz * a.y, yz * a.x};
       } else if (MODE == kModeDensity) {
-        const cpx<T> beta = buf[j * LD + c];
+        const cpx<T> beta = buf[tpad(j, LD, c)];
         o1 = cpx<T>{beta.x * inv_L3 * Phi, beta.y * inv_L3 * Phi};
       } else {
         o1 = alpha[gi];
       }
     }
-    buf[j * LD + BC + c] = o1;
-    buf[j * LD + 2 * BC + c] = o2;
-    buf[j * LD + 3 * BC + c] = o3;
+    buf[tpad(j, LD, BC + c)] = o1;
+    buf[tpad(j, LD, 2 * BC + c)] = o2;
+    buf[tpad(j, LD, 3 * BC + c)] = o3;
   }
   __syncthreads();
   constexpr int nout = (MODE == kModeStep || MODE == kModeGradOnly) ? 3 : 1;
@@ -646,17 +654,17 @@ __device__ __forceinline__ void spectral_body(const cpx<T>* __restrict__ T1, cpx
     if (col % BC >= nb) continue;
     cpx<T> v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = buf[(lane + 32 * m) * LD + c];
+    for (int m = 0; m < E; ++m) v[m] = buf[tpad(lane + 32 * m, LD, c)];
     warp_fft<T, E, +1>(v, lane, tw);
 #pragma unroll
-    for (int k1 = 0; k1 < E; ++k1) buf[out_index(k1, E, lane) * LD + c] = v[k1];
+    for (int k1 = 0; k1 < E; ++k1) buf[tpad(out_index(k1, E, lane), LD, c)] = v[k1];
   }
   __syncthreads();
   for (int t = threadIdx.x; t < N * BC; t += blockDim.x) {
     const int j = t / BC, c = t - j * BC;
     if (c < nb) {
 #pragma unroll
-      for (int d = 0; d < nout; ++d) T2[d * S + (size_t)j * B + b0 + c] = buf[j * LD + (d + 1) * BC + c];
+      for (int d = 0; d < nout; ++d) T2[d * S + (size_t)j * B + b0 + c] = buf[tpad(j, LD, (d + 1) * BC + c)];
     }
   }
 }
@@ -681,7 +689,7 @@ __device__ __forceinline__ void rows_c2r_body(const cpx<T>* __restrict__ in, siz
   constexpr int N = 32 * E, NH = N / 2 + 1;
   constexpr int NOUT = NCOMP == 3 ? 4 : 1;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  cpx<T>* zb = zb_all + wib * N;
+  cpx<T>* zb = zb_all + wib * padded_len(N);
   T* ob = ob_all + wib * 2 * N * NOUT;
   const int nwarps = gx * 8;
   double mx = -INFINITY;
@@ -695,13 +703,13 @@ __device__ __forceinline__ void rows_c2r_body(const cpx<T>* __restrict__ in, siz
           A.y = T(0);
           Bv.y = T(0);
         }
-        zb[k] = cpx<T>{A.x - Bv.y, A.y + Bv.x};
-        if (k > 0 && k < N / 2) zb[N - k] = cpx<T>{A.x + Bv.y, -A.y + Bv.x};   // conj A + i conj B
+        zb[zpad(k)] = cpx<T>{A.x - Bv.y, A.y + Bv.x};
+        if (k > 0 && k < N / 2) zb[zpad(N - k)] = cpx<T>{A.x + Bv.y, -A.y + Bv.x};   // conj A + i conj B
       }
       __syncwarp();
       cpx<T> v[E];
 #pragma unroll
-      for (int m = 0; m < E; ++m) v[m] = zb[lane + 32 * m];
+      for (int m = 0; m < E; ++m) v[m] = zb[zpad(lane + 32 * m)];
       __syncwarp();
       warp_fft<T, E, +1>(v, lane, tw);
 #pragma unroll
@@ -749,7 +757,7 @@ kw_rows_c2r(const cpx<T>* __restrict__ in, size_t comp_stride, T* __restrict__ o
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* zb_all = tw + kNmax;
-  T* ob_all = reinterpret_cast<T*>(zb_all + 8 * N);
+  T* ob_all = reinterpret_cast<T*>(zb_all + 8 * padded_len(N));
   load_tw_full(tw);
   __syncthreads();
   rows_c2r_body<T, E, NCOMP>(in, comp_stride, out, rows, max_acc, blockIdx.x, gridDim.x, tw, zb_all, ob_all);
@@ -762,7 +770,7 @@ kw_rows_c2r(const cpx<T>* __restrict__ in, size_t comp_stride, T* __restrict__ o
 template <typename T, int E>
 __global__ void __launch_bounds__(256) kwb_rows_r2c(const FftRun<T>* __restrict__ runs) {
   __shared__ cpx<T> tw[kNmax];
-  __shared__ cpx<T> zb[8][32 * E];
+  __shared__ cpx<T> zb[8][33 * E];
   load_tw_full(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.y];
@@ -803,7 +811,7 @@ __global__ void __launch_bounds__(256) kwb_rows_c2r(const FftRun<T>* __restrict_
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* zb_all = tw + kNmax;
-  T* ob_all = reinterpret_cast<T*>(zb_all + 8 * N);
+  T* ob_all = reinterpret_cast<T*>(zb_all + 8 * padded_len(N));
   load_tw_full(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.y];
@@ -826,7 +834,8 @@ constexpr int kDefaultPlaneWarps = 8;      // warps per block of the plane kerne
 constexpr int kDefaultSpectralWarps = 8;   // warps per block of the fused x pass
 
 template <typename T, int E> constexpr size_t plane_smem_bytes(int nw) {
-  return ((size_t)32 * E * (16 * E + 1) + (size_t)nw * 32 * E + kNmax) * sizeof(cpx<T>);
+  // plane: H rows of H/2+1 plus one slot per 32 rows; one padded pencil per warp
+  return ((size_t)32 * E * (16 * E + 1) + E + (size_t)nw * padded_len(32 * E) + kNmax) * sizeof(cpx<T>);
 }
 
 template <typename T, int E, typename Tin>
@@ -834,7 +843,7 @@ __device__ __forceinline__ void plane_fwd_body(Tin* __restrict__ in, double in_s
                                                const cpx<T>* tw, cpx<T>* P, cpx<T>* zball) {
   constexpr int N = 32 * E, NH = N / 2 + 1;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  cpx<T>* zb = zball + wib * N;
+  cpx<T>* zb = zball + wib * padded_len(N);
   // 1. rows: two real rows as one complex pencil, split into their half spectra
   for (int pr = wib; pr < N / 2; pr += (int)(blockDim.x >> 5)) {
     const size_t ra = (size_t)(2 * pr) * N, rb = ra + N;
@@ -858,12 +867,12 @@ __device__ __forceinline__ void plane_fwd_body(Tin* __restrict__ in, double in_s
     }
     warp_fft<T, E, -1>(v, lane, tw);
 #pragma unroll
-    for (int k1 = 0; k1 < E; ++k1) zb[out_index(k1, E, lane)] = v[k1];
+    for (int k1 = 0; k1 < E; ++k1) zb[zpad(out_index(k1, E, lane))] = v[k1];
     __syncwarp();
-    cpx<T>* pa = P + (size_t)(2 * pr) * NH;
+    cpx<T>* pa = P + tpad(2 * pr, NH, 0);   // rows 2 pr and 2 pr + 1 are adjacent
     for (int k = lane; k < NH; k += 32) {
-      const cpx<T> zk = zb[k];
-      const cpx<T> zm = cconj(zb[(N - k) & (N - 1)]);
+      const cpx<T> zk = zb[zpad(k)];
+      const cpx<T> zm = cconj(zb[zpad((N - k) & (N - 1))]);
       const cpx<T> d = csub(zk, zm);
       pa[k] = cpx<T>{(zk.x + zm.x) * T(0.5), (zk.y + zm.y) * T(0.5)};
       pa[NH + k] = cpx<T>{d.y * T(0.5), -d.x * T(0.5)};
@@ -875,13 +884,13 @@ __device__ __forceinline__ void plane_fwd_body(Tin* __restrict__ in, double in_s
   for (int c = wib; c < NH; c += (int)(blockDim.x >> 5)) {
     cpx<T> v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = P[(lane + 32 * m) * NH + c];
+    for (int m = 0; m < E; ++m) v[m] = P[tpad(lane + 32 * m, NH, c)];
     warp_fft<T, E, -1>(v, lane, tw);
 #pragma unroll
-    for (int k1 = 0; k1 < E; ++k1) P[out_index(k1, E, lane) * NH + c] = v[k1];
+    for (int k1 = 0; k1 < E; ++k1) P[tpad(out_index(k1, E, lane), NH, c)] = v[k1];
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < N * NH; t += blockDim.x) out[t] = P[t];
+  for (int t = threadIdx.x; t < N * NH; t += blockDim.x) out[t] = P[t + ((t / NH) >> 5)];
 }
 
 template <typename T, int E>
@@ -889,23 +898,23 @@ __device__ __forceinline__ void plane_inv_body(const cpx<T>* __restrict__ in, T*
                                                const cpx<T>* tw, cpx<T>* P, cpx<T>* zball) {
   constexpr int N = 32 * E, NH = N / 2 + 1;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  cpx<T>* zb = zball + wib * N;
-  for (int t = threadIdx.x; t < N * NH; t += blockDim.x) P[t] = in[t];
+  cpx<T>* zb = zball + wib * padded_len(N);
+  for (int t = threadIdx.x; t < N * NH; t += blockDim.x) P[t + ((t / NH) >> 5)] = in[t];
   __syncthreads();
   // 1. y axis inverse: one column per warp
   for (int c = wib; c < NH; c += (int)(blockDim.x >> 5)) {
     cpx<T> v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = P[(lane + 32 * m) * NH + c];
+    for (int m = 0; m < E; ++m) v[m] = P[tpad(lane + 32 * m, NH, c)];
     warp_fft<T, E, +1>(v, lane, tw);
 #pragma unroll
-    for (int k1 = 0; k1 < E; ++k1) P[out_index(k1, E, lane) * NH + c] = v[k1];
+    for (int k1 = 0; k1 < E; ++k1) P[tpad(out_index(k1, E, lane), NH, c)] = v[k1];
   }
   __syncthreads();
   // 2. rows: two Hermitian half rows A, B as the pencil A + i B; the inverse
   //    transform's real part is row A, its imaginary part row B
   for (int pr = wib; pr < N / 2; pr += (int)(blockDim.x >> 5)) {
-    cpx<T>* pa = P + (size_t)(2 * pr) * NH;
+    const cpx<T>* pa = P + tpad(2 * pr, NH, 0);   // rows 2 pr and 2 pr + 1 are adjacent
     const cpx<T>* pb = pa + NH;
     for (int k = lane; k < NH; k += 32) {
       cpx<T> A = pa[k], Bv = pb[k];
@@ -913,26 +922,27 @@ __device__ __forceinline__ void plane_inv_body(const cpx<T>* __restrict__ in, T*
         A.y = T(0);
         Bv.y = T(0);
       }
-      zb[k] = cpx<T>{A.x - Bv.y, A.y + Bv.x};
-      if (k > 0 && k < N / 2) zb[N - k] = cpx<T>{A.x + Bv.y, -A.y + Bv.x};   // conj A + i conj B
+      zb[zpad(k)] = cpx<T>{A.x - Bv.y, A.y + Bv.x};
+      if (k > 0 && k < N / 2) zb[zpad(N - k)] = cpx<T>{A.x + Bv.y, -A.y + Bv.x};   // conj A + i conj B
     }
     __syncwarp();
     cpx<T> v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = zb[lane + 32 * m];
+    for (int m = 0; m < E; ++m) v[m] = zb[zpad(lane + 32 * m)];
     __syncwarp();
     warp_fft<T, E, +1>(v, lane, tw);
-    // stage the two output rows in the two plane rows just consumed
-    T* ob = reinterpret_cast<T*>(pa);
+    // stage the two output rows (2N reals, padded per 32) in the warp's pencil,
+    // whose N + N/32 complex slots hold exactly that
+    T* ob = reinterpret_cast<T*>(zb);
 #pragma unroll
     for (int k1 = 0; k1 < E; ++k1) {
       const int j = out_index(k1, E, lane);
-      ob[j] = v[k1].x;
-      ob[N + j] = v[k1].y;
+      ob[zpad(j)] = v[k1].x;
+      ob[zpad(N + j)] = v[k1].y;
     }
     __syncwarp();
     T* orow = out + ((size_t)x * N + 2 * pr) * N * 4 + d;
-    for (int t = lane; t < 2 * N; t += 32) orow[(size_t)t * 4] = ob[t];
+    for (int t = lane; t < 2 * N; t += 32) orow[(size_t)t * 4] = ob[zpad(t)];
     __syncwarp();
   }
 }
@@ -943,7 +953,7 @@ __global__ void __launch_bounds__(1024) kwp_fwd(const FftRun<T>* __restrict__ ru
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* zb = tw + kNmax;
-  cpx<T>* P = zb + (blockDim.x >> 5) * N;
+  cpx<T>* P = zb + (blockDim.x >> 5) * padded_len(N);
   load_tw_full(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.y];
@@ -962,7 +972,7 @@ __global__ void __launch_bounds__(1024) kwp_inv(const FftRun<T>* __restrict__ ru
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* zb = tw + kNmax;
-  cpx<T>* P = zb + (blockDim.x >> 5) * N;
+  cpx<T>* P = zb + (blockDim.x >> 5) * padded_len(N);
   load_tw_full(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.z];
@@ -990,7 +1000,7 @@ static cudaError_t warp_rows_r2c(const void* in, int in_kind, double in_scale, b
 template <typename T, int E, int DIR>
 static cudaError_t warp_cols(cpx<T>* data, int A, int B, int ncomp, size_t comp_stride, double scale, cudaStream_t s) {
   constexpr int BC = 16;
-  const size_t smem = (kNmax + (size_t)32 * E * (BC + 1)) * sizeof(cpx<T>);
+  const size_t smem = (kNmax + (size_t)32 * E * (BC + 1) + E) * sizeof(cpx<T>);
   auto k = kw_cols<T, E, DIR, BC>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
@@ -1005,7 +1015,7 @@ static cudaError_t warp_spectral(const cpx<T>* T1, cpx<T>* alpha, cpx<T>* T2, Sp
   constexpr int N = 32 * E;
   constexpr int BC = (sizeof(T) == 8 && E == 8) ? 4 : ((sizeof(T) == 8 || E == 8) ? 8 : 16);
   const int B = N * (N / 2 + 1);
-  const size_t smem = (kNmax + (size_t)N * (4 * BC + 1)) * sizeof(cpx<T>);
+  const size_t smem = (kNmax + (size_t)N * (4 * BC + 1) + E) * sizeof(cpx<T>);
   auto k = kw_spectral_x<T, E, MODE, BC>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
@@ -1018,7 +1028,7 @@ static cudaError_t warp_rows_c2r(const cpx<T>* in, size_t comp_stride, T* out, i
                                  cudaStream_t s) {
   constexpr int N = 32 * E;
   constexpr int NOUT = NCOMP == 3 ? 4 : 1;
-  const size_t smem = (kNmax + (size_t)8 * N) * sizeof(cpx<T>) + (size_t)8 * 2 * N * NOUT * sizeof(T);
+  const size_t smem = (kNmax + (size_t)8 * padded_len(N)) * sizeof(cpx<T>) + (size_t)8 * 2 * N * NOUT * sizeof(T);
   auto k = kw_rows_c2r<T, E, NCOMP>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
@@ -1187,11 +1197,11 @@ constexpr size_t kMaxSmem = 227 * 1024;
 
 template <typename T, int E, int BC>
 static size_t cols_smem() {
-  return (kNmax + (size_t)32 * E * (BC + 1)) * sizeof(cpx<T>);
+  return (kNmax + (size_t)32 * E * (BC + 1) + E) * sizeof(cpx<T>);
 }
 template <typename T, int E, int SBC>
 static size_t spectral_smem() {
-  return (kNmax + (size_t)32 * E * (4 * SBC + 1)) * sizeof(cpx<T>);
+  return (kNmax + (size_t)32 * E * (4 * SBC + 1) + E) * sizeof(cpx<T>);
 }
 
 template <typename T, int E, int DIR, int BC>
@@ -1241,14 +1251,20 @@ static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, c
   const int rblocks = max(1, min(rows_budget / max(nruns, 1), (N * N / 2 + 7) / 8));
   const int bc = tune.bc > 0 ? tune.bc : 16;
   const int sbc = tune.sbc > 0 ? tune.sbc : default_sbc<T, E>();
-  const int pnw = tune.plane_nw > 0 ? tune.plane_nw : kDefaultPlaneWarps;
+  // default plane warps: 8, or, for a kernel whose blocks fill the 152 SMs
+  // less than twice, up to one warp per 4 plane rows
+  auto plane_warps = [&](int blocks) {
+    return tune.plane_nw > 0 ? tune.plane_nw
+                             : (blocks <= 2 * 152 ? max(kDefaultPlaneWarps, min(32, N / 4)) : kDefaultPlaneWarps);
+  };
+  const int fnw = plane_warps(nruns * N), inw = plane_warps(3 * nruns * N);
   const int snw = tune.spec_nw > 0 ? tune.spec_nw : kDefaultSpectralWarps;
-  const size_t psm = plane_smem_bytes<T, E>(pnw);
-  const bool planes = tune.plane_mode == 0 && E <= 4 && psm <= kMaxSmem;
+  const size_t fsm = plane_smem_bytes<T, E>(fnw), ism = plane_smem_bytes<T, E>(inw);
+  const bool planes = tune.plane_mode == 0 && E <= 4 && fsm <= kMaxSmem && ism <= kMaxSmem;
   if (stages & kFieldForward) {
     if (planes) {
-      if ((e = set_smem(kwp_fwd<T, E>, psm)) != cudaSuccess) return e;
-      kwp_fwd<T, E><<<dim3(N, nruns), 32 * pnw, psm, s>>>(runs);
+      if ((e = set_smem(kwp_fwd<T, E>, fsm)) != cudaSuccess) return e;
+      kwp_fwd<T, E><<<dim3(N, nruns), 32 * fnw, fsm, s>>>(runs);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       nk += 1;
     } else {
@@ -1268,13 +1284,13 @@ static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, c
     nk += 1;
   }
   if ((stages & kFieldInverse) && planes) {
-    if ((e = set_smem(kwp_inv<T, E>, psm)) != cudaSuccess) return e;
-    kwp_inv<T, E><<<dim3(N, 3, nruns), 32 * pnw, psm, s>>>(runs);
+    if ((e = set_smem(kwp_inv<T, E>, ism)) != cudaSuccess) return e;
+    kwp_inv<T, E><<<dim3(N, 3, nruns), 32 * inw, ism, s>>>(runs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     nk += 1;
   } else if (stages & kFieldInverse) {
     if ((e = kwb_cols_bc<T, E, +1>(runs, nruns, 3, bc, s)) != cudaSuccess) return e;
-    const size_t smr = (kNmax + (size_t)8 * N) * sizeof(cpx<T>) + (size_t)8 * 2 * N * 4 * sizeof(T);
+    const size_t smr = (kNmax + (size_t)8 * padded_len(N)) * sizeof(cpx<T>) + (size_t)8 * 2 * N * 4 * sizeof(T);
     if ((e = set_smem(kwb_rows_c2r<T, E>, smr)) != cudaSuccess) return e;
     kwb_rows_c2r<T, E><<<dim3(rblocks, nruns), 256, smr, s>>>(runs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
