@@ -381,6 +381,20 @@ __device__ __forceinline__ cpx<T> twid(const cpx<T>* tw, int m) {
   return w;
 }
 
+// The warp kernels' shared twiddles: the full table (kNmax entries), then the
+// per-lane twiddles of the warp FFT laid out lane-contiguously so a warp's
+// reads hit distinct banks (read from the full table they are strided and
+// collide up to 8-fold):
+//   [kNmax + s + j]        cross-lane stage s (1..16), j = lane mod s: e^{-i pi j/s}
+//   [kNmax + 32 k1 + lane] register twiddle W_N^(lane k1), k1 = 1..E-1
+// Same values as the full table's entries, so the same bits.
+constexpr int kTwLen = kNmax + 32 * 8;
+template <typename T, int DIR> __device__ __forceinline__ cpx<T> twx(const cpx<T>* tw, int i) {
+  cpx<T> w = tw[kNmax + i];
+  if (DIR > 0) w.y = -w.y;
+  return w;
+}
+
 template <typename T, int E, int DIR>
 __device__ __forceinline__ void reg_dft(cpx<T> (&v)[E], const cpx<T>* tw) {
   if (E == 1) return;
@@ -419,15 +433,13 @@ template <typename T> __device__ __forceinline__ cpx<T> shfl_xor_c(cpx<T> v, int
 
 template <typename T, int E, int DIR>
 __device__ __forceinline__ void warp_fft(cpx<T> (&v)[E], int lane, const cpx<T>* tw) {
-  constexpr int N = 32 * E;
-  constexpr int SC = kNmax / N;
   reg_dft<T, E, DIR>(v, tw);
 #pragma unroll
-  for (int k1 = 1; k1 < E; ++k1) v[k1] = cmul(v[k1], twid<T, DIR>(tw, lane * k1 * SC));
+  for (int k1 = 1; k1 < E; ++k1) v[k1] = cmul(v[k1], twx<T, DIR>(tw, 32 * k1 + lane));   // W_N^(lane k1)
 #pragma unroll
   for (int s = 16; s >= 1; s >>= 1) {
     const bool up = (lane & s) != 0;
-    const cpx<T> w = up ? twid<T, DIR>(tw, (lane & (s - 1)) * (kNmax / (2 * s))) : cpx<T>{T(1), T(0)};
+    const cpx<T> w = up ? twx<T, DIR>(tw, s + (lane & (s - 1))) : cpx<T>{T(1), T(0)};
 #pragma unroll
     for (int k1 = 0; k1 < E; ++k1) {
       const cpx<T> u = shfl_xor_c(v[k1], s);
@@ -447,8 +459,22 @@ __device__ __forceinline__ int zpad(int i) { return i + (i >> 5); }
 __device__ __forceinline__ int tpad(int j, int LD, int c) { return j * LD + (j >> 5) + c; }
 constexpr int padded_len(int n) { return n + n / 32; }
 
-template <typename T> __device__ __forceinline__ void load_tw_full(cpx<T>* tw) {
-  for (int i = threadIdx.x; i < kNmax; i += blockDim.x) tw[i] = cpx<T>{(T)g_twiddle[i].x, (T)g_twiddle[i].y};
+template <typename T, int E> __device__ __forceinline__ void load_tw_full(cpx<T>* tw) {
+  constexpr int SC = kNmax / (32 * E);
+  for (int i = threadIdx.x; i < kNmax + 32 * E; i += blockDim.x) {
+    int m;
+    if (i < kNmax) {
+      m = i;
+    } else if (i < kNmax + 32) {   // stage s = 2^floor(log2 j), j - s = lane mod s (entry kNmax: unused, 1)
+      const int j = i - kNmax;
+      const int st = 1 << (31 - __clz(j | 1));
+      m = j == 0 ? 0 : (j - st) * (kNmax / (2 * st));
+    } else {
+      const int j = i - kNmax, k1 = j >> 5, lane = j & 31;
+      m = (lane * k1 * SC) & (kNmax - 1);
+    }
+    tw[i] = cpx<T>{(T)g_twiddle[m].x, (T)g_twiddle[m].y};
+  }
 }
 
 // Kernel bodies take their arrays and block coordinates explicitly so the same
@@ -515,9 +541,9 @@ template <typename T, int E, typename Tin>
 __global__ void __launch_bounds__(256)
 kw_rows_r2c(Tin* __restrict__ in, double in_scale, int zero_input, cpx<T>* __restrict__ out, int rows,
             double* mass_acc) {
-  __shared__ cpx<T> tw[kNmax];
+  __shared__ cpx<T> tw[kTwLen];
   __shared__ cpx<T> zb[8][33 * E];
-  load_tw_full(tw);
+  load_tw_full<T, E>(tw);
   __syncthreads();
   rows_r2c_body<T, E, Tin>(in, in_scale, zero_input, out, rows, mass_acc, blockIdx.x, gridDim.x, tw, zb);
 }
@@ -558,9 +584,9 @@ __global__ void __launch_bounds__(256)
 kw_cols(cpx<T>* __restrict__ data, int B, size_t comp_stride, T scale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  load_tw_full(tw);
+  load_tw_full<T, E>(tw);
   cpx<T>* base = data + blockIdx.z * comp_stride + (size_t)blockIdx.y * (32 * E) * B;
-  cols_body<T, E, DIR, BC>(base, B, scale, blockIdx.x * BC, tw, tw + kNmax);
+  cols_body<T, E, DIR, BC>(base, B, scale, blockIdx.x * BC, tw, tw + kTwLen);
 }
 
 // x-axis pass fused with the spectral work (as k_spectral_x), warp FFTs.
@@ -675,8 +701,8 @@ kw_spectral_x(const cpx<T>* __restrict__ T1, cpx<T>* __restrict__ alpha, cpx<T>*
               double* alpha0_shadow) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  load_tw_full(tw);
-  spectral_body<T, E, MODE, BC>(T1, alpha, T2, sp, alpha0_shadow, blockIdx.x * BC, tw, tw + kNmax);
+  load_tw_full<T, E>(tw);
+  spectral_body<T, E, MODE, BC>(T1, alpha, T2, sp, alpha0_shadow, blockIdx.x * BC, tw, tw + kTwLen);
 }
 
 // Rows c2r: each warp takes a row pair of every component, rebuilds the
@@ -756,9 +782,9 @@ kw_rows_c2r(const cpx<T>* __restrict__ in, size_t comp_stride, T* __restrict__ o
   constexpr int N = 32 * E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* zb_all = tw + kNmax;
+  cpx<T>* zb_all = tw + kTwLen;
   T* ob_all = reinterpret_cast<T*>(zb_all + 8 * padded_len(N));
-  load_tw_full(tw);
+  load_tw_full<T, E>(tw);
   __syncthreads();
   rows_c2r_body<T, E, NCOMP>(in, comp_stride, out, rows, max_acc, blockIdx.x, gridDim.x, tw, zb_all, ob_all);
 }
@@ -769,9 +795,9 @@ kw_rows_c2r(const cpx<T>* __restrict__ in, size_t comp_stride, T* __restrict__ o
 // ---------------------------------------------------------------------------
 template <typename T, int E>
 __global__ void __launch_bounds__(256) kwb_rows_r2c(const FftRun<T>* __restrict__ runs) {
-  __shared__ cpx<T> tw[kNmax];
+  __shared__ cpx<T> tw[kTwLen];
   __shared__ cpx<T> zb[8][33 * E];
-  load_tw_full(tw);
+  load_tw_full<T, E>(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.y];
   constexpr int N = 32 * E;
@@ -787,22 +813,22 @@ template <typename T, int E, int DIR, int BC>
 __global__ void __launch_bounds__(256) kwb_cols(const FftRun<T>* __restrict__ runs, int ncomp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  load_tw_full(tw);
+  load_tw_full<T, E>(tw);
   constexpr int N = 32 * E, NHH = N / 2 + 1;
   const int run = blockIdx.z / ncomp, comp = blockIdx.z - run * ncomp;
   const FftRun<T>& r = runs[run];
   const size_t S = (size_t)N * N * NHH;
   cpx<T>* data = DIR < 0 ? r.T1 : r.T2 + comp * S;
-  cols_body<T, E, DIR, BC>(data + (size_t)blockIdx.y * N * NHH, NHH, T(1), blockIdx.x * BC, tw, tw + kNmax);
+  cols_body<T, E, DIR, BC>(data + (size_t)blockIdx.y * N * NHH, NHH, T(1), blockIdx.x * BC, tw, tw + kTwLen);
 }
 
 template <typename T, int E, int BC>
 __global__ void __launch_bounds__(512) kwb_spectral_x(const FftRun<T>* __restrict__ runs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  load_tw_full(tw);
+  load_tw_full<T, E>(tw);
   const FftRun<T>& r = runs[blockIdx.y];
-  spectral_body<T, E, kModeStep, BC>(r.T1, r.alpha, r.T2, r.sp, r.shadow, blockIdx.x * BC, tw, tw + kNmax);
+  spectral_body<T, E, kModeStep, BC>(r.T1, r.alpha, r.T2, r.sp, r.shadow, blockIdx.x * BC, tw, tw + kTwLen);
 }
 
 template <typename T, int E>
@@ -810,9 +836,9 @@ __global__ void __launch_bounds__(256) kwb_rows_c2r(const FftRun<T>* __restrict_
   constexpr int N = 32 * E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* zb_all = tw + kNmax;
+  cpx<T>* zb_all = tw + kTwLen;
   T* ob_all = reinterpret_cast<T*>(zb_all + 8 * padded_len(N));
-  load_tw_full(tw);
+  load_tw_full<T, E>(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.y];
   const size_t S = (size_t)N * N * (N / 2 + 1);
@@ -835,7 +861,7 @@ constexpr int kDefaultSpectralWarps = 8;   // warps per block of the fused x pas
 
 template <typename T, int E> constexpr size_t plane_smem_bytes(int nw) {
   // plane: H rows of H/2+1 plus one slot per 32 rows; one padded pencil per warp
-  return ((size_t)32 * E * (16 * E + 1) + E + (size_t)nw * padded_len(32 * E) + kNmax) * sizeof(cpx<T>);
+  return ((size_t)32 * E * (16 * E + 1) + E + (size_t)nw * padded_len(32 * E) + kTwLen) * sizeof(cpx<T>);
 }
 
 template <typename T, int E, typename Tin>
@@ -952,9 +978,9 @@ __global__ void __launch_bounds__(1024) kwp_fwd(const FftRun<T>* __restrict__ ru
   constexpr int N = 32 * E, NH = N / 2 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* zb = tw + kNmax;
+  cpx<T>* zb = tw + kTwLen;
   cpx<T>* P = zb + (blockDim.x >> 5) * padded_len(N);
-  load_tw_full(tw);
+  load_tw_full<T, E>(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.y];
   const int x = blockIdx.x;
@@ -971,9 +997,9 @@ __global__ void __launch_bounds__(1024) kwp_inv(const FftRun<T>* __restrict__ ru
   constexpr int N = 32 * E, NH = N / 2 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* zb = tw + kNmax;
+  cpx<T>* zb = tw + kTwLen;
   cpx<T>* P = zb + (blockDim.x >> 5) * padded_len(N);
-  load_tw_full(tw);
+  load_tw_full<T, E>(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.z];
   const int x = blockIdx.x, d = blockIdx.y;
@@ -1000,7 +1026,7 @@ static cudaError_t warp_rows_r2c(const void* in, int in_kind, double in_scale, b
 template <typename T, int E, int DIR>
 static cudaError_t warp_cols(cpx<T>* data, int A, int B, int ncomp, size_t comp_stride, double scale, cudaStream_t s) {
   constexpr int BC = 16;
-  const size_t smem = (kNmax + (size_t)32 * E * (BC + 1) + E) * sizeof(cpx<T>);
+  const size_t smem = (kTwLen + (size_t)32 * E * (BC + 1) + E) * sizeof(cpx<T>);
   auto k = kw_cols<T, E, DIR, BC>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
@@ -1015,7 +1041,7 @@ static cudaError_t warp_spectral(const cpx<T>* T1, cpx<T>* alpha, cpx<T>* T2, Sp
   constexpr int N = 32 * E;
   constexpr int BC = (sizeof(T) == 8 && E == 8) ? 4 : ((sizeof(T) == 8 || E == 8) ? 8 : 16);
   const int B = N * (N / 2 + 1);
-  const size_t smem = (kNmax + (size_t)N * (4 * BC + 1) + E) * sizeof(cpx<T>);
+  const size_t smem = (kTwLen + (size_t)N * (4 * BC + 1) + E) * sizeof(cpx<T>);
   auto k = kw_spectral_x<T, E, MODE, BC>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
@@ -1028,7 +1054,7 @@ static cudaError_t warp_rows_c2r(const cpx<T>* in, size_t comp_stride, T* out, i
                                  cudaStream_t s) {
   constexpr int N = 32 * E;
   constexpr int NOUT = NCOMP == 3 ? 4 : 1;
-  const size_t smem = (kNmax + (size_t)8 * padded_len(N)) * sizeof(cpx<T>) + (size_t)8 * 2 * N * NOUT * sizeof(T);
+  const size_t smem = (kTwLen + (size_t)8 * padded_len(N)) * sizeof(cpx<T>) + (size_t)8 * 2 * N * NOUT * sizeof(T);
   auto k = kw_rows_c2r<T, E, NCOMP>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
@@ -1197,11 +1223,11 @@ constexpr size_t kMaxSmem = 227 * 1024;
 
 template <typename T, int E, int BC>
 static size_t cols_smem() {
-  return (kNmax + (size_t)32 * E * (BC + 1) + E) * sizeof(cpx<T>);
+  return (kTwLen + (size_t)32 * E * (BC + 1) + E) * sizeof(cpx<T>);
 }
 template <typename T, int E, int SBC>
 static size_t spectral_smem() {
-  return (kNmax + (size_t)32 * E * (4 * SBC + 1) + E) * sizeof(cpx<T>);
+  return (kTwLen + (size_t)32 * E * (4 * SBC + 1) + E) * sizeof(cpx<T>);
 }
 
 template <typename T, int E, int DIR, int BC>
@@ -1290,7 +1316,7 @@ static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, c
     nk += 1;
   } else if (stages & kFieldInverse) {
     if ((e = kwb_cols_bc<T, E, +1>(runs, nruns, 3, bc, s)) != cudaSuccess) return e;
-    const size_t smr = (kNmax + (size_t)8 * padded_len(N)) * sizeof(cpx<T>) + (size_t)8 * 2 * N * 4 * sizeof(T);
+    const size_t smr = (kTwLen + (size_t)8 * padded_len(N)) * sizeof(cpx<T>) + (size_t)8 * 2 * N * 4 * sizeof(T);
     if ((e = set_smem(kwb_rows_c2r<T, E>, smr)) != cudaSuccess) return e;
     kwb_rows_c2r<T, E><<<dim3(rblocks, nruns), 256, smr, s>>>(runs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
