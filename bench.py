@@ -42,6 +42,11 @@ BYTES_PER_PARTICLE = 24
 # taken on (a changed kernel reports null until it is captured again).
 MOVE_TRAFFIC = {"e1d74287d6d04a5fe5958c30225cafbff0b9494a050c60d01650c6c806ac274c": 449.1e6}
 FALLBACK_HBM_GBS = 6800.0
+# FP64 form: FP64-pipe thread instructions (DFMA + DADD + DMUL) of one FP64 step
+# at P = 1e7, H = 128 (move 2.590e9, deposit 0.819e9, forward plane 0.112e9,
+# x pass 0.279e9, inverse plane 0.334e9), from an ncu capture of the bench's
+# FP64 leg, keyed by the SHA-256 of the kernel sources it was taken on.
+FP64_PIPE_INSTR = {"af7657d678017968571aabcea3743ff98cffbc126a69573688e9cd64724464de": 4.134262261e9}
 
 
 def _env_int(name, default):
@@ -60,9 +65,9 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(names=("particle_kernels.cu", "sipf_device.cuh")):
     h = hashlib.sha256()
-    for name in ("particle_kernels.cu", "sipf_device.cuh"):
+    for name in names:
         with open(os.path.join(ROOT, "paper_2512_03452_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -228,6 +233,17 @@ def run_ours(args, world, rank, local):
     ms64 = dist_max(f0.elapsed_time(f1), world, dev)
     sim64.sync()
     sim64.close()
+    # the FP64 form is bound by the FP64 pipe: its instruction rate against
+    # this GPU's measured FP64 FMA issue rate
+    fma_gflops = _abi.sipf_measure_fp64_fma(stream.cuda_stream)
+    n64 = FP64_PIPE_INSTR.get(kernel_source_hash(("particle_kernels.cu", "sipf_device.cuh", "fft_kernels.cu")))
+    fp64_alu = None
+    if n64 is not None:
+        ach = n64 / (ms64 / K64 * 1e-3)
+        pk = fma_gflops * 1e9 / 2.0
+        fp64_alu = {"bound": "alu", "unit": "FP64 instructions/s", "achieved": ach, "peak": pk, "frac": ach / pk,
+                    "instructions_per_step": n64,
+                    "peak_source": "measured: sipf_measure_fp64_fma (dependent-chain FP64 FMAs over all SMs)"}
 
     # end to end through the C ABI with host buffers: every step uploads the
     # positions from pinned host memory, steps, and reads them back
@@ -282,7 +298,7 @@ def run_ours(args, world, rank, local):
             "gpu_launches": int(tim.kernels),
             "clocks": clocks,
             "fp64": {"value": world * P_FULL * K64 / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64 / K64,
-                     "steps": K64},
+                     "steps": K64, "fma_gflops": fma_gflops, "roofline": fp64_alu},
             "diagnostics": {k: diag[k] for k in ("mass", "peak", "m2", "ring_radius", "step")},
             "batch": batch,
             "adjoint": adjoint,
