@@ -267,15 +267,29 @@ __device__ __forceinline__ void binned_chunk(const BinArgs<T>& a, const ChunkDes
       rank = __popc(peers & ((1u << lane) - 1u));
       if (valid && lane == leader) b0 = atomicAdd(a.dst_cursor + t, __popc(peers));
     }
+    bool fits = DEPOSIT && valid && has_win;
+    int sx = 0, sy = 0, sz = 0;
+    if (!WHOLE && fits) {
+      sx = (cx - 1 - ox) & mask;
+      sy = (cy - 1 - oy) & mask;
+      sz = (cz - 1 - oz) & mask;
+      fits = sx <= kWin - 4 && sy <= kWin - 4 && sz <= kWin - 4;
+    }
+    // Copy of the tile window each lane adds into.  A slot's kTileReps copies
+    // cover a fixed group of banks, and the group of every stencil node of a
+    // particle is its base slot's group shifted by the same amount for all
+    // lanes; so lanes whose base slots share a group are ranked and take
+    // distinct copies (conflict-free while at most kTileReps share a group).
+    int cpy = lane & (kTileReps - 1);
+    if (DEPOSIT && !WHOLE) {
+      constexpr int kGroups = 32 * 4 / (kTileReps * (int)sizeof(A));   // bank groups: 4 (int), 2 (long long)
+      const int cls = fits ? ((((sx * kWin) + sy) * kWin + sz) & (kGroups - 1)) : kGroups;
+      const unsigned m0 = __ballot_sync(0xFFFFFFFFu, cls & 1), m1 = __ballot_sync(0xFFFFFFFFu, cls & 2),
+                     m2 = __ballot_sync(0xFFFFFFFFu, cls & 4);
+      const unsigned peers = ((cls & 1) ? m0 : ~m0) & ((cls & 2) ? m1 : ~m1) & ((cls & 4) ? m2 : ~m2);
+      cpy = __popc(peers & ((1u << lane) - 1u)) & (kTileReps - 1);
+    }
     if (DEPOSIT && valid) {
-      bool fits = has_win;
-      int sx = 0, sy = 0, sz = 0;
-      if (!WHOLE && fits) {
-        sx = (cx - 1 - ox) & mask;
-        sy = (cy - 1 - oy) & mask;
-        sz = (cz - 1 - oz) & mask;
-        fits = sx <= kWin - 4 && sy <= kWin - 4 && sz <= kWin - 4;
-      }
       if (fits) {
         int ix[4], iy[4], iz[4];
         if (WHOLE) {
@@ -286,7 +300,7 @@ __device__ __forceinline__ void binned_chunk(const BinArgs<T>& a, const ChunkDes
                            [&](int idx, T f) { win_add(my_win + idx, WinType<T>::round(f)); });
         } else {
           // base slot plus compile-time offsets of the 4x4x4 box (interleaved copies)
-          A* wb = win + (((sx * kWin) + sy) * kWin + sz) * kTileReps + (lane & (kTileReps - 1));
+          A* wb = win + (((sx * kWin) + sy) * kWin + sz) * kTileReps + cpy;
 #pragma unroll
           for (int o = 0; o < 4; ++o) {
             ix[o] = o * (kWin * kWin * kTileReps);
