@@ -37,16 +37,16 @@ P_FULL, H_FULL = 10_000_000, 128
 # algorithmic bytes of the particle kernel per particle-step (FP32): read X (12 B) + write X (12 B)
 BYTES_PER_PARTICLE = 24
 # DRAM traffic (read + write bytes) of the particle phase, move + re-bin
-# (314.4 MB) and deposit (134.7 MB) launches of one step, from ncu captures of
+# (314.8 MB) and deposit (135.1 MB) launches of one step, from ncu captures of
 # the torus workload, keyed by the SHA-256 of the kernel sources they were
 # taken on (a changed kernel reports null until it is captured again).
-MOVE_TRAFFIC = {"e1d74287d6d04a5fe5958c30225cafbff0b9494a050c60d01650c6c806ac274c": 449.1e6}
+MOVE_TRAFFIC = {"61e5f33ee0ec7359df677efb11d122d8a36cd82770c67535ff6691c3b0b2367b": 449.9e6}
 FALLBACK_HBM_GBS = 6800.0
 # FP64 form: FP64-pipe thread instructions (DFMA + DADD + DMUL) of one FP64 step
-# at P = 1e7, H = 128 (move 2.590e9, deposit 0.819e9, forward plane 0.112e9,
+# at P = 1e7, H = 128 (move 2.590e9, deposit 0.823e9, forward plane 0.112e9,
 # x pass 0.279e9, inverse plane 0.334e9), from an ncu capture of the bench's
 # FP64 leg, keyed by the SHA-256 of the kernel sources it was taken on.
-FP64_PIPE_INSTR = {"af7657d678017968571aabcea3743ff98cffbc126a69573688e9cd64724464de": 4.134262261e9}
+FP64_PIPE_INSTR = {"6be929f00cb73dc0175e21b95629296df68a43a165d5f7f52008acdc78b2e4d7": 4.137509184e9}
 
 
 def _env_int(name, default):
