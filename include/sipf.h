@@ -243,6 +243,10 @@ typedef struct sipf_batch_tuning {
                                      direction; 0: separate pencil passes        */
   int32_t plane_warps[4];         /* warps per block of the plane kernels: 8, 16, 32 */
   int32_t xpass_warps[4];         /* warps per block of the fused x pass: 8, 16      */
+  int32_t inverse_all_components[4]; /* inverse plane kernel: 1 one block per x-plane for
+                                     all three gradient components, writing whole
+                                     nodes (H <= 64); 2 one block per (component,
+                                     x-plane); 0 chosen by the number of blocks    */
   int32_t move_blocks_per_sm;     /* move + re-bin blocks per SM (0: occupancy limit) */
   int32_t deposit_blocks_per_sm;  /* deposit blocks per SM (0: occupancy limit)       */
   double field_ms[4];             /* best device ms per step of each group's field solve */
@@ -255,7 +259,7 @@ typedef struct sipf_batch_tuning {
  * candidates above, each timed with CUDA events on steps_per_trial (>= 2)
  * real steps of the batch (the first step of a trial is not timed).  Shapes
  * do not change results, so the runs advance by out->steps_used steps (about
- * steps_per_trial x (16 per group + 9)).  Later steps use the chosen shapes;
+ * steps_per_trial x (18 per group + 9)).  Later steps use the chosen shapes;
  * out may be NULL.  Synchronises. */
 int sipf_batch_autotune(sipf_batch* b, int32_t steps_per_trial, sipf_batch_tuning* out);
 

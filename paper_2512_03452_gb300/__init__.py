@@ -142,6 +142,7 @@ class Batch:
         return {"groups": [{"H": t.H[i], "cols_tile": t.cols_tile[i], "xpass_tile": t.xpass_tile[i],
                             "rows_blocks_per_sm": t.rows_blocks_per_sm[i], "plane_kernels": t.plane_kernels[i],
                             "plane_warps": t.plane_warps[i], "xpass_warps": t.xpass_warps[i],
+                            "inverse_all_components": t.inverse_all_components[i],
                             "field_ms": t.field_ms[i]}
                            for i in range(g)],
                 "move_blocks_per_sm": t.move_blocks_per_sm, "deposit_blocks_per_sm": t.deposit_blocks_per_sm,

@@ -59,7 +59,7 @@ class sipf_batch_tuning(ctypes.Structure):
     _fields_ = [("ngroups", ctypes.c_int32), ("H", ctypes.c_int32 * 4), ("cols_tile", ctypes.c_int32 * 4),
                 ("xpass_tile", ctypes.c_int32 * 4), ("rows_blocks_per_sm", ctypes.c_int32 * 4),
                 ("plane_kernels", ctypes.c_int32 * 4), ("plane_warps", ctypes.c_int32 * 4),
-                ("xpass_warps", ctypes.c_int32 * 4),
+                ("xpass_warps", ctypes.c_int32 * 4), ("inverse_all_components", ctypes.c_int32 * 4),
                 ("move_blocks_per_sm", ctypes.c_int32), ("deposit_blocks_per_sm", ctypes.c_int32),
                 ("field_ms", ctypes.c_double * 4), ("move_ms", ctypes.c_double), ("deposit_ms", ctypes.c_double),
                 ("steps_used", ctypes.c_int64)]

@@ -870,26 +870,48 @@ __device__ __forceinline__ void plane_fwd_body(Tin* __restrict__ in, double in_s
   constexpr int N = 32 * E, NH = N / 2 + 1;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   cpx<T>* zb = zball + wib * padded_len(N);
-  // 1. rows: two real rows as one complex pencil, split into their half spectra
-  for (int pr = wib; pr < N / 2; pr += (int)(blockDim.x >> 5)) {
-    const size_t ra = (size_t)(2 * pr) * N, rb = ra + N;
-    cpx<T> v[E];
+  const int nw = (int)(blockDim.x >> 5);
+  // 1. rows: two real rows as one complex pencil, split into their half
+  //    spectra.  In single precision the raw values of a warp's next row
+  //    pair are loaded one iteration ahead, so their latency overlaps this
+  //    pair's transform (in double precision the extra registers spill).
+  constexpr bool PF = sizeof(T) == 4;
+  Tin na[E], nb[E];
+  if (PF && wib < N / 2) {
 #pragma unroll
     for (int m = 0; m < E; ++m) {
-      T a, b;
-      if constexpr (sizeof(Tin) == 8 && !std::is_floating_point<Tin>::value) {
-        a = (T)((double)(long long)in[ra + lane + 32 * m] * in_scale);
-        b = (T)((double)(long long)in[rb + lane + 32 * m] * in_scale);
-      } else {
-        a = (T)in[ra + lane + 32 * m];
-        b = (T)in[rb + lane + 32 * m];
+      na[m] = in[(size_t)(2 * wib) * N + lane + 32 * m];
+      nb[m] = in[(size_t)(2 * wib + 1) * N + lane + 32 * m];
+    }
+  }
+  for (int pr = wib; pr < N / 2; pr += nw) {
+    const size_t ra = (size_t)(2 * pr) * N, rb = ra + N;
+    Tin ca[E], cb[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      ca[m] = PF ? na[m] : in[ra + lane + 32 * m];
+      cb[m] = PF ? nb[m] : in[rb + lane + 32 * m];
+    }
+    if (PF && pr + nw < N / 2) {
+      const size_t qa = (size_t)(2 * (pr + nw)) * N, qb = qa + N;
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        na[m] = in[qa + lane + 32 * m];
+        nb[m] = in[qb + lane + 32 * m];
       }
-      v[m] = cpx<T>{a, b};
     }
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       in[ra + lane + 32 * m] = Tin(0);
       in[rb + lane + 32 * m] = Tin(0);
+    }
+    cpx<T> v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      if constexpr (sizeof(Tin) == 8 && !std::is_floating_point<Tin>::value)
+        v[m] = cpx<T>{(T)((double)(long long)ca[m] * in_scale), (T)((double)(long long)cb[m] * in_scale)};
+      else
+        v[m] = cpx<T>{(T)ca[m], (T)cb[m]};
     }
     warp_fft<T, E, -1>(v, lane, tw);
 #pragma unroll
@@ -1005,6 +1027,107 @@ __global__ void __launch_bounds__(1024) kwp_inv(const FftRun<T>* __restrict__ ru
   const int x = blockIdx.x, d = blockIdx.y;
   const size_t S = (size_t)N * N * NH;
   plane_inv_body<T, E>(r.T2 + d * S + (size_t)x * N * NH, r.grad, x, d, tw, P, zb);
+}
+
+// Inverse plane kernel over all three gradient components of one x-plane
+// (H <= 64): y-axis inverse of the three planes, then c2r of row pairs per
+// component into per-warp staging rows, then whole (gx, gy, gz, 0) nodes
+// written as 16-byte vectors.  Every node is written once, in full sectors
+// (the per-component kernel writes each node's sector three times in part,
+// which costs a DRAM read per sector once the nodes exceed L2).
+template <typename T, int E> constexpr size_t plane3_smem_bytes(int nw) {
+  return ((size_t)kTwLen + (size_t)nw * padded_len(32 * E) + 3 * ((size_t)32 * E * (16 * E + 1) + E)) * sizeof(cpx<T>) +
+         (size_t)nw * 3 * padded_len(64 * E) * sizeof(T);
+}
+
+template <typename T> __device__ __forceinline__ void store_node4(T* p, T a, T b, T c) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, 0.f);
+  } else {
+    reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+    reinterpret_cast<double2*>(p)[1] = make_double2(c, 0.0);
+  }
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void plane_inv3_body(const cpx<T>* __restrict__ in, size_t S, T* __restrict__ out, int x,
+                                                const cpx<T>* tw, cpx<T>* P, cpx<T>* zball, T* oball) {
+  constexpr int N = 32 * E, NH = N / 2 + 1;
+  constexpr int PL = N * NH + E;             // one padded plane
+  constexpr int OL = padded_len(2 * N);      // one component's two staged rows, padded
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  cpx<T>* zb = zball + wib * padded_len(N);
+  T* ob = oball + wib * 3 * OL;
+  for (int d = 0; d < 3; ++d)
+    for (int t = threadIdx.x; t < N * NH; t += blockDim.x) P[d * PL + t + ((t / NH) >> 5)] = in[d * S + t];
+  __syncthreads();
+  // 1. y axis inverse: one (component, column) per warp
+  for (int c = wib; c < 3 * NH; c += nw) {
+    const int d = c / NH, col = c - d * NH;
+    cpx<T>* Pd = P + d * PL;
+    cpx<T> v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = Pd[tpad(lane + 32 * m, NH, col)];
+    warp_fft<T, E, +1>(v, lane, tw);
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) Pd[tpad(out_index(k1, E, lane), NH, col)] = v[k1];
+  }
+  __syncthreads();
+  // 2. rows: per component, the two Hermitian half rows A, B as the pencil
+  //    A + i B (real part: row A, imaginary part: row B), staged; then the
+  //    two rows of nodes
+  for (int pr = wib; pr < N / 2; pr += nw) {
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+      const cpx<T>* pa = P + d * PL + tpad(2 * pr, NH, 0);   // rows 2 pr and 2 pr + 1 are adjacent
+      const cpx<T>* pb = pa + NH;
+      for (int k = lane; k < NH; k += 32) {
+        cpx<T> A = pa[k], Bv = pb[k];
+        if (k == 0 || k == N / 2) {
+          A.y = T(0);
+          Bv.y = T(0);
+        }
+        zb[zpad(k)] = cpx<T>{A.x - Bv.y, A.y + Bv.x};
+        if (k > 0 && k < N / 2) zb[zpad(N - k)] = cpx<T>{A.x + Bv.y, -A.y + Bv.x};   // conj A + i conj B
+      }
+      __syncwarp();
+      cpx<T> v[E];
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = zb[zpad(lane + 32 * m)];
+      __syncwarp();
+      warp_fft<T, E, +1>(v, lane, tw);
+      T* obd = ob + d * OL;
+#pragma unroll
+      for (int k1 = 0; k1 < E; ++k1) {
+        const int j = out_index(k1, E, lane);
+        obd[zpad(j)] = v[k1].x;
+        obd[zpad(N + j)] = v[k1].y;
+      }
+    }
+    __syncwarp();
+    T* orow = out + ((size_t)x * N + 2 * pr) * N * 4;
+    for (int t = lane; t < 2 * N; t += 32) {
+      const int q = zpad(t);
+      store_node4<T>(orow + (size_t)t * 4, ob[q], ob[OL + q], ob[2 * OL + q]);
+    }
+    __syncwarp();
+  }
+}
+
+template <typename T, int E>
+__global__ void __launch_bounds__(1024) kwp_inv3(const FftRun<T>* __restrict__ runs) {
+  constexpr int N = 32 * E, NH = N / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* zb = tw + kTwLen;
+  cpx<T>* P = zb + (blockDim.x >> 5) * padded_len(N);
+  T* ob = reinterpret_cast<T*>(P + 3 * ((size_t)N * NH + E));
+  load_tw_full<T, E>(tw);
+  __syncthreads();
+  const FftRun<T>& r = runs[blockIdx.y];
+  const int x = blockIdx.x;
+  const size_t S = (size_t)N * N * NH;
+  plane_inv3_body<T, E>(r.T2 + (size_t)x * N * NH, S, r.grad, x, tw, P, zb, ob);
 }
 
 static int warp_blocks(int rows) {
@@ -1283,10 +1406,17 @@ static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, c
     return tune.plane_nw > 0 ? tune.plane_nw
                              : (blocks <= 2 * 152 ? max(kDefaultPlaneWarps, min(32, N / 4)) : kDefaultPlaneWarps);
   };
-  const int fnw = plane_warps(nruns * N), inw = plane_warps(3 * nruns * N);
+  const int fnw = plane_warps(nruns * N), inw = plane_warps(3 * nruns * N), i3nw = plane_warps(nruns * N);
   const int snw = tune.spec_nw > 0 ? tune.spec_nw : kDefaultSpectralWarps;
   const size_t fsm = plane_smem_bytes<T, E>(fnw), ism = plane_smem_bytes<T, E>(inw);
+  const size_t i3sm = plane3_smem_bytes<T, E>(i3nw);
   const bool planes = tune.plane_mode == 0 && E <= 4 && fsm <= kMaxSmem && ism <= kMaxSmem;
+  // all three components per inverse plane block: where asked, or by default
+  // where the x-plane blocks fill the SMs four times over and two blocks fit
+  // an SM (many runs: the gradient nodes then exceed L2)
+  const bool inv3 = planes && E <= 2 &&
+                    (tune.inv3 == 1 ? i3sm <= kMaxSmem
+                                    : tune.inv3 == 0 && nruns * N >= 4 * 152 && 2 * i3sm <= kMaxSmem);
   if (stages & kFieldForward) {
     if (planes) {
       if ((e = set_smem(kwp_fwd<T, E>, fsm)) != cudaSuccess) return e;
@@ -1309,7 +1439,14 @@ static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, c
     if (e != cudaSuccess) return e;
     nk += 1;
   }
-  if ((stages & kFieldInverse) && planes) {
+  if ((stages & kFieldInverse) && inv3) {
+    if constexpr (E <= 2) {
+      if ((e = set_smem(kwp_inv3<T, E>, i3sm)) != cudaSuccess) return e;
+      kwp_inv3<T, E><<<dim3(N, nruns), 32 * i3nw, i3sm, s>>>(runs);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      nk += 1;
+    }
+  } else if ((stages & kFieldInverse) && planes) {
     if ((e = set_smem(kwp_inv<T, E>, ism)) != cudaSuccess) return e;
     kwp_inv<T, E><<<dim3(N, 3, nruns), 32 * inw, ism, s>>>(runs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1332,9 +1469,11 @@ template <typename T, int E> static bool field_tune_valid_e(const FieldTune& t) 
   const bool pnw_ok = t.plane_nw == 0 || t.plane_nw == 8 || t.plane_nw == 16 || t.plane_nw == 32;
   const bool snw_ok = t.spec_nw == 0 || t.spec_nw == 8 || t.spec_nw == 16;
   const int pnw = t.plane_nw > 0 ? t.plane_nw : kDefaultPlaneWarps;
+  const bool inv3_ok = t.inv3 == 0 || t.inv3 == 2 ||
+                       (t.inv3 == 1 && t.plane_mode == 0 && E <= 2 && plane3_smem_bytes<T, E>(pnw) <= kMaxSmem);
   return (bc == 8 || bc == 16 || bc == 32) && (sbc == 4 || sbc == 8 || sbc == 16) && c <= kMaxSmem &&
          x <= kMaxSmem && t.rows_per_sm >= 0 && t.rows_per_sm <= 32 && (t.plane_mode == 0 || t.plane_mode == 1) &&
-         pnw_ok && snw_ok && (t.plane_mode == 1 || E > 4 || plane_smem_bytes<T, E>(pnw) <= kMaxSmem);
+         pnw_ok && snw_ok && inv3_ok && (t.plane_mode == 1 || E > 4 || plane_smem_bytes<T, E>(pnw) <= kMaxSmem);
 }
 
 template <typename T> FieldTune field_tune_default(int H) {

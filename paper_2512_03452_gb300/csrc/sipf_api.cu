@@ -1211,11 +1211,11 @@ template <typename T> int batch_autotune_impl(sipf_batch* b, int trial, sipf_bat
     float best = 3.0e38f;
     // plane kernels or pencil passes first, then the x-pass tile, then the
     // pencil-pass shapes (which only matter if pencils won)
-    static const std::vector<int> cand[6] = {{0, 1}, {8, 16, 32}, {4, 8, 16}, {8, 16}, {8, 16, 32}, {4, 8, 16}};
-    for (int dim = 0; dim < 6; ++dim) {
+    static const std::vector<int> cand[7] = {{0, 1}, {8, 16, 32}, {1, 2}, {4, 8, 16}, {8, 16}, {8, 16, 32}, {4, 8, 16}};
+    for (int dim = 0; dim < 7; ++dim) {
       for (int v : cand[dim]) {
         FieldTune t = best_t;
-        int* f[6] = {&t.plane_mode, &t.plane_nw, &t.sbc, &t.spec_nw, &t.bc, &t.rows_per_sm};
+        int* f[7] = {&t.plane_mode, &t.plane_nw, &t.inv3, &t.sbc, &t.spec_nw, &t.bc, &t.rows_per_sm};
         *f[dim] = v;
         if (!field_tune_valid<T>(b->group_H[g], t)) continue;
         b->field_tune[g] = t;
@@ -1276,6 +1276,7 @@ template <typename T> int batch_autotune_impl(sipf_batch* b, int trial, sipf_bat
       out->plane_kernels[g] = b->field_tune[g].plane_mode == 0 ? 1 : 0;
       out->plane_warps[g] = b->field_tune[g].plane_nw;
       out->xpass_warps[g] = b->field_tune[g].spec_nw;
+      out->inverse_all_components[g] = b->field_tune[g].inv3;
       out->field_ms[g] = field_ms[g];
     }
     out->move_blocks_per_sm = b->move_bps;
@@ -1393,7 +1394,7 @@ int sipf_batch_step(sipf_batch* b, int64_t nsteps) {
 int sipf_batch_autotune(sipf_batch* b, int32_t steps_per_trial, sipf_batch_tuning* out) {
   if (!b) return fail(SIPF_EINVAL, "batch is NULL");
   if (steps_per_trial < 2) return fail(SIPF_EINVAL, "steps_per_trial (>= 2)");
-  const int64_t most = (int64_t)steps_per_trial * (16 * (int64_t)b->group_H.size() + 9);
+  const int64_t most = (int64_t)steps_per_trial * (18 * (int64_t)b->group_H.size() + 9);
   if (b->n + most > 0xFFFFFFFFLL) return fail(SIPF_EINVAL, "step counter would exceed 2^32 - 1");
   int r = b->precision == 64 ? batch_autotune_impl<double>(b, steps_per_trial, out)
                              : batch_autotune_impl<float>(b, steps_per_trial, out);
@@ -1413,6 +1414,7 @@ int sipf_batch_set_tuning(sipf_batch* b, const sipf_batch_tuning* t) {
     ft[g].plane_mode = t->plane_kernels[g] ? 0 : 1;
     ft[g].plane_nw = t->plane_warps[g];
     ft[g].spec_nw = t->xpass_warps[g];
+    ft[g].inv3 = t->inverse_all_components[g];
     const bool ok = b->precision == 64 ? field_tune_valid<double>(b->group_H[g], ft[g])
                                        : field_tune_valid<float>(b->group_H[g], ft[g]);
     if (!ok) return fail(SIPF_EINVAL, "tuning group " + std::to_string(g) + " has an unsupported tile shape");

@@ -81,6 +81,8 @@ struct FieldTune {
   int plane_mode = 0;   // 0: plane kernels for the inner axes where they fit (H <= 128), 1: pencil passes
   int plane_nw = 0;     // warps per block of the plane kernels (8, 16, 32)
   int spec_nw = 0;      // warps per block of the fused x pass (8, 16)
+  int inv3 = 0;         // inverse plane kernel: 0 by grid size, 1 one block per x-plane for all three
+                        // gradient components (H <= 64), 2 one block per (component, x-plane)
 };
 template <typename T>
 cudaError_t launch_field_batch(const FftRun<T>* runs, int nruns, int H, int stages, cudaStream_t s,
