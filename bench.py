@@ -46,7 +46,7 @@ FALLBACK_HBM_GBS = 6800.0
 # at P = 1e7, H = 128 (move 2.590e9, deposit 0.823e9, forward plane 0.112e9,
 # x pass 0.279e9, inverse plane 0.334e9), from an ncu capture of the bench's
 # FP64 leg, keyed by the SHA-256 of the kernel sources it was taken on.
-FP64_PIPE_INSTR = {"6be929f00cb73dc0175e21b95629296df68a43a165d5f7f52008acdc78b2e4d7": 4.137509184e9}
+FP64_PIPE_INSTR = {"52ac0c91be0c03773dd3d8034deff21b52d071a3d881cce019e16e84e42dea5e": 4.137509184e9}
 
 
 def _env_int(name, default):
