@@ -149,15 +149,51 @@ constexpr int kReplicas = 4;                  // whole-grid window copies (lane 
 constexpr int kTileReps = 8;
 constexpr int kChunk = 4096;                  // particles per work item
 
-// Add the shared window (all replicas) to the grid and clear it: consecutive
-// threads walk consecutive slots along the fastest axis, so the reductions of
-// a warp hit contiguous nodes.  (ox, oy, oz): node of slot (0,0,0).
+// Add the shared window (all replicas) to the grid and clear it; the
+// reductions of a warp hit contiguous nodes along the fastest axis.  Tile
+// windows of ints go 32 slots per warp pass in 16-byte pieces; whole-grid and
+// 64-bit windows one slot per thread.  (ox, oy, oz): node of slot (0,0,0).
 template <typename T, bool FIXED, bool WHOLE>
 __device__ __forceinline__ void window_flush(const BinArgs<T>& a, typename WinType<T>::type* win, int wslots, int ox,
                                              int oy, int oz, T wwin) {
   using A = typename WinType<T>::type;
   const int H = a.g.H, mask = a.g.mask;
   const T unit = a.wmass / wwin;   // M0/P * 2^-K
+  if (!WHOLE && sizeof(A) == 4) {
+    // Tile window of ints: a warp takes 32 consecutive slots (1 KB) per pass.
+    // Lane l reads 16-byte pieces l and 32 + l (halves of slots l/2 and
+    // 16 + l/2), the two halves of a slot are summed with the neighbour lane,
+    // and lane l adds slot l/2 (even l) or 16 + l/2 (odd l) to the grid: 4
+    // shared wavefronts per 512 bytes and a reduction from every lane.
+    static_assert(kTileReps == 8, "two 16-byte halves per slot");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (int)(blockDim.x >> 5);
+    for (int s0 = warp * 32; s0 < wslots; s0 += nwarps * 32) {
+      int4* base = reinterpret_cast<int4*>(win + (size_t)s0 * kTileReps);
+      const int sa = s0 + (lane >> 1), sb = sa + 16;
+      A va = A(0), vb = A(0);
+      if (sa < wslots) {
+        const int4 q = base[lane];
+        va = (A)(q.x + q.y + q.z + q.w);
+        base[lane] = make_int4(0, 0, 0, 0);
+      }
+      if (sb < wslots) {
+        const int4 q = base[32 + lane];
+        vb = (A)(q.x + q.y + q.z + q.w);
+        base[32 + lane] = make_int4(0, 0, 0, 0);
+      }
+      va += __shfl_xor_sync(0xFFFFFFFFu, va, 1);
+      vb += __shfl_xor_sync(0xFFFFFFFFu, vb, 1);
+      const int sidx = (lane & 1) ? sb : sa;
+      const A v = (lane & 1) ? vb : va;
+      if (sidx < wslots && v != A(0)) {
+        const int c = sidx % kWin, b = (sidx / kWin) % kWin, aa = sidx / (kWin * kWin);
+        const int gi = (((ox + aa) & mask) * H + ((oy + b) & mask)) * H + ((oz + c) & mask);
+        if (FIXED) atomicAdd(static_cast<unsigned long long*>(a.phi) + gi, (unsigned long long)(long long)v);
+        else atomicAdd(static_cast<T*>(a.phi) + gi, (T)v * unit);
+      }
+    }
+    return;
+  }
   for (int sidx = threadIdx.x; sidx < wslots; sidx += blockDim.x) {
     A v = A(0);
     if (WHOLE) {
