@@ -159,7 +159,7 @@ __device__ __forceinline__ void window_flush(const BinArgs<T>& a, typename WinTy
   using A = typename WinType<T>::type;
   const int H = a.g.H, mask = a.g.mask;
   const T unit = a.wmass / wwin;   // M0/P * 2^-K
-  if (!WHOLE && sizeof(A) == 4) {
+  if constexpr (!WHOLE && sizeof(A) == 4) {
     // Tile window of ints: a warp takes 32 consecutive slots (1 KB) per pass.
     // Lane l reads 16-byte pieces l and 32 + l (halves of slots l/2 and
     // 16 + l/2), the two halves of a slot are summed with the neighbour lane,
@@ -192,33 +192,33 @@ __device__ __forceinline__ void window_flush(const BinArgs<T>& a, typename WinTy
         else atomicAdd(static_cast<T*>(a.phi) + gi, (T)v * unit);
       }
     }
-    return;
-  }
-  for (int sidx = threadIdx.x; sidx < wslots; sidx += blockDim.x) {
-    A v = A(0);
-    if (WHOLE) {
-#pragma unroll
-      for (int r = 0; r < kReplicas; ++r) {
-        v += win[r * wslots + sidx];
-        win[r * wslots + sidx] = A(0);
-      }
-    } else {
-#pragma unroll
-      for (int r = 0; r < kTileReps; ++r) {
-        v += win[sidx * kTileReps + r];
-        win[sidx * kTileReps + r] = A(0);
-      }
-    }
-    if (v != A(0)) {
-      int gi;
+  } else {
+    for (int sidx = threadIdx.x; sidx < wslots; sidx += blockDim.x) {
+      A v = A(0);
       if (WHOLE) {
-        gi = sidx;
+#pragma unroll
+        for (int r = 0; r < kReplicas; ++r) {
+          v += win[r * wslots + sidx];
+          win[r * wslots + sidx] = A(0);
+        }
       } else {
-        const int c = sidx % kWin, b = (sidx / kWin) % kWin, aa = sidx / (kWin * kWin);
-        gi = (((ox + aa) & mask) * H + ((oy + b) & mask)) * H + ((oz + c) & mask);
+#pragma unroll
+        for (int r = 0; r < kTileReps; ++r) {
+          v += win[sidx * kTileReps + r];
+          win[sidx * kTileReps + r] = A(0);
+        }
       }
-      if (FIXED) atomicAdd(static_cast<unsigned long long*>(a.phi) + gi, (unsigned long long)(long long)v);
-      else atomicAdd(static_cast<T*>(a.phi) + gi, (T)v * unit);
+      if (v != A(0)) {
+        int gi;
+        if (WHOLE) {
+          gi = sidx;
+        } else {
+          const int c = sidx % kWin, b = (sidx / kWin) % kWin, aa = sidx / (kWin * kWin);
+          gi = (((ox + aa) & mask) * H + ((oy + b) & mask)) * H + ((oz + c) & mask);
+        }
+        if (FIXED) atomicAdd(static_cast<unsigned long long*>(a.phi) + gi, (unsigned long long)(long long)v);
+        else atomicAdd(static_cast<T*>(a.phi) + gi, (T)v * unit);
+      }
     }
   }
 }
