@@ -476,7 +476,9 @@ k_deposit_batch(const BinArgs<T>* __restrict__ table, const long long* __restric
 // ---------------------------------------------------------------------------
 constexpr int kNbr = 125;   // 5^3 destination tiles around the source tile
 
-template <typename T> struct MoveRound { static constexpr int n = sizeof(T) == 4 ? 2048 : 1024; };
+constexpr int kMoveThreads = 256;   // threads per move block
+template <typename T> struct MoveRound { static constexpr int n = (sizeof(T) == 4 ? 8 : 4) * kMoveThreads; };
+template <typename T> constexpr int move_min_blocks() { return sizeof(T) == 4 ? 3 : 2; }
 
 template <typename T>
 struct MoveSmem {
@@ -500,7 +502,7 @@ template <typename T, bool MOVE>
 __device__ __forceinline__ void move_chunk(const BinArgs<T>& a, const ChunkDesc& cur, uint32_t n, MoveSmem<T>& sm,
                                            uint32_t& phase) {
   constexpr int R = MoveRound<T>::n;
-  constexpr int PER = R / 256;
+  constexpr int PER = R / kMoveThreads;
   const int mask = a.g.mask, ntx = a.ntx, tmask = a.ntx - 1;   // tiles per axis: a power of two
   const bool in_tile = cur.bin < a.NT;
   const int stz = cur.bin & tmask, sty = (cur.bin / ntx) & tmask, stx = cur.bin / (ntx * ntx);
@@ -534,7 +536,7 @@ __device__ __forceinline__ void move_chunk(const BinArgs<T>& a, const ChunkDesc&
     // 1. move and stage
 #pragma unroll 1
     for (int k = 0; k < PER; ++k) {
-      const int i = k * 256 + threadIdx.x;
+      const int i = k * kMoveThreads + threadIdx.x;
       if (i >= cnt) break;
       T x = sm.x[i], y = sm.y[i], z = sm.z[i];
       if (MOVE) {
@@ -628,7 +630,7 @@ __device__ __forceinline__ void move_chunk(const BinArgs<T>& a, const ChunkDesc&
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kMoveThreads, move_min_blocks<T>())
 k_move(BinArgs<T> a) {
   __shared__ MoveSmem<T> sm;
   const long long nchunks = a.chunk_start[a.NT + 1];
@@ -658,7 +660,7 @@ k_move(BinArgs<T> a) {
 // Batched move (MOVE) or re-bin (!MOVE): work items of all runs from one
 // counter; run r's arguments at table[r]; the step index from device memory.
 template <typename T, bool MOVE>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kMoveThreads, move_min_blocks<T>())
 k_move_batch(const BinArgs<T>* __restrict__ table, const long long* __restrict__ prefix, int nruns,
              unsigned long long* work, const uint32_t* step) {
   __shared__ MoveSmem<T> sm;
@@ -705,9 +707,9 @@ template <typename T> cudaError_t launch_move(const BinArgs<T>& a, cudaStream_t 
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_move<T>, 256, 0)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_move<T>, kMoveThreads, 0)) != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  k_move<T><<<sms * per_sm, 256, 0, s>>>(a);
+  k_move<T><<<sms * per_sm, kMoveThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -1280,10 +1282,10 @@ cudaError_t launch_move_batch(const BinArgs<T>* table, const long long* prefix, 
   auto k = move ? k_move_batch<T, true> : k_move_batch<T, false>;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, 0)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kMoveThreads, 0)) != cudaSuccess) return e;
   if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
   if (per_sm < 1) per_sm = 1;
-  k<<<sms * per_sm, 256, 0, s>>>(table, prefix, nruns, work, step);
+  k<<<sms * per_sm, kMoveThreads, 0, s>>>(table, prefix, nruns, work, step);
   return cudaGetLastError();
 }
 
