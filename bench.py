@@ -37,16 +37,16 @@ P_FULL, H_FULL = 10_000_000, 128
 # algorithmic bytes of the particle kernel per particle-step (FP32): read X (12 B) + write X (12 B)
 BYTES_PER_PARTICLE = 24
 # DRAM traffic (read + write bytes) of the particle phase, move + re-bin
-# (314.8 MB) and deposit (135.1 MB) launches of one step, from ncu captures of
+# (314.7 MB) and deposit (135.2 MB) launches of one step, from ncu captures of
 # the torus workload, keyed by the SHA-256 of the kernel sources they were
 # taken on (a changed kernel reports null until it is captured again).
-MOVE_TRAFFIC = {"61e5f33ee0ec7359df677efb11d122d8a36cd82770c67535ff6691c3b0b2367b": 449.9e6}
+MOVE_TRAFFIC = {"89e797763bb54f02e00e069aa8c60d52948cab59c6720217741e300350c295c5": 449.9e6}
 FALLBACK_HBM_GBS = 6800.0
 # FP64 form: FP64-pipe thread instructions (DFMA + DADD + DMUL) of one FP64 step
 # at P = 1e7, H = 128 (move 2.590e9, deposit 0.823e9, forward plane 0.112e9,
 # x pass 0.279e9, inverse plane 0.334e9), from an ncu capture of the bench's
 # FP64 leg, keyed by the SHA-256 of the kernel sources it was taken on.
-FP64_PIPE_INSTR = {"52ac0c91be0c03773dd3d8034deff21b52d071a3d881cce019e16e84e42dea5e": 4.137509184e9}
+FP64_PIPE_INSTR = {"55a9035dd9ff79700201acf3dc38eb105b212bcac8025b2ba7f54586930fd347": 4.137509184e9}
 
 
 def _env_int(name, default):
