@@ -42,6 +42,10 @@ BYTES_PER_PARTICLE = 24
 # taken on (a changed kernel reports null until it is captured again).
 MOVE_TRAFFIC = {"89e797763bb54f02e00e069aa8c60d52948cab59c6720217741e300350c295c5": 449.9e6}
 FALLBACK_HBM_GBS = 6800.0
+# Warp-instructions of one move + re-bin launch (148.18 M) and one deposit
+# launch (108.80 M) at P = 1e7, H = 128, FP32, from the same ncu captures,
+# keyed like the traffic: the particle kernels against the SMs' issue rate.
+PARTICLE_WARP_INSTR = {"89e797763bb54f02e00e069aa8c60d52948cab59c6720217741e300350c295c5": 256.98e6}
 # FP64 form: FP64-pipe thread instructions (DFMA + DADD + DMUL) of one FP64 step
 # at P = 1e7, H = 128 (move 2.590e9, deposit 0.823e9, forward plane 0.112e9,
 # x pass 0.279e9, inverse plane 0.334e9), from an ncu capture of the bench's
@@ -54,6 +58,14 @@ def _env_int(name, default):
         return int(os.environ.get(name, default))
     except ValueError:
         return default
+
+
+def sm_max_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"]), "measured"
+    except Exception:
+        return 2070.0, "nominal"
 
 
 def measured_peaks():
@@ -216,6 +228,18 @@ def run_ours(args, world, rank, local):
     part_ms = move_ms + dep_ms
     achieved = BYTES_PER_PARTICLE * P_FULL / (part_ms * 1e-3) / 1e9
     traffic = MOVE_TRAFFIC.get(kernel_source_hash())
+    # the same kernels against the SMs' instruction issue rate (4 warp-
+    # instructions per clock per SM), the bound they actually meet
+    n_issue = PARTICLE_WARP_INSTR.get(kernel_source_hash())
+    issue = None
+    if n_issue is not None:
+        mhz, mhz_kind = sm_max_mhz()
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        pk = 4.0 * sms * mhz * 1e6
+        ach = n_issue / (part_ms * 1e-3)
+        issue = {"bound": "issue", "unit": "warp-instructions/s", "achieved": ach, "peak": pk, "frac": ach / pk,
+                 "instructions_per_step": n_issue,
+                 "peak_source": f"4 per clock x {sms} SMs x {mhz:.0f} MHz ({mhz_kind} maximum SM clock)"}
     stages = {k: getattr(tim, k) / max(tim.steps, 1) for k in
               ("forward_ms", "spectral_ms", "inverse_ms", "move_ms", "bookkeeping_ms", "deposit_ms")}
 
@@ -291,7 +315,8 @@ def run_ours(args, world, rank, local):
             "roofline": {"bound": "hbm", "kernel": "particle phase: k_binned move+rebin and k_binned deposit",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "peak_source": peak_kind, "bytes_per_particle": BYTES_PER_PARTICLE,
-                         "kernel_ms": part_ms, "overflow_per_step": tim.overflow / max(tim.steps, 1)},
+                         "kernel_ms": part_ms, "overflow_per_step": tim.overflow / max(tim.steps, 1),
+                         "issue": issue},
             "stages_ms_per_step": stages,
             "cpu_baseline": cpu,
             "e2e": e2e,
