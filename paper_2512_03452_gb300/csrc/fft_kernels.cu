@@ -590,12 +590,14 @@ kw_cols(cpx<T>* __restrict__ data, int B, size_t comp_stride, T scale) {
 }
 
 // x-axis pass fused with the spectral work (as k_spectral_x), warp FFTs.
-// Shared tile: [N][4 BC + 1]; slot 0 = beta, slots 1..3 the outputs.
+// Shared tile: [N][3 BC + 1]; slot 0 = beta, then the first output (each
+// element's beta is read before its outputs are written), slots 1, 2 the other
+// two outputs: 3 slots per pencil, so a 128^3 x pass fits one wave of blocks.
 template <typename T, int E, int MODE, int BC>
 __device__ __forceinline__ void spectral_body(const cpx<T>* __restrict__ T1, cpx<T>* __restrict__ alpha,
                                               cpx<T>* __restrict__ T2, const SpecParams& sp, double* alpha0_shadow,
                                               int b0, const cpx<T>* tw, cpx<T>* buf) {
-  constexpr int N = 32 * E, NHH = N / 2 + 1, LD = 4 * BC + 1;
+  constexpr int N = 32 * E, NHH = N / 2 + 1, LD = 3 * BC + 1;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int B = N * NHH;
   const size_t S = (size_t)N * B;
@@ -669,14 +671,14 @@ __device__ __forceinline__ void spectral_body(const cpx<T>* __restrict__ T1, cpx
         o1 = alpha[gi];
       }
     }
-    buf[tpad(j, LD, BC + c)] = o1;
-    buf[tpad(j, LD, 2 * BC + c)] = o2;
-    buf[tpad(j, LD, 3 * BC + c)] = o3;
+    buf[tpad(j, LD, c)] = o1;
+    buf[tpad(j, LD, BC + c)] = o2;
+    buf[tpad(j, LD, 2 * BC + c)] = o3;
   }
   __syncthreads();
   constexpr int nout = (MODE == kModeStep || MODE == kModeGradOnly) ? 3 : 1;
   for (int col = wib; col < nout * BC; col += (int)(blockDim.x >> 5)) {
-    const int c = BC + col;
+    const int c = col;
     if (col % BC >= nb) continue;
     cpx<T> v[E];
 #pragma unroll
@@ -690,7 +692,7 @@ __device__ __forceinline__ void spectral_body(const cpx<T>* __restrict__ T1, cpx
     const int j = t / BC, c = t - j * BC;
     if (c < nb) {
 #pragma unroll
-      for (int d = 0; d < nout; ++d) T2[d * S + (size_t)j * B + b0 + c] = buf[tpad(j, LD, (d + 1) * BC + c)];
+      for (int d = 0; d < nout; ++d) T2[d * S + (size_t)j * B + b0 + c] = buf[tpad(j, LD, d * BC + c)];
     }
   }
 }
@@ -1164,7 +1166,7 @@ static cudaError_t warp_spectral(const cpx<T>* T1, cpx<T>* alpha, cpx<T>* T2, Sp
   constexpr int N = 32 * E;
   constexpr int BC = (sizeof(T) == 8 && E == 8) ? 4 : ((sizeof(T) == 8 || E == 8) ? 8 : 16);
   const int B = N * (N / 2 + 1);
-  const size_t smem = (kTwLen + (size_t)N * (4 * BC + 1) + E) * sizeof(cpx<T>);
+  const size_t smem = (kTwLen + (size_t)N * (3 * BC + 1) + E) * sizeof(cpx<T>);
   auto k = kw_spectral_x<T, E, MODE, BC>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
@@ -1350,7 +1352,7 @@ static size_t cols_smem() {
 }
 template <typename T, int E, int SBC>
 static size_t spectral_smem() {
-  return (kTwLen + (size_t)32 * E * (4 * SBC + 1) + E) * sizeof(cpx<T>);
+  return (kTwLen + (size_t)32 * E * (3 * SBC + 1) + E) * sizeof(cpx<T>);
 }
 
 template <typename T, int E, int DIR, int BC>
@@ -1401,12 +1403,15 @@ static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, c
   const int bc = tune.bc > 0 ? tune.bc : 16;
   const int sbc = tune.sbc > 0 ? tune.sbc : default_sbc<T, E>();
   // default plane warps: 8, or, for a kernel whose blocks fill the 152 SMs
-  // less than twice, up to one warp per 4 plane rows
-  auto plane_warps = [&](int blocks) {
+  // less than `fill` times over, up to `most` (at most one warp per 4 plane
+  // rows); measured at H = 128, one run: 32 for the forward kernel's 128
+  // blocks, 16 for the inverse kernel's 384 (two blocks per SM)
+  auto plane_warps = [&](int blocks, int fill, int most) {
     return tune.plane_nw > 0 ? tune.plane_nw
-                             : (blocks <= 2 * 152 ? max(kDefaultPlaneWarps, min(32, N / 4)) : kDefaultPlaneWarps);
+                             : (blocks <= fill * 152 ? max(kDefaultPlaneWarps, min(most, N / 4)) : kDefaultPlaneWarps);
   };
-  const int fnw = plane_warps(nruns * N), inw = plane_warps(3 * nruns * N), i3nw = plane_warps(nruns * N);
+  const int fnw = plane_warps(nruns * N, 2, 32), inw = plane_warps(3 * nruns * N, 4, 16),
+            i3nw = plane_warps(nruns * N, 2, 32);
   const int snw = tune.spec_nw > 0 ? tune.spec_nw : kDefaultSpectralWarps;
   const size_t fsm = plane_smem_bytes<T, E>(fnw), ism = plane_smem_bytes<T, E>(inw);
   const size_t i3sm = plane3_smem_bytes<T, E>(i3nw);
