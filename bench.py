@@ -37,15 +37,15 @@ P_FULL, H_FULL = 10_000_000, 128
 # algorithmic bytes of the particle kernel per particle-step (FP32): read X (12 B) + write X (12 B)
 BYTES_PER_PARTICLE = 24
 # DRAM traffic (read + write bytes) of the particle phase, move + re-bin
-# (314.7 MB) and deposit (135.2 MB) launches of one step, from ncu captures of
+# (314.4 MB) and deposit (135.2 MB) launches of one step, from ncu captures of
 # the torus workload, keyed by the SHA-256 of the kernel sources they were
 # taken on (a changed kernel reports null until it is captured again).
-MOVE_TRAFFIC = {"89e797763bb54f02e00e069aa8c60d52948cab59c6720217741e300350c295c5": 449.9e6}
+MOVE_TRAFFIC = {"4959deacb513d80b17bd67223857caad29c7f2b18a710a52bd600adce0e6f305": 449.6e6}
 FALLBACK_HBM_GBS = 6800.0
 # Warp-instructions of one move + re-bin launch (148.18 M) and one deposit
-# launch (108.80 M) at P = 1e7, H = 128, FP32, from the same ncu captures,
+# launch (108.79 M) at P = 1e7, H = 128, FP32, from the same ncu captures,
 # keyed like the traffic: the particle kernels against the SMs' issue rate.
-PARTICLE_WARP_INSTR = {"89e797763bb54f02e00e069aa8c60d52948cab59c6720217741e300350c295c5": 256.98e6}
+PARTICLE_WARP_INSTR = {"4959deacb513d80b17bd67223857caad29c7f2b18a710a52bd600adce0e6f305": 256.97e6}
 # FP64 form: FP64-pipe thread instructions (DFMA + DADD + DMUL) of one FP64 step
 # at P = 1e7, H = 128 (move 2.590e9, deposit 0.823e9, forward plane 0.112e9,
 # x pass 0.279e9, inverse plane 0.334e9), from an ncu capture of the bench's

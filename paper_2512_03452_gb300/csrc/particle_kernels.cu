@@ -827,7 +827,10 @@ __device__ __forceinline__ void chunk_emit_body(const ChunkListArgs& a, int blk,
   }
   if (blk == nblk - 1 && threadIdx.x == 0) {
     a.chunk_start[nb] = off + total;
-    if (work) *work = 0ULL;
+    if (work) {   // a context's two work counters (deposit / re-bin, move)
+      work[0] = 0ULL;
+      work[1] = 0ULL;
+    }
     if (ovf_total) *ovf_total += (unsigned long long)a.count[a.NT];
   }
 }

@@ -316,8 +316,10 @@ template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
     SIPF_CK(mark(&ev[3]));
     // X^(n-1) -> X^n, re-bin into the other buffer by the new tile
     const int src = c->cur, dst = 1 - c->cur;
-    SIPF_CK(cudaMemsetAsync(c->work, 0, sizeof(unsigned long long), c->stream));
-    SIPF_CK(launch_move<T>(bin_args<T>(c, src, c->lc, dst, c->lc), c->stream));
+    // the move's work counter was cleared by the last chunk-list emission
+    BinArgs<T> ma = bin_args<T>(c, src, c->lc, dst, c->lc);
+    ma.work = c->work + 1;
+    SIPF_CK(launch_move<T>(ma, c->stream));
     SIPF_CK(mark(&ev[4]));
     SIPF_CK(launch_chunk_list(cl_args(c, c->cursor[dst], c->lcap[c->lc], c->lbase[c->lc], c->cursor[src]), c->work,
                               c->timing ? c->ovf : nullptr, c->stream));
@@ -338,8 +340,8 @@ template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
       c->since_layout = 0;
     }
     SIPF_CK(mark(&ev[5]));
-    // deposit X^n from its bins (Algorithm 2) for the next step
-    SIPF_CK(cudaMemsetAsync(c->work, 0, sizeof(unsigned long long), c->stream));
+    // deposit X^n from its bins (Algorithm 2) for the next step (its work
+    // counter was cleared by the chunk-list emission above)
     SIPF_CK(launch_binned<T>(bin_args<T>(c, c->cur, c->lc, -1, 0), 0, 1, 0, c->stream));
     c->launches += 1;
     SIPF_CK(mark(&ev[6]));
@@ -638,7 +640,10 @@ int sipf_init(const sipf_params* p, const double* X0, void* stream, sipf_ctx** o
   if (e == cudaSuccess) e = cudaMalloc(&c->chunk_start, (nb + 1) * sizeof(long long));
   if (e == cudaSuccess) e = cudaMalloc(&c->chunks, (size_t)c->max_chunks() * sizeof(ChunkDesc));
   if (e == cudaSuccess) e = cudaMalloc(&c->part, (size_t)chunk_list_blocks(c->NT) * sizeof(long long));
-  if (e == cudaSuccess) e = cudaMalloc(&c->work, sizeof(unsigned long long));
+  // work counters: [0] deposit and re-bin passes, [1] the move (both cleared by
+  // every chunk-list emission, so a step needs no separate clears)
+  if (e == cudaSuccess) e = cudaMalloc(&c->work, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->work, 0, 2 * sizeof(unsigned long long), c->stream);
   if (e == cudaSuccess) e = cudaMalloc(&c->ovf, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ovf, 0, sizeof(unsigned long long), c->stream);
   if (e == cudaSuccess) e = cudaMalloc(&c->hist, nb * sizeof(int));

@@ -192,8 +192,9 @@ template <typename T> cudaError_t launch_move(const BinArgs<T>& a, cudaStream_t 
 // From fill cursors: clamped counts, chunk prefix sums and chunk descriptors
 // (slots from `base`); clears other_cursor and the work counter.  ovf_total
 // (nullable) accumulates the number of particles in the overflow bin.
-// Chunk list of one buffer: two launches (count, emit); clears *work and adds
-// the overflow-bin count to *ovf_total when those are non-NULL.
+// Chunk list of one buffer: two launches (count, emit); clears work[0] and
+// work[1] (a context's deposit / re-bin and move counters) and adds the
+// overflow-bin count to *ovf_total when those are non-NULL.
 int chunk_list_blocks(int NT);
 cudaError_t launch_chunk_list(const ChunkListArgs& a, unsigned long long* work, unsigned long long* ovf_total,
                               cudaStream_t s);
