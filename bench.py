@@ -50,7 +50,7 @@ PARTICLE_WARP_INSTR = {"4959deacb513d80b17bd67223857caad29c7f2b18a710a52bd600adc
 # at P = 1e7, H = 128 (move 2.590e9, deposit 0.823e9, forward plane 0.112e9,
 # x pass 0.279e9, inverse plane 0.334e9), from an ncu capture of the bench's
 # FP64 leg, keyed by the SHA-256 of the kernel sources it was taken on.
-FP64_PIPE_INSTR = {"c9906beb79f7277dc452381cf4593be2a7cc7607617386f2b53533cea1698f86": 4.137509184e9}
+FP64_PIPE_INSTR = {"3558a2a16795e9998204b5824f419c4273c6a8cd171dec4730433dae951411d0": 4.137509184e9}
 
 
 def _env_int(name, default):
