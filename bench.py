@@ -512,6 +512,34 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batch_case(args):
+    """A small batch for kernel captures: 128 runs at H = 64 with 1e4 particles
+    each (Gaussian blobs), `warmup` directly issued steps, then `steps` timed
+    ones; prints the device ms per step.  Not a benchmark line."""
+    import torch
+
+    from paper_2512_03452_gb300 import Batch, _abi, build, params_from_workload, workloads
+
+    build.build()
+    _abi.load()
+    ws = [workloads.Workload(f"r{i}", P=10_000, H=64, L=1.0, mass=50.0, chi=1.0, dt=1e-4, steps=100, seed=i,
+                             sigma=0.1) for i in range(128)]
+    params = [params_from_workload(w, precision=32) for w in ws]
+    X0s = [workloads.sample_positions(w) for w in ws]
+    stream = torch.cuda.Stream()
+    with Batch(params, X0s, stream=stream.cuda_stream) as b:
+        b.use_graph(False)
+        b.step(args.warmup)
+        b.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        print(json.dumps({"case": "batch of 128 runs, H=64, P=1e4 each, FP32",
+                          "ms_per_step": e0.elapsed_time(e1) / max(args.steps, 1)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -522,7 +550,12 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     ap.add_argument("--no-extra", action="store_true", help="skip the H sweep, deterministic, cuFFT and FP64 legs")
+    ap.add_argument("--batch-case", action="store_true",
+                    help="only run a small 128-run H = 64 batch (for kernel captures) and print its ms per step")
     args = ap.parse_args()
+    if args.batch_case:
+        run_batch_case(args)
+        return
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     world, rank, local = dist_init(args)
     if args.impl == "reference":
