@@ -202,6 +202,26 @@ def test_launch_shapes_give_identical_bits(shape):
         assert np.array_equal(got[r][1], ref[r][1]), r
 
 
+def test_inverse_over_all_components_in_fp64_gives_identical_bits():
+    """The three-component inverse plane kernel in double precision (chosen
+    only by tuning there): the same bits as the default shapes."""
+    _, params, X0s = _runs(64, mode=1, n=4, seed=12)
+
+    def run(t):
+        with Batch(params, X0s) as b:
+            if t is not None:
+                _abi.sipf_batch_set_tuning(b.handle, t)
+            b.step(40)
+            b.sync()
+            return [(b.positions(r), b.spectrum(r)) for r in range(len(params))]
+
+    ref = run(None)
+    got = run(_tuning([32, 64], g0_inverse_all_components=1, g1_inverse_all_components=1))
+    for r in range(len(params)):
+        assert np.array_equal(got[r][0], ref[r][0]), r
+        assert np.array_equal(got[r][1], ref[r][1]), r
+
+
 def test_set_tuning_rejects_bad_shapes():
     _, params, X0s = _runs(32, mode=0, n=2, seed=1)
     with Batch(params, X0s) as b:
