@@ -540,6 +540,18 @@ def run_batch_case(args):
                           "ms_per_step": e0.elapsed_time(e1) / max(args.steps, 1)}), flush=True)
 
 
+def run_adjoint_case():
+    """Only the adjoint leg (for kernel captures); prints its JSON object."""
+    import torch
+
+    from paper_2512_03452_gb300 import _abi, build
+
+    build.build()
+    _abi.load()
+    dev = torch.device("cuda", 0)
+    print(json.dumps(run_adjoint_leg(1, dev, torch.cuda.Stream(device=dev))), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -552,9 +564,13 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the H sweep, deterministic, cuFFT and FP64 legs")
     ap.add_argument("--batch-case", action="store_true",
                     help="only run a small 128-run H = 64 batch (for kernel captures) and print its ms per step")
+    ap.add_argument("--adjoint-case", action="store_true", help="only run the adjoint leg (for kernel captures)")
     args = ap.parse_args()
     if args.batch_case:
         run_batch_case(args)
+        return
+    if args.adjoint_case:
+        run_adjoint_case()
         return
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     world, rank, local = dist_init(args)

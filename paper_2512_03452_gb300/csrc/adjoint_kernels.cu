@@ -127,7 +127,18 @@ __device__ __forceinline__ A3<T> deposit_adjoint(const T* __restrict__ phibar, i
   return A3<T>{s.x * w_inv_h, s.y * w_inv_h, s.z * w_inv_h};
 }
 
-template <typename T> __device__ __forceinline__ void red_add(T* p, T v) { atomicAdd(p, v); }
+// Add (a, b, c) to one (x, y, z, -) node of the interleaved cotangent grid:
+// one 16-byte vector reduction in single precision (one L2 sector operation
+// instead of three), three scalar ones in double precision.
+template <typename T> __device__ __forceinline__ void red_node3(T* node, T a, T b, T c);
+template <> __device__ __forceinline__ void red_node3<float>(float* node, float a, float b, float c) {
+  atomicAdd(reinterpret_cast<float4*>(node), make_float4(a, b, c, 0.f));
+}
+template <> __device__ __forceinline__ void red_node3<double>(double* node, double a, double b, double c) {
+  atomicAdd(node, a);
+  atomicAdd(node + 1, b);
+  atomicAdd(node + 2, c);
+}
 
 // Block sum of two values into FP64 accumulators (one atomic pair per block).
 template <typename T> __device__ __forceinline__ void block_acc2(T a, T b, double* acc) {
@@ -162,14 +173,14 @@ template <typename T> __device__ __forceinline__ void block_acc2(T a, T b, doubl
 
 // One reverse step n for every particle p (id order).  In: X^{n-1}, the
 // gradient grids g^{n-1} as (gx, gy, gz, 0) nodes, phibar^{n-1} and Xbar^n;
-// out: Xbar^{n-1} (in place), the gradient-grid cotangents gbar (3 planes of
-// H^3, accumulated) and the sums for dJ/dchi and dJ/ds.
+// out: Xbar^{n-1} (in place), the gradient-grid cotangents gbar (H^3
+// interleaved (x, y, z, -) nodes, accumulated) and the sums for dJ/dchi and
+// dJ/ds.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_adj_step(AdjArgs<T> a) {
   T chi_part = T(0), s_part = T(0);
   const Geo<T> g = a.g;
-  const size_t H3 = (size_t)g.H * g.H * g.H;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.P; p += (int64_t)gridDim.x * blockDim.x) {
     const T x = a.x[p], y = a.y[p], z = a.z[p];
     const T bx = a.xb[p], by = a.xb[a.P + p], bz = a.xb[2 * a.P + p];
@@ -205,9 +216,7 @@ k_adj_step(AdjArgs<T> a) {
     // gbar_d += F_gamma(q) chi tau Xbar_d  (transpose of the gather)
     const T cbx = a.chitau * bx, cby = a.chitau * by, cbz = a.chitau * bz;
     stencil_grad_visit<T>(a.g2p, qx, qy, qz, g, [&](int idx, T f, T, T, T) {
-      red_add(a.gbar + idx, f * cbx);
-      red_add(a.gbar + H3 + idx, f * cby);
-      red_add(a.gbar + 2 * H3 + idx, f * cbz);
+      red_node3<T>(a.gbar + (size_t)idx * 4, f * cbx, f * cby, f * cbz);
     });
     // transpose of the deposit of X^{n-1}
     const A3<T> dp = deposit_adjoint<T>(a.phibar, a.p2g, x, y, z, a.w_inv_h, g);
@@ -216,6 +225,21 @@ k_adj_step(AdjArgs<T> a) {
     a.xb[2 * a.P + p] = ybz + dp.z;
   }
   block_acc2<T>(chi_part, s_part, a.acc);
+}
+
+// Interleaved cotangent nodes -> three planes of H^3 (the transforms' input);
+// the nodes are cleared for the next step's accumulation.
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_planes(T* __restrict__ gbar4, T* __restrict__ planes, int64_t H3) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < H3; i += (int64_t)gridDim.x * blockDim.x) {
+    T* node = gbar4 + (size_t)i * 4;
+    planes[i] = node[0];
+    planes[H3 + i] = node[1];
+    planes[2 * H3 + i] = node[2];
+    node[0] = T(0);
+    node[1] = T(0);
+    node[2] = T(0);
+  }
 }
 
 // Terminal cotangent: Xbar^N = transpose of the deposit at X^N applied to phibar^N.
@@ -294,6 +318,11 @@ template <typename T> cudaError_t launch_adj_step(const AdjArgs<T>& a, cudaStrea
   return cudaGetLastError();
 }
 
+template <typename T> cudaError_t launch_adj_planes(T* gbar4, T* planes, int64_t H3, cudaStream_t s) {
+  k_adj_planes<T><<<grid_blocks(H3), 256, 0, s>>>(gbar4, planes, H3);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_adj_terminal(const T* x, const T* y, const T* z, int64_t P, const T* phibar, int p2g, T w_inv_h,
                                 Geo<T> g, T* xb, cudaStream_t s) {
@@ -312,6 +341,7 @@ cudaError_t launch_adj_spectral(const cpx<T>* ghat, cpx<T>* abar, cpx<T>* spec, 
 
 #define SIPF_ADJ_INST(T)                                                                                          \
   template cudaError_t launch_adj_step<T>(const AdjArgs<T>&, cudaStream_t);                                      \
+  template cudaError_t launch_adj_planes<T>(T*, T*, int64_t, cudaStream_t);                                      \
   template cudaError_t launch_adj_terminal<T>(const T*, const T*, const T*, int64_t, const T*, int, T, Geo<T>, T*, \
                                               cudaStream_t);                                                     \
   template cudaError_t launch_adj_spectral<T>(const cpx<T>*, cpx<T>*, cpx<T>*, int, SpecParams, cudaStream_t);

@@ -1501,7 +1501,8 @@ struct sipf_adjoint {
   void* xb = nullptr;      // 3P T: Xbar
   void* abar = nullptr;    // S complex T
   void* spec = nullptr;    // S complex T: L^-3 B abar, then inverse-transform work
-  void* gbar = nullptr;    // 3 H^3 T
+  void* gbar = nullptr;    // 3 H^3 T: cotangent planes (the transforms' input)
+  void* gbar4 = nullptr;   // 4 H^3 T: cotangents accumulated as (x, y, z, -) nodes, kept zero between steps
   void* ghat = nullptr;    // 3 S complex T
   void* phibar = nullptr;  // H^3 T
   double* acc = nullptr;   // [dJ/dchi, dJ/ds]
@@ -1518,7 +1519,8 @@ constexpr int kAdjCheckpoint = 20;
 void adjoint_free(sipf_adjoint* a) {
   if (!a) return;
   if (a->c && a->c->stream) cudaStreamSynchronize(a->c->stream);
-  for (void* p : {a->ckX, a->ckA, a->segX, a->segG, a->XN, a->xb, a->abar, a->spec, a->gbar, a->ghat, a->phibar})
+  for (void* p : {a->ckX, a->ckA, a->segX, a->segG, a->XN, a->xb, a->abar, a->spec, a->gbar, a->gbar4, a->ghat,
+                  a->phibar})
     cudaFree(p);
   cudaFree(a->acc);
   for (cudaEvent_t e : a->ev)
@@ -1616,7 +1618,6 @@ int adjoint_backward_impl(sipf_adjoint* a, const double* rho_bar, double* grad_c
     }
     for (int64_t n = k1; n > k0; --n) {
       const size_t i = (size_t)(n - 1 - k0);
-      SIPF_CK(cudaMemsetAsync(a->gbar, 0, 3 * H3 * sizeof(T), s));
       AdjArgs<T> aa{};
       aa.x = segX + i * 3 * P;
       aa.y = aa.x + P;
@@ -1624,7 +1625,7 @@ int adjoint_backward_impl(sipf_adjoint* a, const double* rho_bar, double* grad_c
       aa.grad4 = segG + i * 4 * H3;
       aa.phibar = (const T*)a->phibar;
       aa.xb = xb;
-      aa.gbar = (T*)a->gbar;
+      aa.gbar = (T*)a->gbar4;
       aa.acc = a->acc;
       aa.g = geo;
       aa.s_noise = (T)sn;
@@ -1638,6 +1639,7 @@ int adjoint_backward_impl(sipf_adjoint* a, const double* rho_bar, double* grad_c
       aa.g2p = p.g2p_order;
       aa.split = p.splitting;
       SIPF_CK(launch_adj_step<T>(aa, s));
+      SIPF_CK(launch_adj_planes<T>((T*)a->gbar4, (T*)a->gbar, (int64_t)H3, s));
       // ghat = unnormalised DFT of the three cotangent grids
       cpx<T>* gh = (cpx<T>*)a->ghat;
       SIPF_CK(launch_rows_r2c<T>(a->gbar, 0, 1.0, false, gh, H, 3 * H * H, nullptr, s));
@@ -1650,7 +1652,7 @@ int adjoint_backward_impl(sipf_adjoint* a, const double* rho_bar, double* grad_c
       SIPF_CK(launch_cols<T>(sc, H, 1, H * nh, 1, 0, +1, 1.0, s));
       SIPF_CK(launch_cols<T>(sc, H, H, nh, 1, 0, +1, 1.0, s));
       SIPF_CK(launch_rows_c2r<T>(sc, 1, 0, (T*)a->phibar, H, H * H, nullptr, s));
-      a->launches += 8;
+      a->launches += 9;
     }
   }
   SIPF_CK(cudaEventRecord(a->ev[3], s));
@@ -1706,6 +1708,8 @@ int sipf_adjoint_init(const sipf_params* p, const double* X0, int64_t nsteps, in
   if (e == cudaSuccess) e = cudaMalloc(&a->abar, 2 * S * esz);
   if (e == cudaSuccess) e = cudaMalloc(&a->spec, 2 * S * esz);
   if (e == cudaSuccess) e = cudaMalloc(&a->gbar, 3 * H3 * esz);
+  if (e == cudaSuccess) e = cudaMalloc(&a->gbar4, 4 * H3 * esz);
+  if (e == cudaSuccess) e = cudaMemset(a->gbar4, 0, 4 * H3 * esz);
   if (e == cudaSuccess) e = cudaMalloc(&a->ghat, 3 * 2 * S * esz);
   if (e == cudaSuccess) e = cudaMalloc(&a->phibar, H3 * esz);
   if (e == cudaSuccess) e = cudaMalloc(&a->acc, 2 * sizeof(double));

@@ -103,7 +103,7 @@ struct AdjArgs {
   const T* grad4;      // g^{n-1}: (gx, gy, gz, 0) per node, 4 H^3
   const T* phibar;     // transpose-of-deposit cotangent grid phibar^{n-1}, H^3
   T* xb;               // Xbar: 3 planes of P (in: Xbar^n, out: Xbar^{n-1})
-  T* gbar;             // 3 planes of H^3 (accumulated)
+  T* gbar;             // H^3 interleaved (x, y, z, -) nodes (accumulated)
   double* acc;         // [0] += sum tau V.Xbar (dJ/dchi), [1] += dJ/ds terms
   Geo<T> g;
   T s_noise, chitau, tau, w_inv_h;
@@ -113,6 +113,8 @@ struct AdjArgs {
   int p2g, g2p, split;
 };
 template <typename T> cudaError_t launch_adj_step(const AdjArgs<T>& a, cudaStream_t s);
+// gbar nodes -> three planes of H^3 (and the nodes cleared)
+template <typename T> cudaError_t launch_adj_planes(T* gbar4, T* planes, int64_t H3, cudaStream_t s);
 template <typename T>
 cudaError_t launch_adj_terminal(const T* x, const T* y, const T* z, int64_t P, const T* phibar, int p2g, T w_inv_h,
                                 Geo<T> g, T* xb, cudaStream_t s);
