@@ -498,7 +498,7 @@ struct MoveSmem {
 
 // One work item of the move + re-bin pass (see above).  n: step index of the
 // move (noise counter).  MOVE = false only re-bins (capacity rebuilds).
-template <typename T, bool MOVE>
+template <typename T, bool MOVE, int G2P = 0>
 __device__ __forceinline__ void move_chunk(const BinArgs<T>& a, const ChunkDesc& cur, uint32_t n, MoveSmem<T>& sm,
                                            uint32_t& phase) {
   constexpr int R = MoveRound<T>::n;
@@ -545,13 +545,13 @@ __device__ __forceinline__ void move_chunk(const BinArgs<T>& a, const ChunkDesc&
         if (a.split == 0) {
           // Z = X + W^- + chi tau I*(grad c)(X + W^-),  X^n = Z + W^+
           const T yx = x + a.s_noise * nz[0], yy = y + a.s_noise * nz[1], yz = z + a.s_noise * nz[2];
-          const V3<T> gr = gather_grad(a.grad4, a.g2p, yx, yy, yz, a.g);
+          const V3<T> gr = gather_grad(a.grad4, G2P ? G2P : a.g2p, yx, yy, yz, a.g);
           x = wrap_coord((yx + a.chitau * gr.x) + a.s_noise * nz[3], a.g);
           y = wrap_coord((yy + a.chitau * gr.y) + a.s_noise * nz[4], a.g);
           z = wrap_coord((yz + a.chitau * gr.z) + a.s_noise * nz[5], a.g);
         } else {
           // X^n = X + chi tau I*(grad c)(X) + W,  W ~ N(0, 2 mu tau I)
-          const V3<T> gr = gather_grad(a.grad4, a.g2p, x, y, z, a.g);
+          const V3<T> gr = gather_grad(a.grad4, G2P ? G2P : a.g2p, x, y, z, a.g);
           x = wrap_coord((x + a.chitau * gr.x) + a.s_noise * nz[0], a.g);
           y = wrap_coord((y + a.chitau * gr.y) + a.s_noise * nz[1], a.g);
           z = wrap_coord((z + a.chitau * gr.z) + a.s_noise * nz[2], a.g);
@@ -629,7 +629,7 @@ __device__ __forceinline__ void move_chunk(const BinArgs<T>& a, const ChunkDesc&
   }
 }
 
-template <typename T>
+template <typename T, int G2P>
 __global__ void __launch_bounds__(kMoveThreads, move_min_blocks<T>())
 k_move(BinArgs<T> a) {
   __shared__ MoveSmem<T> sm;
@@ -650,7 +650,7 @@ k_move(BinArgs<T> a) {
       const long long c = (long long)atomicAdd(a.work, 1ULL);
       if (c < nchunks) nxt = a.chunks[c];
     }
-    move_chunk<T, true>(a, cur, a.n, sm, phase);
+    move_chunk<T, true, G2P>(a, cur, a.n, sm, phase);
     if (threadIdx.x == 0) sm.desc[buf ^ 1] = nxt;
     __syncthreads();
   }
@@ -707,9 +707,10 @@ template <typename T> cudaError_t launch_move(const BinArgs<T>& a, cudaStream_t 
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_move<T>, kMoveThreads, 0)) != cudaSuccess) return e;
+  auto k = a.g2p == 4 ? k_move<T, 4> : k_move<T, 2>;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kMoveThreads, 0)) != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  k_move<T><<<sms * per_sm, kMoveThreads, 0, s>>>(a);
+  k<<<sms * per_sm, kMoveThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
