@@ -659,7 +659,7 @@ k_move(BinArgs<T> a) {
 
 // Batched move (MOVE) or re-bin (!MOVE): work items of all runs from one
 // counter; run r's arguments at table[r]; the step index from device memory.
-template <typename T, bool MOVE>
+template <typename T, bool MOVE, int G2P>
 __global__ void __launch_bounds__(kMoveThreads, move_min_blocks<T>())
 k_move_batch(const BinArgs<T>* __restrict__ table, const long long* __restrict__ prefix, int nruns,
              unsigned long long* work, const uint32_t* step) {
@@ -693,7 +693,7 @@ k_move_batch(const BinArgs<T>* __restrict__ table, const long long* __restrict__
         nxt = table[nrun].chunks[c - prefix[nrun]];
       }
     }
-    move_chunk<T, MOVE>(table[run], cur, n, sm, phase);
+    move_chunk<T, MOVE, G2P>(table[run], cur, n, sm, phase);
     if (threadIdx.x == 0) {
       sm.desc[buf ^ 1] = nxt;
       sm.run[buf ^ 1] = nrun;
@@ -1280,10 +1280,12 @@ cudaError_t launch_chunk_list(const ChunkListArgs& a, unsigned long long* work, 
 
 template <typename T>
 cudaError_t launch_move_batch(const BinArgs<T>* table, const long long* prefix, int nruns, unsigned long long* work,
-                              const uint32_t* step, bool move, cudaStream_t s, int blocks_per_sm) {
+                              const uint32_t* step, bool move, cudaStream_t s, int blocks_per_sm, int g2p) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e;
-  auto k = move ? k_move_batch<T, true> : k_move_batch<T, false>;
+  // the gather order fixed at compile time when every run uses the same one
+  auto k = !move ? k_move_batch<T, false, 0>
+                 : (g2p == 2 ? k_move_batch<T, true, 2> : g2p == 4 ? k_move_batch<T, true, 4> : k_move_batch<T, true, 0>);
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kMoveThreads, 0)) != cudaSuccess) return e;
@@ -1433,7 +1435,7 @@ template <typename T> cudaError_t launch_alpha_energy(const cpx<T>* alpha, int H
   template cudaError_t launch_binned<T>(const BinArgs<T>&, int, int, int, cudaStream_t);                       \
   template cudaError_t launch_move<T>(const BinArgs<T>&, cudaStream_t);                                       \
   template cudaError_t launch_move_batch<T>(const BinArgs<T>*, const long long*, int, unsigned long long*,     \
-                                            const uint32_t*, bool, cudaStream_t, int);                       \
+                                            const uint32_t*, bool, cudaStream_t, int, int);                  \
   template cudaError_t launch_deposit_batch<T>(const BinArgs<T>*, const long long*, int, unsigned long long*,  \
                                                bool, cudaStream_t, int);                                      \
   template cudaError_t launch_tile_hist<T>(const T*, const T*, const T*, int64_t, Geo<T>, int, int, int, int*, \

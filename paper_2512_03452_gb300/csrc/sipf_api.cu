@@ -1000,6 +1000,7 @@ struct sipf_batch {
   bool own_stream = false;
   int precision = 32;
   bool fixed = false;
+  int g2p = 0;   // the gather order shared by all runs (2 or 4), 0 if they differ
   std::vector<int> group_H, group_n;
   std::vector<void*> fft_tab;                    // device FftRun<T>[group_n]
   void* move_tab[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -1114,7 +1115,7 @@ template <typename T> int batch_issue_step(sipf_batch* b) {
   SIPF_CK(mark(2 * G));
   SIPF_CK(cudaMemsetAsync(b->work, 0, sizeof(unsigned long long), s));
   SIPF_CK(launch_move_batch<T>((const BinArgs<T>*)b->move_tab[b->cur][b->lc], b->prefix, R, b->work, b->step, true, s,
-                               b->move_bps));
+                               b->move_bps, b->g2p));
   SIPF_CK(launch_chunk_list_batch(b->cl_tab[1 - b->cur][b->lc], R, b->max_NT, s));
   SIPF_CK(launch_run_prefix(b->cl_tab[1 - b->cur][b->lc], R, b->prefix, b->work, b->step, 1, s));
   SIPF_CK(mark(2 * G + 1));
@@ -1327,6 +1328,9 @@ int sipf_batch_init(int32_t nruns, const sipf_params* params, const double* cons
   b->nruns = nruns;
   b->precision = params[0].precision;
   b->fixed = params[0].deposit_mode == SIPF_DEPOSIT_DETERMINISTIC;
+  b->g2p = params[0].g2p_order;
+  for (int r = 1; r < nruns; ++r)
+    if (params[r].g2p_order != b->g2p) b->g2p = 0;
   if (stream) {
     b->stream = (cudaStream_t)stream;
   } else {

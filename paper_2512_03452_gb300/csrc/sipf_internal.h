@@ -177,7 +177,8 @@ struct LayoutArgs {
 };
 template <typename T>
 cudaError_t launch_move_batch(const BinArgs<T>* table, const long long* prefix, int nruns, unsigned long long* work,
-                              const uint32_t* step, bool move, cudaStream_t s, int blocks_per_sm = 0);
+                              const uint32_t* step, bool move, cudaStream_t s, int blocks_per_sm = 0,
+                              int g2p = 0);   // g2p: 2 or 4 when all runs use that gather order, else 0
 template <typename T>
 cudaError_t launch_deposit_batch(const BinArgs<T>* table, const long long* prefix, int nruns,
                                  unsigned long long* work, bool fixed, cudaStream_t s, int blocks_per_sm = 0);
