@@ -37,20 +37,20 @@ P_FULL, H_FULL = 10_000_000, 128
 # algorithmic bytes of the particle kernel per particle-step (FP32): read X (12 B) + write X (12 B)
 BYTES_PER_PARTICLE = 24
 # DRAM traffic (read + write bytes) of the particle phase, move + re-bin
-# (314.4 MB) and deposit (135.2 MB) launches of one step, from ncu captures of
+# (310.5 MB) and deposit (134.9 MB) launches of one step, from ncu captures of
 # the torus workload, keyed by the SHA-256 of the kernel sources they were
 # taken on (a changed kernel reports null until it is captured again).
-MOVE_TRAFFIC = {"4959deacb513d80b17bd67223857caad29c7f2b18a710a52bd600adce0e6f305": 449.6e6}
+MOVE_TRAFFIC = {"3aa7ef42b508f4fb22dde175a6eae49270fe6815f9effe077ca4283e86987548": 445.4e6}
 FALLBACK_HBM_GBS = 6800.0
-# Warp-instructions of one move + re-bin launch (148.18 M) and one deposit
+# Warp-instructions of one move + re-bin launch (140.77 M) and one deposit
 # launch (108.79 M) at P = 1e7, H = 128, FP32, from the same ncu captures,
 # keyed like the traffic: the particle kernels against the SMs' issue rate.
-PARTICLE_WARP_INSTR = {"4959deacb513d80b17bd67223857caad29c7f2b18a710a52bd600adce0e6f305": 256.97e6}
+PARTICLE_WARP_INSTR = {"3aa7ef42b508f4fb22dde175a6eae49270fe6815f9effe077ca4283e86987548": 249.56e6}
 # FP64 form: FP64-pipe thread instructions (DFMA + DADD + DMUL) of one FP64 step
-# at P = 1e7, H = 128 (move 2.590e9, deposit 0.823e9, forward plane 0.112e9,
+# at P = 1e7, H = 128 (move 2.580e9, deposit 0.823e9, forward plane 0.112e9,
 # x pass 0.279e9, inverse plane 0.334e9), from an ncu capture of the bench's
 # FP64 leg, keyed by the SHA-256 of the kernel sources it was taken on.
-FP64_PIPE_INSTR = {"3558a2a16795e9998204b5824f419c4273c6a8cd171dec4730433dae951411d0": 4.137509184e9}
+FP64_PIPE_INSTR = {"2901fb5a59c85627da52387eabb49c523afdd22cac068213e6e944af6a4b37a8": 4.127587276e9}
 
 
 def _env_int(name, default):
