@@ -40,17 +40,17 @@ BYTES_PER_PARTICLE = 24
 # (310.5 MB) and deposit (134.9 MB) launches of one step, from ncu captures of
 # the torus workload, keyed by the SHA-256 of the kernel sources they were
 # taken on (a changed kernel reports null until it is captured again).
-MOVE_TRAFFIC = {"3aa7ef42b508f4fb22dde175a6eae49270fe6815f9effe077ca4283e86987548": 445.4e6}
+MOVE_TRAFFIC = {"b12b7dc35a599f9a5e2a97a647d5d945ce9cc4950abd422a23a36b356188ef64": 445.4e6}
 FALLBACK_HBM_GBS = 6800.0
 # Warp-instructions of one move + re-bin launch (140.77 M) and one deposit
 # launch (108.79 M) at P = 1e7, H = 128, FP32, from the same ncu captures,
 # keyed like the traffic: the particle kernels against the SMs' issue rate.
-PARTICLE_WARP_INSTR = {"3aa7ef42b508f4fb22dde175a6eae49270fe6815f9effe077ca4283e86987548": 249.56e6}
+PARTICLE_WARP_INSTR = {"b12b7dc35a599f9a5e2a97a647d5d945ce9cc4950abd422a23a36b356188ef64": 249.56e6}
 # FP64 form: FP64-pipe thread instructions (DFMA + DADD + DMUL) of one FP64 step
 # at P = 1e7, H = 128 (move 2.580e9, deposit 0.823e9, forward plane 0.112e9,
 # x pass 0.279e9, inverse plane 0.334e9), from an ncu capture of the bench's
 # FP64 leg, keyed by the SHA-256 of the kernel sources it was taken on.
-FP64_PIPE_INSTR = {"2901fb5a59c85627da52387eabb49c523afdd22cac068213e6e944af6a4b37a8": 4.127587276e9}
+FP64_PIPE_INSTR = {"2578d6fa0633f430b4f401a011db67e61830806bac45bb8bc6994df9e9b364d0": 4.127587276e9}
 
 
 def _env_int(name, default):

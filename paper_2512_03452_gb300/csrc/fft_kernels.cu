@@ -1,13 +1,17 @@
-// Pencil FFTs of the SIPF-PIC field solve (Sec. 3.2, Algorithm 4) on H^3 grids,
-// H a power of two in [8, 256], float or double.
+// FFTs of the SIPF-PIC field solve (Sec. 3.2, Algorithm 4) on H^3 grids, H a
+// power of two in [8, 256], float or double.
 //
-// Forward F_H:  rows r2c along the fastest axis (two real rows per complex
+// Forward F_H: rows r2c along the fastest axis (two real rows per complex
 // FFT), then c2c along the middle axis, then the x-axis pass fused with the
 // implicit spectral update and the filtered gradient; the inverse runs the
-// x-axis back inside that same kernel, then the middle axis, then c2r rows.
-// Every pass stages its pencils in shared memory and runs an in-place radix-2
-// decimation-in-time transform there; global traffic is one read and one
-// write of the array per pass, coalesced along the contiguous axis.
+// x axis back inside that same kernel, then the middle axis, then c2r rows.
+// For H >= 32 each pencil of H = 32 E points is transformed by one warp
+// (E values per lane: a radix-2 DFT in registers, then five shuffle stages);
+// for H <= 128 the two inner axes of an x-plane are done in one block with
+// the plane in shared memory (plane kernels kwp_*), for H = 256 by separate
+// pencil passes (kwb_*).  H < 32 uses block-wide shared-memory transforms
+// (k_*).  Every kernel's complex products spell out their roundings, so all
+// shapes and paths give the same bits.
 #include <cuda_runtime.h>
 #include <math.h>
 

@@ -1,15 +1,21 @@
 // Particle kernels of the SIPF-PIC step.
 //
-// Particles live in tile bins: the grid is cut into tiles of E^3 cells and the
+// Particles live in tile bins: the grid is cut into tiles of 8^3 cells and the
 // particle arrays (x, y, z, id) are grouped by the tile of their cell, each bin
-// with some spare capacity, plus an overflow bin.  The move of Algorithm 4
-// (noise keyed by the particle id, gather of grad c with I* (Algorithm 3),
-// drift, periodic wrap) is fused with the deposit I of the new position
-// (Algorithm 2) and with re-binning into the other buffer.  A block works on a
-// chunk of one bin and deposits into a shared-memory window that covers the
-// tile plus a margin; the window is then added to the global grid with
-// coalesced reductions.  Particles that left the window, or sit in the overflow
-// bin, deposit with global reductions.
+// with some spare capacity, plus an overflow bin; two such buffers alternate.
+//   k_move:   the move of Algorithm 4 (noise keyed by the particle id, gather
+//             of grad c with I* (Algorithm 3), drift, periodic wrap) for rounds
+//             of a bin's particles staged in shared memory by bulk copies,
+//             each particle then written into the bin of its new tile in the
+//             other buffer (one global reservation per round and tile);
+//   chunk lists: per bin, work items of up to 4096 particles;
+//   k_binned (deposit): the deposit I of the new positions (Algorithm 2), a
+//             block per work item, into a shared-memory integer window over
+//             the tile and the stencil halo (several copies, chosen per lane
+//             so that a warp's atomics fall into distinct banks), then added
+//             to the grid with coalesced reductions.  Particles outside the
+//             window (the overflow bin) deposit with global reductions.
+// Batched forms take the work items of many runs from one counter.
 #include <cuda_runtime.h>
 #include <math.h>
 
