@@ -105,6 +105,13 @@ int sipf_params_default(sipf_params* p);
  * first offending field in sipf_last_error(). */
 int sipf_validate(const sipf_params* p);
 
+/* The Gaussian filter scale a context built from *p uses (host only, no GPU):
+ * p->H0 when it is >= 0, else the automatic H0 = ceil(8 H^(8/13) L^(5/13)) of
+ * Sec. 5.1, evaluated exactly where the value is an integer (H = L = 8 gives
+ * 64).  *H0_out receives it.  SIPF_EINVAL for NULL pointers or parameters
+ * sipf_validate rejects. */
+int sipf_filter_scale(const sipf_params* p, double* H0_out);
+
 /* Create a context: validate *p, allocate the state on the current CUDA
  * device, copy X0 (host, P x 3 row-major float64, i.e. x0 y0 z0 x1 ...;
  * points outside the box are wrapped into it), set alpha^(0) = 0 and deposit

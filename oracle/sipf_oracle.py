@@ -233,8 +233,18 @@ def mode_numbers(H):
 
 
 def auto_H0(H, L):
-    """H0 = ceil(8 H^(8/13) L^(5/13)), the filter scale used in Sec. 5."""
-    return float(math.ceil(8.0 * H ** (8.0 / 13.0) * L ** (5.0 / 13.0)))
+    """H0 = ceil(8 H^(8/13) L^(5/13)), the filter scale used in Sec. 5.1.
+
+    Evaluated exactly: the smallest integer m >= 0 with m^13 >= 8^13 H^8 L^5,
+    L taken as the exact rational value of the float.  (A floating-point power
+    can land just above an exact integer -- 8 * 8^(8/13) * 8^(5/13) = 64
+    evaluates to 64.00000000000001 -- and its ceiling is then one too large.)"""
+    from fractions import Fraction
+    target = Fraction(8) ** 13 * Fraction(H) ** 8 * Fraction(L) ** 5
+    m = max(0, math.ceil(8.0 * H ** (8.0 / 13.0) * L ** (5.0 / 13.0)) - 2)
+    while Fraction(m) ** 13 < target:
+        m += 1
+    return float(m)
 
 
 def filter_phi(H, H0):

@@ -78,6 +78,7 @@ _D = ctypes.POINTER(ctypes.c_double)
 _SIGS = {
     "sipf_params_default": (ctypes.c_int, [ctypes.POINTER(sipf_params)]),
     "sipf_validate": (ctypes.c_int, [ctypes.POINTER(sipf_params)]),
+    "sipf_filter_scale": (ctypes.c_int, [ctypes.POINTER(sipf_params), _D]),
     "sipf_init": (ctypes.c_int, [ctypes.POINTER(sipf_params), _D, _P, ctypes.POINTER(_P)]),
     "sipf_step": (ctypes.c_int, [_P, ctypes.c_int64]),
     "sipf_run": (ctypes.c_int, [_P]),
@@ -173,6 +174,12 @@ def sipf_params_default() -> sipf_params:
 
 def sipf_validate(p: sipf_params) -> None:
     _check(load().sipf_validate(ctypes.byref(p)), "sipf_validate")
+
+
+def sipf_filter_scale(p: sipf_params) -> float:
+    out = ctypes.c_double()
+    _check(load().sipf_filter_scale(ctypes.byref(p), ctypes.byref(out)), "sipf_filter_scale")
+    return out.value
 
 
 def sipf_init(p: sipf_params, X0, stream: int | None = None) -> int:

@@ -36,8 +36,38 @@ int cuda_fail(cudaError_t e, const char* where) {
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// H0 = ceil(8 H^(8/13) L^(5/13)) (Sec. 5.1).  With H = 2^h and L = a 2^e (a
+// odd), x^13 = 2^(39 + 8h + 5e) a^5, so x is an integer exactly when a = c^13
+// for an odd integer c (c <= 15 for a 53-bit a) and 13 divides t = 39 + 8h + 5e
+// with t >= 0; then x = 2^(t/13) c^5.  That case is returned exactly (a
+// floating-point power can land just above the integer, e.g. 64.00000000000001
+// at H = L = 8, and its ceiling would be one too large); otherwise x is not an
+// integer and the ceiling of the floating-point value is taken.
+double auto_H0(int H, double L) {
+  const double x = 8.0 * pow((double)H, 8.0 / 13.0) * pow(L, 5.0 / 13.0);
+  int e = 0;
+  const double fr = frexp(L, &e);
+  uint64_t a = (uint64_t)ldexp(fr, 53);
+  int e2 = e - 53;
+  while (a && !(a & 1)) {
+    a >>= 1;
+    ++e2;
+  }
+  int h = 0;
+  while ((1 << h) < H) ++h;
+  const long t = 39L + 8L * h + 5L * e2;
+  if (t >= 0 && t % 13 == 0) {
+    for (uint64_t c = 1; c <= 15; c += 2) {
+      uint64_t c13 = 1;
+      for (int i = 0; i < 13; ++i) c13 *= c;
+      if (c13 == a) return ldexp((double)(c * c * c * c * c), (int)(t / 13));
+    }
+  }
+  return ceil(x);
+}
+
 double effective_H0(const sipf_params& p) {
-  if (p.H0 < 0) return ceil(8.0 * pow((double)p.H, 8.0 / 13.0) * pow(p.L, 5.0 / 13.0));
+  if (p.H0 < 0) return auto_H0(p.H, p.L);
   return p.H0;
 }
 
@@ -588,6 +618,14 @@ int sipf_params_default(sipf_params* p) {
 }
 
 int sipf_validate(const sipf_params* p) { return validate(p); }
+
+int sipf_filter_scale(const sipf_params* p, double* H0_out) {
+  if (!H0_out) return fail(SIPF_EINVAL, "H0_out is NULL");
+  const int r = validate(p);
+  if (r) return r;
+  *H0_out = effective_H0(*p);
+  return SIPF_OK;
+}
 
 int sipf_init(const sipf_params* p, const double* X0, void* stream, sipf_ctx** out) {
   if (!out) return fail(SIPF_EINVAL, "out is NULL");

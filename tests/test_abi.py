@@ -79,3 +79,18 @@ def test_init_rejects_nonfinite_positions_before_touching_a_device(lib):
     with pytest.raises(_abi.SipfError) as e:
         _abi.sipf_init(p, X)
     assert e.value.code == _abi.SIPF_ENONFINITE
+
+
+def test_filter_scale_matches_the_exact_rule(lib):
+    """The library's automatic H0 equals the oracle's exact ceil(8 H^(8/13)
+    L^(5/13)) (Sec. 5.1) over the supported H and a spread of box sides,
+    including H = L = 8 where the value is an exact integer (64)."""
+    from oracle import sipf_oracle as O
+    for H in (8, 16, 32, 64, 128, 256):
+        for L in (1.0, 2.0, 8.0, 0.7, 3.3, 10.0, 40.0, 2.0 ** -13, 2.0 ** 13):
+            assert _abi.sipf_filter_scale(make_params(P=10, H=H, L=L)) == O.auto_H0(H, L), (H, L)
+    assert _abi.sipf_filter_scale(make_params(P=10, H=8, L=8.0)) == 64.0
+    assert _abi.sipf_filter_scale(make_params(P=10, H=64, L=1.0, H0=12.5)) == 12.5
+    assert _abi.sipf_filter_scale(make_params(P=10, H=64, L=1.0, H0=0.0)) == 0.0
+    with pytest.raises(_abi.SipfError):
+        _abi.sipf_filter_scale(make_params(P=10, H=12))

@@ -454,3 +454,71 @@ def test_philox_matches_curand_host_generator():
         i = np.arange(got.shape[0], dtype=np.uint64)
         ref = np.stack(O.philox4x32_10(0, 0, i, 0, seed & 0xFFFFFFFF, seed >> 32), axis=1)
         assert np.array_equal(got, np.broadcast_to(ref, got.shape))
+
+
+# ----------------------------------------------------------------- filter scale and HF-energy share
+def test_auto_H0_exact_values():
+    """H0 = ceil(8 H^(8/13) L^(5/13)) (Sec. 5.1).  Exact powers fix each
+    exponent separately: H = 2^13, L = 1 gives 8 * 2^8 = 2048 (the H exponent),
+    H = 1, L = 2^13 gives 8 * 2^5 = 256 (the L exponent); swapping or mistyping
+    either fails.  H = L = 8 is the geometry of the Sec. 5.1 convergence study
+    and gives exactly 8 * 8^(8/13) * 8^(5/13) = 64 (not 65)."""
+    assert O.auto_H0(2 ** 13, 1.0) == 2048.0
+    assert O.auto_H0(1, 2.0 ** 13) == 256.0
+    assert O.auto_H0(8, 8.0) == 64.0
+    assert O.auto_H0(2 ** 16, 8.0) == 8.0 * 2 ** 11      # 8 * 2^((8*16 + 15)/13)
+
+
+@pytest.mark.parametrize("H,L", [(16, 1.0), (128, 1.0), (64, 2.0), (256, 8.0), (32, 0.7)])
+def test_auto_H0_is_the_smallest_integer_above_the_rule(H, L):
+    """Brute force on the definition: m = H0 satisfies m^13 >= 8^13 H^8 L^5 >
+    (m-1)^13 in exact rational arithmetic."""
+    from fractions import Fraction
+    m = int(O.auto_H0(H, L))
+    t = Fraction(8) ** 13 * Fraction(H) ** 8 * Fraction(L) ** 5
+    assert Fraction(m) ** 13 >= t > Fraction(m - 1) ** 13
+
+
+def _half(full):
+    """Half layout (qz index 0..H/2) of a full H^3 spectrum."""
+    H = full.shape[0]
+    return full[:, :, : H // 2 + 1].copy()
+
+
+def test_hf_energy_fraction_planted_modes():
+    """Sec. 5.2 indicator: share of sum_q |alpha_q|^2 over the FULL spectrum in
+    modes with ||q|| >= 4.  Planted Hermitian pairs with known energies:
+    (+-3,0,0) amplitude 1 on the kz = 0 plane (both members stored), (0,0,+-3)
+    amplitude 2 off it (only +3 stored), (+-4,0,0) amplitude 4 on the plane,
+    (0,0,+-4) amplitude 3 off it, and (0,0,-8) amplitude 1 on the Nyquist
+    plane (its own partner at H = 16).  Full energies: ||q|| = 3: 2 + 8 = 10;
+    ||q|| >= 4: 32 + 18 + 1 = 51; share 51/61.  Counting the kz = 0 plane
+    twice, the Nyquist plane twice, the off-plane modes once, or using
+    ||q|| > 4, each gives another value."""
+    H = 16
+    full = np.zeros((H, H, H), dtype=complex)
+
+    def plant(q, a):
+        full[q[0] % H, q[1] % H, q[2] % H] = a
+        full[-q[0] % H, -q[1] % H, -q[2] % H] = np.conj(a)
+
+    plant((3, 0, 0), 1.0)
+    plant((0, 0, 3), 2.0)
+    plant((4, 0, 0), 4.0j)
+    plant((0, 0, 4), 3.0)
+    plant((0, 0, -8), 1.0)
+    assert O.hf_energy_fraction(_half(full)) == pytest.approx(51.0 / 61.0, rel=1e-15)
+
+
+def test_hf_energy_fraction_matches_full_spectrum_of_a_real_field():
+    """Library special case: for a real field f, numpy's full complex FFT holds
+    every mode once; the share of |F_q|^2 with ||q|| >= 4 from it must equal the
+    oracle's share computed from the r2c half layout."""
+    H = 16
+    f = np.random.default_rng(5).normal(size=(H, H, H))
+    F = np.fft.fftn(f)
+    q = np.fft.fftfreq(H, 1.0 / H)
+    qn = np.sqrt(q[:, None, None] ** 2 + q[None, :, None] ** 2 + q[None, None, :] ** 2)
+    e = np.abs(F) ** 2
+    ref = e[qn >= 4].sum() / e.sum()
+    assert O.hf_energy_fraction(np.fft.rfftn(f)) == pytest.approx(ref, rel=1e-13)
