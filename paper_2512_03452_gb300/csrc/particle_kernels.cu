@@ -67,6 +67,19 @@ template <> struct WinType<double> {
 
 __device__ __forceinline__ int ceil_log2(int v) { return v <= 1 ? 0 : 32 - __clz(v - 1); }
 
+// Most particles of a work item of `len` that can add into one copy of an
+// int32 window, for blocks of `threads`.  Tile windows rank a warp's lanes
+// within the G bank groups of their base slot and take copy = rank mod C
+// (C copies, G = 32 / C groups), so one copy gets at most ceil(n_g / C) lanes
+// of group g: at most sum_g ceil(n_g / C) <= (32 + G (C - 1)) / C of a warp
+// (7 for C = 8, 14 for C = 4).  Whole-grid windows take copy = lane mod 4:
+// 8 lanes of a warp.  Every particle adds at most once to a node with
+// |round(F 2^K)| <= 2^K (|F| <= 1), so a copy's node sum stays within
+// load * 2^K; K = 30 - ceil(log2(load + 1)) keeps it below 2^30.
+__device__ __forceinline__ int win_copy_load(int per_warp, int len, int threads) {
+  return per_warp * (threads >> 5) * ((len + threads - 1) / threads);
+}
+
 // 2^k from the exponent bits (no FP64 or transcendental call), |k| < 126
 template <typename T> __device__ __forceinline__ T pow2(int k);
 template <> __device__ __forceinline__ float pow2<float>(int k) { return __int_as_float((127 + k) << 23); }
@@ -173,25 +186,26 @@ __device__ __forceinline__ void window_flush(const BinArgs<T>& a, typename WinTy
     // shared wavefronts per 512 bytes and a reduction from every lane.
     static_assert(kTileReps == 8, "two 16-byte halves per slot");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (int)(blockDim.x >> 5);
+    // (copies summed in 64 bits: a node's total over all copies may exceed 2^31)
     for (int s0 = warp * 32; s0 < wslots; s0 += nwarps * 32) {
       int4* base = reinterpret_cast<int4*>(win + (size_t)s0 * kTileReps);
       const int sa = s0 + (lane >> 1), sb = sa + 16;
-      A va = A(0), vb = A(0);
+      long long va = 0, vb = 0;
       if (sa < wslots) {
         const int4 q = base[lane];
-        va = (A)(q.x + q.y + q.z + q.w);
+        va = (long long)q.x + q.y + q.z + q.w;
         base[lane] = make_int4(0, 0, 0, 0);
       }
       if (sb < wslots) {
         const int4 q = base[32 + lane];
-        vb = (A)(q.x + q.y + q.z + q.w);
+        vb = (long long)q.x + q.y + q.z + q.w;
         base[32 + lane] = make_int4(0, 0, 0, 0);
       }
       va += __shfl_xor_sync(0xFFFFFFFFu, va, 1);
       vb += __shfl_xor_sync(0xFFFFFFFFu, vb, 1);
       const int sidx = (lane & 1) ? sb : sa;
-      const A v = (lane & 1) ? vb : va;
-      if (sidx < wslots && v != A(0)) {
+      const long long v = (lane & 1) ? vb : va;
+      if (sidx < wslots && v != 0) {
         const int c = sidx % kWin, b = (sidx / kWin) % kWin, aa = sidx / (kWin * kWin);
         const int gi = (((ox + aa) & mask) * H + ((oy + b) & mask)) * H + ((oz + c) & mask);
         if (FIXED) atomicAdd(static_cast<unsigned long long*>(a.phi) + gi, (unsigned long long)(long long)v);
@@ -200,7 +214,7 @@ __device__ __forceinline__ void window_flush(const BinArgs<T>& a, typename WinTy
     }
   } else {
     for (int sidx = threadIdx.x; sidx < wslots; sidx += blockDim.x) {
-      A v = A(0);
+      long long v = 0;
       if (WHOLE) {
 #pragma unroll
         for (int r = 0; r < kReplicas; ++r) {
@@ -214,7 +228,7 @@ __device__ __forceinline__ void window_flush(const BinArgs<T>& a, typename WinTy
           win[sidx * kTileReps + r] = A(0);
         }
       }
-      if (v != A(0)) {
+      if (v != 0) {
         int gi;
         if (WHOLE) {
           gi = sidx;
@@ -250,8 +264,11 @@ __device__ __forceinline__ void binned_chunk(const BinArgs<T>& a, const ChunkDes
     oy = ty * kTileE - kMargin - 1;
     oz = tz * kTileE - kMargin - 1;
   }
-  // window scale 2^K
-  const int K = FIXED ? a.fix_k : WinType<T>::bits - ceil_log2(len + 1);
+  // window scale 2^K: no copy's node sum can reach 2^30 (int32 windows; see
+  // win_copy_load) or 2^62 (int64 windows: the whole chunk's sum)
+  const int K = FIXED ? a.fix_k
+                      : (sizeof(A) == 4 ? 30 - ceil_log2(win_copy_load(WHOLE ? 8 : 7, len, blockDim.x) + 1)
+                                        : WinType<T>::bits - ceil_log2(len + 1));
   const T wwin = pow2<T>(K);
   const int iters = (len + blockDim.x - 1) / blockDim.x;
   // next particle's data is loaded one iteration ahead

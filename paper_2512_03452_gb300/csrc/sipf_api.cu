@@ -101,8 +101,12 @@ int validate(const sipf_params* p) {
 // float runs: K = 18 (an int32 shared window of 4096 particles cannot
 // overflow); double runs: K = 61 - ceil(log2 P), capped at 40, so that even a
 // node that gathered every particle stays inside int64.
+// Fixed-point unit 2^-K of a stencil weight in the deterministic mode.  FP32:
+// int32 shared windows whose copies receive at most 1024 particles of a
+// 4096-particle work item (tile windows 896, whole-grid windows 1024), so
+// 1024 * 2^19 < 2^30.  FP64: int64 throughout, the total of P particles.
 int fixed_k(const sipf_params& p) {
-  if (p.precision == 32) return 18;
+  if (p.precision == 32) return 19;
   int lg = 0;
   while ((1LL << lg) < p.P + 1) ++lg;
   int k = 61 - lg;

@@ -37,6 +37,7 @@ class Workload:
     sigma: float = 0.1             # blob std or torus minor-radius std, in units of L
     major: float = 0.25            # torus major radius, in units of L
     background: float = 0.0        # fraction of particles uniform on the box
+    radius: float = 0.125          # ball radius, in units of L (shape "ball")
     H0: float = -1.0               # Gaussian filter resolution; <0 auto, 0 off
 
 
@@ -64,6 +65,11 @@ def sample_positions(w: Workload, seed: int | None = None) -> np.ndarray:
         B = rng.uniform(-0.5 * L, 0.5 * L, size=(n_bg, 3))
         X = np.concatenate([T, B], axis=0)
         X = X[rng.permutation(w.P)]
+    elif w.shape == "ball":
+        # uniform in the ball |x| <= radius L: radius r U^(1/3), uniform direction
+        v = rng.normal(size=(w.P, 3))
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        X = (w.radius * L) * np.cbrt(rng.uniform(size=(w.P, 1))) * v
     elif w.shape == "uniform":
         X = rng.uniform(-0.5 * L, 0.5 * L, size=(w.P, 3))
     else:
@@ -92,6 +98,14 @@ def torus_ring(H: int = 128, P: int = 10_000_000) -> Workload:
                     P=P, H=H, L=1.0, mass=300.0, chi=1.0, mu=0.5, eps=1.0, k=1.0,
                     dt=5e-5, steps=500, seed=0, shape="torus", sigma=0.03,
                     major=0.25, background=0.05)
+
+
+def uniform_ball(P: int = 2 ** 14, H: int = 32, seed: int = 0) -> Workload:
+    """The initial data of the Sec. 5.1 convergence study: uniform density
+    60/pi on the unit ball (M0 = 80), L = 8, mu = chi = 1, eps = 1e-4,
+    k = 0.1, tau = 1e-5, T = 0.02 (2000 steps)."""
+    return Workload(f"uniform_ball_P{P}_H{H}", P=P, H=H, L=8.0, mass=80.0, chi=1.0, mu=1.0,
+                    eps=1e-4, k=0.1, dt=1e-5, steps=2000, seed=seed, shape="ball", radius=1.0 / 8.0)
 
 
 def ensemble(n_runs: int = 256, seed: int = 0) -> list[Workload]:

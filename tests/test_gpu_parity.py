@@ -261,6 +261,104 @@ def test_chi0_free_diffusion_on_gpu():
     assert np.max(np.abs(O.min_image(X - X0 - disp, w.L))) < 1e-12
 
 
+# ----------------------------------------------------------------- larger grids
+@pytest.mark.parametrize("H,prec", [(256, 64), (256, 32), (128, 64)])
+def test_step_large_grid_matches_oracle(H, prec):
+    """Torus data, P = 2e4, 5 whole steps at H = 128 (plane FFT kernels, as the
+    benchmark runs them) and H = 256 (the pencil passes of the field solve):
+    FP64 within 1e-10; FP32 positions within 1e-4 and the fields' relative L2
+    within 1e-4 of the FP64 oracle."""
+    w = workloads.torus_ring(H=H, P=20_000)
+    X0 = workloads.sample_positions(w)
+    n = 5
+    s, p = _oracle_run(w, X0, n)
+    X, alpha, diag, dens = _gpu_run(w, X0, n, precision=prec)
+    phi = O.deposit(s.X, p.mass / p.P, p.H, p.L, p.p2g_order)
+    d = dens * (p.L / p.H) ** 3
+    dx = np.max(np.abs(O.min_image(X - s.X, w.L)))
+    if prec == 64:
+        assert dx < 1e-10
+        assert _rel(alpha, s.alpha) < 1e-10
+        assert _rel(d, phi) < 1e-10
+    else:
+        assert dx < 1e-4
+        assert np.linalg.norm(alpha - s.alpha) / np.linalg.norm(s.alpha) < 1e-4
+        assert np.linalg.norm(d - phi) / np.linalg.norm(phi) < 1e-4
+    assert abs(diag["mass"] - w.mass) < (1e-12 if prec == 64 else 1e-5) * w.mass
+
+
+@pytest.mark.parametrize("H", [8, 16])
+def test_step_fp64_sec51_ball_geometry(H):
+    """The Sec. 5.1 set-up (uniform unit ball, M0 = 80, L = 8, eps = 1e-4,
+    k = 0.1, tau = 1e-5, automatic filter scale) at H = 8, where
+    H0 = 8 * 8^(8/13) * 8^(5/13) = 64 exactly, and H = 16: 10 FP64 steps
+    within 1e-10 of the oracle."""
+    w = workloads.uniform_ball(P=4000, H=H)
+    X0 = workloads.sample_positions(w)
+    s, p = _oracle_run(w, X0, 10)
+    assert p.H0_eff == (64.0 if H == 8 else O.auto_H0(H, w.L))
+    assert _abi.sipf_filter_scale(params_from_workload(w, precision=64)) == p.H0_eff
+    X, alpha, _, _ = _gpu_run(w, X0, 10, precision=64)
+    assert np.max(np.abs(O.min_image(X - s.X, w.L))) < 1e-10
+    assert _rel(alpha, s.alpha) < 1e-10
+
+
+# ----------------------------------------------------------------- full-size deposit
+K_MIN = 19           # smallest fixed-point exponent of any FP32 window (chunks of <= 4096 particles)
+FP32_ROUNDINGS = 12  # roundings in one FP32 stencil weight, incl. the particle weight M0/P
+
+
+def _stencil_counts(X, H, L, chunk=1 << 20):
+    """Per node j: n_j, the number of Gamma_4 contributions, and S_j, the sum of
+    their |F| (the oracle's stencil)."""
+    n = np.zeros(H ** 3)
+    S = np.zeros(H ** 3)
+    for a in range(0, X.shape[0], chunk):
+        cell, lam = O.cell_and_lambda(X[a:a + chunk], H, L)
+        offs, F = O.stencil(lam, 4)
+        idx = O.stencil_indices(cell, offs, H).ravel()
+        n += np.bincount(idx, minlength=H ** 3)
+        S += np.bincount(idx, weights=np.abs(F).ravel(), minlength=H ** 3)
+    return n.reshape(H, H, H), S.reshape(H, H, H)
+
+
+def _check_deposit(got, X, p):
+    """Element by element against the oracle's deposit of the same positions.
+    Bound per node j (w = M0/P, u = 2^-24):
+      w n_j 2^-(K+1)            fixed-point rounding of each weight in the window,
+    + w S_j (c + n_j) u         FP32 weights (c roundings each) and at most n_j
+                                 floating-point additions into phi_j (Higham's
+                                 bound for recursive summation);
+    the relative L2 error must also stay 10x below the FP32 field bar."""
+    w = p.mass / p.P
+    ref = O.deposit(X, w, p.H, p.L, 4)
+    n, S = _stencil_counts(X, p.H, p.L)
+    u = 2.0 ** -24
+    bound = w * n * 2.0 ** -(K_MIN + 1) + w * S * (FP32_ROUNDINGS + n) * u + 1e-300
+    err = np.abs(got - ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-5
+
+
+def test_full_size_deposit_grid_matches_oracle():
+    """P = 1e7, H = 128, FP32 torus workload in the benchmark's launch: the
+    deposited mass grid I rho-hat of X^0 (initial deposit) and of X^1 (the
+    deposit done by the step) against the oracle's Algorithm 2 of the same
+    positions, node by node."""
+    w = workloads.torus_ring()
+    X0 = workloads.sample_positions(w)
+    p = O.Params.from_workload(w)
+    h3 = (p.L / p.H) ** 3
+    with Simulation(params_from_workload(w, precision=32), X0) as sim:
+        X0f = sim.positions()                     # the FP32 positions the GPU holds
+        g0 = sim.density(False) * h3
+        sim.step(1)
+        X1 = sim.positions()
+        g1 = sim.density(False) * h3
+    _check_deposit(g0, X0f, p)
+    _check_deposit(g1, X1, p)
+
+
 # ----------------------------------------------------------------- full size, sampled
 def test_torus_full_size_sampled_outputs():
     """P = 1e7, H = 128, FP32 (the benchmark workload and launch): the first
