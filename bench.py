@@ -148,6 +148,151 @@ def oracle_rate(X_sample, w, steps):
     return X_sample.shape[0] * steps / dt, dt
 
 
+# ----------------------------------------------------------------- oracle on all host cores
+# The oracle's particle loops (Algorithm 2's deposit and the particle move)
+# split over a process pool by particle slices, the grid work (F_H, the
+# gradient grids of alpha^(n-1), the update of alpha) on the calling process,
+# in the order of the oracle's own step.  Workers are started with `spawn` and
+# share X, the gradient grids and their partial deposits through shared memory.
+_PW = {}
+
+
+def _pw_init(names, P, H, nparts, pdict):
+    from multiprocessing import shared_memory
+
+    import numpy as np
+
+    from oracle import sipf_oracle as O
+    shm = [shared_memory.SharedMemory(name=n) for n in names]
+    _PW.update(shm=shm, O=O, p=O.Params(**pdict),
+               X=np.ndarray((P, 3), dtype=np.float64, buffer=shm[0].buf),
+               grads=np.ndarray((3, H, H, H), dtype=np.float64, buffer=shm[1].buf),
+               parts=np.ndarray((nparts, H ** 3), dtype=np.float64, buffer=shm[2].buf))
+
+
+def _pw_deposit(task):
+    k, a, b = task
+    O, p = _PW["O"], _PW["p"]
+    _PW["parts"][k] = O.deposit(_PW["X"][a:b], p.mass / p.P, p.H, p.L, p.p2g_order).ravel()
+
+
+def _pw_move(task):
+    a, b, n = task
+    O, p = _PW["O"], _PW["p"]
+    _PW["X"][a:b] = O.move(_PW["X"][a:b], _PW["grads"], p, n, first=a)
+
+
+class ParallelOracle:
+    """Steps of the FP64 oracle with its particle loops on `workers` processes."""
+
+    def __init__(self, X0, p, workers):
+        import dataclasses
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+
+        import numpy as np
+
+        from oracle import sipf_oracle as O
+        self.O, self.p = O, p
+        P, H = X0.shape[0], p.H
+        self.workers = max(1, int(workers))
+        self.nparts = min(self.workers * 2, max(1, P // 1000))
+        sizes = [P * 3 * 8, 3 * H ** 3 * 8, self.nparts * H ** 3 * 8]
+        self.shm = [shared_memory.SharedMemory(create=True, size=sz) for sz in sizes]
+        self.X = np.ndarray((P, 3), dtype=np.float64, buffer=self.shm[0].buf)
+        self.grads = np.ndarray((3, H, H, H), dtype=np.float64, buffer=self.shm[1].buf)
+        self.parts = np.ndarray((self.nparts, H ** 3), dtype=np.float64, buffer=self.shm[2].buf)
+        self.X[:] = X0
+        self.alpha = np.zeros((H, H, H // 2 + 1), dtype=np.complex128)
+        self.n = 0
+        edges = np.linspace(0, P, self.nparts + 1).astype(np.int64)
+        self.slices = [(int(a), int(b)) for a, b in zip(edges[:-1], edges[1:])]
+        self.pool = mp.get_context("spawn").Pool(
+            self.workers, initializer=_pw_init,
+            initargs=([m.name for m in self.shm], P, H, self.nparts, dataclasses.asdict(p)))
+        self.t_particles = self.t_grid = 0.0
+
+    def step(self):
+        O, p = self.O, self.p
+        n = self.n + 1
+        t0 = time.perf_counter()
+        self.pool.map(_pw_deposit, [(k, a, b) for k, (a, b) in enumerate(self.slices)])
+        t1 = time.perf_counter()
+        phi = self.parts.sum(axis=0).reshape(p.H, p.H, p.H)
+        beta = O.forward_ft(phi, p.L)
+        self.grads[:] = O.gradient_grids(self.alpha, p)           # grad c^(n-1) from alpha^(n-1)
+        if p.propagator == "exp":
+            self.alpha = O.update_alpha_exp(self.alpha, beta, p)
+        else:
+            self.alpha = O.update_alpha(self.alpha, beta, p)
+        t2 = time.perf_counter()
+        self.pool.map(_pw_move, [(a, b, n) for a, b in self.slices])
+        t3 = time.perf_counter()
+        self.t_particles += (t1 - t0) + (t3 - t2)
+        self.t_grid += t2 - t1
+        self.n = n
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        del self.X, self.grads, self.parts
+        for m in self.shm:
+            m.close()
+            m.unlink()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def oracle_rate_parallel(X_sample, w, steps, workers=None, warmup=1):
+    """All-core oracle particle-steps/s on a sample of the workload; also the
+    share of the step spent in the grid work (F_H, gradient grids, update)."""
+    from oracle import sipf_oracle as O
+    workers = workers or os.cpu_count() or 1
+    p = O.Params.from_workload(w, P=X_sample.shape[0])
+    with ParallelOracle(X_sample, p, workers) as po:
+        for _ in range(warmup):
+            po.step()
+        po.t_particles = po.t_grid = 0.0
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            po.step()
+        dt = time.perf_counter() - t0
+        grid_share = po.t_grid / max(po.t_particles + po.t_grid, 1e-30)
+    return X_sample.shape[0] * steps / dt, dt, grid_share, workers
+
+
+def cpu_baselines(X0, w):
+    """The oracle on this host: the benchmark workload on all cores (particle
+    loops over a process pool) and a sample on one core, plus the other
+    workloads (the oracle-sized blob in full, the blow-up blob for 20 steps)."""
+    import numpy as np
+
+    from paper_2512_03452_gb300 import workloads
+    cores = os.cpu_count() or 1
+    rate, dt, share, _ = oracle_rate_parallel(np.asarray(X0, dtype=np.float64), w, 3, workers=cores)
+    ns = 200_000
+    r1, dt1 = oracle_rate(np.asarray(X0[:ns], dtype=np.float64), w, 2)
+    wb = workloads.small_blob()
+    rc1, dtc1 = oracle_rate(workloads.sample_positions(wb), wb, wb.steps)
+    wc2 = workloads.blowup_blob()
+    rc2, dtc2, sh2, _ = oracle_rate_parallel(workloads.sample_positions(wc2), wc2, 20, workers=cores)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the full benchmark workload ({w.P} particles, H={w.H}), 3 steps after 1 warm-up step "
+                      f"({dt:.1f} s, numpy FP64, particle loops over {cores} processes)",
+            "grid_share": share,
+            "single_core": {"value": r1, "unit": UNIT, "cores": 1,
+                            "sample": f"first {ns} particles of the same sample, H={w.H}, 2 steps ({dt1:.1f} s)"},
+            "configs": {
+                wb.name: {"value": rc1, "unit": UNIT, "cores": 1, "s_per_step": dtc1 / wb.steps,
+                          "sample": f"all {wb.P} particles, all {wb.steps} steps"},
+                wc2.name: {"value": rc2, "unit": UNIT, "cores": cores, "s_per_step": dtc2 / 20, "grid_share": sh2,
+                           "sample": f"all {wc2.P} particles, 20 steps after 1 warm-up step"}}}
+
+
 # ----------------------------------------------------------------- distributed
 def dist_init(args):
     world = _env_int("WORLD_SIZE", 1)
@@ -227,10 +372,19 @@ def run_ours(args, world, rank, local):
     dep_ms = tim.deposit_ms / max(tim.steps, 1)
     part_ms = move_ms + dep_ms
     achieved = BYTES_PER_PARTICLE * P_FULL / (part_ms * 1e-3) / 1e9
-    traffic = MOVE_TRAFFIC.get(kernel_source_hash())
+    src_hash = kernel_source_hash()
+    traffic = MOVE_TRAFFIC.get(src_hash)
+    # figures captured on other kernel sources are reported, marked stale,
+    # but never used as this build's traffic
+    stale = None
+    if traffic is None or PARTICLE_WARP_INSTR.get(src_hash) is None:
+        stale = {"traffic": list(MOVE_TRAFFIC.values())[-1] if MOVE_TRAFFIC else None,
+                 "warp_instructions": list(PARTICLE_WARP_INSTR.values())[-1] if PARTICLE_WARP_INSTR else None,
+                 "note": "ncu counters of an earlier build of the particle kernels (sources changed since); "
+                         "not this build's figures"}
     # the same kernels against the SMs' instruction issue rate (4 warp-
     # instructions per clock per SM), the bound they actually meet
-    n_issue = PARTICLE_WARP_INSTR.get(kernel_source_hash())
+    n_issue = PARTICLE_WARP_INSTR.get(src_hash)
     issue = None
     if n_issue is not None:
         mhz, mhz_kind = sm_max_mhz()
@@ -298,10 +452,7 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ns = 200_000
-        rate, dt = oracle_rate(X0[:ns].astype(np.float64), w, 2)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {ns} particles of the same torus sample, H=128, 2 steps ({dt:.1f} s, numpy FP64)"}
+        cpu = cpu_baselines(X0, w)
 
     if rank == 0:
         line = {
@@ -316,7 +467,7 @@ def run_ours(args, world, rank, local):
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "peak_source": peak_kind, "bytes_per_particle": BYTES_PER_PARTICLE,
                          "kernel_ms": part_ms, "overflow_per_step": tim.overflow / max(tim.steps, 1),
-                         "issue": issue},
+                         "issue": issue, "stale_counters": stale},
             "stages_ms_per_step": stages,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -483,31 +634,30 @@ def run_reference(args, world, rank):
     """The FP64 oracle on the host cores, each step a bounded sample of the workload."""
     if rank != 0:
         return
-    import numpy as np
-
     from oracle import sipf_oracle as O
     from paper_2512_03452_gb300 import workloads
 
     w = workloads.torus_ring(H=H_FULL, P=P_FULL)
-    ns = 10_000
-    wsub = workloads.torus_ring(H=H_FULL, P=ns)
-    X = workloads.sample_positions(wsub)
+    ns = 1_000_000
+    X = workloads.sample_positions(w)[:ns]
     p = O.Params.from_workload(w, P=ns)
-    s = O.init_state(X, p)
-    for _ in range(args.warmup):
-        s = O.step(s, p)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        s = O.step(s, p)
-    dt = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    with ParallelOracle(X, p, cores) as po:
+        for _ in range(args.warmup):
+            po.step()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            po.step()
+        dt = time.perf_counter() - t0
     value = ns * args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "P": P_FULL, "H": H_FULL, "precision": "fp64 oracle",
                        "parallelism": "host"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{ns} particles of the torus workload per step, H=128 (numpy FP64)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"the first {ns} particles of the torus workload per step, H=128 "
+                                       f"(numpy FP64, particle loops over {cores} processes)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -365,14 +365,15 @@ def init_state(X0, p):
                  np.zeros((p.H, p.H, p.H // 2 + 1), dtype=np.complex128), 0)
 
 
-def move(X, grads, p, n):
+def move(X, grads, p, n, first=0):
     """Particle update of step n with the gradient grids of grad c^(n-1).
 
     half:  Z = X + W^- + chi tau I*(grad c)(X + W^-),  X^n = Z + W^+,
            W^-, W^+ ~ N(0, mu tau I)  (Algorithm 4)
     plain: X^n = X + chi tau I*(grad c)(X) + W, W ~ N(0, 2 mu tau I)  (Eq. (rho_hat_update))
+    The rows of X are particles first, first+1, ... (their noise indices).
     """
-    z = normals(p.seed, n, X.shape[0])
+    z = normals(p.seed, n, X.shape[0], first=first)
     if p.splitting == "half":
         s = math.sqrt(p.mu * p.dt)
         Y = X + s * z[:, 0:3]
