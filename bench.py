@@ -449,6 +449,7 @@ def run_ours(args, world, rank, local):
     extra = None if args.no_extra else run_extra_legs(world, dev, stream, X0)
     batch = None if args.no_batch else run_batch_leg(world, dev, stream)
     adjoint = None if args.no_adjoint else run_adjoint_leg(world, dev, stream)
+    convergence = None if args.no_convergence else run_convergence_leg(full=args.study)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -478,6 +479,7 @@ def run_ours(args, world, rank, local):
             "diagnostics": {k: diag[k] for k in ("mass", "peak", "m2", "ring_radius", "step")},
             "batch": batch,
             "adjoint": adjoint,
+            "convergence": convergence,
             "sweep": extra,
         }
         print(json.dumps(line), flush=True)
@@ -629,6 +631,50 @@ def run_adjoint_leg(world, dev, stream, nsteps=200, checkpoint=20, reps=2):
             "gpu_launches_total": launches}
 
 
+def run_convergence_leg(full=False):
+    """The Sec. 5.1 convergence study on this GPU: the uniform-ball set-up
+    (FP32, 2000 steps to T = 0.02) against the stored radial finite-volume
+    reference (tests/golden/sec51_reference_quantiles.json, written from the
+    oracle); E = the truncated quantile W1 averaged over seeds; slopes of
+    log2 E against log2 P (H fixed) and log2 H (P fixed), beside the paper's.
+    Default: 8 seeds, P = 2^11..2^19 at H = 128 and H = 16..128 at P = 2^19;
+    full: the paper's sweep, 30 seeds, P = 2^11..2^20 at H = 256 and
+    H = 8..256 at P = 2^20."""
+    import numpy as np
+
+    from paper_2512_03452_gb300 import convergence as C
+
+    with open(os.path.join(ROOT, "tests", "golden", "sec51_reference_quantiles.json")) as f:
+        gold = json.load(f)
+    with open(os.path.join(ROOT, "tests", "golden", "paper_constants.json")) as f:
+        paper = json.load(f)["convergence_slopes"]
+    levels, q_ref = np.array(gold["levels"]), np.array(gold["quantiles"])
+    if full:
+        seeds, Hfix, Pfix = range(30), 256, 2 ** 20
+        Ps, Hs = [2 ** e for e in range(11, 21)], [8, 16, 32, 64, 128, 256]
+    else:
+        seeds, Hfix, Pfix = range(8), 128, 2 ** 19
+        Ps, Hs = [2 ** e for e in range(11, 20, 2)], [16, 32, 64, 128]
+    cells, t0, psteps = {}, time.perf_counter(), 0
+
+    def cell(P, H):
+        nonlocal psteps
+        if (P, H) not in cells:
+            errs = [float(np.mean(np.abs(C.radial_quantiles(r, levels) - q_ref))) for r in C.final_radii(P, H, seeds)]
+            cells[(P, H)] = {"P": P, "H": H, "E_mean": float(np.mean(errs)), "E_std": float(np.std(errs)),
+                             "runs_below_2x_mean": float(np.mean(np.array(errs) < 2 * np.mean(errs)))}
+            psteps += P * 2000 * len(seeds)
+        return cells[(P, H)]["E_mean"]
+
+    EP = [cell(P, Hfix) for P in Ps]
+    EH = [cell(Pfix, H) for H in Hs]
+    dt = time.perf_counter() - t0
+    return {"workload": "Sec. 5.1 uniform ball (M0 = 80, L = 8, eps = 1e-4, k = 0.1, tau = 1e-5, 2000 steps), FP32",
+            "seeds": len(seeds), "slope_P": C.fitted_slope(Ps, EP), "slope_P_at_H": Hfix,
+            "slope_H": C.fitted_slope(Hs, EH), "slope_H_at_P": Pfix, "paper_slopes": {"P": paper["P"], "H": paper["H"]},
+            "cells": list(cells.values()), "seconds": dt, "particle_steps_per_s": psteps / dt}
+
+
 # ----------------------------------------------------------------- reference arm
 def run_reference(args, world, rank):
     """The FP64 oracle on the host cores, each step a bounded sample of the workload."""
@@ -711,6 +757,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
+    ap.add_argument("--no-convergence", action="store_true", help="skip the Sec. 5.1 convergence-study leg")
+    ap.add_argument("--study", action="store_true",
+                    help="run the convergence leg over the paper's full sweep (30 seeds, P up to 2^20, H up to 256)")
     ap.add_argument("--no-extra", action="store_true", help="skip the H sweep, deterministic, cuFFT and FP64 legs")
     ap.add_argument("--batch-case", action="store_true",
                     help="only run a small 128-run H = 64 batch (for kernel captures) and print its ms per step")

@@ -1025,18 +1025,20 @@ k_rebin_plain(const T* __restrict__ x, const T* __restrict__ y, const T* __restr
               const uint32_t* __restrict__ id, int64_t P, Geo<T> g, int shift, int ntx, int NT,
               T* __restrict__ dx, T* __restrict__ dy, T* __restrict__ dz, uint32_t* __restrict__ did,
               const long long* __restrict__ dst_base, const int* __restrict__ dst_cap, int* __restrict__ dst_cursor,
-              int* err) {
+              int* err, int64_t id0, int wrap) {
   extern __shared__ int s_cnt[];
   for (int t = threadIdx.x; t < NT; t += blockDim.x) s_cnt[t] = 0;
   __syncthreads();
   const int64_t per = (P + gridDim.x - 1) / gridDim.x;
   const int64_t b0 = (int64_t)blockIdx.x * per, b1 = min(P, b0 + per);
+  // positions, wrapped into the box if asked (the periodic wrap of uploaded data)
+  auto pos = [&](const T* a, int64_t p) { return wrap ? wrap_coord(a[p], g) : a[p]; };
   auto tile = [&](int64_t p) {
     int cx, cy, cz;
     T l;
-    cell_lambda(x[p], g, cx, l);
-    cell_lambda(y[p], g, cy, l);
-    cell_lambda(z[p], g, cz, l);
+    cell_lambda(pos(x, p), g, cx, l);
+    cell_lambda(pos(y, p), g, cy, l);
+    cell_lambda(pos(z, p), g, cz, l);
     return tile_of(cx & g.mask, cy & g.mask, cz & g.mask, shift, ntx);
   };
   for (int64_t p = b0 + threadIdx.x; p < b1; p += blockDim.x) atomicAdd(s_cnt + tile(p), 1);
@@ -1055,10 +1057,10 @@ k_rebin_plain(const T* __restrict__ x, const T* __restrict__ y, const T* __restr
       slot = o < dst_cap[NT] ? dst_base[NT] + o : -1;
     }
     if (slot >= 0) {
-      dx[slot] = x[p];
-      dy[slot] = y[p];
-      dz[slot] = z[p];
-      did[slot] = id[p];
+      dx[slot] = pos(x, p);
+      dy[slot] = pos(y, p);
+      dz[slot] = pos(z, p);
+      did[slot] = id ? id[p] : (uint32_t)(id0 + p);
     } else {
       atomicOr(err, 2);
     }
@@ -1379,12 +1381,28 @@ cudaError_t launch_tile_hist(const T* x, const T* y, const T* z, int64_t P, Geo<
 template <typename T>
 bool launch_rebin_plain(const T* x, const T* y, const T* z, const uint32_t* id, int64_t P, Geo<T> g, int shift,
                         int ntx, int NT, T* dx, T* dy, T* dz, uint32_t* did, const long long* dst_base,
-                        const int* dst_cap, int* dst_cursor, int* err, cudaStream_t s, cudaError_t* e) {
+                        const int* dst_cap, int* dst_cursor, int* err, cudaStream_t s, cudaError_t* e, int64_t id0,
+                        bool wrap) {
   if (NT > kMaxSmemTiles) return false;
   k_rebin_plain<T><<<plain_blocks(P), 256, NT * sizeof(int), s>>>(x, y, z, id, P, g, shift, ntx, NT, dx, dy, dz, did,
-                                                                 dst_base, dst_cap, dst_cursor, err);
+                                                                 dst_base, dst_cap, dst_cursor, err, id0,
+                                                                 wrap ? 1 : 0);
   *e = cudaGetLastError();
   return true;
+}
+
+int rebin_plain_max_tiles() { return kMaxSmemTiles; }
+
+template <typename T>
+cudaError_t launch_unbin_aos(const BinArgs<T>& a, int64_t max_chunks, T* aos, cudaStream_t s) {
+  k_unbin_aos<T><<<(unsigned)max_chunks, 256, 0, s>>>(a, aos);
+  return cudaGetLastError();
+}
+
+template <typename T> cudaError_t launch_aos4_to_soa(const T* aos, int64_t P, T* x, T* y, T* z, cudaStream_t s) {
+  const int64_t b = (P + 255) / 256;
+  k_aos4_to_soa<T><<<(unsigned)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b)), 256, 0, s>>>(aos, P, x, y, z);
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -1465,7 +1483,9 @@ template <typename T> cudaError_t launch_alpha_energy(const cpx<T>* alpha, int H
                                            cudaStream_t);                                                    \
   template bool launch_rebin_plain<T>(const T*, const T*, const T*, const uint32_t*, int64_t, Geo<T>, int, int, \
                                       int, T*, T*, T*, uint32_t*, const long long*, const int*, int*, int*,    \
-                                      cudaStream_t, cudaError_t*);                                            \
+                                      cudaStream_t, cudaError_t*, int64_t, bool);                             \
+  template cudaError_t launch_unbin_aos<T>(const BinArgs<T>&, int64_t, T*, cudaStream_t);                     \
+  template cudaError_t launch_aos4_to_soa<T>(const T*, int64_t, T*, T*, T*, cudaStream_t);                    \
   template cudaError_t launch_unbin<T>(const BinArgs<T>&, int64_t, T*, T*, T*, T*, int64_t, cudaStream_t);    \
   template cudaError_t launch_deposit<T>(const T*, const T*, const T*, int64_t, Geo<T>, T, T*, int,           \
                                          cudaStream_t);                                                      \

@@ -159,6 +159,16 @@ struct sipf_ctx {
   std::vector<cudaEvent_t> ev;
   int64_t timed_steps = 0, timed_kernels = 0;
   int64_t launches = 0;
+  // host-buffer transfers (sipf_upload_soa / sipf_download_soa) run in pieces
+  // on two side streams so copies overlap the re-binning, the un-binning and
+  // the step's last deposit; every transfer ends with the context stream
+  // waiting for them
+  cudaStream_t side[2] = {nullptr, nullptr};   // [0] kernels, [1] copies
+  static constexpr int kPieces = 8;
+  cudaEvent_t ev_piece[kPieces] = {};
+  cudaEvent_t ev_pos = nullptr;     // recorded once the current bins are final (before the deposit)
+  cudaEvent_t ev_begin = nullptr, ev_done = nullptr;
+  bool pos_ready = false;           // ev_pos describes the current bins
   int64_t H3() const { return (int64_t)p.H * p.H * p.H; }
   int64_t S() const { return (int64_t)p.H * p.H * (p.H / 2 + 1); }
   bool fixed() const { return p.deposit_mode == SIPF_DEPOSIT_DETERMINISTIC; }
@@ -257,6 +267,18 @@ ChunkListArgs cl_args(sipf_ctx* c, const int* cursor, const int* cap, const long
   return ChunkListArgs{cursor, cap, base, c->count, c->chunk_start, c->chunks, other, c->NT, c->part};
 }
 
+// The current bins are final (positions of step n, before their deposit):
+// a download may start from here on a side stream.
+cudaError_t mark_positions(sipf_ctx* c) {
+  const cudaError_t e = cudaEventRecord(c->ev_pos, c->stream);
+  c->pos_ready = e == cudaSuccess;
+  return e;
+}
+
+// Pieces [a, b) of P particles for the pipelined host transfers.
+inline int64_t piece_begin(int64_t P, int npieces, int k) { return P * k / npieces; }
+inline int pieces_for(int64_t P) { return P >= (1 << 20) ? sipf_ctx::kPieces : 1; }
+
 // Deposit the current bins into phi (initialisation of Algorithm 4 and after
 // positions are replaced).
 template <typename T> int deposit_current(sipf_ctx* c) {
@@ -293,6 +315,7 @@ template <typename T> int rebin_from_staging(sipf_ctx* c) {
   c->cur = d;
   c->lc = L;
   c->since_layout = 0;
+  SIPF_CK(mark_positions(c));
   return deposit_current<T>(c);
 }
 
@@ -374,6 +397,7 @@ template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
       c->since_layout = 0;
     }
     SIPF_CK(mark(&ev[5]));
+    SIPF_CK(mark_positions(c));
     // deposit X^n from its bins (Algorithm 2) for the next step (its work
     // counter was cleared by the chunk-list emission above)
     SIPF_CK(launch_binned<T>(bin_args<T>(c, c->cur, c->lc, -1, 0), 0, 1, 0, c->stream));
@@ -528,20 +552,76 @@ template <typename T> int positions_host(sipf_ctx* c, double* out) {
   return SIPF_OK;
 }
 
+// Upload of host SoA positions.  With few enough tiles for the block-private
+// re-bin, the positions are copied in pieces on the copy stream and each piece
+// is wrapped and re-binned into the current buffer, with the current bin
+// capacities, as soon as it has arrived (positions that do not fit a bin go to
+// the overflow bin until the next capacity rebuild, at most resort_every
+// steps later; results do not depend on the binning).  Otherwise: one copy,
+// then the capacities are rebuilt from a tile histogram of the new positions.
 template <typename T> int upload_soa_impl(sipf_ctx* c, const void* const src[3]) {
-  for (int d = 0; d < 3; ++d)
-    SIPF_CK(cudaMemcpyAsync(c->st[d], src[d], (size_t)c->p.P * sizeof(T), cudaMemcpyHostToDevice, c->stream));
-  SIPF_CK(launch_wrap_soa<T>(c->p.P, make_geo<T>(c->p.L, c->p.H), (T*)c->st[0], (T*)c->st[1], (T*)c->st[2],
-                             c->stream));
-  SIPF_CK(launch_iota(c->st_id, c->p.P, c->stream));
-  return rebin_from_staging<T>(c);
+  const int64_t P = c->p.P;
+  const Geo<T> g = make_geo<T>(c->p.L, c->p.H);
+  if (c->NT > rebin_plain_max_tiles()) {
+    for (int d = 0; d < 3; ++d)
+      SIPF_CK(cudaMemcpyAsync(c->st[d], src[d], (size_t)P * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    SIPF_CK(launch_wrap_soa<T>(P, g, (T*)c->st[0], (T*)c->st[1], (T*)c->st[2], c->stream));
+    SIPF_CK(launch_iota(c->st_id, P, c->stream));
+    return rebin_from_staging<T>(c);
+  }
+  c->pos_ready = false;
+  const int b = c->cur;
+  SIPF_CK(cudaMemsetAsync(c->cursor[b], 0, (size_t)(c->NT + 1) * sizeof(int), c->stream));
+  // the staging arrays are free once the context stream reaches this point
+  SIPF_CK(cudaEventRecord(c->ev_begin, c->stream));
+  SIPF_CK(cudaStreamWaitEvent(c->side[1], c->ev_begin, 0));
+  const int np = pieces_for(P);
+  for (int k = 0; k < np; ++k) {
+    const int64_t a0 = piece_begin(P, np, k), a1 = piece_begin(P, np, k + 1);
+    if (a1 <= a0) continue;
+    for (int d = 0; d < 3; ++d)
+      SIPF_CK(cudaMemcpyAsync((T*)c->st[d] + a0, (const T*)src[d] + a0, (size_t)(a1 - a0) * sizeof(T),
+                              cudaMemcpyHostToDevice, c->side[1]));
+    SIPF_CK(cudaEventRecord(c->ev_piece[k], c->side[1]));
+    SIPF_CK(cudaStreamWaitEvent(c->stream, c->ev_piece[k], 0));
+    cudaError_t e = cudaSuccess;
+    launch_rebin_plain<T>((const T*)c->st[0] + a0, (const T*)c->st[1] + a0, (const T*)c->st[2] + a0, nullptr, a1 - a0,
+                          g, c->shift, c->ntx, c->NT, (T*)c->bx[b][0], (T*)c->bx[b][1], (T*)c->bx[b][2], c->bid[b],
+                          c->lbase[c->lc], c->lcap[c->lc], c->cursor[b], c->err, c->stream, &e, a0, true);
+    SIPF_CK(e);
+  }
+  SIPF_CK(launch_chunk_list(cl_args(c, c->cursor[b], c->lcap[c->lc], c->lbase[c->lc], c->cursor[1 - b]), c->work,
+                            nullptr, c->stream));
+  SIPF_CK(mark_positions(c));
+  return deposit_current<T>(c);
 }
 
+// Download to host SoA positions: the bins are un-binned into the 4-wide
+// scratch on a side stream as soon as they are final (the last step's deposit
+// may still be running on the context stream), then transposed and copied
+// back in pieces, each piece's copy overlapping the next piece's transpose.
 template <typename T> int download_soa_impl(sipf_ctx* c, void* const dst[3]) {
-  int r = unbin_to<T>(c, (T*)c->st[0], (T*)c->st[1], (T*)c->st[2]);
-  if (r) return r;
-  for (int d = 0; d < 3; ++d)
-    SIPF_CK(cudaMemcpyAsync(dst[d], c->st[d], (size_t)c->p.P * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+  const int64_t P = c->p.P;
+  // the other bin buffer is free between steps (the next move overwrites it)
+  T* aos = (T*)c->bx[1 - c->cur][0];
+  if (!c->pos_ready) SIPF_CK(mark_positions(c));
+  SIPF_CK(cudaStreamWaitEvent(c->side[0], c->ev_pos, 0));
+  SIPF_CK(cudaStreamWaitEvent(c->side[0], c->ev_done, 0));   // a previous download's copies
+  SIPF_CK(launch_unbin_aos<T>(bin_args<T>(c, c->cur, c->lc, -1, 0), c->max_chunks(), aos, c->side[0]));
+  const int np = pieces_for(P);
+  for (int k = 0; k < np; ++k) {
+    const int64_t a0 = piece_begin(P, np, k), a1 = piece_begin(P, np, k + 1);
+    if (a1 <= a0) continue;
+    SIPF_CK(launch_aos4_to_soa<T>(aos + 4 * a0, a1 - a0, (T*)c->st[0] + a0, (T*)c->st[1] + a0, (T*)c->st[2] + a0,
+                                  c->side[0]));
+    SIPF_CK(cudaEventRecord(c->ev_piece[k], c->side[0]));
+    SIPF_CK(cudaStreamWaitEvent(c->side[1], c->ev_piece[k], 0));
+    for (int d = 0; d < 3; ++d)
+      SIPF_CK(cudaMemcpyAsync((T*)dst[d] + a0, (const T*)c->st[d] + a0, (size_t)(a1 - a0) * sizeof(T),
+                              cudaMemcpyDeviceToHost, c->side[1]));
+  }
+  SIPF_CK(cudaEventRecord(c->ev_done, c->side[1]));
+  SIPF_CK(cudaStreamWaitEvent(c->stream, c->ev_done, 0));
   return SIPF_OK;
 }
 
@@ -562,6 +642,15 @@ void free_ctx(sipf_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  for (cudaStream_t t : c->side)
+    if (t) {
+      cudaStreamSynchronize(t);
+      cudaStreamDestroy(t);
+    }
+  for (cudaEvent_t e : c->ev_piece)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : {c->ev_pos, c->ev_begin, c->ev_done})
+    if (e) cudaEventDestroy(e);
   for (int b = 0; b < 2; ++b) {
     for (int d = 0; d < 3; ++d) cudaFree(c->bx[b][d]);
     cudaFree(c->bid[b]);
@@ -696,6 +785,11 @@ int sipf_init(const sipf_params* p, const double* X0, void* stream, sipf_ctx** o
   if (e == cudaSuccess) e = cudaMalloc(&c->grad, 4 * N * c->esz);
   if (e == cudaSuccess) e = cudaMalloc(&c->dsc, kDscCount * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(int));
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking);
+  for (int i = 0; i < sipf_ctx::kPieces && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&c->ev_piece[i], cudaEventDisableTiming);
+  for (cudaEvent_t* ev : {&c->ev_pos, &c->ev_begin, &c->ev_done})
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
   if (e == cudaSuccess && p->H >= 32) {
     e = cudaMalloc(&c->fft_run, p->precision == 64 ? sizeof(FftRun<double>) : sizeof(FftRun<float>));
     if (e == cudaSuccess) {

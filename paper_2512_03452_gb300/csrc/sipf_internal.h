@@ -210,7 +210,15 @@ cudaError_t launch_tile_hist(const T* x, const T* y, const T* z, int64_t P, Geo<
 template <typename T>
 bool launch_rebin_plain(const T* x, const T* y, const T* z, const uint32_t* id, int64_t P, Geo<T> g, int shift,
                         int ntx, int NT, T* dx, T* dy, T* dz, uint32_t* did, const long long* dst_base,
-                        const int* dst_cap, int* dst_cursor, int* err, cudaStream_t s, cudaError_t* e);
+                        const int* dst_cap, int* dst_cursor, int* err, cudaStream_t s, cudaError_t* e,
+                        int64_t id0 = 0,      // id == NULL: particle p gets id id0 + p
+                        bool wrap = false);   // wrap the positions into the box as they are read
+int rebin_plain_max_tiles();
+// The two passes of launch_unbin with a scratch array, separately: binned
+// particles to their ids' slots of the 4-wide scratch, and (any range of)
+// the scratch to three arrays.
+template <typename T> cudaError_t launch_unbin_aos(const BinArgs<T>& a, int64_t max_chunks, T* aos, cudaStream_t s);
+template <typename T> cudaError_t launch_aos4_to_soa(const T* aos, int64_t P, T* x, T* y, T* z, cudaStream_t s);
 template <typename T>
 // Particle order from the bins; with aos_scratch (4 P elements) through a
 // 4-wide scratch array and a transpose, else by three scattered stores.
