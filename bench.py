@@ -450,6 +450,7 @@ def run_ours(args, world, rank, local):
     batch = None if args.no_batch else run_batch_leg(world, dev, stream)
     adjoint = None if args.no_adjoint else run_adjoint_leg(world, dev, stream)
     convergence = None if args.no_convergence else run_convergence_leg(full=args.study)
+    two_d = None if args.no_2d else run_2d_leg(world, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -480,6 +481,7 @@ def run_ours(args, world, rank, local):
             "batch": batch,
             "adjoint": adjoint,
             "convergence": convergence,
+            "two_d": two_d,
             "sweep": extra,
         }
         print(json.dumps(line), flush=True)
@@ -675,6 +677,56 @@ def run_convergence_leg(full=False):
             "cells": list(cells.values()), "seconds": dt, "particle_steps_per_s": psteps / dt}
 
 
+def run_2d_leg(world, dev, stream):
+    """The 2D parabolic-elliptic variant (Sec. 5.2) on this GPU: device time of
+    the step at P = 2^20, H = 256, L = 10 (FP32, unit disk, M0 = 25), and the
+    second-moment experiment -- unit disk, (k, eps, mu, chi) = (0, 0, 1, 1),
+    tau = 5e-4 to T = 2 (4000 steps), P = 2^20, H = 256 -- at masses around
+    8 pi and box sides 10 and 20, beside the whole-plane value
+    m2(2) = 17/2 - M0/pi."""
+    import numpy as np
+    import torch
+
+    from paper_2512_03452_gb300 import Simulation2D, make_params
+
+    def disk(P, seed):
+        rng = np.random.default_rng(seed)
+        r = np.sqrt(rng.uniform(size=P))
+        th = rng.uniform(0, 2 * math.pi, size=P)
+        return np.stack([r * np.cos(th), r * np.sin(th)], axis=1)
+
+    P = 2 ** 20
+    X0 = disk(P, 0)
+
+    def params(L, M0):
+        return make_params(P=P, H=256, L=L, mass=M0, chi=1.0, mu=1.0, eps=0.0, k=0.0, dt=5e-4, seed=1, precision=32)
+
+    out = {"workload": "2D parabolic-elliptic (Sec. 5.2): unit disk, P = 2^20, H = 256, tau = 5e-4, FP32"}
+    with Simulation2D(params(10.0, 25.0), X0, stream=stream.cuda_stream) as sim:
+        sim.step(20)
+        sim.sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            sim.step(200)
+            b.record(stream)
+        b.synchronize()
+        ms = dist_max(a.elapsed_time(b), world, dev) / 200
+    out["ms_per_step"] = ms
+    out["value"] = world * P / (ms * 1e-3)
+    out["unit"] = UNIT
+    rows = []
+    for L in (10.0, 20.0):
+        for M0 in (24.6, 25.0, 25.6):
+            with Simulation2D(params(L, M0), X0, stream=stream.cuda_stream) as sim:
+                sim.step(4000)
+                d = sim.diagnostics()
+            rows.append({"L": L, "h": L / 256, "M0": M0, "m2_T2": d["m2"], "closed_form": 8.5 - M0 / math.pi,
+                         "peak": d["peak"], "hf_frac": d["hf_frac"]})
+    out["second_moment"] = rows
+    return out
+
+
 # ----------------------------------------------------------------- reference arm
 def run_reference(args, world, rank):
     """The FP64 oracle on the host cores, each step a bounded sample of the workload."""
@@ -758,6 +810,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     ap.add_argument("--no-convergence", action="store_true", help="skip the Sec. 5.1 convergence-study leg")
+    ap.add_argument("--no-2d", action="store_true", help="skip the 2D parabolic-elliptic leg (Sec. 5.2)")
     ap.add_argument("--study", action="store_true",
                     help="run the convergence leg over the paper's full sweep (30 seeds, P up to 2^20, H up to 256)")
     ap.add_argument("--no-extra", action="store_true", help="skip the H sweep, deterministic, cuFFT and FP64 legs")

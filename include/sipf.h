@@ -407,6 +407,47 @@ int sipf_inverse_ft_dev(int precision, int32_t H, void* spec, void* grid,
 int sipf_inverse_ft_noalloc_dev(int precision, int32_t H, const void* spec, void* grid,
                                 void* stream);
 
+/* ---- 2D variant: the parabolic-elliptic system of Sec. 5.2 ---------------
+ * The Keller-Segel system in two dimensions on [-L/2, L/2)^2 with an H x H
+ * grid, H a power of two in [8, 256]: eps = 0 is the parabolic-elliptic
+ * system of Sec. 5.2 ((|y|^2 + k^2) c-hat = F_H I rho-hat, the field of level
+ * n-1 driving the move of step n; k = 0 leaves the zero mode at 0), eps > 0
+ * the 2D parabolic-parabolic system with the implicit update of
+ * Eq. (alpha_hat_update).  Deposit with the 12-node 2D analogue of Eq. (4ord)
+ * (p2g_order 4) or the bilinear stencil, gather with the bilinear stencil
+ * (g2p_order 2) or the 12-node one; noise W^- = s (z0, z1), W^+ = s (z2, z3)
+ * from the first Philox block of particle p at step n (the 3D generator's
+ * first four normals).  Fields of sipf_params as in 3D; deposit_mode must be
+ * SIPF_DEPOSIT_ATOMIC and propagator SIPF_PROP_IMPLICIT.  Particles stay in
+ * particle order (no bins).  Same conventions as the 3D context (owned device
+ * memory, stream ordering, not thread-safe). */
+typedef struct sipf2d_ctx sipf2d_ctx;
+
+/* Create a 2D context: X0 host P x 2 row-major float64 (wrapped into the box);
+ * the initial positions are deposited.  SIPF_EINVAL for parameters outside the
+ * 2D ranges above, SIPF_ENONFINITE for a non-finite coordinate. */
+int sipf2d_init(const sipf_params* p, const double* X0, void* stream, sipf2d_ctx** out);
+/* Advance nsteps >= 0 steps (asynchronous on the context's stream). */
+int sipf2d_step(sipf2d_ctx* ctx, int64_t nsteps);
+/* Steps taken since sipf2d_init (-1 for NULL). */
+int64_t sipf2d_current_step(const sipf2d_ctx* ctx);
+/* Positions X^(n), host P x 2 row-major float64.  Synchronises. */
+int sipf2d_positions(sipf2d_ctx* ctx, double* out);
+/* The field spectrum of the last step, host H x (H/2+1) x 2 float64 (eps = 0:
+ * c-hat of level n-1; eps > 0: alpha^(n)).  Synchronises. */
+int sipf2d_spectrum(sipf2d_ctx* ctx, double* out);
+/* Host H x H float64: the deposited density I rho-hat / h^2 of X^(n)
+ * (filtered = 0) or rho_num = F_H^-1(Phi F_H I rho-hat) (filtered = 1). */
+int sipf2d_density(sipf2d_ctx* ctx, double* out, int filtered);
+/* FP64 diagnostics: mass (sum of the deposit grid), peak of rho_num, hf_frac
+ * (share of the field spectrum's energy with ||q|| >= 4), m2 = (1/P) sum |X|^2
+ * (Sec. 5.2), step; alpha0 and ring_radius are 0.  Synchronises. */
+int sipf2d_diagnostics(sipf2d_ctx* ctx, sipf_diag* out);
+/* Wait for the context's work; SIPF_ENONFINITE if a position became non-finite. */
+int sipf2d_sync(sipf2d_ctx* ctx);
+/* Release the context (NULL is ignored). */
+void sipf2d_destroy(sipf2d_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,7 +13,7 @@ from . import _abi
 from ._abi import (DEPOSIT_ATOMIC, DEPOSIT_DETERMINISTIC, PROP_EXP, PROP_IMPLICIT, SPLIT_HALF,
                    SPLIT_PLAIN, SipfError)
 
-__all__ = ["Simulation", "Batch", "make_params", "SipfError", "SPLIT_HALF", "SPLIT_PLAIN",
+__all__ = ["Simulation", "Simulation2D", "Batch", "make_params", "SipfError", "SPLIT_HALF", "SPLIT_PLAIN",
            "DEPOSIT_ATOMIC", "DEPOSIT_DETERMINISTIC", "PROP_IMPLICIT", "PROP_EXP"]
 
 
@@ -99,6 +99,63 @@ class Simulation:
     def close(self):
         if self.ctx:
             _abi.sipf_destroy(self.ctx)
+            self.ctx = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Simulation2D:
+    """One run of the 2D variant (Sec. 5.2: eps = 0 is the parabolic-elliptic
+    system) on the current CUDA device; X0 is (P, 2)."""
+
+    def __init__(self, params, X0, stream: int | None = None):
+        self.params = params
+        self.P = int(params.P)
+        self.H = int(params.H)
+        self.ctx = _abi.sipf2d_init(params, X0, stream)
+
+    def step(self, n: int = 1):
+        _abi.sipf2d_step(self.ctx, n)
+
+    @property
+    def n(self) -> int:
+        return _abi.sipf2d_current_step(self.ctx)
+
+    def sync(self):
+        _abi.sipf2d_sync(self.ctx)
+
+    def positions(self) -> np.ndarray:
+        out = np.empty((self.P, 2), dtype=np.float64)
+        _abi.sipf2d_positions(self.ctx, out)
+        return out
+
+    def spectrum(self) -> np.ndarray:
+        out = np.empty((self.H, self.H // 2 + 1, 2), dtype=np.float64)
+        _abi.sipf2d_spectrum(self.ctx, out)
+        return out[..., 0] + 1j * out[..., 1]
+
+    def density(self, filtered: bool = False) -> np.ndarray:
+        out = np.empty((self.H, self.H), dtype=np.float64)
+        _abi.sipf2d_density(self.ctx, out, int(filtered))
+        return out
+
+    def diagnostics(self) -> dict:
+        d = _abi.sipf2d_diagnostics(self.ctx)
+        return {name: getattr(d, name) for name in ("mass", "peak", "hf_frac", "m2", "step")}
+
+    def close(self):
+        if self.ctx:
+            _abi.sipf2d_destroy(self.ctx)
             self.ctx = 0
 
     def __enter__(self):

@@ -130,6 +130,15 @@ _SIGS = {
     "sipf_adjoint_kernel_launches": (ctypes.c_int64, [_P]),
     "sipf_adjoint_destroy": (None, [_P]),
     "sipf_measure_fp64_fma": (ctypes.c_int, [_P, _D]),
+    "sipf2d_init": (ctypes.c_int, [ctypes.POINTER(sipf_params), _D, _P, ctypes.POINTER(_P)]),
+    "sipf2d_step": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "sipf2d_current_step": (ctypes.c_int64, [_P]),
+    "sipf2d_positions": (ctypes.c_int, [_P, _D]),
+    "sipf2d_spectrum": (ctypes.c_int, [_P, _D]),
+    "sipf2d_density": (ctypes.c_int, [_P, _D, ctypes.c_int]),
+    "sipf2d_diagnostics": (ctypes.c_int, [_P, ctypes.POINTER(sipf_diag)]),
+    "sipf2d_sync": (ctypes.c_int, [_P]),
+    "sipf2d_destroy": (None, [_P]),
 }
 
 
@@ -415,3 +424,47 @@ def sipf_measure_fp64_fma(stream: int = 0) -> float:
     g = ctypes.c_double()
     _check(load().sipf_measure_fp64_fma(_P(stream), ctypes.byref(g)), "sipf_measure_fp64_fma")
     return g.value
+
+
+# ---- 2D variant (Sec. 5.2) ----------------------------------------------------
+def sipf2d_init(p: sipf_params, X0, stream: int | None = None) -> int:
+    """X0: contiguous (P, 2) float64 numpy array.  Returns the 2D context handle."""
+    import numpy as np
+    X0 = np.ascontiguousarray(X0, dtype=np.float64)
+    h = _P()
+    _check(load().sipf2d_init(ctypes.byref(p), _dptr(X0), _P(stream or 0), ctypes.byref(h)), "sipf2d_init")
+    return h.value
+
+
+def sipf2d_step(ctx: int, nsteps: int) -> None:
+    _check(load().sipf2d_step(_P(ctx), int(nsteps)), "sipf2d_step")
+
+
+def sipf2d_current_step(ctx: int) -> int:
+    return int(load().sipf2d_current_step(_P(ctx)))
+
+
+def sipf2d_positions(ctx: int, out) -> None:
+    _check(load().sipf2d_positions(_P(ctx), _dptr(out)), "sipf2d_positions")
+
+
+def sipf2d_spectrum(ctx: int, out) -> None:
+    _check(load().sipf2d_spectrum(_P(ctx), _dptr(out)), "sipf2d_spectrum")
+
+
+def sipf2d_density(ctx: int, out, filtered: int) -> None:
+    _check(load().sipf2d_density(_P(ctx), _dptr(out), int(filtered)), "sipf2d_density")
+
+
+def sipf2d_diagnostics(ctx: int) -> sipf_diag:
+    d = sipf_diag()
+    _check(load().sipf2d_diagnostics(_P(ctx), ctypes.byref(d)), "sipf2d_diagnostics")
+    return d
+
+
+def sipf2d_sync(ctx: int) -> None:
+    _check(load().sipf2d_sync(_P(ctx)), "sipf2d_sync")
+
+
+def sipf2d_destroy(ctx: int) -> None:
+    load().sipf2d_destroy(_P(ctx))

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsipf.so")
-SOURCES = ["sipf_api.cu", "fft_kernels.cu", "particle_kernels.cu", "adjoint_kernels.cu"]
+SOURCES = ["sipf_api.cu", "fft_kernels.cu", "particle_kernels.cu", "adjoint_kernels.cu", "sipf2d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -115,6 +115,14 @@ int fixed_k(const sipf_params& p) {
 
 }  // namespace
 
+// Shared with the other translation units of the library (sipf_internal.h).
+namespace sipf {
+int report_error(int code, const std::string& msg) { return fail(code, msg); }
+int report_cuda(cudaError_t e, const char* where) { return cuda_fail(e, where); }
+double filter_scale(const sipf_params& p) { return effective_H0(p); }
+}  // namespace sipf
+
+
 struct sipf_ctx {
   sipf_params p{};
   double H0 = 0;

@@ -116,6 +116,52 @@ __device__ __forceinline__ void normals6(uint64_t seed, uint64_t p, uint32_t n, 
   }
 }
 
+// Four standard normals for particle p at step n from block 0 alone (the 2D
+// move): the same values as the first four of normals6.
+__device__ __forceinline__ void philox1block(u32x4& a, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    philox_round(a, k0, k1);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+__device__ __forceinline__ void normals4(uint64_t seed, uint64_t p, uint32_t n, double z[4]) {
+  u32x4 a{(uint32_t)p, (uint32_t)(p >> 32), n, 0u};
+  philox1block(a, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+  const double two_m32 = 2.3283064365386963e-10;   // 2^-32
+  const double two_pi = 6.283185307179586;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const double u1 = ((double)w[2 * j] + 0.5) * two_m32;
+    const double u2 = ((double)w[2 * j + 1] + 0.5) * two_m32;
+    const double r = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincos(two_pi * u2, &s, &c);
+    z[2 * j] = r * c;
+    z[2 * j + 1] = r * s;
+  }
+}
+__device__ __forceinline__ void normals4(uint64_t seed, uint64_t p, uint32_t n, float z[4]) {
+  u32x4 a{(uint32_t)p, (uint32_t)(p >> 32), n, 0u};
+  philox1block(a, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+  const float two_pi = 6.28318530717958648f;
+  const float ln2x2 = 1.3862943611198906f;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const float u1 = unit32(w[2 * j]);
+    const float u2 = unit23(w[2 * j + 1]);
+    const float r2 = -ln2x2 * __log2f(u1);
+    const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+    float s, c;
+    __sincosf(two_pi * (u2 - 0.5f), &s, &c);
+    z[2 * j] = -r * c;
+    z[2 * j + 1] = -r * s;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Geometry helpers.
 // ---------------------------------------------------------------------------

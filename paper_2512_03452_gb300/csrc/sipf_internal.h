@@ -243,4 +243,9 @@ cudaError_t launch_alpha_energy(const cpx<T>* alpha, int H, double* acc2, cudaSt
 
 template <typename T> Geo<T> make_geo(double L, int H);
 
+// Error reporting and parameter helpers of the C ABI (sipf_api.cu): set the
+// calling thread's last error message and return the code.
+int report_error(int code, const std::string& msg);
+int report_cuda(cudaError_t e, const char* where);
+
 }  // namespace sipf

@@ -24,7 +24,7 @@ def lib():
 def declared_symbols():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(sipf_[a-z_0-9]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(sipf[a-z0-9]*_[a-z_0-9]+)\s*\(", text)))
 
 
 def test_header_declarations_match_binding():
@@ -33,7 +33,7 @@ def test_header_declarations_match_binding():
 
 def test_library_exports_every_declared_symbol(lib):
     out = subprocess.run(["nm", "-D", "--defined-only", _abi.LIB_PATH], capture_output=True, text=True).stdout
-    exported = set(re.findall(r"\bT (sipf_\w+)", out))
+    exported = set(re.findall(r"\bT (sipf\w+)", out))
     for name in declared_symbols():
         assert name in exported, name
         assert getattr(lib, name) is not None
