@@ -247,7 +247,11 @@ typedef struct sipf_batch_tuning {
   int32_t xpass_tile[4];          /* pencils per block of the fused x pass: 4, 8, 16 */
   int32_t rows_blocks_per_sm[4];  /* blocks per SM shared by the row passes          */
   int32_t plane_kernels[4];       /* 1: both inner axes in one plane kernel per
-                                     direction; 0: separate pencil passes        */
+                                     direction (one x-plane per block); 2: the same
+                                     with each x-plane's columns spread over a
+                                     cluster of 2 (H <= 128) or 4 (H = 256) blocks
+                                     sharing rows through distributed shared
+                                     memory (H >= 64); 0: separate pencil passes */
   int32_t plane_warps[4];         /* warps per block of the plane kernels: 8, 16, 32 */
   int32_t xpass_warps[4];         /* warps per block of the fused x pass: 8, 16      */
   int32_t inverse_all_components[4]; /* inverse plane kernel: 1 one block per x-plane for

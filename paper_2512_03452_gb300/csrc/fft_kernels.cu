@@ -12,6 +12,7 @@
 // pencil passes (kwb_*).  H < 32 uses block-wide shared-memory transforms
 // (k_*).  Every kernel's complex products spell out their roundings, so all
 // shapes and paths give the same bits.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -1136,6 +1137,223 @@ __global__ void __launch_bounds__(1024) kwp_inv3(const FftRun<T>* __restrict__ r
   plane_inv3_body<T, E>(r.T2 + (size_t)x * N * NH, S, r.grad, x, tw, P, zb, ob);
 }
 
+// ---------------------------------------------------------------------------
+// Cluster plane kernels: one x-plane per cluster of CS CTAs (CS = 2 at
+// H = 128, 4 at H = 256, where a whole plane does not fit one CTA's shared
+// memory or would leave SMs idle).  Each CTA owns a contiguous range of the
+// plane's H/2+1 columns for all H rows, so the y-axis FFTs are local; the
+// rows are shared out through distributed shared memory:
+//   forward: CTA r transforms rows [r H/CS, (r+1) H/CS) (two real rows per
+//            complex warp FFT) and stores each output column into the shared
+//            memory of the CTA that owns it; after a cluster barrier every
+//            CTA transforms its columns along y and writes them;
+//   inverse: every CTA loads its columns of one gradient component, does their
+//            y-axis inverse, and after a cluster barrier its rows' c2r pull
+//            the other columns from the peers' shared memory; a second
+//            barrier keeps each CTA's columns alive until all peers are done.
+// The arithmetic is that of the plane kernels (same warp FFT, same order), so
+// the results are the same bits.
+// ---------------------------------------------------------------------------
+template <int N, int CS> struct ColSplit {
+  static constexpr int NH = N / 2 + 1;
+  static constexpr int CP = (NH + CS - 1) / CS;   // columns per CTA (the last one may hold fewer)
+  static constexpr int LD = CP;                   // row stride of the column block (odd for CS = 2, 4)
+  static __device__ __forceinline__ int first(int r) { return r * CP; }
+  static __device__ __forceinline__ int count(int r) { return min(CP, NH - r * CP); }
+};
+
+template <typename T, int E, int CS> constexpr size_t cplane_smem_bytes(int nw) {
+  // column block: H rows of CP plus one slot per 32 rows; one padded pencil per warp
+  return ((size_t)32 * E * ColSplit<32 * E, CS>::LD + E + (size_t)nw * padded_len(32 * E) + kTwLen) * sizeof(cpx<T>);
+}
+
+template <typename T, int E, int CS, typename Tin>
+__device__ __forceinline__ void cplane_fwd_body(Tin* __restrict__ in, double in_scale, cpx<T>* __restrict__ out,
+                                                const cpx<T>* tw, cpx<T>* Q, cpx<T>* zball) {
+  namespace cg = cooperative_groups;
+  constexpr int N = 32 * E;
+  using CSp = ColSplit<N, CS>;
+  constexpr int NH = CSp::NH, LD = CSp::LD;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  cpx<T>* zb = zball + wib * padded_len(N);
+  cpx<T>* peer[CS];
+#pragma unroll
+  for (int o = 0; o < CS; ++o) peer[o] = cluster.map_shared_rank(Q, o);
+  // every CTA of the cluster is running before any stores into its shared memory
+  cluster.sync();
+  // 1. this CTA's rows (row pairs), results pushed to the owners' column blocks
+  constexpr int PAIRS = N / 2 / CS;
+  for (int i = wib; i < PAIRS; i += nw) {
+    const int pr = rank * PAIRS + i;
+    const size_t ra = (size_t)(2 * pr) * N, rb = ra + N;
+    cpx<T> v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const Tin a = in[ra + lane + 32 * m], b = in[rb + lane + 32 * m];
+      if constexpr (sizeof(Tin) == 8 && !std::is_floating_point<Tin>::value)
+        v[m] = cpx<T>{(T)((double)(long long)a * in_scale), (T)((double)(long long)b * in_scale)};
+      else
+        v[m] = cpx<T>{(T)a, (T)b};
+    }
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      in[ra + lane + 32 * m] = Tin(0);
+      in[rb + lane + 32 * m] = Tin(0);
+    }
+    warp_fft<T, E, -1>(v, lane, tw);
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) zb[zpad(out_index(k1, E, lane))] = v[k1];
+    __syncwarp();
+    for (int k = lane; k < NH; k += 32) {
+      const cpx<T> zk = zb[zpad(k)];
+      const cpx<T> zm = cconj(zb[zpad((N - k) & (N - 1))]);
+      const cpx<T> d = csub(zk, zm);
+      const int o = k / LD, kl = k - o * LD;
+      cpx<T>* dst = peer[o];
+      dst[tpad(2 * pr, LD, kl)] = cpx<T>{(zk.x + zm.x) * T(0.5), (zk.y + zm.y) * T(0.5)};
+      dst[tpad(2 * pr + 1, LD, kl)] = cpx<T>{d.y * T(0.5), -d.x * T(0.5)};
+    }
+    __syncwarp();
+  }
+  cluster.sync();
+  // 2. y axis of this CTA's columns
+  const int c0 = CSp::first(rank), nc = CSp::count(rank);
+  for (int c = wib; c < nc; c += nw) {
+    cpx<T> v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = Q[tpad(lane + 32 * m, LD, c)];
+    warp_fft<T, E, -1>(v, lane, tw);
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) Q[tpad(out_index(k1, E, lane), LD, c)] = v[k1];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < N * nc; t += blockDim.x) {
+    const int j = t / nc, c = t - j * nc;
+    out[(size_t)j * NH + c0 + c] = Q[tpad(j, LD, c)];
+  }
+}
+
+template <typename T, int E, int CS>
+__device__ __forceinline__ void cplane_inv_body(const cpx<T>* __restrict__ in, T* __restrict__ out, int x, int d,
+                                                const cpx<T>* tw, cpx<T>* Q, cpx<T>* zball) {
+  namespace cg = cooperative_groups;
+  constexpr int N = 32 * E;
+  using CSp = ColSplit<N, CS>;
+  constexpr int NH = CSp::NH, LD = CSp::LD;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  cpx<T>* zb = zball + wib * padded_len(N);
+  const int c0 = CSp::first(rank), nc = CSp::count(rank);
+  for (int t = threadIdx.x; t < N * nc; t += blockDim.x) {
+    const int j = t / nc, c = t - j * nc;
+    Q[tpad(j, LD, c)] = in[(size_t)j * NH + c0 + c];
+  }
+  __syncthreads();
+  // 1. y-axis inverse of this CTA's columns
+  for (int c = wib; c < nc; c += nw) {
+    cpx<T> v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = Q[tpad(lane + 32 * m, LD, c)];
+    warp_fft<T, E, +1>(v, lane, tw);
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) Q[tpad(out_index(k1, E, lane), LD, c)] = v[k1];
+  }
+  cluster.sync();
+  const cpx<T>* peer[CS];
+#pragma unroll
+  for (int o = 0; o < CS; ++o) peer[o] = cluster.map_shared_rank(Q, o);
+  // 2. this CTA's rows: two Hermitian half rows A, B as the pencil A + i B
+  constexpr int PAIRS = N / 2 / CS;
+  for (int i = wib; i < PAIRS; i += nw) {
+    const int pr = rank * PAIRS + i;
+    for (int k = lane; k < NH; k += 32) {
+      const int o = k / LD, kl = k - o * LD;
+      cpx<T> A = peer[o][tpad(2 * pr, LD, kl)], Bv = peer[o][tpad(2 * pr + 1, LD, kl)];
+      if (k == 0 || k == N / 2) {
+        A.y = T(0);
+        Bv.y = T(0);
+      }
+      zb[zpad(k)] = cpx<T>{A.x - Bv.y, A.y + Bv.x};
+      if (k > 0 && k < N / 2) zb[zpad(N - k)] = cpx<T>{A.x + Bv.y, -A.y + Bv.x};
+    }
+    __syncwarp();
+    cpx<T> v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = zb[zpad(lane + 32 * m)];
+    __syncwarp();
+    warp_fft<T, E, +1>(v, lane, tw);
+    T* ob = reinterpret_cast<T*>(zb);
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) {
+      const int j = out_index(k1, E, lane);
+      ob[zpad(j)] = v[k1].x;
+      ob[zpad(N + j)] = v[k1].y;
+    }
+    __syncwarp();
+    T* orow = out + ((size_t)x * N + 2 * pr) * N * 4 + d;
+    for (int t = lane; t < 2 * N; t += 32) orow[(size_t)t * 4] = ob[zpad(t)];
+    __syncwarp();
+  }
+  // the peers may still read this CTA's columns
+  cluster.sync();
+}
+
+template <typename T, int E, int CS>
+__global__ void __launch_bounds__(1024) kwc_fwd(const FftRun<T>* __restrict__ runs) {
+  constexpr int N = 32 * E, NH = N / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* zb = tw + kTwLen;
+  cpx<T>* Q = zb + (blockDim.x >> 5) * padded_len(N);
+  load_tw_full<T, E>(tw);
+  __syncthreads();
+  const FftRun<T>& r = runs[blockIdx.y];
+  const int x = blockIdx.x / CS;
+  cpx<T>* out = r.T1 + (size_t)x * N * NH;
+  if (r.phi_fixed)
+    cplane_fwd_body<T, E, CS, unsigned long long>(static_cast<unsigned long long*>(r.phi) + (size_t)x * N * N,
+                                                  r.in_scale, out, tw, Q, zb);
+  else
+    cplane_fwd_body<T, E, CS, T>(static_cast<T*>(r.phi) + (size_t)x * N * N, 1.0, out, tw, Q, zb);
+}
+
+template <typename T, int E, int CS>
+__global__ void __launch_bounds__(1024) kwc_inv(const FftRun<T>* __restrict__ runs) {
+  constexpr int N = 32 * E, NH = N / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* zb = tw + kTwLen;
+  cpx<T>* Q = zb + (blockDim.x >> 5) * padded_len(N);
+  load_tw_full<T, E>(tw);
+  __syncthreads();
+  const FftRun<T>& r = runs[blockIdx.z];
+  const int x = blockIdx.x / CS, d = blockIdx.y;
+  const size_t S = (size_t)N * N * NH;
+  cplane_inv_body<T, E, CS>(r.T2 + d * S + (size_t)x * N * NH, r.grad, x, d, tw, Q, zb);
+}
+
+// Launch with a cluster of CS CTAs along x.
+template <typename K, typename... Args>
+static cudaError_t launch_cluster(K kernel, dim3 grid, int threads, size_t smem, int cs, cudaStream_t s,
+                                  Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 static int warp_blocks(int rows) {
   int b = (rows / 2 + 7) / 8;
   return b > 152 * 8 ? 152 * 8 : (b < 1 ? 1 : b);
@@ -1419,7 +1637,15 @@ static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, c
   const int snw = tune.spec_nw > 0 ? tune.spec_nw : kDefaultSpectralWarps;
   const size_t fsm = plane_smem_bytes<T, E>(fnw), ism = plane_smem_bytes<T, E>(inw);
   const size_t i3sm = plane3_smem_bytes<T, E>(i3nw);
-  const bool planes = tune.plane_mode == 0 && E <= 4 && fsm <= kMaxSmem && ism <= kMaxSmem;
+  // cluster plane kernels (CS = 2 at H <= 128, 4 at H = 256) when asked: at
+  // H = 128 (one run) and H = 256 they measured slower than the plane kernels
+  // and the pencil passes, so they are a tuning candidate, not a default
+  constexpr int CS = E >= 8 ? 4 : 2;
+  const int cnw = tune.plane_nw > 0 ? tune.plane_nw : (E >= 8 ? 8 : 16);
+  const size_t csm = cplane_smem_bytes<T, E, CS>(cnw);
+  const bool cluster_ok = E >= 2 && csm <= kMaxSmem;
+  const bool clusters = cluster_ok && tune.plane_mode == 2;
+  const bool planes = !clusters && tune.plane_mode == 0 && E <= 4 && fsm <= kMaxSmem && ism <= kMaxSmem;
   // all three components per inverse plane block: where asked, or by default
   // where the x-plane blocks fill the SMs four times over and two blocks fit
   // an SM (many runs: the gradient nodes then exceed L2)
@@ -1427,7 +1653,12 @@ static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, c
                     (tune.inv3 == 1 ? i3sm <= kMaxSmem
                                     : tune.inv3 == 0 && nruns * N >= 4 * 152 && 2 * i3sm <= kMaxSmem);
   if (stages & kFieldForward) {
-    if (planes) {
+    if (clusters) {
+      if ((e = set_smem(kwc_fwd<T, E, CS>, csm)) != cudaSuccess) return e;
+      if ((e = launch_cluster(kwc_fwd<T, E, CS>, dim3(N * CS, nruns), 32 * cnw, csm, CS, s, runs)) != cudaSuccess)
+        return e;
+      nk += 1;
+    } else if (planes) {
       if ((e = set_smem(kwp_fwd<T, E>, fsm)) != cudaSuccess) return e;
       kwp_fwd<T, E><<<dim3(N, nruns), 32 * fnw, fsm, s>>>(runs);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1448,7 +1679,12 @@ static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, c
     if (e != cudaSuccess) return e;
     nk += 1;
   }
-  if ((stages & kFieldInverse) && inv3) {
+  if ((stages & kFieldInverse) && clusters) {
+    if ((e = set_smem(kwc_inv<T, E, CS>, csm)) != cudaSuccess) return e;
+    if ((e = launch_cluster(kwc_inv<T, E, CS>, dim3(N * CS, 3, nruns), 32 * cnw, csm, CS, s, runs)) != cudaSuccess)
+      return e;
+    nk += 1;
+  } else if ((stages & kFieldInverse) && inv3) {
     if constexpr (E <= 2) {
       if ((e = set_smem(kwp_inv3<T, E>, i3sm)) != cudaSuccess) return e;
       kwp_inv3<T, E><<<dim3(N, nruns), 32 * i3nw, i3sm, s>>>(runs);
@@ -1481,8 +1717,11 @@ template <typename T, int E> static bool field_tune_valid_e(const FieldTune& t) 
   const bool inv3_ok = t.inv3 == 0 || t.inv3 == 2 ||
                        (t.inv3 == 1 && t.plane_mode == 0 && E <= 2 && plane3_smem_bytes<T, E>(pnw) <= kMaxSmem);
   return (bc == 8 || bc == 16 || bc == 32) && (sbc == 4 || sbc == 8 || sbc == 16) && c <= kMaxSmem &&
-         x <= kMaxSmem && t.rows_per_sm >= 0 && t.rows_per_sm <= 32 && (t.plane_mode == 0 || t.plane_mode == 1) &&
-         pnw_ok && snw_ok && inv3_ok && (t.plane_mode == 1 || E > 4 || plane_smem_bytes<T, E>(pnw) <= kMaxSmem);
+         x <= kMaxSmem && t.rows_per_sm >= 0 && t.rows_per_sm <= 32 &&
+         (t.plane_mode == 0 || t.plane_mode == 1 ||
+          (t.plane_mode == 2 && E >= 2 && cplane_smem_bytes<T, E, (E >= 8 ? 4 : 2)>(pnw) <= kMaxSmem)) &&
+         pnw_ok && snw_ok && inv3_ok &&
+         (t.plane_mode != 0 || E > 4 || plane_smem_bytes<T, E>(pnw) <= kMaxSmem);
 }
 
 template <typename T> FieldTune field_tune_default(int H) {

@@ -1361,7 +1361,7 @@ template <typename T> int batch_autotune_impl(sipf_batch* b, int trial, sipf_bat
     float best = 3.0e38f;
     // plane kernels or pencil passes first, then the x-pass tile, then the
     // pencil-pass shapes (which only matter if pencils won)
-    static const std::vector<int> cand[7] = {{0, 1}, {8, 16, 32}, {1, 2}, {4, 8, 16}, {8, 16}, {8, 16, 32}, {4, 8, 16}};
+    static const std::vector<int> cand[7] = {{0, 1, 2}, {8, 16, 32}, {1, 2}, {4, 8, 16}, {8, 16}, {8, 16, 32}, {4, 8, 16}};
     for (int dim = 0; dim < 7; ++dim) {
       for (int v : cand[dim]) {
         FieldTune t = best_t;
@@ -1423,7 +1423,8 @@ template <typename T> int batch_autotune_impl(sipf_batch* b, int trial, sipf_bat
       out->cols_tile[g] = b->field_tune[g].bc;
       out->xpass_tile[g] = b->field_tune[g].sbc;
       out->rows_blocks_per_sm[g] = b->field_tune[g].rows_per_sm;
-      out->plane_kernels[g] = b->field_tune[g].plane_mode == 0 ? 1 : 0;
+      const int pm = b->field_tune[g].plane_mode;
+      out->plane_kernels[g] = pm == 0 ? 1 : (pm == 1 ? 0 : 2);
       out->plane_warps[g] = b->field_tune[g].plane_nw;
       out->xpass_warps[g] = b->field_tune[g].spec_nw;
       out->inverse_all_components[g] = b->field_tune[g].inv3;
@@ -1564,7 +1565,7 @@ int sipf_batch_set_tuning(sipf_batch* b, const sipf_batch_tuning* t) {
     ft[g].bc = t->cols_tile[g];
     ft[g].sbc = t->xpass_tile[g];
     ft[g].rows_per_sm = t->rows_blocks_per_sm[g];
-    ft[g].plane_mode = t->plane_kernels[g] ? 0 : 1;
+    ft[g].plane_mode = t->plane_kernels[g] == 2 ? 2 : (t->plane_kernels[g] ? 0 : 1);
     ft[g].plane_nw = t->plane_warps[g];
     ft[g].spec_nw = t->xpass_warps[g];
     ft[g].inv3 = t->inverse_all_components[g];

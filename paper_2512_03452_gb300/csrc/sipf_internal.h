@@ -78,7 +78,8 @@ enum { kFieldForward = 1, kFieldSpectral = 2, kFieldInverse = 4, kFieldAll = 7 }
 // passes.  Results agree to rounding; they do not depend on the tile shapes.
 struct FieldTune {
   int bc = 0, sbc = 0, rows_per_sm = 0;
-  int plane_mode = 0;   // 0: plane kernels for the inner axes where they fit (H <= 128), 1: pencil passes
+  int plane_mode = 0;   // 0: plane kernels for the inner axes where they fit (H <= 128), 1: pencil passes,
+                        // 2: cluster plane kernels (H >= 64; each x-plane over 2 or 4 blocks)
   int plane_nw = 0;     // warps per block of the plane kernels (8, 16, 32)
   int spec_nw = 0;      // warps per block of the fused x pass (8, 16)
   int inv3 = 0;         // inverse plane kernel: 0 by grid size, 1 one block per x-plane for all three

@@ -181,10 +181,11 @@ def _tuning(H, **kw):
                                    dict(g1_plane_kernels=0, g1_cols_tile=8, g1_rows_blocks_per_sm=4),
                                    dict(g1_xpass_tile=4), dict(move_blocks_per_sm=1, deposit_blocks_per_sm=1),
                                    dict(g0_inverse_all_components=1, g1_inverse_all_components=1),
-                                   dict(g1_inverse_all_components=1, g1_plane_warps=16)])
+                                   dict(g1_inverse_all_components=1, g1_plane_warps=16),
+                                   dict(g1_plane_kernels=2), dict(g1_plane_kernels=2, g1_plane_warps=8)])
 def test_launch_shapes_give_identical_bits(shape):
-    """Plane or pencil FFT kernels, tile widths, grid sizes and the inverse
-    plane kernel over one or all three gradient components: the same bits
+    """Plane, cluster-plane or pencil FFT kernels, tile widths, grid sizes and
+    the inverse plane kernel over one or all three gradient components: the same bits
     (deterministic deposit; the lone-particle run amplifies any difference)."""
     _, params, X0s = _runs(32, mode=1, n=4, seed=12)
 
