@@ -176,9 +176,13 @@ template <typename T> __device__ __forceinline__ void block_acc2(T a, T b, doubl
 // out: Xbar^{n-1} (in place), the gradient-grid cotangents gbar (H^3
 // interleaved (x, y, z, -) nodes, accumulated) and the sums for dJ/dchi and
 // dJ/ds.
-template <typename T>
-__global__ void __launch_bounds__(256)
+// G2P / P2G: the gather and deposit orders fixed at compile time (0: taken
+// from the arguments at run time); the default pair (2, 4) compiles one
+// stencil of each kind, which keeps the kernel within 80 registers.
+template <typename T, int G2P, int P2G>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? ((G2P && P2G) ? 3 : 2) : 1)
 k_adj_step(AdjArgs<T> a) {
+  const int g2p = G2P ? G2P : a.g2p, p2g = P2G ? P2G : a.p2g;
   T chi_part = T(0), s_part = T(0);
   const Geo<T> g = a.g;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.P; p += (int64_t)gridDim.x * blockDim.x) {
@@ -193,7 +197,7 @@ k_adj_step(AdjArgs<T> a) {
     // V = I* g (q) and its Jacobian J[d][e] = dV_d / dq_e
     T V[3] = {T(0), T(0), T(0)};
     T J[3][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
-    stencil_grad_visit<T>(a.g2p, qx, qy, qz, g, [&](int idx, T f, T fx, T fy, T fz) {
+    stencil_grad_visit<T>(g2p, qx, qy, qz, g, [&](int idx, T f, T fx, T fy, T fz) {
       const T* gp = a.grad4 + (size_t)idx * 4;
       const T v[3] = {__ldg(gp), __ldg(gp + 1), __ldg(gp + 2)};
 #pragma unroll
@@ -215,11 +219,11 @@ k_adj_step(AdjArgs<T> a) {
       s_part += nz[0] * bx + nz[1] * by + nz[2] * bz;
     // gbar_d += F_gamma(q) chi tau Xbar_d  (transpose of the gather)
     const T cbx = a.chitau * bx, cby = a.chitau * by, cbz = a.chitau * bz;
-    stencil_grad_visit<T>(a.g2p, qx, qy, qz, g, [&](int idx, T f, T, T, T) {
+    stencil_grad_visit<T>(g2p, qx, qy, qz, g, [&](int idx, T f, T, T, T) {
       red_node3<T>(a.gbar + (size_t)idx * 4, f * cbx, f * cby, f * cbz);
     });
     // transpose of the deposit of X^{n-1}
-    const A3<T> dp = deposit_adjoint<T>(a.phibar, a.p2g, x, y, z, a.w_inv_h, g);
+    const A3<T> dp = deposit_adjoint<T>(a.phibar, p2g, x, y, z, a.w_inv_h, g);
     a.xb[p] = ybx + dp.x;
     a.xb[a.P + p] = yby + dp.y;
     a.xb[2 * a.P + p] = ybz + dp.z;
@@ -314,7 +318,8 @@ int grid_blocks(int64_t n) {
 
 template <typename T> cudaError_t launch_adj_step(const AdjArgs<T>& a, cudaStream_t s) {
   if (a.P <= 0) return cudaSuccess;
-  k_adj_step<T><<<grid_blocks(a.P), 256, 0, s>>>(a);
+  auto k = (a.g2p == 2 && a.p2g == 4) ? k_adj_step<T, 2, 4> : k_adj_step<T, 0, 0>;
+  k<<<grid_blocks(a.P), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -167,6 +167,10 @@ constexpr int kReplicas = 4;                  // whole-grid window copies (lane 
 // another, whose random slots spread over all 32 banks at random.
 constexpr int kTileReps = 8;
 constexpr int kChunk = 4096;                  // particles per work item
+// Work items with fewer particles deposit with global reductions: clearing
+// and flushing a tile window (11^3 slots x 8 copies) costs more than their
+// 32 reductions per particle.
+constexpr int kWinMinLen = 64;
 
 // Add the shared window (all replicas) to the grid and clear it; the
 // reductions of a warp hit contiguous nodes along the fastest axis.  Tile
@@ -256,7 +260,7 @@ __device__ __forceinline__ void binned_chunk(const BinArgs<T>& a, const ChunkDes
   const int bin = cur.bin, len = cur.len;
   const long long start = cur.start;
   // window origin (node coordinates of slot (0,0,0))
-  bool has_win = DEPOSIT && (WHOLE || bin < a.NT);
+  bool has_win = DEPOSIT && (WHOLE || (bin < a.NT && len >= kWinMinLen));
   int ox = 0, oy = 0, oz = 0;
   if (!WHOLE && bin < a.NT) {
     const int tz = bin % a.ntx, ty = (bin / a.ntx) % a.ntx, tx = bin / (a.ntx * a.ntx);
