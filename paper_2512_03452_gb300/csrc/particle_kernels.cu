@@ -176,6 +176,18 @@ constexpr int kWinMinLen = 64;
 // reductions of a warp hit contiguous nodes along the fastest axis.  Tile
 // windows of ints go 32 slots per warp pass in 16-byte pieces; whole-grid and
 // 64-bit windows one slot per thread.  (ox, oy, oz): node of slot (0,0,0).
+// A window node's 64-bit sum as T with one rounding.  Float: without a 64-bit
+// integer conversion (which runs on the slow FP64 pipe): the copies of an
+// int32 window sum to |v| < 2^34, so hi = v >> 16 and lo = v & 0xffff convert
+// exactly from 32-bit integers, hi * 2^16 is exact, and the fused add rounds
+// once.  Double (int64 windows): the plain conversion.
+template <typename T> __device__ __forceinline__ T sum_to_real(long long v);
+template <> __device__ __forceinline__ float sum_to_real<float>(long long v) {
+  const int hi = (int)(v >> 16), lo = (int)(v & 0xffff);
+  return __fmaf_rn((float)hi, 65536.0f, (float)lo);
+}
+template <> __device__ __forceinline__ double sum_to_real<double>(long long v) { return (double)v; }
+
 template <typename T, bool FIXED, bool WHOLE>
 __device__ __forceinline__ void window_flush(const BinArgs<T>& a, typename WinType<T>::type* win, int wslots, int ox,
                                              int oy, int oz, T wwin) {
@@ -213,7 +225,7 @@ __device__ __forceinline__ void window_flush(const BinArgs<T>& a, typename WinTy
         const int c = sidx % kWin, b = (sidx / kWin) % kWin, aa = sidx / (kWin * kWin);
         const int gi = (((ox + aa) & mask) * H + ((oy + b) & mask)) * H + ((oz + c) & mask);
         if (FIXED) atomicAdd(static_cast<unsigned long long*>(a.phi) + gi, (unsigned long long)(long long)v);
-        else atomicAdd(static_cast<T*>(a.phi) + gi, (T)v * unit);
+        else atomicAdd(static_cast<T*>(a.phi) + gi, sum_to_real<T>(v) * unit);
       }
     }
   } else {
@@ -241,7 +253,7 @@ __device__ __forceinline__ void window_flush(const BinArgs<T>& a, typename WinTy
           gi = (((ox + aa) & mask) * H + ((oy + b) & mask)) * H + ((oz + c) & mask);
         }
         if (FIXED) atomicAdd(static_cast<unsigned long long*>(a.phi) + gi, (unsigned long long)(long long)v);
-        else atomicAdd(static_cast<T*>(a.phi) + gi, (T)v * unit);
+        else atomicAdd(static_cast<T*>(a.phi) + gi, sum_to_real<T>(v) * unit);
       }
     }
   }
