@@ -464,6 +464,169 @@ __device__ __forceinline__ int zpad(int i) { return i + (i >> 5); }
 __device__ __forceinline__ int tpad(int j, int LD, int c) { return j * LD + (j >> 5) + c; }
 constexpr int padded_len(int n) { return n + n / 32; }
 
+// ===========================================================================
+// Group FFT (single precision).  A pencil of N = F Q points is transformed by
+// Q lanes of a warp holding F values each, so one warp takes 32 / Q pencils at
+// a time and the cross-lane part costs one exchange through shared memory
+// instead of five shuffle stages.  With n = q + Q m and k = k1 + F k2
+// (Cooley-Tukey):
+//   1. F-point DFT over m in registers (radix 2, constant twiddles);
+//   2. twiddle W_N^(q k1) from a lane-contiguous table;
+//   3. exchange through the pencil's own shared-memory slots: value (k1, q')
+//      goes to slot k1 Q + (q' ^ (k1 mod Q)); lane q then takes k1 = q + Q r
+//      (r < F / Q), reads its Q values and does the Q-point DFT over q' in
+//      registers.
+// Lane q then holds X[q + Q r + F k2] in register r Q + k2.  The XOR swizzle
+// keeps the exchange's stores (fixed k1, lanes q') and loads (fixed r and q',
+// lanes q) on distinct banks within a group.
+// ===========================================================================
+template <int N> struct GroupShape;
+template <> struct GroupShape<32> { static constexpr int F = 8, Q = 4; };
+template <> struct GroupShape<64> { static constexpr int F = 8, Q = 8; };
+template <> struct GroupShape<128> { static constexpr int F = 16, Q = 8; };
+template <> struct GroupShape<256> { static constexpr int F = 16, Q = 16; };
+// shared entries of a kernel's group-FFT twiddle table (single precision only)
+template <typename T, int N> constexpr int twq_len() { return sizeof(T) == 4 ? N : 0; }
+
+// v * W_16^t (forward: W = e^{-2 pi i / 16}; DIR > 0: the conjugate), t in
+// [0, 8) a compile-time constant after unrolling: the quarter and eighth turns
+// take no general product.
+template <typename T, int DIR>
+__device__ __forceinline__ cpx<T> rot16(cpx<T> v, int t) {
+  const T c1 = T(0.92387953251128674), s1 = T(0.38268343236508977), h = T(0.70710678118654752);
+  if (t == 0) return v;
+  if (t == 4) return DIR < 0 ? cpx<T>{v.y, -v.x} : cpx<T>{-v.y, v.x};
+  if (t == 2)
+    return DIR < 0 ? cpx<T>{t_mul_rn(h, v.x + v.y), t_mul_rn(h, v.y - v.x)}
+                   : cpx<T>{t_mul_rn(h, v.x - v.y), t_mul_rn(h, v.x + v.y)};
+  if (t == 6)
+    return DIR < 0 ? cpx<T>{t_mul_rn(h, v.y - v.x), -t_mul_rn(h, v.x + v.y)}
+                   : cpx<T>{-t_mul_rn(h, v.x + v.y), t_mul_rn(h, v.x - v.y)};
+  // odd t: cos and sin of 2 pi t / 16
+  const T cs = (t == 1 || t == 7) ? c1 : s1, sn = (t == 1 || t == 7) ? s1 : c1;
+  const T wr = t < 4 ? cs : -cs, wi = DIR < 0 ? -sn : sn;
+  return cmul(v, cpx<T>{wr, wi});
+}
+
+__host__ __device__ constexpr int brev_c(int i, int lg) {
+  int r = 0;
+  for (int b = 0; b < lg; ++b) r |= ((i >> b) & 1) << (lg - 1 - b);
+  return r;
+}
+
+// n-point DFT (n = 2, 4, 8, 16) of v[OFF .. OFF + n) in registers, natural
+// order in and out: radix-2 decimation in time over the bit-reversed inputs.
+template <typename T, int n, int DIR, int OFF, int LEN>
+__device__ __forceinline__ void reg_fft(cpx<T> (&v)[LEN]) {
+  constexpr int LG = n == 2 ? 1 : n == 4 ? 2 : n == 8 ? 3 : 4;
+  cpx<T> a[n];
+#pragma unroll
+  for (int i = 0; i < n; ++i) a[brev_c(i, LG)] = v[OFF + i];
+#pragma unroll
+  for (int h = 1; h < n; h <<= 1)
+#pragma unroll
+    for (int g = 0; g < n; g += 2 * h)
+#pragma unroll
+      for (int k = 0; k < h; ++k) {
+        const cpx<T> b = rot16<T, DIR>(a[g + k + h], k * (8 / h));   // W_{2h}^k = W_16^(8 k / h)
+        const cpx<T> u = a[g + k];
+        a[g + k] = cadd(u, b);
+        a[g + k + h] = csub(u, b);
+      }
+#pragma unroll
+  for (int i = 0; i < n; ++i) v[OFF + i] = a[i];
+}
+
+// The group FFT's twiddle table: twq[k1 Q + q] = W_N^(q k1), N entries.
+template <typename T, int N> __device__ __forceinline__ void load_twq(cpx<T>* twq) {
+  constexpr int Q = GroupShape<N>::Q;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const int k1 = i / Q, q = i - k1 * Q;
+    const int m = (q * k1 * (kNmax / N)) & (kNmax - 1);
+    twq[i] = cpx<T>{(T)g_twiddle[m].x, (T)g_twiddle[m].y};
+  }
+}
+
+// One pencil on the Q lanes of a group (q: lane within the group; mask: the
+// lanes of the warp taking part).  On entry v[m] = x[q + Q m]; on return
+// v[r Q + k2] = X[q + Q r + F k2].  slot(j) points at the pencil's element j
+// in shared memory; its inputs must already be in registers (the slots are
+// overwritten by the exchange), and every lane has finished with the slots
+// when this returns.
+template <typename T, int N, int DIR, typename Slot>
+__device__ __forceinline__ void group_fft(cpx<T> (&v)[GroupShape<N>::F], int q, const cpx<T>* twq, unsigned mask,
+                                          Slot slot) {
+  constexpr int F = GroupShape<N>::F, Q = GroupShape<N>::Q, R = F / Q;
+  reg_fft<T, F, DIR, 0>(v);
+#pragma unroll
+  for (int k1 = 1; k1 < F; ++k1) {
+    cpx<T> w = twq[k1 * Q + q];
+    if (DIR > 0) w.y = -w.y;
+    v[k1] = cmul(v[k1], w);
+  }
+  __syncwarp(mask);
+#pragma unroll
+  for (int k1 = 0; k1 < F; ++k1) *slot(k1 * Q + (q ^ (k1 & (Q - 1)))) = v[k1];
+  __syncwarp(mask);
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v[r * Q + i] = *slot((q + Q * r) * Q + (i ^ q));
+  __syncwarp(mask);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    if (r == 0) reg_fft<T, Q, DIR, 0>(v);
+    if (r == 1) reg_fft<T, Q, DIR, Q>(v);
+    if (r == 2) reg_fft<T, Q, DIR, 2 * Q>(v);
+    if (r == 3) reg_fft<T, Q, DIR, 3 * Q>(v);
+  }
+}
+
+// In-place FFTs of P pencils in shared memory (element j of pencil p at
+// at(p, j); pencils with ok(p) false are left alone), spread over the block's
+// warps.  Single precision: group FFTs, the G = 32 / Q pencils of warp task t
+// at p = t, t + T, t + 2T, ...; with T = 16/G mod 32/G and pencils one bank
+// apart (consecutive columns of a tile) the G groups start 16/G banks apart,
+// so a warp's 8-byte accesses take two wavefronts.  Double precision: one
+// pencil per warp (warp_fft).
+template <typename T, int N, int DIR, typename At, typename Ok>
+__device__ __forceinline__ void tile_ffts(int P, const cpx<T>* tw, const cpx<T>* twq, At at, Ok ok) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  if constexpr (sizeof(T) == 4) {
+    constexpr int F = GroupShape<N>::F, Q = GroupShape<N>::Q, G = 32 / Q;
+    const int g = lane / Q, q = lane & (Q - 1);
+    constexpr int MOD = 32 / G, RES = 16 / G;
+    int ntask = (P + G - 1) / G;
+    ntask += ((RES - ntask) % MOD + MOD) % MOD;   // ntask = RES (mod MOD)
+    for (int t = wib; t < ntask; t += nw) {
+      const int p = t + ntask * g;
+      const bool valid = p < P && ok(p);
+      const unsigned mask = __ballot_sync(0xffffffffu, valid);
+      if (valid) {
+        cpx<T> v[F];
+#pragma unroll
+        for (int m = 0; m < F; ++m) v[m] = *at(p, q + Q * m);
+        group_fft<T, N, DIR>(v, q, twq, mask, [&](int j) { return at(p, j); });
+#pragma unroll
+        for (int r = 0; r < F / Q; ++r)
+#pragma unroll
+          for (int k2 = 0; k2 < Q; ++k2) *at(p, q + Q * r + F * k2) = v[r * Q + k2];
+      }
+    }
+  } else {
+    constexpr int E = N / 32;
+    for (int p = wib; p < P; p += nw) {
+      if (!ok(p)) continue;
+      cpx<T> v[E];
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = *at(p, lane + 32 * m);
+      warp_fft<T, E, DIR>(v, lane, tw);
+#pragma unroll
+      for (int k1 = 0; k1 < E; ++k1) *at(p, out_index(k1, E, lane)) = v[k1];
+    }
+  }
+}
+
 template <typename T, int E> __device__ __forceinline__ void load_tw_full(cpx<T>* tw) {
   constexpr int SC = kNmax / (32 * E);
   for (int i = threadIdx.x; i < kNmax + 32 * E; i += blockDim.x) {
@@ -481,6 +644,15 @@ template <typename T, int E> __device__ __forceinline__ void load_tw_full(cpx<T>
     tw[i] = cpx<T>{(T)g_twiddle[m].x, (T)g_twiddle[m].y};
   }
 }
+
+// Shared twiddles of a kernel whose column passes use tile_ffts: the warp
+// FFT's tables (kTwLen entries), then, in single precision, the group FFT's.
+template <typename T, int E> constexpr int tw_len() { return kTwLen + twq_len<T, 32 * E>(); }
+template <typename T, int E> __device__ __forceinline__ void load_tw_group(cpx<T>* tw) {
+  load_tw_full<T, E>(tw);
+  if constexpr (sizeof(T) == 4) load_twq<T, 32 * E>(tw + kTwLen);
+}
+
 
 // Kernel bodies take their arrays and block coordinates explicitly so the same
 // code serves one run (the __global__ wrappers below) and a batch of runs
@@ -559,21 +731,14 @@ template <typename T, int E, int DIR, int BC>
 __device__ __forceinline__ void cols_body(cpx<T>* __restrict__ base, int B, T scale, int b0, const cpx<T>* tw,
                                           cpx<T>* buf) {
   constexpr int N = 32 * E, LD = BC + 1;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int nb = min(BC, B - b0);
   for (int t = threadIdx.x; t < N * BC; t += blockDim.x) {
     const int j = t / BC, c = t - j * BC;
     buf[tpad(j, LD, c)] = c < nb ? base[(size_t)j * B + b0 + c] : cpx<T>{T(0), T(0)};
   }
   __syncthreads();
-  for (int c = wib; c < nb; c += (int)(blockDim.x >> 5)) {
-    cpx<T> v[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = buf[tpad(lane + 32 * m, LD, c)];
-    warp_fft<T, E, DIR>(v, lane, tw);
-#pragma unroll
-    for (int k1 = 0; k1 < E; ++k1) buf[tpad(out_index(k1, E, lane), LD, c)] = v[k1];
-  }
+  tile_ffts<T, N, DIR>(nb, tw, tw + kTwLen, [&](int p, int j) { return buf + tpad(j, LD, p); },
+                       [](int) { return true; });
   __syncthreads();
   for (int t = threadIdx.x; t < N * BC; t += blockDim.x) {
     const int j = t / BC, c = t - j * BC;
@@ -589,9 +754,9 @@ __global__ void __launch_bounds__(256)
 kw_cols(cpx<T>* __restrict__ data, int B, size_t comp_stride, T scale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  load_tw_full<T, E>(tw);
+  load_tw_group<T, E>(tw);
   cpx<T>* base = data + blockIdx.z * comp_stride + (size_t)blockIdx.y * (32 * E) * B;
-  cols_body<T, E, DIR, BC>(base, B, scale, blockIdx.x * BC, tw, tw + kTwLen);
+  cols_body<T, E, DIR, BC>(base, B, scale, blockIdx.x * BC, tw, tw + tw_len<T, E>());
 }
 
 // x-axis pass fused with the spectral work (as k_spectral_x), warp FFTs.
@@ -601,9 +766,8 @@ kw_cols(cpx<T>* __restrict__ data, int B, size_t comp_stride, T scale) {
 template <typename T, int E, int MODE, int BC>
 __device__ __forceinline__ void spectral_body(const cpx<T>* __restrict__ T1, cpx<T>* __restrict__ alpha,
                                               cpx<T>* __restrict__ T2, const SpecParams& sp, double* alpha0_shadow,
-                                              int b0, const cpx<T>* tw, cpx<T>* buf) {
+                                              int b0, const cpx<T>* tw, const cpx<T>* twq, cpx<T>* buf) {
   constexpr int N = 32 * E, NHH = N / 2 + 1, LD = 3 * BC + 1;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int B = N * NHH;
   const size_t S = (size_t)N * B;
   const int nb = min(BC, B - b0);
@@ -614,14 +778,7 @@ __device__ __forceinline__ void spectral_body(const cpx<T>* __restrict__ T1, cpx
       buf[tpad(j, LD, c)] = c < nb ? T1[(size_t)j * B + b0 + c] : cpx<T>{T(0), T(0)};
     }
     __syncthreads();
-    for (int c = wib; c < nb; c += (int)(blockDim.x >> 5)) {
-      cpx<T> v[E];
-#pragma unroll
-      for (int m = 0; m < E; ++m) v[m] = buf[tpad(lane + 32 * m, LD, c)];
-      warp_fft<T, E, -1>(v, lane, tw);
-#pragma unroll
-      for (int k1 = 0; k1 < E; ++k1) buf[tpad(out_index(k1, E, lane), LD, c)] = v[k1];
-    }
+    tile_ffts<T, N, -1>(nb, tw, twq, [&](int p, int j) { return buf + tpad(j, LD, p); }, [](int) { return true; });
   }
   __syncthreads();
   const T two_pi_L = (T)(2.0 * M_PI / sp.L);
@@ -682,16 +839,8 @@ __device__ __forceinline__ void spectral_body(const cpx<T>* __restrict__ T1, cpx
   }
   __syncthreads();
   constexpr int nout = (MODE == kModeStep || MODE == kModeGradOnly) ? 3 : 1;
-  for (int col = wib; col < nout * BC; col += (int)(blockDim.x >> 5)) {
-    const int c = col;
-    if (col % BC >= nb) continue;
-    cpx<T> v[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = buf[tpad(lane + 32 * m, LD, c)];
-    warp_fft<T, E, +1>(v, lane, tw);
-#pragma unroll
-    for (int k1 = 0; k1 < E; ++k1) buf[tpad(out_index(k1, E, lane), LD, c)] = v[k1];
-  }
+  tile_ffts<T, N, +1>(nout * BC, tw, twq, [&](int p, int j) { return buf + tpad(j, LD, p); },
+                      [&](int p) { return p % BC < nb; });
   __syncthreads();
   for (int t = threadIdx.x; t < N * BC; t += blockDim.x) {
     const int j = t / BC, c = t - j * BC;
@@ -702,6 +851,163 @@ __device__ __forceinline__ void spectral_body(const cpx<T>* __restrict__ T1, cpx
   }
 }
 
+// ---------------------------------------------------------------------------
+// Single-precision x pass in registers.  A warp takes G = 32 / Q consecutive
+// pencils (m0 .. m0 + G - 1, x along each; element j of pencil m at j B + m);
+// lane q of group g keeps its pencil's elements j = q + Q s (s < F) in
+// registers from the global load, through the forward group FFT, the
+// spectral update and the inverse group FFTs to the global store, so no
+// block-wide barrier is needed.  The old alpha comes in by cp.async into a
+// per-warp slot while beta is transformed.  The three gradient spectra take
+// two inverse transforms: q_y and q_z are constant along an x pencil, so
+// G_y and G_z are i (2 pi q_d / L) times the x-inverse of Phi alpha; only
+// G_x needs its own.
+// ---------------------------------------------------------------------------
+template <int N> struct XRegShape {
+  static constexpr int F = GroupShape<N>::F, Q = GroupShape<N>::Q, G = 32 / Q;
+  static constexpr int PS = N + 16 / G;     // pencil stride in a warp slot: the G pencils start 16/G banks apart
+  static constexpr int WARP = 2 * G * PS;   // complex entries per warp: exchange slots + alpha slots
+  static constexpr int TASKS = N * (N / 2 + 1) / G;
+  static_assert(N * (N / 2 + 1) % G == 0, "x pencils come in whole groups");
+};
+template <int N> constexpr size_t xreg_smem_bytes(int nw) {
+  return ((size_t)N + (size_t)nw * XRegShape<N>::WARP) * sizeof(cpx<float>);
+}
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <int N, int MODE>
+__device__ __forceinline__ void spectral_reg_task(const cpx<float>* __restrict__ T1, cpx<float>* __restrict__ alpha,
+                                                  cpx<float>* __restrict__ T2, const SpecParams& sp,
+                                                  double* alpha0_shadow, int m0, const cpx<float>* twq,
+                                                  cpx<float>* wslot) {
+  using S = XRegShape<N>;
+  constexpr int F = S::F, Q = S::Q, R = F / Q, NHH = N / 2 + 1, B = N * NHH;
+  constexpr size_t SZ = (size_t)N * B;
+  constexpr bool reads_alpha = MODE != kModeDensity;
+  constexpr bool needs_beta = MODE == kModeStep || MODE == kModeDensity;
+  constexpr bool grad = MODE == kModeStep || MODE == kModeGradOnly;
+  const int lane = threadIdx.x & 31, g = lane / Q, q = lane & (Q - 1);
+  const int m = m0 + g;
+  cpx<float>* X = wslot + g * S::PS;              // this pencil's exchange slots
+  cpx<float>* A = wslot + (S::G + g) * S::PS;     // its old alpha, then Phi alpha
+  auto xs = [X](int j) { return X + j; };
+  if (reads_alpha) {
+#pragma unroll
+    for (int s = 0; s < F; ++s) cp_async8(A + q + Q * s, alpha + (size_t)(q + Q * s) * B + m);
+  }
+  const int ky = m / NHH, kz = m - ky * NHH;
+  const int qy = ky < N / 2 ? ky : ky - N, qz = kz < N / 2 ? kz : kz - N;
+  const float two_pi_L = (float)(2.0 * M_PI / sp.L);
+  const float inv_L3 = (float)sp.inv_L3;
+  const float tau_eps = (float)(sp.tau / sp.eps), eps_tau = (float)(sp.eps / sp.tau), k2 = (float)sp.k2,
+              tau = (float)sp.tau;
+  const float filt = sp.H0 > 0 ? (float)(-2.0 * M_PI * M_PI / (sp.H0 * sp.H0)) : 0.f;
+  cpx<float> v[F];
+  if (needs_beta) {
+#pragma unroll
+    for (int s = 0; s < F; ++s) v[s] = T1[(size_t)(q + Q * s) * B + m];
+    group_fft<float, N, -1>(v, q, twq, 0xffffffffu, xs);   // v[r Q + k2] = beta^[q + Q (r + R k2)]
+  }
+  if (reads_alpha) cp_async_wait_all();
+  cpx<float> w[F];   // the first inverse transform's input, element q + Q s at w[s]
+#pragma unroll
+  for (int s = 0; s < F; ++s) {
+    const int j = q + Q * s;
+    const int qx = j < N / 2 ? j : j - N;
+    const float q2 = (float)(qx * qx + qy * qy + qz * qz);
+    const float Phi = sp.H0 > 0 ? expf(filt * q2) : 1.f;
+    cpx<float> o1{0.f, 0.f};
+    if (grad) {
+      const cpx<float> a = A[q + Q * s];
+      if (MODE == kModeStep) {
+        cpx<float> beta = v[(s % R) * Q + s / R];
+        beta.x *= inv_L3;
+        beta.y *= inv_L3;
+        const float lam = two_pi_L * two_pi_L * q2 + k2;
+        cpx<float> an;
+        if (sp.propagator == 0) {
+          const float kappa = 1.f / (1.f + tau_eps * lam);
+          const float src = 1.f / (lam + eps_tau);
+          an = cpx<float>{kappa * a.x + src * beta.x, kappa * a.y + src * beta.y};
+        } else {
+          const float kappa = expf(-tau_eps * lam);
+          an = cpx<float>{kappa * (a.x + tau * beta.x), kappa * (a.y + tau * beta.y)};
+        }
+        alpha[(size_t)j * B + m] = an;
+        if (m == 0 && j == 0 && alpha0_shadow) {
+          const double lam0 = sp.k2;
+          double sh = *alpha0_shadow;
+          if (sp.propagator == 0) sh = sh / (1.0 + sp.tau / sp.eps * lam0) + sp.beta0 / (lam0 + sp.eps / sp.tau);
+          else sh = exp(-sp.tau / sp.eps * lam0) * (sh + sp.tau * sp.beta0);
+          *alpha0_shadow = sh;
+        }
+      }
+      const float yx = two_pi_L * (float)qx * Phi;
+      if (qx != -N / 2) o1 = cpx<float>{-yx * a.y, yx * a.x};
+      A[q + Q * s] = cpx<float>{Phi * a.x, Phi * a.y};
+    } else if (MODE == kModeDensity) {
+      const cpx<float> beta = v[(s % R) * Q + s / R];
+      o1 = cpx<float>{beta.x * inv_L3 * Phi, beta.y * inv_L3 * Phi};
+    } else {
+      o1 = A[q + Q * s];
+    }
+    w[s] = o1;
+  }
+  group_fft<float, N, +1>(w, q, twq, 0xffffffffu, xs);
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int k = 0; k < Q; ++k) T2[(size_t)(q + Q * (r + R * k)) * B + m] = w[r * Q + k];
+  if (grad) {
+#pragma unroll
+    for (int s = 0; s < F; ++s) w[s] = A[q + Q * s];
+    group_fft<float, N, +1>(w, q, twq, 0xffffffffu, xs);
+    const float cy = qy != -N / 2 ? two_pi_L * (float)qy : 0.f, cz = qz != -N / 2 ? two_pi_L * (float)qz : 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int k = 0; k < Q; ++k) {
+        const size_t gi = (size_t)(q + Q * (r + R * k)) * B + m;
+        const cpx<float> u = w[r * Q + k];
+        T2[SZ + gi] = cpx<float>{-cy * u.y, cy * u.x};
+        T2[2 * SZ + gi] = cpx<float>{-cz * u.y, cz * u.x};
+      }
+  }
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(256)
+kwr_spectral_x(const cpx<float>* __restrict__ T1, cpx<float>* __restrict__ alpha, cpx<float>* __restrict__ T2,
+               SpecParams sp, double* alpha0_shadow) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<float>* twq = reinterpret_cast<cpx<float>*>(smem_raw);
+  load_twq<float, N>(twq);
+  __syncthreads();
+  const int wib = threadIdx.x >> 5;
+  const int t = blockIdx.x * (int)(blockDim.x >> 5) + wib;
+  if (t < XRegShape<N>::TASKS)
+    spectral_reg_task<N, MODE>(T1, alpha, T2, sp, alpha0_shadow, t * XRegShape<N>::G, twq,
+                               twq + N + wib * XRegShape<N>::WARP);
+}
+
+template <int N>
+__global__ void __launch_bounds__(512) kwrb_spectral_x(const FftRun<float>* __restrict__ runs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<float>* twq = reinterpret_cast<cpx<float>*>(smem_raw);
+  load_twq<float, N>(twq);
+  __syncthreads();
+  const FftRun<float>& r = runs[blockIdx.y];
+  const int wib = threadIdx.x >> 5;
+  const int t = blockIdx.x * (int)(blockDim.x >> 5) + wib;
+  if (t < XRegShape<N>::TASKS)
+    spectral_reg_task<N, kModeStep>(r.T1, r.alpha, r.T2, r.sp, r.shadow, t * XRegShape<N>::G, twq,
+                                    twq + N + wib * XRegShape<N>::WARP);
+}
+
 template <typename T, int E, int MODE, int BC>
 __global__ void __launch_bounds__(256)
 kw_spectral_x(const cpx<T>* __restrict__ T1, cpx<T>* __restrict__ alpha, cpx<T>* __restrict__ T2, SpecParams sp,
@@ -709,7 +1015,10 @@ kw_spectral_x(const cpx<T>* __restrict__ T1, cpx<T>* __restrict__ alpha, cpx<T>*
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
   load_tw_full<T, E>(tw);
-  spectral_body<T, E, MODE, BC>(T1, alpha, T2, sp, alpha0_shadow, blockIdx.x * BC, tw, tw + kTwLen);
+  cpx<T>* twq = tw + kTwLen;
+  if constexpr (sizeof(T) == 4) load_twq<T, 32 * E>(twq);
+  spectral_body<T, E, MODE, BC>(T1, alpha, T2, sp, alpha0_shadow, blockIdx.x * BC, tw, twq,
+                                twq + twq_len<T, 32 * E>());
 }
 
 // Rows c2r: each warp takes a row pair of every component, rebuilds the
@@ -820,13 +1129,13 @@ template <typename T, int E, int DIR, int BC>
 __global__ void __launch_bounds__(256) kwb_cols(const FftRun<T>* __restrict__ runs, int ncomp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  load_tw_full<T, E>(tw);
+  load_tw_group<T, E>(tw);
   constexpr int N = 32 * E, NHH = N / 2 + 1;
   const int run = blockIdx.z / ncomp, comp = blockIdx.z - run * ncomp;
   const FftRun<T>& r = runs[run];
   const size_t S = (size_t)N * N * NHH;
   cpx<T>* data = DIR < 0 ? r.T1 : r.T2 + comp * S;
-  cols_body<T, E, DIR, BC>(data + (size_t)blockIdx.y * N * NHH, NHH, T(1), blockIdx.x * BC, tw, tw + kTwLen);
+  cols_body<T, E, DIR, BC>(data + (size_t)blockIdx.y * N * NHH, NHH, T(1), blockIdx.x * BC, tw, tw + tw_len<T, E>());
 }
 
 template <typename T, int E, int BC>
@@ -834,8 +1143,11 @@ __global__ void __launch_bounds__(512) kwb_spectral_x(const FftRun<T>* __restric
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
   load_tw_full<T, E>(tw);
+  cpx<T>* twq = tw + kTwLen;
+  if constexpr (sizeof(T) == 4) load_twq<T, 32 * E>(twq);
   const FftRun<T>& r = runs[blockIdx.y];
-  spectral_body<T, E, kModeStep, BC>(r.T1, r.alpha, r.T2, r.sp, r.shadow, blockIdx.x * BC, tw, tw + kTwLen);
+  spectral_body<T, E, kModeStep, BC>(r.T1, r.alpha, r.T2, r.sp, r.shadow, blockIdx.x * BC, tw, twq,
+                                     twq + twq_len<T, 32 * E>());
 }
 
 template <typename T, int E>
@@ -868,7 +1180,7 @@ constexpr int kDefaultSpectralWarps = 8;   // warps per block of the fused x pas
 
 template <typename T, int E> constexpr size_t plane_smem_bytes(int nw) {
   // plane: H rows of H/2+1 plus one slot per 32 rows; one padded pencil per warp
-  return ((size_t)32 * E * (16 * E + 1) + E + (size_t)nw * padded_len(32 * E) + kTwLen) * sizeof(cpx<T>);
+  return ((size_t)32 * E * (16 * E + 1) + E + (size_t)nw * padded_len(32 * E) + tw_len<T, E>()) * sizeof(cpx<T>);
 }
 
 template <typename T, int E, typename Tin>
@@ -935,15 +1247,9 @@ __device__ __forceinline__ void plane_fwd_body(Tin* __restrict__ in, double in_s
     __syncwarp();
   }
   __syncthreads();
-  // 2. y axis: one column per warp
-  for (int c = wib; c < NH; c += (int)(blockDim.x >> 5)) {
-    cpx<T> v[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = P[tpad(lane + 32 * m, NH, c)];
-    warp_fft<T, E, -1>(v, lane, tw);
-#pragma unroll
-    for (int k1 = 0; k1 < E; ++k1) P[tpad(out_index(k1, E, lane), NH, c)] = v[k1];
-  }
+  // 2. y axis: the plane's columns in place
+  tile_ffts<T, N, -1>(NH, tw, tw + kTwLen, [&](int p, int j) { return P + tpad(j, NH, p); },
+                      [](int) { return true; });
   __syncthreads();
   for (int t = threadIdx.x; t < N * NH; t += blockDim.x) out[t] = P[t + ((t / NH) >> 5)];
 }
@@ -956,15 +1262,9 @@ __device__ __forceinline__ void plane_inv_body(const cpx<T>* __restrict__ in, T*
   cpx<T>* zb = zball + wib * padded_len(N);
   for (int t = threadIdx.x; t < N * NH; t += blockDim.x) P[t + ((t / NH) >> 5)] = in[t];
   __syncthreads();
-  // 1. y axis inverse: one column per warp
-  for (int c = wib; c < NH; c += (int)(blockDim.x >> 5)) {
-    cpx<T> v[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = P[tpad(lane + 32 * m, NH, c)];
-    warp_fft<T, E, +1>(v, lane, tw);
-#pragma unroll
-    for (int k1 = 0; k1 < E; ++k1) P[tpad(out_index(k1, E, lane), NH, c)] = v[k1];
-  }
+  // 1. y axis inverse: the plane's columns in place
+  tile_ffts<T, N, +1>(NH, tw, tw + kTwLen, [&](int p, int j) { return P + tpad(j, NH, p); },
+                      [](int) { return true; });
   __syncthreads();
   // 2. rows: two Hermitian half rows A, B as the pencil A + i B; the inverse
   //    transform's real part is row A, its imaginary part row B
@@ -1007,9 +1307,9 @@ __global__ void __launch_bounds__(1024) kwp_fwd(const FftRun<T>* __restrict__ ru
   constexpr int N = 32 * E, NH = N / 2 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* zb = tw + kTwLen;
+  cpx<T>* zb = tw + tw_len<T, E>();
   cpx<T>* P = zb + (blockDim.x >> 5) * padded_len(N);
-  load_tw_full<T, E>(tw);
+  load_tw_group<T, E>(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.y];
   const int x = blockIdx.x;
@@ -1026,9 +1326,9 @@ __global__ void __launch_bounds__(1024) kwp_inv(const FftRun<T>* __restrict__ ru
   constexpr int N = 32 * E, NH = N / 2 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* zb = tw + kTwLen;
+  cpx<T>* zb = tw + tw_len<T, E>();
   cpx<T>* P = zb + (blockDim.x >> 5) * padded_len(N);
-  load_tw_full<T, E>(tw);
+  load_tw_group<T, E>(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.z];
   const int x = blockIdx.x, d = blockIdx.y;
@@ -1043,7 +1343,7 @@ __global__ void __launch_bounds__(1024) kwp_inv(const FftRun<T>* __restrict__ ru
 // (the per-component kernel writes each node's sector three times in part,
 // which costs a DRAM read per sector once the nodes exceed L2).
 template <typename T, int E> constexpr size_t plane3_smem_bytes(int nw) {
-  return ((size_t)kTwLen + (size_t)nw * padded_len(32 * E) + 3 * ((size_t)32 * E * (16 * E + 1) + E)) * sizeof(cpx<T>) +
+  return ((size_t)tw_len<T, E>() + (size_t)nw * padded_len(32 * E) + 3 * ((size_t)32 * E * (16 * E + 1) + E)) * sizeof(cpx<T>) +
          (size_t)nw * 3 * padded_len(64 * E) * sizeof(T);
 }
 
@@ -1068,16 +1368,11 @@ __device__ __forceinline__ void plane_inv3_body(const cpx<T>* __restrict__ in, s
   for (int d = 0; d < 3; ++d)
     for (int t = threadIdx.x; t < N * NH; t += blockDim.x) P[d * PL + t + ((t / NH) >> 5)] = in[d * S + t];
   __syncthreads();
-  // 1. y axis inverse: one (component, column) per warp
-  for (int c = wib; c < 3 * NH; c += nw) {
-    const int d = c / NH, col = c - d * NH;
+  // 1. y axis inverse: the three planes' columns in place
+  for (int d = 0; d < 3; ++d) {
     cpx<T>* Pd = P + d * PL;
-    cpx<T> v[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = Pd[tpad(lane + 32 * m, NH, col)];
-    warp_fft<T, E, +1>(v, lane, tw);
-#pragma unroll
-    for (int k1 = 0; k1 < E; ++k1) Pd[tpad(out_index(k1, E, lane), NH, col)] = v[k1];
+    tile_ffts<T, N, +1>(NH, tw, tw + kTwLen, [&](int p, int j) { return Pd + tpad(j, NH, p); },
+                        [](int) { return true; });
   }
   __syncthreads();
   // 2. rows: per component, the two Hermitian half rows A, B as the pencil
@@ -1126,10 +1421,10 @@ __global__ void __launch_bounds__(1024) kwp_inv3(const FftRun<T>* __restrict__ r
   constexpr int N = 32 * E, NH = N / 2 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* zb = tw + kTwLen;
+  cpx<T>* zb = tw + tw_len<T, E>();
   cpx<T>* P = zb + (blockDim.x >> 5) * padded_len(N);
   T* ob = reinterpret_cast<T*>(P + 3 * ((size_t)N * NH + E));
-  load_tw_full<T, E>(tw);
+  load_tw_group<T, E>(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.y];
   const int x = blockIdx.x;
@@ -1164,7 +1459,8 @@ template <int N, int CS> struct ColSplit {
 
 template <typename T, int E, int CS> constexpr size_t cplane_smem_bytes(int nw) {
   // column block: H rows of CP plus one slot per 32 rows; one padded pencil per warp
-  return ((size_t)32 * E * ColSplit<32 * E, CS>::LD + E + (size_t)nw * padded_len(32 * E) + kTwLen) * sizeof(cpx<T>);
+  return ((size_t)32 * E * ColSplit<32 * E, CS>::LD + E + (size_t)nw * padded_len(32 * E) + tw_len<T, E>()) *
+         sizeof(cpx<T>);
 }
 
 template <typename T, int E, int CS, typename Tin>
@@ -1220,14 +1516,8 @@ __device__ __forceinline__ void cplane_fwd_body(Tin* __restrict__ in, double in_
   cluster.sync();
   // 2. y axis of this CTA's columns
   const int c0 = CSp::first(rank), nc = CSp::count(rank);
-  for (int c = wib; c < nc; c += nw) {
-    cpx<T> v[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = Q[tpad(lane + 32 * m, LD, c)];
-    warp_fft<T, E, -1>(v, lane, tw);
-#pragma unroll
-    for (int k1 = 0; k1 < E; ++k1) Q[tpad(out_index(k1, E, lane), LD, c)] = v[k1];
-  }
+  tile_ffts<T, N, -1>(nc, tw, tw + kTwLen, [&](int p, int j) { return Q + tpad(j, LD, p); },
+                      [](int) { return true; });
   __syncthreads();
   for (int t = threadIdx.x; t < N * nc; t += blockDim.x) {
     const int j = t / nc, c = t - j * nc;
@@ -1253,14 +1543,8 @@ __device__ __forceinline__ void cplane_inv_body(const cpx<T>* __restrict__ in, T
   }
   __syncthreads();
   // 1. y-axis inverse of this CTA's columns
-  for (int c = wib; c < nc; c += nw) {
-    cpx<T> v[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = Q[tpad(lane + 32 * m, LD, c)];
-    warp_fft<T, E, +1>(v, lane, tw);
-#pragma unroll
-    for (int k1 = 0; k1 < E; ++k1) Q[tpad(out_index(k1, E, lane), LD, c)] = v[k1];
-  }
+  tile_ffts<T, N, +1>(nc, tw, tw + kTwLen, [&](int p, int j) { return Q + tpad(j, LD, p); },
+                      [](int) { return true; });
   cluster.sync();
   const cpx<T>* peer[CS];
 #pragma unroll
@@ -1306,9 +1590,9 @@ __global__ void __launch_bounds__(1024) kwc_fwd(const FftRun<T>* __restrict__ ru
   constexpr int N = 32 * E, NH = N / 2 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* zb = tw + kTwLen;
+  cpx<T>* zb = tw + tw_len<T, E>();
   cpx<T>* Q = zb + (blockDim.x >> 5) * padded_len(N);
-  load_tw_full<T, E>(tw);
+  load_tw_group<T, E>(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.y];
   const int x = blockIdx.x / CS;
@@ -1325,9 +1609,9 @@ __global__ void __launch_bounds__(1024) kwc_inv(const FftRun<T>* __restrict__ ru
   constexpr int N = 32 * E, NH = N / 2 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* zb = tw + kTwLen;
+  cpx<T>* zb = tw + tw_len<T, E>();
   cpx<T>* Q = zb + (blockDim.x >> 5) * padded_len(N);
-  load_tw_full<T, E>(tw);
+  load_tw_group<T, E>(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.z];
   const int x = blockIdx.x / CS, d = blockIdx.y;
@@ -1373,7 +1657,7 @@ static cudaError_t warp_rows_r2c(const void* in, int in_kind, double in_scale, b
 template <typename T, int E, int DIR>
 static cudaError_t warp_cols(cpx<T>* data, int A, int B, int ncomp, size_t comp_stride, double scale, cudaStream_t s) {
   constexpr int BC = 16;
-  const size_t smem = (kTwLen + (size_t)32 * E * (BC + 1) + E) * sizeof(cpx<T>);
+  const size_t smem = (tw_len<T, E>() + (size_t)32 * E * (BC + 1) + E) * sizeof(cpx<T>);
   auto k = kw_cols<T, E, DIR, BC>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
@@ -1386,14 +1670,24 @@ template <typename T, int E, int MODE>
 static cudaError_t warp_spectral(const cpx<T>* T1, cpx<T>* alpha, cpx<T>* T2, SpecParams sp, double* shadow,
                                  cudaStream_t s) {
   constexpr int N = 32 * E;
+  if constexpr (sizeof(T) == 4 && N <= 128) {
+    constexpr int nw = 8;
+    const size_t smem = xreg_smem_bytes<N>(nw);
+    auto k = kwr_spectral_x<N, MODE>;
+    cudaError_t e = set_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    k<<<(XRegShape<N>::TASKS + nw - 1) / nw, 32 * nw, smem, s>>>(T1, alpha, T2, sp, shadow);
+    return cudaGetLastError();
+  } else {
   constexpr int BC = (sizeof(T) == 8 && E == 8) ? 4 : ((sizeof(T) == 8 || E == 8) ? 8 : 16);
   const int B = N * (N / 2 + 1);
-  const size_t smem = (kTwLen + (size_t)N * (3 * BC + 1) + E) * sizeof(cpx<T>);
+  const size_t smem = (kTwLen + twq_len<T, N>() + (size_t)N * (3 * BC + 1) + E) * sizeof(cpx<T>);
   auto k = kw_spectral_x<T, E, MODE, BC>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   k<<<(B + BC - 1) / BC, 256, smem, s>>>(T1, alpha, T2, sp, shadow);
   return cudaGetLastError();
+  }
 }
 
 template <typename T, int E, int NCOMP>
@@ -1570,11 +1864,11 @@ constexpr size_t kMaxSmem = 227 * 1024;
 
 template <typename T, int E, int BC>
 static size_t cols_smem() {
-  return (kTwLen + (size_t)32 * E * (BC + 1) + E) * sizeof(cpx<T>);
+  return (tw_len<T, E>() + (size_t)32 * E * (BC + 1) + E) * sizeof(cpx<T>);
 }
 template <typename T, int E, int SBC>
 static size_t spectral_smem() {
-  return (kTwLen + (size_t)32 * E * (3 * SBC + 1) + E) * sizeof(cpx<T>);
+  return (kTwLen + twq_len<T, 32 * E>() + (size_t)32 * E * (3 * SBC + 1) + E) * sizeof(cpx<T>);
 }
 
 template <typename T, int E, int DIR, int BC>
@@ -1600,12 +1894,20 @@ static cudaError_t kwb_cols_bc(const FftRun<T>* runs, int nruns, int ncomp, int 
 template <typename T, int E, int SBC>
 static cudaError_t kwb_spectral_launch(const FftRun<T>* runs, int nruns, int nw, cudaStream_t s) {
   constexpr int N = 32 * E, NHH = N / 2 + 1;
-  const size_t sms = spectral_smem<T, E, SBC>();
-  if (sms > kMaxSmem) return cudaErrorInvalidValue;
   cudaError_t e;
-  if ((e = set_smem(kwb_spectral_x<T, E, SBC>, sms)) != cudaSuccess) return e;
-  kwb_spectral_x<T, E, SBC><<<dim3((N * NHH + SBC - 1) / SBC, nruns), 32 * nw, sms, s>>>(runs);
-  return cudaGetLastError();
+  if constexpr (sizeof(T) == 4 && N <= 128) {
+    const size_t smr = xreg_smem_bytes<N>(nw);
+    if (smr > kMaxSmem) return cudaErrorInvalidValue;
+    if ((e = set_smem(kwrb_spectral_x<N>, smr)) != cudaSuccess) return e;
+    kwrb_spectral_x<N><<<dim3((XRegShape<N>::TASKS + nw - 1) / nw, nruns), 32 * nw, smr, s>>>(runs);
+    return cudaGetLastError();
+  } else {
+    const size_t sms = spectral_smem<T, E, SBC>();
+    if (sms > kMaxSmem) return cudaErrorInvalidValue;
+    if ((e = set_smem(kwb_spectral_x<T, E, SBC>, sms)) != cudaSuccess) return e;
+    kwb_spectral_x<T, E, SBC><<<dim3((N * NHH + SBC - 1) / SBC, nruns), 32 * nw, sms, s>>>(runs);
+    return cudaGetLastError();
+  }
 }
 
 // Default x-pass tile: as wide as shared memory comfortably allows.
