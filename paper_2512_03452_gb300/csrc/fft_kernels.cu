@@ -485,6 +485,14 @@ template <> struct GroupShape<32> { static constexpr int F = 8, Q = 4; };
 template <> struct GroupShape<64> { static constexpr int F = 8, Q = 8; };
 template <> struct GroupShape<128> { static constexpr int F = 16, Q = 8; };
 template <> struct GroupShape<256> { static constexpr int F = 16, Q = 16; };
+// shared stride of a group's pencil slot: the G = 32 / Q groups of a warp
+// then start 16 / G banks (of 8-byte entries) apart
+template <int N> constexpr int group_ps() { return N + 16 / (32 / GroupShape<N>::Q); }
+// Row passes (r2c / c2r of row pairs) by group FFTs: single precision at
+// N = 256 (measured faster there; at N <= 128 the warp FFT's rows, whose warp
+// loads and stores take whole 128-byte lines, measured faster).  Every kernel
+// of one grid size takes the same choice, so all its paths give the same bits.
+template <typename T, int N> constexpr bool group_rows() { return sizeof(T) == 4 && N == 256; }
 // shared entries of a kernel's group-FFT twiddle table (single precision only)
 template <typename T, int N> constexpr int twq_len() { return sizeof(T) == 4 ? N : 0; }
 
@@ -582,13 +590,142 @@ __device__ __forceinline__ void group_fft(cpx<T> (&v)[GroupShape<N>::F], int q, 
   }
 }
 
+// Task count for G pencils per warp task at pencil p = t + T g: the smallest
+// T >= ceil(P / G) with T * S16 = 16 / G (mod 16), where S16 is the shared
+// stride (complex entries, mod 16) between the storage of consecutive
+// pencils, so the G groups of a warp start 16 / G banks apart.
+template <int G>
+__device__ __forceinline__ int spread_tasks(int P, int S16) {
+  int t = (P + G - 1) / G;
+  if (G > 2 && (S16 & 15))
+    for (int i = 0; i < 16 && ((t * S16) & 15) != 16 / G; ++i) ++t;
+  return t;
+}
+
+// Per-warp scratch of the row kernels (complex entries): single precision,
+// one slot of XRegShape<N>::PS entries per group; double, one padded pencil.
+template <typename T, int N> constexpr int row_scratch() {
+  return group_rows<T, N>() ? (32 / GroupShape<N>::Q) * group_ps<N>() : N + N / 32;
+}
+
+// Row pairs r2c with group FFTs (single precision).  Pair pr: real rows 2 pr
+// and 2 pr + 1 read as one complex pencil z = a + i b (load(pr, j, a, b)),
+// transformed, and split into the half spectra A_k = (Z_k + conj Z_{N-k}) / 2
+// and B_k = -i (Z_k - conj Z_{N-k}) / 2, k <= N / 2, handed to
+// store(pr, k, A, B).  slot(pr, g) gives N shared entries for the pencil's
+// exchange and split; every Z is read before store is called, so the
+// destination rows themselves may serve.  S16: see spread_tasks.  (Staging
+// each warp's row pairs through shared memory with whole-warp loads instead
+// of the groups' 32-byte row segments measured slower.)
+template <typename T, int N, typename Load, typename Slot, typename Store>
+__device__ __forceinline__ void group_r2c_pairs(int npairs, int S16, const cpx<T>* twq, Load load, Slot slot,
+                                                Store store) {
+  constexpr int F = GroupShape<N>::F, Q = GroupShape<N>::Q, G = 32 / Q, R = F / Q, NH = N / 2 + 1;
+  constexpr int KI = (NH + Q - 1) / Q;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  const int g = lane / Q, q = lane & (Q - 1);
+  const int ntask = spread_tasks<G>(npairs, S16);
+  for (int t = wib; t < ntask; t += nw) {
+    const int pr = t + ntask * g;
+    const bool valid = pr < npairs;
+    const unsigned mask = __ballot_sync(0xffffffffu, valid);
+    if (valid) {
+      cpx<T> v[F];
+#pragma unroll
+      for (int m = 0; m < F; ++m) load(pr, q + Q * m, v[m].x, v[m].y);
+      cpx<T>* z = slot(pr, g);
+      group_fft<T, N, -1>(v, q, twq, mask, [z](int j) { return z + j; });
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) z[q + Q * r + F * k2] = v[r * Q + k2];
+      __syncwarp(mask);
+      cpx<T> zk[KI], zm[KI];
+#pragma unroll
+      for (int i = 0; i < KI; ++i) {
+        const int k = q + Q * i;
+        if (k < NH) {
+          zk[i] = z[k];
+          zm[i] = cconj(z[(N - k) & (N - 1)]);
+        }
+      }
+      __syncwarp(mask);
+#pragma unroll
+      for (int i = 0; i < KI; ++i) {
+        const int k = q + Q * i;
+        if (k < NH) {
+          const cpx<T> d = csub(zk[i], zm[i]);
+          store(pr, k, cpx<T>{(zk[i].x + zm[i].x) * T(0.5), (zk[i].y + zm[i].y) * T(0.5)},
+                cpx<T>{d.y * T(0.5), -d.x * T(0.5)});
+        }
+      }
+      __syncwarp(mask);
+    }
+  }
+}
+
+// Row pairs c2r with group FFTs (single precision).  Pair pr's Hermitian half
+// rows A (row 2 pr) and B (row 2 pr + 1), k <= N / 2, from half(pr, k, A, B),
+// become the pencil Z = A + i B (Z_k = A_k + i B_k, Z_{N-k} = conj A_k +
+// i conj B_k), whose inverse transform gives row 2 pr as its real part and
+// row 2 pr + 1 as its imaginary part: out(pr, j, re, im).  slot(pr, g): N
+// shared entries (every half value is read before the slot is written, so
+// the pair's own rows may serve).
+template <typename T, int N, typename Half, typename Slot, typename Out>
+__device__ __forceinline__ void group_c2r_pairs(int npairs, int S16, const cpx<T>* twq, Half half, Slot slot,
+                                                Out out) {
+  constexpr int F = GroupShape<N>::F, Q = GroupShape<N>::Q, G = 32 / Q, R = F / Q, NH = N / 2 + 1;
+  constexpr int KI = (NH + Q - 1) / Q;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  const int g = lane / Q, q = lane & (Q - 1);
+  const int ntask = spread_tasks<G>(npairs, S16);
+  for (int t = wib; t < ntask; t += nw) {
+    const int pr = t + ntask * g;
+    const bool valid = pr < npairs;
+    const unsigned mask = __ballot_sync(0xffffffffu, valid);
+    if (valid) {
+      cpx<T> a[KI], b[KI];
+#pragma unroll
+      for (int i = 0; i < KI; ++i) {
+        const int k = q + Q * i;
+        if (k < NH) half(pr, k, a[i], b[i]);
+      }
+      cpx<T>* z = slot(pr, g);
+      __syncwarp(mask);
+#pragma unroll
+      for (int i = 0; i < KI; ++i) {
+        const int k = q + Q * i;
+        if (k < NH) {
+          cpx<T> A = a[i], B = b[i];
+          if (k == 0 || k == N / 2) {
+            A.y = T(0);
+            B.y = T(0);
+          }
+          z[k] = cpx<T>{A.x - B.y, A.y + B.x};
+          if (k > 0 && k < N / 2) z[N - k] = cpx<T>{A.x + B.y, -A.y + B.x};   // conj A + i conj B
+        }
+      }
+      __syncwarp(mask);
+      cpx<T> v[F];
+#pragma unroll
+      for (int m = 0; m < F; ++m) v[m] = z[q + Q * m];
+      group_fft<T, N, +1>(v, q, twq, mask, [z](int j) { return z + j; });
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) out(pr, q + Q * r + F * k2, v[r * Q + k2].x, v[r * Q + k2].y);
+      __syncwarp(mask);
+    }
+  }
+}
+
 // In-place FFTs of P pencils in shared memory (element j of pencil p at
 // at(p, j); pencils with ok(p) false are left alone), spread over the block's
 // warps.  Single precision: group FFTs, the G = 32 / Q pencils of warp task t
 // at p = t, t + T, t + 2T, ...; with T = 16/G mod 32/G and pencils one bank
 // apart (consecutive columns of a tile) the G groups start 16/G banks apart,
-// so a warp's 8-byte accesses take two wavefronts.  Double precision: one
-// pencil per warp (warp_fft).
+// so a warp's 8-byte accesses take two wavefronts (for G = 2 they do at any
+// T).  Double precision: one pencil per warp (warp_fft).
 template <typename T, int N, int DIR, typename At, typename Ok>
 __device__ __forceinline__ void tile_ffts(int P, const cpx<T>* tw, const cpx<T>* twq, At at, Ok ok) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
@@ -597,7 +734,8 @@ __device__ __forceinline__ void tile_ffts(int P, const cpx<T>* tw, const cpx<T>*
     const int g = lane / Q, q = lane & (Q - 1);
     constexpr int MOD = 32 / G, RES = 16 / G;
     int ntask = (P + G - 1) / G;
-    ntask += ((RES - ntask) % MOD + MOD) % MOD;   // ntask = RES (mod MOD)
+    // ntask = RES (mod MOD); two groups (N = 256) take two wavefronts anyway
+    if (G > 2) ntask += ((RES - ntask) % MOD + MOD) % MOD;
     for (int t = wib; t < ntask; t += nw) {
       const int p = t + ntask * g;
       const bool valid = p < P && ok(p);
@@ -662,12 +800,40 @@ template <typename T, int E> __device__ __forceinline__ void load_tw_group(cpx<T
 template <typename T, int E, typename Tin>
 __device__ __forceinline__ void rows_r2c_body(Tin* __restrict__ in, double in_scale, int zero_input,
                                               cpx<T>* __restrict__ out, int rows, double* mass_acc, int bx, int gx,
-                                              const cpx<T>* tw, cpx<T> (*zball)[33 * E]) {
+                                              const cpx<T>* tw, cpx<T>* zball) {
   constexpr int N = 32 * E, NH = N / 2 + 1;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  cpx<T>* zb = zball[wib];
-  const int nwarps = gx * 8;
+  cpx<T>* zb = zball + wib * row_scratch<T, N>();
   double msum = 0.0;
+  if constexpr (group_rows<T, N>()) {
+    // group FFTs over this block's contiguous range of row pairs
+    constexpr int PS = group_ps<N>();
+    const int np = rows / 2, per = (np + gx - 1) / gx, p0 = bx * per, cnt = max(0, min(per, np - p0));
+    group_r2c_pairs<T, N>(
+        cnt, 0, tw + kTwLen,
+        [&](int pr, int j, T& a, T& b) {
+          const size_t ra = (size_t)(2 * (p0 + pr)) * N + j, rb = ra + N;
+          if constexpr (sizeof(Tin) == 8 && !std::is_floating_point<Tin>::value) {
+            a = (T)((double)(long long)in[ra] * in_scale);
+            b = (T)((double)(long long)in[rb] * in_scale);
+          } else {
+            a = (T)in[ra];
+            b = (T)in[rb];
+          }
+          if (zero_input) {
+            in[ra] = Tin(0);
+            in[rb] = Tin(0);
+          }
+          if (mass_acc) msum += (double)a + (double)b;
+        },
+        [&](int, int g) { return zb + g * PS; },
+        [&](int pr, int k, cpx<T> A, cpx<T> B) {
+          cpx<T>* oa = out + (size_t)(2 * (p0 + pr)) * NH;
+          oa[k] = A;
+          oa[NH + k] = B;
+        });
+  } else {
+  const int nwarps = gx * 8;
   for (int pr = bx * 8 + wib; pr < rows / 2; pr += nwarps) {
     const size_t ra = (size_t)(2 * pr) * N, rb = ra + N;
     cpx<T> v[E];
@@ -708,6 +874,7 @@ __device__ __forceinline__ void rows_r2c_body(Tin* __restrict__ in, double in_sc
     }
     __syncwarp();
   }
+  }
   if (mass_acc) {
     for (int o = 16; o > 0; o >>= 1) msum += __shfl_xor_sync(0xffffffffu, msum, o);
     if (lane == 0) atomicAdd(mass_acc, msum);
@@ -718,9 +885,9 @@ template <typename T, int E, typename Tin>
 __global__ void __launch_bounds__(256)
 kw_rows_r2c(Tin* __restrict__ in, double in_scale, int zero_input, cpx<T>* __restrict__ out, int rows,
             double* mass_acc) {
-  __shared__ cpx<T> tw[kTwLen];
-  __shared__ cpx<T> zb[8][33 * E];
-  load_tw_full<T, E>(tw);
+  __shared__ cpx<T> tw[tw_len<T, E>()];
+  __shared__ cpx<T> zb[8 * row_scratch<T, 32 * E>()];
+  load_tw_group<T, E>(tw);
   __syncthreads();
   rows_r2c_body<T, E, Tin>(in, in_scale, zero_input, out, rows, mass_acc, blockIdx.x, gridDim.x, tw, zb);
 }
@@ -865,7 +1032,7 @@ __device__ __forceinline__ void spectral_body(const cpx<T>* __restrict__ T1, cpx
 // ---------------------------------------------------------------------------
 template <int N> struct XRegShape {
   static constexpr int F = GroupShape<N>::F, Q = GroupShape<N>::Q, G = 32 / Q;
-  static constexpr int PS = N + 16 / G;     // pencil stride in a warp slot: the G pencils start 16/G banks apart
+  static constexpr int PS = group_ps<N>();  // pencil stride in a warp slot
   static constexpr int WARP = 2 * G * PS;   // complex entries per warp: exchange slots + alpha slots
   static constexpr int TASKS = N * (N / 2 + 1) / G;
   static_assert(N * (N / 2 + 1) % G == 0, "x pencils come in whole groups");
@@ -1031,10 +1198,39 @@ __device__ __forceinline__ void rows_c2r_body(const cpx<T>* __restrict__ in, siz
   constexpr int N = 32 * E, NH = N / 2 + 1;
   constexpr int NOUT = NCOMP == 3 ? 4 : 1;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  cpx<T>* zb = zb_all + wib * padded_len(N);
+  cpx<T>* zb = zb_all + wib * row_scratch<T, N>();
+  double mx = -INFINITY;
+  if constexpr (group_rows<T, N>()) {
+    // group FFTs over this block's contiguous range of row pairs, one
+    // component after another (a node's three components are written by the
+    // same warp within a short time, so L2 merges the partial sectors)
+    constexpr int PS = group_ps<N>();
+    const int np = rows / 2, per = (np + gx - 1) / gx, p0 = bx * per, cnt = max(0, min(per, np - p0));
+    for (int d = 0; d < NCOMP; ++d) {
+      const cpx<T>* src = in + d * comp_stride;
+      group_c2r_pairs<T, N>(
+          cnt, 0, tw + kTwLen,
+          [&](int pr, int k, cpx<T>& A, cpx<T>& B) {
+            const cpx<T>* ra = src + (size_t)(2 * (p0 + pr)) * NH;
+            A = ra[k];
+            B = ra[NH + k];
+          },
+          [&](int, int g) { return zb + g * PS; },
+          [&](int pr, int j, T re, T im) {
+            T* oa = out + (size_t)(2 * (p0 + pr)) * N * NOUT;
+            if (NOUT == 4) {
+              oa[(size_t)j * 4 + d] = re;
+              oa[(size_t)(N + j) * 4 + d] = im;
+            } else {
+              oa[j] = re;
+              oa[N + j] = im;
+              mx = fmax(mx, fmax((double)re, (double)im));
+            }
+          });
+    }
+  } else {
   T* ob = ob_all + wib * 2 * N * NOUT;
   const int nwarps = gx * 8;
-  double mx = -INFINITY;
   for (int pr = bx * 8 + wib; pr < rows / 2; pr += nwarps) {
     for (int d = 0; d < NCOMP; ++d) {
       const cpx<T>* ra = in + d * comp_stride + (size_t)(2 * pr) * NH;
@@ -1082,6 +1278,7 @@ __device__ __forceinline__ void rows_c2r_body(const cpx<T>* __restrict__ in, siz
     }
     __syncwarp();
   }
+  }
   if (NOUT == 1 && max_acc) {
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) {
@@ -1098,9 +1295,9 @@ kw_rows_c2r(const cpx<T>* __restrict__ in, size_t comp_stride, T* __restrict__ o
   constexpr int N = 32 * E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* zb_all = tw + kTwLen;
-  T* ob_all = reinterpret_cast<T*>(zb_all + 8 * padded_len(N));
-  load_tw_full<T, E>(tw);
+  cpx<T>* zb_all = tw + tw_len<T, E>();
+  T* ob_all = reinterpret_cast<T*>(zb_all + 8 * row_scratch<T, N>());
+  load_tw_group<T, E>(tw);
   __syncthreads();
   rows_c2r_body<T, E, NCOMP>(in, comp_stride, out, rows, max_acc, blockIdx.x, gridDim.x, tw, zb_all, ob_all);
 }
@@ -1111,9 +1308,9 @@ kw_rows_c2r(const cpx<T>* __restrict__ in, size_t comp_stride, T* __restrict__ o
 // ---------------------------------------------------------------------------
 template <typename T, int E>
 __global__ void __launch_bounds__(256) kwb_rows_r2c(const FftRun<T>* __restrict__ runs) {
-  __shared__ cpx<T> tw[kTwLen];
-  __shared__ cpx<T> zb[8][33 * E];
-  load_tw_full<T, E>(tw);
+  __shared__ cpx<T> tw[tw_len<T, E>()];
+  __shared__ cpx<T> zb[8 * row_scratch<T, 32 * E>()];
+  load_tw_group<T, E>(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.y];
   constexpr int N = 32 * E;
@@ -1155,13 +1352,20 @@ __global__ void __launch_bounds__(256) kwb_rows_c2r(const FftRun<T>* __restrict_
   constexpr int N = 32 * E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* zb_all = tw + kTwLen;
-  T* ob_all = reinterpret_cast<T*>(zb_all + 8 * padded_len(N));
-  load_tw_full<T, E>(tw);
+  cpx<T>* zb_all = tw + tw_len<T, E>();
+  T* ob_all = reinterpret_cast<T*>(zb_all + 8 * row_scratch<T, N>());
+  load_tw_group<T, E>(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.y];
   const size_t S = (size_t)N * N * (N / 2 + 1);
   rows_c2r_body<T, E, 3>(r.T2, S, r.grad, N * N, nullptr, blockIdx.x, gridDim.x, tw, zb_all, ob_all);
+}
+
+// Shared bytes of the row c2r kernels: twiddles, per-warp scratch and, in
+// double precision, per-warp staging of the output rows.
+template <typename T, int E, int NOUT> constexpr size_t row_c2r_smem() {
+  return ((size_t)tw_len<T, E>() + (size_t)8 * row_scratch<T, 32 * E>()) * sizeof(cpx<T>) +
+         (group_rows<T, 32 * E>() ? 0 : (size_t)8 * 2 * 32 * E * NOUT * sizeof(T));
 }
 
 // ---------------------------------------------------------------------------
@@ -1180,7 +1384,9 @@ constexpr int kDefaultSpectralWarps = 8;   // warps per block of the fused x pas
 
 template <typename T, int E> constexpr size_t plane_smem_bytes(int nw) {
   // plane: H rows of H/2+1 plus one slot per 32 rows; one padded pencil per warp
-  return ((size_t)32 * E * (16 * E + 1) + E + (size_t)nw * padded_len(32 * E) + tw_len<T, E>()) * sizeof(cpx<T>);
+  return ((size_t)32 * E * (16 * E + 1) + E + (group_rows<T, 32 * E>() ? 0 : (size_t)nw * padded_len(32 * E)) +
+          tw_len<T, E>()) *
+         sizeof(cpx<T>);
 }
 
 template <typename T, int E, typename Tin>
@@ -1194,6 +1400,30 @@ __device__ __forceinline__ void plane_fwd_body(Tin* __restrict__ in, double in_s
   //    spectra.  In single precision the raw values of a warp's next row
   //    pair are loaded one iteration ahead, so their latency overlaps this
   //    pair's transform (in double precision the extra registers spill).
+  if constexpr (group_rows<T, N>()) {
+    // group FFTs, each row pair transformed and split in its own rows of P
+    group_r2c_pairs<T, N>(
+        N / 2, 2 * NH, tw + kTwLen,
+        [&](int pr, int j, T& a, T& b) {
+          const size_t ra = (size_t)(2 * pr) * N + j, rb = ra + N;
+          const Tin va = in[ra], vb = in[rb];
+          in[ra] = Tin(0);
+          in[rb] = Tin(0);
+          if constexpr (sizeof(Tin) == 8 && !std::is_floating_point<Tin>::value) {
+            a = (T)((double)(long long)va * in_scale);
+            b = (T)((double)(long long)vb * in_scale);
+          } else {
+            a = (T)va;
+            b = (T)vb;
+          }
+        },
+        [&](int pr, int) { return P + tpad(2 * pr, NH, 0); },
+        [&](int pr, int k, cpx<T> A, cpx<T> B) {
+          cpx<T>* pa = P + tpad(2 * pr, NH, 0);
+          pa[k] = A;
+          pa[NH + k] = B;
+        });
+  } else {
   constexpr bool PF = sizeof(T) == 4;
   Tin na[E], nb[E];
   if (PF && wib < N / 2) {
@@ -1246,6 +1476,7 @@ __device__ __forceinline__ void plane_fwd_body(Tin* __restrict__ in, double in_s
     }
     __syncwarp();
   }
+  }
   __syncthreads();
   // 2. y axis: the plane's columns in place
   tile_ffts<T, N, -1>(NH, tw, tw + kTwLen, [&](int p, int j) { return P + tpad(j, NH, p); },
@@ -1268,6 +1499,21 @@ __device__ __forceinline__ void plane_inv_body(const cpx<T>* __restrict__ in, T*
   __syncthreads();
   // 2. rows: two Hermitian half rows A, B as the pencil A + i B; the inverse
   //    transform's real part is row A, its imaginary part row B
+  if constexpr (group_rows<T, N>()) {
+    group_c2r_pairs<T, N>(
+        N / 2, 2 * NH, tw + kTwLen,
+        [&](int pr, int k, cpx<T>& A, cpx<T>& B) {
+          const cpx<T>* pa = P + tpad(2 * pr, NH, 0);
+          A = pa[k];
+          B = pa[NH + k];
+        },
+        [&](int pr, int) { return P + tpad(2 * pr, NH, 0); },
+        [&](int pr, int j, T re, T im) {
+          T* orow = out + ((size_t)x * N + 2 * pr) * N * 4 + d;
+          orow[(size_t)j * 4] = re;
+          orow[(size_t)(N + j) * 4] = im;
+        });
+  } else {
   for (int pr = wib; pr < N / 2; pr += (int)(blockDim.x >> 5)) {
     const cpx<T>* pa = P + tpad(2 * pr, NH, 0);   // rows 2 pr and 2 pr + 1 are adjacent
     const cpx<T>* pb = pa + NH;
@@ -1300,15 +1546,16 @@ __device__ __forceinline__ void plane_inv_body(const cpx<T>* __restrict__ in, T*
     for (int t = lane; t < 2 * N; t += 32) orow[(size_t)t * 4] = ob[zpad(t)];
     __syncwarp();
   }
+  }
 }
 
 template <typename T, int E>
-__global__ void __launch_bounds__(1024) kwp_fwd(const FftRun<T>* __restrict__ runs) {
+__global__ void __launch_bounds__(group_rows<T, 32 * E>() ? 512 : 1024) kwp_fwd(const FftRun<T>* __restrict__ runs) {
   constexpr int N = 32 * E, NH = N / 2 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* zb = tw + tw_len<T, E>();
-  cpx<T>* P = zb + (blockDim.x >> 5) * padded_len(N);
+  cpx<T>* P = zb + (group_rows<T, N>() ? 0 : (blockDim.x >> 5) * padded_len(N));
   load_tw_group<T, E>(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.y];
@@ -1322,12 +1569,12 @@ __global__ void __launch_bounds__(1024) kwp_fwd(const FftRun<T>* __restrict__ ru
 }
 
 template <typename T, int E>
-__global__ void __launch_bounds__(1024) kwp_inv(const FftRun<T>* __restrict__ runs) {
+__global__ void __launch_bounds__(group_rows<T, 32 * E>() ? 512 : 1024) kwp_inv(const FftRun<T>* __restrict__ runs) {
   constexpr int N = 32 * E, NH = N / 2 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* zb = tw + tw_len<T, E>();
-  cpx<T>* P = zb + (blockDim.x >> 5) * padded_len(N);
+  cpx<T>* P = zb + (group_rows<T, N>() ? 0 : (blockDim.x >> 5) * padded_len(N));
   load_tw_group<T, E>(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.z];
@@ -1343,6 +1590,7 @@ __global__ void __launch_bounds__(1024) kwp_inv(const FftRun<T>* __restrict__ ru
 // (the per-component kernel writes each node's sector three times in part,
 // which costs a DRAM read per sector once the nodes exceed L2).
 template <typename T, int E> constexpr size_t plane3_smem_bytes(int nw) {
+  if (group_rows<T, 32 * E>()) return ((size_t)tw_len<T, E>() + 3 * ((size_t)32 * E * (16 * E + 1) + E)) * sizeof(cpx<T>);
   return ((size_t)tw_len<T, E>() + (size_t)nw * padded_len(32 * E) + 3 * ((size_t)32 * E * (16 * E + 1) + E)) * sizeof(cpx<T>) +
          (size_t)nw * 3 * padded_len(64 * E) * sizeof(T);
 }
@@ -1375,6 +1623,35 @@ __device__ __forceinline__ void plane_inv3_body(const cpx<T>* __restrict__ in, s
                         [](int) { return true; });
   }
   __syncthreads();
+  if constexpr (group_rows<T, N>()) {
+    // 2. rows: per component, the pencils A + i B of the row pairs, each
+    //    pair's two output rows staged as reals in its own rows of the plane;
+    //    then whole (gx, gy, gz, 0) nodes
+    for (int d = 0; d < 3; ++d) {
+      cpx<T>* Pd = P + d * PL;
+      group_c2r_pairs<T, N>(
+          N / 2, 2 * NH, tw + kTwLen,
+          [&](int pr, int k, cpx<T>& A, cpx<T>& B) {
+            const cpx<T>* pa = Pd + tpad(2 * pr, NH, 0);
+            A = pa[k];
+            B = pa[NH + k];
+          },
+          [&](int pr, int) { return Pd + tpad(2 * pr, NH, 0); },
+          [&](int pr, int j, T re, T im) {
+            T* ob = reinterpret_cast<T*>(Pd + tpad(2 * pr, NH, 0));
+            ob[j] = re;
+            ob[N + j] = im;
+          });
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
+      const int y = t / N, j = t - y * N;
+      const int off = tpad(y & ~1, NH, 0);
+      const int f = (y & 1) * N + j;
+      store_node4<T>(out + (((size_t)x * N + y) * N + j) * 4, reinterpret_cast<const T*>(P + off)[f],
+                     reinterpret_cast<const T*>(P + PL + off)[f], reinterpret_cast<const T*>(P + 2 * PL + off)[f]);
+    }
+  } else {
   // 2. rows: per component, the two Hermitian half rows A, B as the pencil
   //    A + i B (real part: row A, imaginary part: row B), staged; then the
   //    two rows of nodes
@@ -1414,15 +1691,16 @@ __device__ __forceinline__ void plane_inv3_body(const cpx<T>* __restrict__ in, s
     }
     __syncwarp();
   }
+  }
 }
 
 template <typename T, int E>
-__global__ void __launch_bounds__(1024) kwp_inv3(const FftRun<T>* __restrict__ runs) {
+__global__ void __launch_bounds__(group_rows<T, 32 * E>() ? 512 : 1024) kwp_inv3(const FftRun<T>* __restrict__ runs) {
   constexpr int N = 32 * E, NH = N / 2 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* zb = tw + tw_len<T, E>();
-  cpx<T>* P = zb + (blockDim.x >> 5) * padded_len(N);
+  cpx<T>* P = zb + (group_rows<T, N>() ? 0 : (blockDim.x >> 5) * padded_len(N));
   T* ob = reinterpret_cast<T*>(P + 3 * ((size_t)N * NH + E));
   load_tw_group<T, E>(tw);
   __syncthreads();
@@ -1459,7 +1737,7 @@ template <int N, int CS> struct ColSplit {
 
 template <typename T, int E, int CS> constexpr size_t cplane_smem_bytes(int nw) {
   // column block: H rows of CP plus one slot per 32 rows; one padded pencil per warp
-  return ((size_t)32 * E * ColSplit<32 * E, CS>::LD + E + (size_t)nw * padded_len(32 * E) + tw_len<T, E>()) *
+  return ((size_t)32 * E * ColSplit<32 * E, CS>::LD + E + (size_t)nw * row_scratch<T, 32 * E>() + tw_len<T, E>()) *
          sizeof(cpx<T>);
 }
 
@@ -1481,6 +1759,31 @@ __device__ __forceinline__ void cplane_fwd_body(Tin* __restrict__ in, double in_
   cluster.sync();
   // 1. this CTA's rows (row pairs), results pushed to the owners' column blocks
   constexpr int PAIRS = N / 2 / CS;
+  if constexpr (group_rows<T, N>()) {
+    cpx<T>* zs = zball + wib * row_scratch<T, N>();
+    group_r2c_pairs<T, N>(
+        PAIRS, 0, tw + kTwLen,
+        [&](int pr, int j, T& a, T& b) {
+          const size_t ra = (size_t)(2 * (rank * PAIRS + pr)) * N + j, rb = ra + N;
+          const Tin va = in[ra], vb = in[rb];
+          in[ra] = Tin(0);
+          in[rb] = Tin(0);
+          if constexpr (sizeof(Tin) == 8 && !std::is_floating_point<Tin>::value) {
+            a = (T)((double)(long long)va * in_scale);
+            b = (T)((double)(long long)vb * in_scale);
+          } else {
+            a = (T)va;
+            b = (T)vb;
+          }
+        },
+        [&](int, int g) { return zs + g * group_ps<N>(); },
+        [&](int pr, int k, cpx<T> A, cpx<T> B) {
+          const int row = 2 * (rank * PAIRS + pr), o = k / LD, kl = k - o * LD;
+          cpx<T>* dst = peer[o];
+          dst[tpad(row, LD, kl)] = A;
+          dst[tpad(row + 1, LD, kl)] = B;
+        });
+  } else {
   for (int i = wib; i < PAIRS; i += nw) {
     const int pr = rank * PAIRS + i;
     const size_t ra = (size_t)(2 * pr) * N, rb = ra + N;
@@ -1512,6 +1815,7 @@ __device__ __forceinline__ void cplane_fwd_body(Tin* __restrict__ in, double in_
       dst[tpad(2 * pr + 1, LD, kl)] = cpx<T>{d.y * T(0.5), -d.x * T(0.5)};
     }
     __syncwarp();
+  }
   }
   cluster.sync();
   // 2. y axis of this CTA's columns
@@ -1551,6 +1855,22 @@ __device__ __forceinline__ void cplane_inv_body(const cpx<T>* __restrict__ in, T
   for (int o = 0; o < CS; ++o) peer[o] = cluster.map_shared_rank(Q, o);
   // 2. this CTA's rows: two Hermitian half rows A, B as the pencil A + i B
   constexpr int PAIRS = N / 2 / CS;
+  if constexpr (group_rows<T, N>()) {
+    cpx<T>* zs = zball + wib * row_scratch<T, N>();
+    group_c2r_pairs<T, N>(
+        PAIRS, 0, tw + kTwLen,
+        [&](int pr, int k, cpx<T>& A, cpx<T>& B) {
+          const int row = 2 * (rank * PAIRS + pr), o = k / LD, kl = k - o * LD;
+          A = peer[o][tpad(row, LD, kl)];
+          B = peer[o][tpad(row + 1, LD, kl)];
+        },
+        [&](int, int g) { return zs + g * group_ps<N>(); },
+        [&](int pr, int j, T re, T im) {
+          T* orow = out + ((size_t)x * N + 2 * (rank * PAIRS + pr)) * N * 4 + d;
+          orow[(size_t)j * 4] = re;
+          orow[(size_t)(N + j) * 4] = im;
+        });
+  } else {
   for (int i = wib; i < PAIRS; i += nw) {
     const int pr = rank * PAIRS + i;
     for (int k = lane; k < NH; k += 32) {
@@ -1581,6 +1901,7 @@ __device__ __forceinline__ void cplane_inv_body(const cpx<T>* __restrict__ in, T
     for (int t = lane; t < 2 * N; t += 32) orow[(size_t)t * 4] = ob[zpad(t)];
     __syncwarp();
   }
+  }
   // the peers may still read this CTA's columns
   cluster.sync();
 }
@@ -1591,7 +1912,7 @@ __global__ void __launch_bounds__(1024) kwc_fwd(const FftRun<T>* __restrict__ ru
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* zb = tw + tw_len<T, E>();
-  cpx<T>* Q = zb + (blockDim.x >> 5) * padded_len(N);
+  cpx<T>* Q = zb + (blockDim.x >> 5) * row_scratch<T, N>();
   load_tw_group<T, E>(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.y];
@@ -1610,7 +1931,7 @@ __global__ void __launch_bounds__(1024) kwc_inv(const FftRun<T>* __restrict__ ru
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* zb = tw + tw_len<T, E>();
-  cpx<T>* Q = zb + (blockDim.x >> 5) * padded_len(N);
+  cpx<T>* Q = zb + (blockDim.x >> 5) * row_scratch<T, N>();
   load_tw_group<T, E>(tw);
   __syncthreads();
   const FftRun<T>& r = runs[blockIdx.z];
@@ -1695,7 +2016,7 @@ static cudaError_t warp_rows_c2r(const cpx<T>* in, size_t comp_stride, T* out, i
                                  cudaStream_t s) {
   constexpr int N = 32 * E;
   constexpr int NOUT = NCOMP == 3 ? 4 : 1;
-  const size_t smem = (kTwLen + (size_t)8 * padded_len(N)) * sizeof(cpx<T>) + (size_t)8 * 2 * N * NOUT * sizeof(T);
+  const size_t smem = row_c2r_smem<T, E, NOUT>();
   auto k = kw_rows_c2r<T, E, NCOMP>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
@@ -1934,8 +2255,13 @@ static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, c
     return tune.plane_nw > 0 ? tune.plane_nw
                              : (blocks <= fill * 152 ? max(kDefaultPlaneWarps, min(most, N / 4)) : kDefaultPlaneWarps);
   };
-  const int fnw = plane_warps(nruns * N, 2, 32), inw = plane_warps(3 * nruns * N, 4, 16),
-            i3nw = plane_warps(nruns * N, 2, 32);
+  // rows by group FFTs (at most 16 warps a block, no per-warp pencils): 16
+  // warps for the forward and three-component kernels, 8 for the
+  // per-component inverse (three of its blocks fit an SM)
+  constexpr bool SP = group_rows<T, N>();
+  const int fnw = plane_warps(nruns * N, 2, SP ? 16 : 32), inw = SP ? (tune.plane_nw > 0 ? tune.plane_nw : 8)
+                                                                     : plane_warps(3 * nruns * N, 4, 16),
+            i3nw = plane_warps(nruns * N, 2, SP ? 16 : 32);
   const int snw = tune.spec_nw > 0 ? tune.spec_nw : kDefaultSpectralWarps;
   const size_t fsm = plane_smem_bytes<T, E>(fnw), ism = plane_smem_bytes<T, E>(inw);
   const size_t i3sm = plane3_smem_bytes<T, E>(i3nw);
@@ -2000,7 +2326,7 @@ static cudaError_t field_batch_e(const FftRun<T>* runs, int nruns, int stages, c
     nk += 1;
   } else if (stages & kFieldInverse) {
     if ((e = kwb_cols_bc<T, E, +1>(runs, nruns, 3, bc, s)) != cudaSuccess) return e;
-    const size_t smr = (kTwLen + (size_t)8 * padded_len(N)) * sizeof(cpx<T>) + (size_t)8 * 2 * N * 4 * sizeof(T);
+    const size_t smr = row_c2r_smem<T, E, 4>();
     if ((e = set_smem(kwb_rows_c2r<T, E>, smr)) != cudaSuccess) return e;
     kwb_rows_c2r<T, E><<<dim3(rblocks, nruns), 256, smr, s>>>(runs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -2013,7 +2339,8 @@ template <typename T, int E> static bool field_tune_valid_e(const FieldTune& t) 
   const int bc = t.bc > 0 ? t.bc : 16, sbc = t.sbc > 0 ? t.sbc : default_sbc<T, E>();
   size_t c = bc == 8 ? cols_smem<T, E, 8>() : bc == 32 ? cols_smem<T, E, 32>() : cols_smem<T, E, 16>();
   size_t x = sbc == 4 ? spectral_smem<T, E, 4>() : sbc == 8 ? spectral_smem<T, E, 8>() : spectral_smem<T, E, 16>();
-  const bool pnw_ok = t.plane_nw == 0 || t.plane_nw == 8 || t.plane_nw == 16 || t.plane_nw == 32;
+  const bool pnw_ok =
+      t.plane_nw == 0 || t.plane_nw == 8 || t.plane_nw == 16 || (!group_rows<T, 32 * E>() && t.plane_nw == 32);
   const bool snw_ok = t.spec_nw == 0 || t.spec_nw == 8 || t.spec_nw == 16;
   const int pnw = t.plane_nw > 0 ? t.plane_nw : kDefaultPlaneWarps;
   const bool inv3_ok = t.inv3 == 0 || t.inv3 == 2 ||
