@@ -431,13 +431,20 @@ def run_ours(args, world, rank, local):
                     "peak_source": "measured: sipf_measure_fp64_fma (dependent-chain FP64 FMAs over all SMs)"}
 
     # end to end through the C ABI with host buffers: every step uploads the
-    # positions from pinned host memory, steps, and reads them back
+    # positions from pinned host memory, steps, and reads them back.  The host
+    # copy starts from the context's own positions, so the loop continues its
+    # trajectory (re-sending X0 would hand the bins, sized for the evolved
+    # distribution, particles they no longer fit until the next capacity
+    # rebuild)
     Ke = max(1, min(K, 20))
-    hx = [torch.from_numpy(np.ascontiguousarray(X0[:, d], dtype=np.float32)).pin_memory() for d in range(3)]
+    hx = [torch.empty(P_FULL, dtype=torch.float32).pin_memory() for _ in range(3)]
     ptrs = [t.data_ptr() for t in hx]
-    _abi.sipf_upload_soa(sim.ctx, *ptrs)
-    sim.step(1)
     _abi.sipf_download_soa(sim.ctx, *ptrs)
+    sim.sync()
+    for _ in range(2):
+        _abi.sipf_upload_soa(sim.ctx, *ptrs)
+        sim.step(1)
+        _abi.sipf_download_soa(sim.ctx, *ptrs)
     sim.sync()
     dist_barrier(world, dev)
     t0 = time.perf_counter()
