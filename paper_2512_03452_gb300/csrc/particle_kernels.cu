@@ -1127,6 +1127,66 @@ __global__ void __launch_bounds__(256) k_unbin_aos(BinArgs<T> a, T* __restrict__
   }
 }
 
+// Read-back in particle order, step 1: the particles of the current bins
+// partitioned by id into the host copy's pieces (piece k: ids
+// [pb.b[k], pb.b[k+1])) as SoA records, piece k's at pb.b[k] on.  A block
+// takes one work item, counts its particles per piece in shared memory,
+// reserves each piece's range with one global atomic and writes.  The ids
+// are a permutation of 0 .. P-1, so piece k receives exactly its own range.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_partition_pieces(BinArgs<T> a, PieceBounds pb, int* __restrict__ cursor, T* __restrict__ rx, T* __restrict__ ry,
+                   T* __restrict__ rz, uint32_t* __restrict__ rid) {
+  __shared__ int cnt[PieceBounds::kMax], base[PieceBounds::kMax];
+  const long long c = blockIdx.x;
+  if (c >= a.chunk_start[a.NT + 1]) return;
+  const ChunkDesc d = a.chunks[c];
+  auto piece_of = [&](uint32_t id) {
+    int k = pb.np - 1;
+    while (k > 0 && (long long)id < pb.b[k]) --k;
+    return k;
+  };
+  if (threadIdx.x < PieceBounds::kMax) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < d.len; i += blockDim.x) atomicAdd(&cnt[piece_of(a.sid[d.start + i])], 1);
+  __syncthreads();
+  if (threadIdx.x < pb.np) {
+    const int n = cnt[threadIdx.x];
+    base[threadIdx.x] = n ? atomicAdd(cursor + threadIdx.x, n) : 0;
+    cnt[threadIdx.x] = 0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < d.len; i += blockDim.x) {
+    const long long s = d.start + i;
+    const uint32_t id = a.sid[s];
+    const int k = piece_of(id);
+    const long long o = pb.b[k] + base[k] + atomicAdd(&cnt[k], 1);
+    rx[o] = a.sx[s];
+    ry[o] = a.sy[s];
+    rz[o] = a.sz[s];
+    rid[o] = id;
+  }
+}
+
+// Step 2, per piece: its records scattered to their particles' slots.  A
+// piece's slots span 1/8 of the output arrays, small enough to stay in L2
+// while its partial sectors fill.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_scatter_piece(const T* __restrict__ rx, const T* __restrict__ ry, const T* __restrict__ rz,
+                const uint32_t* __restrict__ rid, int64_t a0, int64_t n, int64_t P, T* __restrict__ ox,
+                T* __restrict__ oy, T* __restrict__ oz) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = a0 + i;
+    const uint32_t id = rid[s];
+    if ((int64_t)id < P) {
+      ox[id] = rx[s];
+      oy[id] = ry[s];
+      oz[id] = rz[s];
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_aos4_to_soa(const T* __restrict__ aos, int64_t P, T* __restrict__ ox, T* __restrict__ oy, T* __restrict__ oz) {
@@ -1415,6 +1475,24 @@ cudaError_t launch_unbin_aos(const BinArgs<T>& a, int64_t max_chunks, T* aos, cu
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_partition_pieces(const BinArgs<T>& a, int64_t max_chunks, const PieceBounds& pb, int* cursor, T* rx,
+                                    T* ry, T* rz, uint32_t* rid, cudaStream_t s) {
+  if (pb.np < 1 || pb.np > PieceBounds::kMax) return cudaErrorInvalidValue;
+  if (max_chunks < 1) return cudaSuccess;
+  k_partition_pieces<T><<<(unsigned)max_chunks, 256, 0, s>>>(a, pb, cursor, rx, ry, rz, rid);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_scatter_piece(const T* rx, const T* ry, const T* rz, const uint32_t* rid, int64_t a0, int64_t n,
+                                 int64_t P, T* x, T* y, T* z, cudaStream_t s) {
+  if (n < 1) return cudaSuccess;
+  const int64_t b = (n + 255) / 256;
+  k_scatter_piece<T><<<(unsigned)(b > 152 * 8 ? 152 * 8 : b), 256, 0, s>>>(rx, ry, rz, rid, a0, n, P, x, y, z);
+  return cudaGetLastError();
+}
+
 template <typename T> cudaError_t launch_aos4_to_soa(const T* aos, int64_t P, T* x, T* y, T* z, cudaStream_t s) {
   const int64_t b = (P + 255) / 256;
   k_aos4_to_soa<T><<<(unsigned)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b)), 256, 0, s>>>(aos, P, x, y, z);
@@ -1502,6 +1580,10 @@ template <typename T> cudaError_t launch_alpha_energy(const cpx<T>* alpha, int H
                                       cudaStream_t, cudaError_t*, int64_t, bool);                             \
   template cudaError_t launch_unbin_aos<T>(const BinArgs<T>&, int64_t, T*, cudaStream_t);                     \
   template cudaError_t launch_aos4_to_soa<T>(const T*, int64_t, T*, T*, T*, cudaStream_t);                    \
+  template cudaError_t launch_partition_pieces<T>(const BinArgs<T>&, int64_t, const PieceBounds&, int*, T*, T*, \
+                                                  T*, uint32_t*, cudaStream_t);                                \
+  template cudaError_t launch_scatter_piece<T>(const T*, const T*, const T*, const uint32_t*, int64_t, int64_t, \
+                                               int64_t, T*, T*, T*, cudaStream_t);                             \
   template cudaError_t launch_unbin<T>(const BinArgs<T>&, int64_t, T*, T*, T*, T*, int64_t, cudaStream_t);    \
   template cudaError_t launch_deposit<T>(const T*, const T*, const T*, int64_t, Geo<T>, T, T*, int,           \
                                          cudaStream_t);                                                      \

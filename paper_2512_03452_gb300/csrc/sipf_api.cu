@@ -172,7 +172,8 @@ struct sipf_ctx {
   // the step's last deposit; every transfer ends with the context stream
   // waiting for them
   cudaStream_t side[2] = {nullptr, nullptr};   // [0] kernels, [1] copies
-  static constexpr int kPieces = 8;
+  static constexpr int kPieces = PieceBounds::kMax;
+  int* pcur = nullptr;     // per-piece cursors of the read-back partition
   cudaEvent_t ev_piece[kPieces] = {};
   cudaEvent_t ev_pos = nullptr;     // recorded once the current bins are final (before the deposit)
   cudaEvent_t ev_begin = nullptr, ev_done = nullptr;
@@ -604,24 +605,38 @@ template <typename T> int upload_soa_impl(sipf_ctx* c, const void* const src[3])
   return deposit_current<T>(c);
 }
 
-// Download to host SoA positions: the bins are un-binned into the 4-wide
-// scratch on a side stream as soon as they are final (the last step's deposit
-// may still be running on the context stream), then transposed and copied
-// back in pieces, each piece's copy overlapping the next piece's transpose.
+// Download to host SoA positions, on side streams as soon as the bins are
+// final (the last step's deposit may still be running on the context
+// stream): the bins' particles are partitioned by id into the copy's pieces
+// (records in the other bin buffer), then each piece is scattered to particle
+// order in the staging arrays and copied back, each piece's copy overlapping
+// the next piece's scatter.  A piece's slots stay in L2 while its scattered
+// sectors fill, where one scatter over all particles (16-byte records to
+// random ids) wrote partial sectors to DRAM and had to finish before the
+// first copy.
 template <typename T> int download_soa_impl(sipf_ctx* c, void* const dst[3]) {
   const int64_t P = c->p.P;
   // the other bin buffer is free between steps (the next move overwrites it)
-  T* aos = (T*)c->bx[1 - c->cur][0];
+  const int ob = 1 - c->cur;
+  T* rx = (T*)c->bx[ob][0];
+  T* ry = (T*)c->bx[ob][1];
+  T* rz = (T*)c->bx[ob][2];
+  uint32_t* rid = c->bid[ob];
   if (!c->pos_ready) SIPF_CK(mark_positions(c));
   SIPF_CK(cudaStreamWaitEvent(c->side[0], c->ev_pos, 0));
   SIPF_CK(cudaStreamWaitEvent(c->side[0], c->ev_done, 0));   // a previous download's copies
-  SIPF_CK(launch_unbin_aos<T>(bin_args<T>(c, c->cur, c->lc, -1, 0), c->max_chunks(), aos, c->side[0]));
   const int np = pieces_for(P);
+  PieceBounds pb{};
+  pb.np = np;
+  for (int k = 0; k <= np; ++k) pb.b[k] = piece_begin(P, np, k);
+  SIPF_CK(cudaMemsetAsync(c->pcur, 0, PieceBounds::kMax * sizeof(int), c->side[0]));
+  SIPF_CK(launch_partition_pieces<T>(bin_args<T>(c, c->cur, c->lc, -1, 0), c->max_chunks(), pb, c->pcur, rx, ry, rz,
+                                     rid, c->side[0]));
   for (int k = 0; k < np; ++k) {
     const int64_t a0 = piece_begin(P, np, k), a1 = piece_begin(P, np, k + 1);
     if (a1 <= a0) continue;
-    SIPF_CK(launch_aos4_to_soa<T>(aos + 4 * a0, a1 - a0, (T*)c->st[0] + a0, (T*)c->st[1] + a0, (T*)c->st[2] + a0,
-                                  c->side[0]));
+    SIPF_CK(launch_scatter_piece<T>(rx, ry, rz, rid, a0, a1 - a0, P, (T*)c->st[0], (T*)c->st[1], (T*)c->st[2],
+                                    c->side[0]));
     SIPF_CK(cudaEventRecord(c->ev_piece[k], c->side[0]));
     SIPF_CK(cudaStreamWaitEvent(c->side[1], c->ev_piece[k], 0));
     for (int d = 0; d < 3; ++d)
@@ -678,6 +693,7 @@ void free_ctx(sipf_ctx* c) {
   cudaFree(c->work);
   cudaFree(c->ovf);
   cudaFree(c->hist);
+  cudaFree(c->pcur);
   cudaFree(c->phi);
   cudaFree(c->T1);
   cudaFree(c->alpha);
@@ -786,6 +802,7 @@ int sipf_init(const sipf_params* p, const double* X0, void* stream, sipf_ctx** o
   if (e == cudaSuccess) e = cudaMalloc(&c->ovf, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ovf, 0, sizeof(unsigned long long), c->stream);
   if (e == cudaSuccess) e = cudaMalloc(&c->hist, nb * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->pcur, PieceBounds::kMax * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&c->phi, N * (c->fixed() ? 8 : c->esz));
   if (e == cudaSuccess) e = cudaMalloc(&c->T1, S * 2 * c->esz);
   if (e == cudaSuccess) e = cudaMalloc(&c->alpha, S * 2 * c->esz);

@@ -220,6 +220,22 @@ int rebin_plain_max_tiles();
 // the scratch to three arrays.
 template <typename T> cudaError_t launch_unbin_aos(const BinArgs<T>& a, int64_t max_chunks, T* aos, cudaStream_t s);
 template <typename T> cudaError_t launch_aos4_to_soa(const T* aos, int64_t P, T* x, T* y, T* z, cudaStream_t s);
+// Read-back in particle order by pieces of ids: np pieces, piece k holding ids
+// [b[k], b[k+1]) (b[0] = 0, b[np] = P).
+struct PieceBounds {
+  static constexpr int kMax = 8;
+  long long b[kMax + 1];
+  int np;
+};
+// the current bins' particles as SoA records grouped by piece (piece k's at
+// b[k] on); cursor: np ints, zeroed before the launch
+template <typename T>
+cudaError_t launch_partition_pieces(const BinArgs<T>& a, int64_t max_chunks, const PieceBounds& pb, int* cursor, T* rx,
+                                    T* ry, T* rz, uint32_t* rid, cudaStream_t s);
+// records [a0, a0 + n) scattered to x, y, z at their ids (ids >= P skipped)
+template <typename T>
+cudaError_t launch_scatter_piece(const T* rx, const T* ry, const T* rz, const uint32_t* rid, int64_t a0, int64_t n,
+                                 int64_t P, T* x, T* y, T* z, cudaStream_t s);
 template <typename T>
 // Particle order from the bins; with aos_scratch (4 P elements) through a
 // 4-wide scratch array and a transpose, else by three scattered stores.
