@@ -178,6 +178,12 @@ struct sipf_ctx {
   cudaEvent_t ev_pos = nullptr;     // recorded once the current bins are final (before the deposit)
   cudaEvent_t ev_begin = nullptr, ev_done = nullptr;
   bool pos_ready = false;           // ev_pos describes the current bins
+  // phi does not hold the deposit of the current positions yet: the deposit
+  // is made when phi is next read (the next step's field solve, a density
+  // query), so positions replaced before that (a host upload every step)
+  // are not deposited twice; phi_zero: phi is known to be all zero
+  bool dep_pending = false;
+  bool phi_zero = false;
   int64_t H3() const { return (int64_t)p.H * p.H * p.H; }
   int64_t S() const { return (int64_t)p.H * p.H * (p.H / 2 + 1); }
   bool fixed() const { return p.deposit_mode == SIPF_DEPOSIT_DETERMINISTIC; }
@@ -288,18 +294,22 @@ cudaError_t mark_positions(sipf_ctx* c) {
 inline int64_t piece_begin(int64_t P, int npieces, int k) { return P * k / npieces; }
 inline int pieces_for(int64_t P) { return P >= (1 << 20) ? sipf_ctx::kPieces : 1; }
 
-// Deposit the current bins into phi (initialisation of Algorithm 4 and after
-// positions are replaced).
-template <typename T> int deposit_current(sipf_ctx* c) {
-  const size_t gb = (size_t)c->H3() * (c->fixed() ? 8 : sizeof(T));
-  SIPF_CK(cudaMemsetAsync(c->phi, 0, gb, c->stream));
-  SIPF_CK(cudaMemsetAsync(c->work, 0, sizeof(unsigned long long), c->stream));
+// The deposit of the current positions, if it is still owed (see
+// dep_pending).  The work counter it uses was cleared by the chunk-list
+// emission that made the current bins.
+template <typename T> int flush_deposit(sipf_ctx* c) {
+  if (!c->dep_pending) return SIPF_OK;
+  if (!c->phi_zero)
+    SIPF_CK(cudaMemsetAsync(c->phi, 0, (size_t)c->H3() * (c->fixed() ? 8 : sizeof(T)), c->stream));
   SIPF_CK(launch_binned<T>(bin_args<T>(c, c->cur, c->lc, -1, 0), 0, 1, 0, c->stream));
+  c->launches += 1;
+  c->dep_pending = false;
+  c->phi_zero = false;
   return SIPF_OK;
 }
 
 // Bin the particle-order staging (wrapped positions and ids) into a fresh
-// layout sized from its tile histogram, then deposit.
+// layout sized from its tile histogram; the deposit is owed.
 template <typename T> int rebin_from_staging(sipf_ctx* c) {
   const int d = c->cur, L = 1 - c->lc;
   const size_t nb = (size_t)(c->NT + 1);
@@ -325,7 +335,8 @@ template <typename T> int rebin_from_staging(sipf_ctx* c) {
   c->lc = L;
   c->since_layout = 0;
   SIPF_CK(mark_positions(c));
-  return deposit_current<T>(c);
+  c->dep_pending = true;
+  return SIPF_OK;
 }
 
 // Particle order -> staging arrays (or caller-owned device arrays).
@@ -355,6 +366,10 @@ template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
     cudaEvent_t ev[7] = {};
     const int64_t l0 = c->launches;
     SIPF_CK(mark(&ev[0]));
+    // deposit X^(n-1) from its bins (Algorithm 2), owed since the last move or
+    // upload
+    { const int r = flush_deposit<T>(c); if (r) return r; }
+    SIPF_CK(mark(&ev[1]));
     const FftRun<T>* fr = (const FftRun<T>*)c->fft_run;
     int fk = 0;   // field-solve kernels launched this step
     // beta^(n-1) = F_H I(rho-hat^(n-1)); the deposit grid is cleared as it is read
@@ -365,28 +380,29 @@ template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
                                  c->stream));
       SIPF_CK(launch_cols<T>(T1, H, H, nh, 1, 0, -1, 1.0, c->stream));
     }
-    SIPF_CK(mark(&ev[1]));
+    c->phi_zero = true;
+    SIPF_CK(mark(&ev[2]));
     // alpha^n and G(alpha^(n-1)), x axis back-transformed
     if (fr) {
       SIPF_CK(launch_field_batch<T>(fr, 1, H, kFieldSpectral, c->stream, FieldTune{}, &fk));
     } else {
       SIPF_CK(launch_spectral_x<T>(T1, al, T2, H, sp, kModeStep, c->dsc + kDscAlpha0, c->stream));
     }
-    SIPF_CK(mark(&ev[2]));
+    SIPF_CK(mark(&ev[3]));
     if (fr) {
       SIPF_CK(launch_field_batch<T>(fr, 1, H, kFieldInverse, c->stream, FieldTune{}, &fk));
     } else {
       SIPF_CK(launch_cols<T>(T2, H, H, nh, 3, S, +1, 1.0, c->stream));
       SIPF_CK(launch_rows_c2r<T>(T2, 3, S, (T*)c->grad, H, H * H, nullptr, c->stream));
     }
-    SIPF_CK(mark(&ev[3]));
+    SIPF_CK(mark(&ev[4]));
     // X^(n-1) -> X^n, re-bin into the other buffer by the new tile
     const int src = c->cur, dst = 1 - c->cur;
     // the move's work counter was cleared by the last chunk-list emission
     BinArgs<T> ma = bin_args<T>(c, src, c->lc, dst, c->lc);
     ma.work = c->work + 1;
     SIPF_CK(launch_move<T>(ma, c->stream));
-    SIPF_CK(mark(&ev[4]));
+    SIPF_CK(mark(&ev[5]));
     SIPF_CK(launch_chunk_list(cl_args(c, c->cursor[dst], c->lcap[c->lc], c->lbase[c->lc], c->cursor[src]), c->work,
                               c->timing ? c->ovf : nullptr, c->stream));
     c->launches += (fr ? fk : 5) + 3;
@@ -405,13 +421,11 @@ template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
       c->lc = L;
       c->since_layout = 0;
     }
-    SIPF_CK(mark(&ev[5]));
     SIPF_CK(mark_positions(c));
-    // deposit X^n from its bins (Algorithm 2) for the next step (its work
-    // counter was cleared by the chunk-list emission above)
-    SIPF_CK(launch_binned<T>(bin_args<T>(c, c->cur, c->lc, -1, 0), 0, 1, 0, c->stream));
-    c->launches += 1;
     SIPF_CK(mark(&ev[6]));
+    // the deposit of X^n is made when phi is next read (the next step, or a
+    // density query); an upload of new positions before then replaces it
+    c->dep_pending = true;
     if (c->timing) {
       c->ev.insert(c->ev.end(), ev, ev + 7);
       c->timed_steps += 1;
@@ -424,6 +438,7 @@ template <typename T> int step_impl(sipf_ctx* c, int64_t nsteps) {
 // rho_num (filtered) or the plain deposited density into the grad scratch
 // buffer as an H^3 real grid; FP64 mass sum and max into dsc.
 template <typename T> int density_impl(sipf_ctx* c, int filtered, T** out_grid) {
+  { const int r = flush_deposit<T>(c); if (r) return r; }
   const int H = c->p.H, nh = H / 2 + 1;
   const size_t S = (size_t)c->S();
   cpx<T>* T1 = (cpx<T>*)c->T1;
@@ -449,6 +464,7 @@ template <typename T> int copy_grid_to_host(sipf_ctx* c, const T* dev, int64_t c
 }
 
 template <typename T> int density_host(sipf_ctx* c, double* out, int filtered) {
+  { const int r = flush_deposit<T>(c); if (r) return r; }
   const double h3 = pow(c->p.L / c->p.H, 3);
   if (!filtered) {
     // I rho-hat / h^3 straight from the deposit grid
@@ -602,7 +618,8 @@ template <typename T> int upload_soa_impl(sipf_ctx* c, const void* const src[3])
   SIPF_CK(launch_chunk_list(cl_args(c, c->cursor[b], c->lcap[c->lc], c->lbase[c->lc], c->cursor[1 - b]), c->work,
                             nullptr, c->stream));
   SIPF_CK(mark_positions(c));
-  return deposit_current<T>(c);
+  c->dep_pending = true;
+  return SIPF_OK;
 }
 
 // Download to host SoA positions, on side streams as soon as the bins are
@@ -847,6 +864,9 @@ int sipf_init(const sipf_params* p, const double* X0, void* stream, sipf_ctx** o
     return cuda_fail(e, "sipf_init allocation");
   }
   r = DISPATCH(c, upload_aos, c, X0);
+  // X^(0) deposited now (Algorithm 4's initialisation), so phi is current for
+  // callers that read the runs' grids directly (the batched form)
+  if (!r) r = DISPATCH(c, flush_deposit, c);
   if (r) { free_ctx(c); return r; }
   *out = c;
   return SIPF_OK;
@@ -960,12 +980,13 @@ int sipf_timing_read(sipf_ctx* c, sipf_timing* out) {
       SIPF_CK(cudaEventElapsedTime(&ms, c->ev[i + k], c->ev[i + k + 1]));
       acc[k] += ms;
     }
-  out->forward_ms = acc[0];
-  out->spectral_ms = acc[1];
-  out->inverse_ms = acc[2];
-  out->move_ms = acc[3];
-  out->bookkeeping_ms = acc[4];
-  out->deposit_ms = acc[5];
+  // event order of a step: deposit, forward, spectral, inverse, move, bookkeeping
+  out->deposit_ms = acc[0];
+  out->forward_ms = acc[1];
+  out->spectral_ms = acc[2];
+  out->inverse_ms = acc[3];
+  out->move_ms = acc[4];
+  out->bookkeeping_ms = acc[5];
   out->steps = c->timed_steps;
   out->kernels = c->timed_kernels;
   unsigned long long ovf = 0;
