@@ -2014,7 +2014,6 @@ static cudaError_t warp_spectral(const cpx<T>* T1, cpx<T>* alpha, cpx<T>* T2, Sp
 template <typename T, int E, int NCOMP>
 static cudaError_t warp_rows_c2r(const cpx<T>* in, size_t comp_stride, T* out, int rows, double* max_acc,
                                  cudaStream_t s) {
-  constexpr int N = 32 * E;
   constexpr int NOUT = NCOMP == 3 ? 4 : 1;
   const size_t smem = row_c2r_smem<T, E, NOUT>();
   auto k = kw_rows_c2r<T, E, NCOMP>;

@@ -535,11 +535,25 @@ struct MoveSmem {
   int abort;
 };
 
+// Warm L2 with the next round's particle arrays (x, y, z, id from slot s0,
+// cnt particles; slots 4-aligned, bins padded to 4) while the current round
+// is moved, so its bulk copies into shared memory do not wait on DRAM.
+template <typename T>
+__device__ __forceinline__ void prefetch_round(const BinArgs<T>& a, long long s0, int cnt) {
+  const uint32_t n4 = (uint32_t)((cnt + 3) & ~3);
+  l2_prefetch(a.sx + s0, n4 * sizeof(T));
+  l2_prefetch(a.sy + s0, n4 * sizeof(T));
+  l2_prefetch(a.sz + s0, n4 * sizeof(T));
+  l2_prefetch(a.sid + s0, n4 * 4);
+}
+
 // One work item of the move + re-bin pass (see above).  n: step index of the
 // move (noise counter).  MOVE = false only re-bins (capacity rebuilds).
+// nxt / na (thread 0; na nullable): the block's next work item and its run's
+// arguments, whose first round is prefetched during this item's last round.
 template <typename T, bool MOVE, int G2P = 0>
 __device__ __forceinline__ void move_chunk(const BinArgs<T>& a, const ChunkDesc& cur, uint32_t n, MoveSmem<T>& sm,
-                                           uint32_t& phase) {
+                                           uint32_t& phase, const ChunkDesc& nxt, const BinArgs<T>* na) {
   constexpr int R = MoveRound<T>::n;
   constexpr int PER = R / kMoveThreads;
   const int mask = a.g.mask, ntx = a.ntx, tmask = a.ntx - 1;   // tiles per axis: a power of two
@@ -563,6 +577,7 @@ __device__ __forceinline__ void move_chunk(const BinArgs<T>& a, const ChunkDesc&
       tma_load_1d(sm.y, a.sy + s0, n4 * sizeof(T), &sm.bar);
       tma_load_1d(sm.z, a.sz + s0, n4 * sizeof(T), &sm.bar);
       tma_load_1d(sm.id, a.sid + s0, n4 * 4, &sm.bar);
+      if (r0 + R < cur.len) prefetch_round(a, s0 + R, min(R, cur.len - r0 - R));
     }
     for (int k = threadIdx.x; k < kNbr; k += blockDim.x) sm.cnt[k] = 0;
     if (!mbar_wait(&sm.bar, phase, 1u << 26)) {
@@ -621,6 +636,8 @@ __device__ __forceinline__ void move_chunk(const BinArgs<T>& a, const ChunkDesc&
       sm.meta[i] = meta;
     }
     __syncthreads();
+    // (the next item's descriptor has arrived by now)
+    if (threadIdx.x == 0 && r0 + R >= cur.len && nxt.len > 0 && na) prefetch_round(*na, nxt.start, min(R, nxt.len));
     // 2. one reservation per destination tile (with its capacity and first slot)
     for (int k = threadIdx.x; k < kNbr; k += blockDim.x) {
       const int c = sm.cnt[k];
@@ -689,7 +706,7 @@ k_move(BinArgs<T> a) {
       const long long c = (long long)atomicAdd(a.work, 1ULL);
       if (c < nchunks) nxt = a.chunks[c];
     }
-    move_chunk<T, true, G2P>(a, cur, a.n, sm, phase);
+    move_chunk<T, true, G2P>(a, cur, a.n, sm, phase, nxt, &a);
     if (threadIdx.x == 0) sm.desc[buf ^ 1] = nxt;
     __syncthreads();
   }
@@ -732,7 +749,7 @@ k_move_batch(const BinArgs<T>* __restrict__ table, const long long* __restrict__
         nxt = table[nrun].chunks[c - prefix[nrun]];
       }
     }
-    move_chunk<T, MOVE, G2P>(table[run], cur, n, sm, phase);
+    move_chunk<T, MOVE, G2P>(table[run], cur, n, sm, phase, nxt, nxt.len > 0 ? table + nrun : nullptr);
     if (threadIdx.x == 0) {
       sm.desc[buf ^ 1] = nxt;
       sm.run[buf ^ 1] = nrun;

@@ -336,6 +336,10 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
       "l"(src), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
 }
+// Hint: bring [p, p + bytes) into L2 (bytes: multiple of 16; p 16-byte aligned).
+__device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 // Wait for phase `parity` of the barrier; gives up after `limit` polls and
 // returns false (the caller reports the timeout instead of hanging).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
