@@ -171,6 +171,32 @@ constexpr int kChunk = 4096;                  // particles per work item
 // and flushing a tile window (11^3 slots x 8 copies) costs more than their
 // 32 reductions per particle.
 constexpr int kWinMinLen = 64;
+// Sparse bins are taken together: the bins with fewer than kSmall particles
+// (the overflow bin excepted) of each window of kMerge consecutive bins form
+// one work item, marked by bin < 0 with the window index in `start` and the
+// bins' total in `len` (at most kMerge (kSmall - 1) < 2048).  A sparse region
+// then costs the move one round per window instead of one per bin.
+constexpr int kMerge = 4;
+constexpr int kSmall = 256;
+__device__ __forceinline__ bool bin_is_small(int b, int count, int NT) { return b < NT && count > 0 && count < kSmall; }
+
+// Calls fn(slot) for every particle of work item d, the block's threads
+// striding over each run of slots (all threads take the same bins).
+template <typename T, typename Fn>
+__device__ __forceinline__ void item_slots(const BinArgs<T>& a, const ChunkDesc& d, Fn&& fn) {
+  if (d.bin >= 0) {
+    for (int i = threadIdx.x; i < d.len; i += blockDim.x) fn(d.start + i);
+    return;
+  }
+  for (int k = 0; k < kMerge; ++k) {
+    const int b = (int)d.start * kMerge + k;
+    if (b > a.NT) break;
+    const int c = a.src_count[b];
+    if (!bin_is_small(b, c, a.NT)) continue;
+    const long long s0 = a.src_base[b];
+    for (int i = threadIdx.x; i < c; i += blockDim.x) fn(s0 + i);
+  }
+}
 
 // Add the shared window (all replicas) to the grid and clear it; the
 // reductions of a warp hit contiguous nodes along the fastest axis.  Tile
@@ -424,6 +450,34 @@ __device__ __forceinline__ void binned_chunk(const BinArgs<T>& a, const ChunkDes
   }
 }
 
+// A work item of k_binned: one bin's chunk, or each small bin of a merged item
+// in turn (each with its own window).
+template <typename T, bool FIXED, bool MOVE, bool DEPOSIT, bool REBIN, bool WHOLE>
+__device__ __forceinline__ void binned_item(const BinArgs<T>& a, const ChunkDesc& cur,
+                                            typename WinType<T>::type* win) {
+  if (cur.bin >= 0) {
+    binned_chunk<T, FIXED, MOVE, DEPOSIT, REBIN, WHOLE>(a, cur, win);
+    return;
+  }
+  // the window's bins, looked up together
+  __shared__ int s_cnt[kMerge];
+  __shared__ long long s_base[kMerge];
+  if (threadIdx.x < kMerge) {
+    const int b = (int)cur.start * kMerge + threadIdx.x;
+    int c = b <= a.NT ? a.src_count[b] : 0;
+    if (!bin_is_small(b, c, a.NT)) c = 0;
+    s_cnt[threadIdx.x] = c;
+    s_base[threadIdx.x] = c ? a.src_base[b] : 0;
+  }
+  __syncthreads();
+  for (int k = 0; k < kMerge; ++k) {
+    const int c = s_cnt[k];
+    if (c == 0) continue;
+    binned_chunk<T, FIXED, MOVE, DEPOSIT, REBIN, WHOLE>(a, ChunkDesc{s_base[k], (int)cur.start * kMerge + k, c}, win);
+    __syncthreads();   // the window's flush (which clears it) ends before the next bin adds into it
+  }
+}
+
 template <typename T, bool FIXED, bool MOVE, bool DEPOSIT, bool REBIN, bool WHOLE>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
 k_binned(BinArgs<T> a) {
@@ -450,7 +504,7 @@ k_binned(BinArgs<T> a) {
       const long long c = (long long)atomicAdd(a.work, 1ULL);
       if (c < nchunks) nxt = a.chunks[c];
     }
-    binned_chunk<T, FIXED, MOVE, DEPOSIT, REBIN, WHOLE>(a, cur, win);
+    binned_item<T, FIXED, MOVE, DEPOSIT, REBIN, WHOLE>(a, cur, win);
     if (threadIdx.x == 0) s_desc[buf ^ 1] = nxt;
     __syncthreads();
   }
@@ -492,7 +546,7 @@ k_deposit_batch(const BinArgs<T>* __restrict__ table, const long long* __restric
         nxt = table[nrun].chunks[c - prefix[nrun]];
       }
     }
-    binned_chunk<T, FIXED, false, true, false, false>(table[run], cur, win);
+    binned_item<T, FIXED, false, true, false, false>(table[run], cur, win);
     if (threadIdx.x == 0) {
       s_desc[buf ^ 1] = nxt;
       s_run[buf ^ 1] = nrun;
@@ -531,9 +585,125 @@ struct MoveSmem {
   int meta[R];        // neighbour slot (0..124) | rank << 7, or -1 - tile for far moves
   int cnt[kNbr], base[kNbr], tile[kNbr], cap[kNbr];
   long long gbase[kNbr];   // first slot of each destination bin
+  long long seg_base[kMerge];   // merged items: first slot and particles of each small bin
+  int seg_cnt[kMerge];
   __align__(8) uint64_t bar;
   int abort;
 };
+
+// The move of one particle (Algorithm 4, particle loop): noise keyed by the
+// id and step n, gather of grad c with I*, drift, periodic wrap.
+template <typename T, int G2P>
+__device__ __forceinline__ void move_one(const BinArgs<T>& a, uint32_t n, uint32_t id, T& x, T& y, T& z) {
+  T nz[6];
+  normals6(a.seed, (uint64_t)id, n, nz);
+  if (a.split == 0) {
+    // Z = X + W^- + chi tau I*(grad c)(X + W^-),  X^n = Z + W^+
+    const T yx = x + a.s_noise * nz[0], yy = y + a.s_noise * nz[1], yz = z + a.s_noise * nz[2];
+    const V3<T> gr = gather_grad(a.grad4, G2P ? G2P : a.g2p, yx, yy, yz, a.g);
+    x = wrap_coord((yx + a.chitau * gr.x) + a.s_noise * nz[3], a.g);
+    y = wrap_coord((yy + a.chitau * gr.y) + a.s_noise * nz[4], a.g);
+    z = wrap_coord((yz + a.chitau * gr.z) + a.s_noise * nz[5], a.g);
+  } else {
+    // X^n = X + chi tau I*(grad c)(X) + W,  W ~ N(0, 2 mu tau I)
+    const V3<T> gr = gather_grad(a.grad4, G2P ? G2P : a.g2p, x, y, z, a.g);
+    x = wrap_coord((x + a.chitau * gr.x) + a.s_noise * nz[0], a.g);
+    y = wrap_coord((y + a.chitau * gr.y) + a.s_noise * nz[1], a.g);
+    z = wrap_coord((z + a.chitau * gr.z) + a.s_noise * nz[2], a.g);
+  }
+  if (!(t_finite(x) && t_finite(y) && t_finite(z))) atomicOr(a.err, 1);
+}
+
+// Tile of a position.
+template <typename T> __device__ __forceinline__ int tile_of_pos(const BinArgs<T>& a, T x, T y, T z) {
+  int cx, cy, cz;
+  T l;
+  cell_lambda(x, a.g, cx, l);
+  cell_lambda(y, a.g, cy, l);
+  cell_lambda(z, a.g, cz, l);
+  const int mask = a.g.mask;
+  return tile_of(cx & mask, cy & mask, cz & mask, a.tile_shift, a.ntx);
+}
+
+// Step 3 of a round: the staged particles written to their slots (meta: a
+// neighbour slot with the rank inside its reservation, or -1 - tile for a
+// particle that reserves its own slot).
+template <typename T> __device__ __forceinline__ void move_write_out(const BinArgs<T>& a, MoveSmem<T>& sm, int cnt) {
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const int meta = sm.meta[i];
+    int r, cap;
+    long long gb;
+    if (meta >= 0) {
+      const int k = meta & 127;
+      r = sm.base[k] + (meta >> 7);
+      cap = sm.cap[k];
+      gb = sm.gbase[k];
+    } else {
+      const int t = -1 - meta;
+      r = atomicAdd(a.dst_cursor + t, 1);
+      cap = a.dst_cap[t];
+      gb = a.dst_base[t];
+    }
+    long long slot;
+    if (r < cap) {
+      slot = gb + r;
+    } else {
+      const int o = atomicAdd(a.dst_cursor + a.NT, 1);
+      slot = o < a.dst_cap[a.NT] ? a.dst_base[a.NT] + o : -1;
+    }
+    if (slot >= 0) {
+      a.dx[slot] = sm.x[i];
+      a.dy[slot] = sm.y[i];
+      a.dz[slot] = sm.z[i];
+      a.did[slot] = sm.id[i];
+    } else {
+      atomicOr(a.err, 2);   // overflow bin full: the particle is lost
+    }
+  }
+}
+
+// A merged work item (small bins of one window): its particles, from several
+// source tiles, are read straight from their bins in rounds, moved, staged
+// and written out, each reserving its own destination slot (sparse bins, so
+// the destination cursors see little contention).
+template <typename T, bool MOVE, int G2P>
+__device__ __forceinline__ void move_merged(const BinArgs<T>& a, const ChunkDesc& cur, uint32_t n, MoveSmem<T>& sm) {
+  constexpr int R = MoveRound<T>::n;
+  if (threadIdx.x < kMerge) {
+    const int b = (int)cur.start * kMerge + threadIdx.x;
+    int c = 0;
+    long long base = 0;
+    if (b <= a.NT) {
+      c = a.src_count[b];
+      base = a.src_base[b];
+      if (!bin_is_small(b, c, a.NT)) c = 0;
+    }
+    sm.seg_cnt[threadIdx.x] = c;
+    sm.seg_base[threadIdx.x] = base;
+  }
+  __syncthreads();
+  for (int r0 = 0; r0 < cur.len; r0 += R) {
+    const int cnt = min(R, cur.len - r0);
+#pragma unroll 1
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      // the bin holding item particle r0 + i
+      int k = 0, o = r0 + i;
+      while (k < kMerge - 1 && o >= sm.seg_cnt[k]) o -= sm.seg_cnt[k++];
+      const long long slot = sm.seg_base[k] + o;
+      T x = a.sx[slot], y = a.sy[slot], z = a.sz[slot];
+      const uint32_t id = a.sid[slot];
+      if (MOVE) move_one<T, G2P>(a, n, id, x, y, z);
+      sm.x[i] = x;
+      sm.y[i] = y;
+      sm.z[i] = z;
+      sm.id[i] = id;
+      sm.meta[i] = -1 - tile_of_pos(a, x, y, z);
+    }
+    __syncthreads();
+    move_write_out(a, sm, cnt);
+    __syncthreads();
+  }
+}
 
 // Warm L2 with the next round's particle arrays (x, y, z, id from slot s0,
 // cnt particles; slots 4-aligned, bins padded to 4) while the current round
@@ -554,6 +724,10 @@ __device__ __forceinline__ void prefetch_round(const BinArgs<T>& a, long long s0
 template <typename T, bool MOVE, int G2P = 0>
 __device__ __forceinline__ void move_chunk(const BinArgs<T>& a, const ChunkDesc& cur, uint32_t n, MoveSmem<T>& sm,
                                            uint32_t& phase, const ChunkDesc& nxt, const BinArgs<T>* na) {
+  if (cur.bin < 0) {
+    move_merged<T, MOVE, G2P>(a, cur, n, sm);
+    return;
+  }
   constexpr int R = MoveRound<T>::n;
   constexpr int PER = R / kMoveThreads;
   const int mask = a.g.mask, ntx = a.ntx, tmask = a.ntx - 1;   // tiles per axis: a power of two
@@ -593,25 +767,7 @@ __device__ __forceinline__ void move_chunk(const BinArgs<T>& a, const ChunkDesc&
       const int i = k * kMoveThreads + threadIdx.x;
       if (i >= cnt) break;
       T x = sm.x[i], y = sm.y[i], z = sm.z[i];
-      if (MOVE) {
-        T nz[6];
-        normals6(a.seed, (uint64_t)sm.id[i], n, nz);
-        if (a.split == 0) {
-          // Z = X + W^- + chi tau I*(grad c)(X + W^-),  X^n = Z + W^+
-          const T yx = x + a.s_noise * nz[0], yy = y + a.s_noise * nz[1], yz = z + a.s_noise * nz[2];
-          const V3<T> gr = gather_grad(a.grad4, G2P ? G2P : a.g2p, yx, yy, yz, a.g);
-          x = wrap_coord((yx + a.chitau * gr.x) + a.s_noise * nz[3], a.g);
-          y = wrap_coord((yy + a.chitau * gr.y) + a.s_noise * nz[4], a.g);
-          z = wrap_coord((yz + a.chitau * gr.z) + a.s_noise * nz[5], a.g);
-        } else {
-          // X^n = X + chi tau I*(grad c)(X) + W,  W ~ N(0, 2 mu tau I)
-          const V3<T> gr = gather_grad(a.grad4, G2P ? G2P : a.g2p, x, y, z, a.g);
-          x = wrap_coord((x + a.chitau * gr.x) + a.s_noise * nz[0], a.g);
-          y = wrap_coord((y + a.chitau * gr.y) + a.s_noise * nz[1], a.g);
-          z = wrap_coord((z + a.chitau * gr.z) + a.s_noise * nz[2], a.g);
-        }
-        if (!(t_finite(x) && t_finite(y) && t_finite(z))) atomicOr(a.err, 1);
-      }
+      if (MOVE) move_one<T, G2P>(a, n, sm.id[i], x, y, z);
       int cx, cy, cz;
       T l;
       cell_lambda(x, a.g, cx, l);
@@ -637,7 +793,8 @@ __device__ __forceinline__ void move_chunk(const BinArgs<T>& a, const ChunkDesc&
     }
     __syncthreads();
     // (the next item's descriptor has arrived by now)
-    if (threadIdx.x == 0 && r0 + R >= cur.len && nxt.len > 0 && na) prefetch_round(*na, nxt.start, min(R, nxt.len));
+    if (threadIdx.x == 0 && r0 + R >= cur.len && nxt.len > 0 && nxt.bin >= 0 && na)
+      prefetch_round(*na, nxt.start, min(R, nxt.len));
     // 2. one reservation per destination tile (with its capacity and first slot)
     for (int k = threadIdx.x; k < kNbr; k += blockDim.x) {
       const int c = sm.cnt[k];
@@ -650,37 +807,7 @@ __device__ __forceinline__ void move_chunk(const BinArgs<T>& a, const ChunkDesc&
     }
     __syncthreads();
     // 3. write out
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-      const int meta = sm.meta[i];
-      int r, cap;
-      long long gb;
-      if (meta >= 0) {
-        const int k = meta & 127;
-        r = sm.base[k] + (meta >> 7);
-        cap = sm.cap[k];
-        gb = sm.gbase[k];
-      } else {
-        const int t = -1 - meta;
-        r = atomicAdd(a.dst_cursor + t, 1);
-        cap = a.dst_cap[t];
-        gb = a.dst_base[t];
-      }
-      long long slot;
-      if (r < cap) {
-        slot = gb + r;
-      } else {
-        const int o = atomicAdd(a.dst_cursor + a.NT, 1);
-        slot = o < a.dst_cap[a.NT] ? a.dst_base[a.NT] + o : -1;
-      }
-      if (slot >= 0) {
-        a.dx[slot] = sm.x[i];
-        a.dy[slot] = sm.y[i];
-        a.dz[slot] = sm.z[i];
-        a.did[slot] = sm.id[i];
-      } else {
-        atomicOr(a.err, 2);   // overflow bin full: the particle is lost
-      }
-    }
+    move_write_out(a, sm, cnt);
     __syncthreads();
   }
 }
@@ -837,12 +964,19 @@ __device__ __forceinline__ void chunk_count_body(const ChunkListArgs& a, int blk
   const int nb = a.NT + 1;
   const int b = blk * kCLBlock + threadIdx.x;
   long long ch = 0;
+  bool small = false;
   if (b < nb) {
     const int c = min(a.cursor[b], a.cap[b]);
     a.count[b] = c;
-    ch = (c + kChunk - 1) / kChunk;
+    small = bin_is_small(b, c, a.NT);
+    ch = small ? 0 : (c + kChunk - 1) / kChunk;
     a.other_cursor[b] = 0;
   }
+  // the first bin of a window (kMerge lanes of a warp) also holds the window's
+  // merged item, if it has small bins
+  const unsigned m = __ballot_sync(0xFFFFFFFFu, small);
+  const int lane = threadIdx.x & 31;
+  if ((lane & (kMerge - 1)) == 0 && ((m >> lane) & ((1u << kMerge) - 1u)) != 0u) ch += 1;
   long long total;
   const long long ex = block_exclusive_scan_ll(ch, total);
   if (b < nb) a.chunk_start[b] = ex;
@@ -878,7 +1012,21 @@ __device__ __forceinline__ void chunk_emit_body(const ChunkListArgs& a, int blk,
     for (int step = kCLBlock / 2; step > 0; step >>= 1)
       if (s_ls[i + step] <= q) i += step;
     const int bin = blk * kCLBlock + i;
-    const int j = (int)(q - s_ls[i]);
+    int j = (int)(q - s_ls[i]);
+    if ((bin & (kMerge - 1)) == 0) {
+      int tot = 0;
+      for (int k = 0; k < kMerge && bin + k < nb; ++k) {
+        const int cc = a.count[bin + k];
+        if (bin_is_small(bin + k, cc, a.NT)) tot += cc;
+      }
+      if (tot > 0) {
+        if (j == 0) {   // the window's merged item comes first
+          a.chunks[off + q] = ChunkDesc{(long long)(bin / kMerge), -1, tot};
+          continue;
+        }
+        j -= 1;
+      }
+    }
     const int c = a.count[bin];
     a.chunks[off + q] = ChunkDesc{a.base[bin] + (long long)j * kChunk, bin, min(kChunk, c - j * kChunk)};
   }
@@ -1107,13 +1255,12 @@ k_unbin(BinArgs<T> a, T* __restrict__ ox, T* __restrict__ oy, T* __restrict__ oz
   const long long c = blockIdx.x;
   if (c >= a.chunk_start[a.NT + 1]) return;
   const ChunkDesc d = a.chunks[c];
-  for (int i = threadIdx.x; i < d.len; i += blockDim.x) {
-    const long long s = d.start + i;
+  item_slots(a, d, [&](long long s) {
     const uint32_t id = a.sid[s];
     ox[id] = a.sx[s];
     oy[id] = a.sy[s];
     oz[id] = a.sz[s];
-  }
+  });
 }
 
 // Gather back to particle order in two coalesced-friendly passes: each
@@ -1138,10 +1285,7 @@ __global__ void __launch_bounds__(256) k_unbin_aos(BinArgs<T> a, T* __restrict__
   const long long c = blockIdx.x;
   if (c >= a.chunk_start[a.NT + 1]) return;
   const ChunkDesc d = a.chunks[c];
-  for (int i = threadIdx.x; i < d.len; i += blockDim.x) {
-    const long long s = d.start + i;
-    Vec4Store<T>::put(aos + (size_t)a.sid[s] * 4, a.sx[s], a.sy[s], a.sz[s]);
-  }
+  item_slots(a, d, [&](long long s) { Vec4Store<T>::put(aos + (size_t)a.sid[s] * 4, a.sx[s], a.sy[s], a.sz[s]); });
 }
 
 // Read-back in particle order, step 1: the particles of the current bins
@@ -1165,7 +1309,7 @@ k_partition_pieces(BinArgs<T> a, PieceBounds pb, int* __restrict__ cursor, T* __
   };
   if (threadIdx.x < PieceBounds::kMax) cnt[threadIdx.x] = 0;
   __syncthreads();
-  for (int i = threadIdx.x; i < d.len; i += blockDim.x) atomicAdd(&cnt[piece_of(a.sid[d.start + i])], 1);
+  item_slots(a, d, [&](long long s) { atomicAdd(&cnt[piece_of(a.sid[s])], 1); });
   __syncthreads();
   if (threadIdx.x < pb.np) {
     const int n = cnt[threadIdx.x];
@@ -1173,8 +1317,7 @@ k_partition_pieces(BinArgs<T> a, PieceBounds pb, int* __restrict__ cursor, T* __
     cnt[threadIdx.x] = 0;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < d.len; i += blockDim.x) {
-    const long long s = d.start + i;
+  item_slots(a, d, [&](long long s) {
     const uint32_t id = a.sid[s];
     const int k = piece_of(id);
     const long long o = pb.b[k] + base[k] + atomicAdd(&cnt[k], 1);
@@ -1182,7 +1325,7 @@ k_partition_pieces(BinArgs<T> a, PieceBounds pb, int* __restrict__ cursor, T* __
     ry[o] = a.sy[s];
     rz[o] = a.sz[s];
     rid[o] = id;
-  }
+  });
 }
 
 // Step 2, per piece: its records scattered to their particles' slots.  A
