@@ -143,7 +143,10 @@ int sipf_set_positions(sipf_ctx* ctx, const double* X);
 /* Host<->device copies of X in the context's own precision and layout
  * (three arrays of P floats or doubles).  Asynchronous on the context's
  * stream when the host buffers are pinned; the caller keeps them alive and
- * unchanged until sipf_sync().  upload re-deposits the new positions. */
+ * unchanged until sipf_sync().  upload re-deposits the new positions.
+ * download into page-locked buffers mapped into the device's address space
+ * (cudaHostAlloc / cudaHostRegister memory) is written by a kernel directly;
+ * other buffers are filled through staged copies. */
 int sipf_upload_soa(sipf_ctx* ctx, const void* x, const void* y, const void* z);
 int sipf_download_soa(sipf_ctx* ctx, void* x, void* y, void* z);
 

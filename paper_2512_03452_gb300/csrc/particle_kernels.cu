@@ -1248,6 +1248,47 @@ k_rebin_plain(const T* __restrict__ x, const T* __restrict__ y, const T* __restr
   }
 }
 
+// Read-back through a slot map: slot_of[id] = slot of particle id in the
+// current bins (one 4-byte store per particle, the map L2-resident), then
+// out[id] = X[slot_of[id]] over ids in order, so the output (host memory the
+// device can address) is written whole lines at a time.
+template <typename T>
+__global__ void __launch_bounds__(256) k_slot_map(BinArgs<T> a, uint32_t* __restrict__ slot_of) {
+  const long long c = blockIdx.x;
+  if (c >= a.chunk_start[a.NT + 1]) return;
+  const ChunkDesc d = a.chunks[c];
+  item_slots(a, d, [&](long long s) { slot_of[a.sid[s]] = (uint32_t)s; });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_gather_slots(const uint32_t* __restrict__ slot_of, const T* __restrict__ bx, const T* __restrict__ by,
+               const T* __restrict__ bz, int64_t P, T* __restrict__ ox, T* __restrict__ oy, T* __restrict__ oz) {
+  // four ids per thread and iteration, their gathers issued together
+  constexpr int U = 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < P; i0 += U * stride) {
+    uint32_t s[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) s[u] = i0 + u * stride < P ? slot_of[i0 + u * stride] : 0u;
+    T vx[U], vy[U], vz[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (i0 + u * stride < P) {
+        vx[u] = bx[s[u]];
+        vy[u] = by[s[u]];
+        vz[u] = bz[s[u]];
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (i0 + u * stride < P) {
+        ox[i0 + u * stride] = vx[u];
+        oy[i0 + u * stride] = vy[u];
+        oz[i0 + u * stride] = vz[u];
+      }
+  }
+}
+
 // Scatter binned particles back to particle order: out[id] = X[slot].
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -1645,6 +1686,18 @@ cudaError_t launch_partition_pieces(const BinArgs<T>& a, int64_t max_chunks, con
 }
 
 template <typename T>
+cudaError_t launch_read_back_mapped(const BinArgs<T>& a, int64_t max_chunks, uint32_t* slot_of, int64_t P, T* x, T* y,
+                                   T* z, cudaStream_t s) {
+  if (max_chunks < 1 || P < 1) return cudaSuccess;
+  k_slot_map<T><<<(unsigned)max_chunks, 256, 0, s>>>(a, slot_of);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t b = (P + 255) / 256;
+  k_gather_slots<T><<<(unsigned)(b > 152 * 16 ? 152 * 16 : b), 256, 0, s>>>(slot_of, a.sx, a.sy, a.sz, P, x, y, z);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_scatter_piece(const T* rx, const T* ry, const T* rz, const uint32_t* rid, int64_t a0, int64_t n,
                                  int64_t P, T* x, T* y, T* z, cudaStream_t s) {
   if (n < 1) return cudaSuccess;
@@ -1744,6 +1797,8 @@ template <typename T> cudaError_t launch_alpha_energy(const cpx<T>* alpha, int H
                                                   T*, uint32_t*, cudaStream_t);                                \
   template cudaError_t launch_scatter_piece<T>(const T*, const T*, const T*, const uint32_t*, int64_t, int64_t, \
                                                int64_t, T*, T*, T*, cudaStream_t);                             \
+  template cudaError_t launch_read_back_mapped<T>(const BinArgs<T>&, int64_t, uint32_t*, int64_t, T*, T*, T*, \
+                                                  cudaStream_t);                                              \
   template cudaError_t launch_unbin<T>(const BinArgs<T>&, int64_t, T*, T*, T*, T*, int64_t, cudaStream_t);    \
   template cudaError_t launch_deposit<T>(const T*, const T*, const T*, int64_t, Geo<T>, T, T*, int,           \
                                          cudaStream_t);                                                      \

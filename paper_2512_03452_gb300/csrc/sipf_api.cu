@@ -577,6 +577,23 @@ template <typename T> int positions_host(sipf_ctx* c, double* out) {
   return SIPF_OK;
 }
 
+// Device addresses of three host buffers, when all three are page-locked
+// allocations mapped into the device's address space (cudaHostAlloc /
+// cudaHostRegister memory): kernels can then write them directly over the
+// host link.  False for pageable memory (copies through the runtime instead).
+bool host_device_views(const void* const h[3], void* d[3]) {
+  for (int k = 0; k < 3; ++k) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, h[k]) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return false;
+    }
+    if (at.type != cudaMemoryTypeHost || at.devicePointer == nullptr) return false;
+    d[k] = at.devicePointer;
+  }
+  return true;
+}
+
 // Upload of host SoA positions.  With few enough tiles for the block-private
 // re-bin, the positions are copied in pieces on the copy stream and each piece
 // is wrapped and re-binned into the current buffer, with the current bin
@@ -614,16 +631,21 @@ template <typename T> int upload_soa_impl(sipf_ctx* c, const void* const src[3])
                           g, c->shift, c->ntx, c->NT, (T*)c->bx[b][0], (T*)c->bx[b][1], (T*)c->bx[b][2], c->bid[b],
                           c->lbase[c->lc], c->lcap[c->lc], c->cursor[b], c->err, c->stream, &e, a0, true);
     SIPF_CK(e);
+    c->launches += 1;
   }
   SIPF_CK(launch_chunk_list(cl_args(c, c->cursor[b], c->lcap[c->lc], c->lbase[c->lc], c->cursor[1 - b]), c->work,
                             nullptr, c->stream));
+  c->launches += 2;
   SIPF_CK(mark_positions(c));
   c->dep_pending = true;
   return SIPF_OK;
 }
 
-// Download to host SoA positions, on side streams as soon as the bins are
-// final (the last step's deposit may still be running on the context
+// Download to host SoA positions.  Page-locked mapped buffers: a slot map
+// of the current bins, then one kernel gathers the positions in id order and
+// writes them straight into the host buffers (whole lines over the host
+// link; no staging copy, no copy engine).  Otherwise on side streams as soon
+// as the bins are final (the last step's deposit may still be running on the context
 // stream): the bins' particles are partitioned by id into the copy's pieces
 // (records in the other bin buffer), then each piece is scattered to particle
 // order in the staging arrays and copied back, each piece's copy overlapping
@@ -633,6 +655,17 @@ template <typename T> int upload_soa_impl(sipf_ctx* c, const void* const src[3])
 // first copy.
 template <typename T> int download_soa_impl(sipf_ctx* c, void* const dst[3]) {
   const int64_t P = c->p.P;
+  void* dv[3];
+  if (c->cap_total <= (int64_t)UINT32_MAX && host_device_views(dst, dv)) {
+    // page-locked mapped buffers: a slot map in the other buffer's id array
+    // (free between steps), then the positions gathered in id order straight
+    // into the host buffers, on the context stream
+    SIPF_CK(cudaStreamWaitEvent(c->stream, c->ev_done, 0));   // a previous pieces download's copies
+    SIPF_CK(launch_read_back_mapped<T>(bin_args<T>(c, c->cur, c->lc, -1, 0), c->max_chunks(), c->bid[1 - c->cur], P,
+                                       (T*)dv[0], (T*)dv[1], (T*)dv[2], c->stream));
+    c->launches += 2;
+    return SIPF_OK;
+  }
   // the other bin buffer is free between steps (the next move overwrites it)
   const int ob = 1 - c->cur;
   T* rx = (T*)c->bx[ob][0];
@@ -649,11 +682,13 @@ template <typename T> int download_soa_impl(sipf_ctx* c, void* const dst[3]) {
   SIPF_CK(cudaMemsetAsync(c->pcur, 0, PieceBounds::kMax * sizeof(int), c->side[0]));
   SIPF_CK(launch_partition_pieces<T>(bin_args<T>(c, c->cur, c->lc, -1, 0), c->max_chunks(), pb, c->pcur, rx, ry, rz,
                                      rid, c->side[0]));
+  c->launches += 1;
   for (int k = 0; k < np; ++k) {
     const int64_t a0 = piece_begin(P, np, k), a1 = piece_begin(P, np, k + 1);
     if (a1 <= a0) continue;
     SIPF_CK(launch_scatter_piece<T>(rx, ry, rz, rid, a0, a1 - a0, P, (T*)c->st[0], (T*)c->st[1], (T*)c->st[2],
                                     c->side[0]));
+    c->launches += 1;
     SIPF_CK(cudaEventRecord(c->ev_piece[k], c->side[0]));
     SIPF_CK(cudaStreamWaitEvent(c->side[1], c->ev_piece[k], 0));
     for (int d = 0; d < 3; ++d)

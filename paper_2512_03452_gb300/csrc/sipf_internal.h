@@ -232,6 +232,12 @@ struct PieceBounds {
 template <typename T>
 cudaError_t launch_partition_pieces(const BinArgs<T>& a, int64_t max_chunks, const PieceBounds& pb, int* cursor, T* rx,
                                     T* ry, T* rz, uint32_t* rid, cudaStream_t s);
+// Particle order from the current bins through a slot map (slot_of: P
+// entries, slots < 2^32): x[id] = X[slot_of[id]], written in id order; x, y, z
+// may be host memory the device can address.
+template <typename T>
+cudaError_t launch_read_back_mapped(const BinArgs<T>& a, int64_t max_chunks, uint32_t* slot_of, int64_t P, T* x, T* y,
+                                   T* z, cudaStream_t s);
 // records [a0, a0 + n) scattered to x, y, z at their ids (ids >= P skipped)
 template <typename T>
 cudaError_t launch_scatter_piece(const T* rx, const T* ry, const T* rz, const uint32_t* rid, int64_t a0, int64_t n,

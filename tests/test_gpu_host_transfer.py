@@ -1,6 +1,7 @@
 """Host copies of the positions through the C ABI (sipf_upload_soa,
-sipf_download_soa): the pieces pipeline of both directions, for one piece
-(P < 2^20) and for eight ragged pieces.
+sipf_download_soa): page-locked buffers (read and written by kernels through
+their mapped device addresses) and pageable ones (the pieces pipeline of both
+directions, for one piece (P < 2^20) and for eight ragged pieces).
 
 * download equals sipf_positions of the same state, bit for bit;
 * upload followed by download returns the uploaded positions, bit for bit;
@@ -46,7 +47,7 @@ def _host_soa(P, dtype, pinned):
 
 
 @pytest.mark.parametrize("prec", [32, 64])
-@pytest.mark.parametrize("P,pinned", [(1000, False), ((1 << 20) + 37, True)])
+@pytest.mark.parametrize("P,pinned", [(1000, False), (1000, True), ((1 << 20) + 37, True), ((1 << 20) + 37, False)])
 def test_download_matches_positions(prec, P, pinned):
     dtype = np.float32 if prec == 32 else np.float64
     with Simulation(_params(P, prec), _blob(P, 1)) as sim:
@@ -67,29 +68,39 @@ def test_download_matches_positions(prec, P, pinned):
 
 @pytest.mark.parametrize("prec", [32, 64])
 @pytest.mark.parametrize("P", [1000, (1 << 20) + 37])
-def test_upload_download_round_trip(prec, P):
+@pytest.mark.parametrize("pinned_src", [False, True])
+def test_upload_download_round_trip(prec, P, pinned_src):
     dtype = np.float32 if prec == 32 else np.float64
     Y = _blob(P, 2).astype(dtype)
+    Y[::97, 0] += 3.0          # outside the box: the upload wraps them back in
     with Simulation(_params(P, prec), _blob(P, 3)) as sim:
-        src = [np.ascontiguousarray(Y[:, d]) for d in range(3)]
-        _abi.sipf_upload_soa(sim.ctx, *[a.ctypes.data for a in src])
+        skeep, src, sptrs = _host_soa(P, dtype, pinned_src)
+        for d in range(3):
+            src[d][:] = Y[:, d]
+        _abi.sipf_upload_soa(sim.ctx, *sptrs)
         keep, views, ptrs = _host_soa(P, dtype, True)
         _abi.sipf_download_soa(sim.ctx, *ptrs)
         sim.sync()
-        assert np.array_equal(np.stack(views, axis=1), Y)
-        assert np.array_equal(sim.positions(), Y.astype(np.float64))
-        del keep
+        # the periodic wrap of x + 3 L gives back x (x in [-L/2, L/2), exact in binary)
+        Yw = Y.copy()
+        Yw[::97, 0] -= 3.0
+        assert np.array_equal(np.stack(views, axis=1), Yw)
+        assert np.array_equal(sim.positions(), Yw.astype(np.float64))
+        del keep, skeep
 
 
 @pytest.mark.parametrize("prec", [32, 64])
-def test_reupload_then_steps_equal_a_fresh_run(prec):
+@pytest.mark.parametrize("pinned_src", [False, True])
+def test_reupload_then_steps_equal_a_fresh_run(prec, pinned_src):
     P = (1 << 20) + 37
     dtype = np.float32 if prec == 32 else np.float64
     X0 = _blob(P, 4).astype(dtype).astype(np.float64)
     prm = _params(P, prec, deposit_mode=DEPOSIT_DETERMINISTIC)
     with Simulation(prm, X0) as a, Simulation(prm, X0) as b:
-        src = [np.ascontiguousarray(X0[:, d].astype(dtype)) for d in range(3)]
-        _abi.sipf_upload_soa(a.ctx, *[s.ctypes.data for s in src])
+        skeep, src, sptrs = _host_soa(P, dtype, pinned_src)
+        for d in range(3):
+            src[d][:] = X0[:, d]
+        _abi.sipf_upload_soa(a.ctx, *sptrs)
         a.step(4)
         b.step(4)
         a.sync()
