@@ -37,20 +37,20 @@ P_FULL, H_FULL = 10_000_000, 128
 # algorithmic bytes of the particle kernel per particle-step (FP32): read X (12 B) + write X (12 B)
 BYTES_PER_PARTICLE = 24
 # DRAM traffic (read + write bytes) of the particle phase, move + re-bin
-# (310.3 MB) and deposit (134.9 MB) launches of one step, from ncu captures of
+# (311.2 MB) and deposit (134.5 MB) launches of one step, from ncu captures of
 # the torus workload, keyed by the SHA-256 of the kernel sources they were
 # taken on (a changed kernel reports null until it is captured again).
-MOVE_TRAFFIC = {"9bc72fa20b06303fca78418d2a7b1709cc0af4b1957fb5f6b67911b3f68a0ee2": 445.1e6}
+MOVE_TRAFFIC = {"ea5c1021ea1634b9c3a3093675c40629518de3b3d4191c52356743f679797366": 445.68e6}
 FALLBACK_HBM_GBS = 6800.0
-# Warp-instructions of one move + re-bin launch (140.77 M) and one deposit
-# launch (115.38 M) at P = 1e7, H = 128, FP32, from the same ncu captures,
+# Warp-instructions of one move + re-bin launch (139.03 M) and one deposit
+# launch (114.57 M) at P = 1e7, H = 128, FP32, from the same ncu captures,
 # keyed like the traffic: the particle kernels against the SMs' issue rate.
-PARTICLE_WARP_INSTR = {"9bc72fa20b06303fca78418d2a7b1709cc0af4b1957fb5f6b67911b3f68a0ee2": 256.15e6}
+PARTICLE_WARP_INSTR = {"ea5c1021ea1634b9c3a3093675c40629518de3b3d4191c52356743f679797366": 253.60e6}
 # FP64 form: FP64-pipe thread instructions (DFMA + DADD + DMUL) of one FP64 step
 # at P = 1e7, H = 128 (move 2.580e9, deposit 0.823e9, forward plane 0.112e9,
 # x pass 0.279e9, inverse plane 0.334e9), from an ncu capture of the bench's
 # FP64 leg, keyed by the SHA-256 of the kernel sources it was taken on.
-FP64_PIPE_INSTR = {"25dcbc2a977a67bcb43fa6a7eff84fd073f6364fac5794788037a669639ae7fc": 4.12745e9}
+FP64_PIPE_INSTR = {"457546566b4895eed5cdd8eb10a2106afa749b57405c546f4aed8c070c3309fb": 4.12745e9}
 
 
 def _env_int(name, default):
