@@ -313,14 +313,15 @@ __device__ __forceinline__ void binned_chunk(const BinArgs<T>& a, const ChunkDes
                                         : WinType<T>::bits - ceil_log2(len + 1));
   const T wwin = pow2<T>(K);
   const int iters = (len + blockDim.x - 1) / blockDim.x;
-  // next particle's data is loaded one iteration ahead
+  // next particle's data is loaded one iteration ahead (streaming loads: the
+  // particle arrays are read once per pass, the grids stay in L2)
   T px = T(0), py = T(0), pz = T(0);
   uint32_t pid = 0;
   if ((int)threadIdx.x < len) {
-    px = a.sx[start + threadIdx.x];
-    py = a.sy[start + threadIdx.x];
-    pz = a.sz[start + threadIdx.x];
-    pid = a.sid[start + threadIdx.x];
+    px = __ldcs(a.sx + start + threadIdx.x);
+    py = __ldcs(a.sy + start + threadIdx.x);
+    pz = __ldcs(a.sz + start + threadIdx.x);
+    pid = __ldcs(a.sid + start + threadIdx.x);
   }
   for (int it = 0; it < iters; ++it) {
     const int i = it * blockDim.x + threadIdx.x;
@@ -329,10 +330,10 @@ __device__ __forceinline__ void binned_chunk(const BinArgs<T>& a, const ChunkDes
     const uint32_t id = pid;
     if (i + (int)blockDim.x < len) {
       const long long s = start + i + blockDim.x;
-      px = a.sx[s];
-      py = a.sy[s];
-      pz = a.sz[s];
-      pid = a.sid[s];
+      px = __ldcs(a.sx + s);
+      py = __ldcs(a.sy + s);
+      pz = __ldcs(a.sz + s);
+      pid = __ldcs(a.sid + s);
     }
     if (MOVE && valid) {
       T nz[6];
@@ -651,11 +652,11 @@ template <typename T> __device__ __forceinline__ void move_write_out(const BinAr
       const int o = atomicAdd(a.dst_cursor + a.NT, 1);
       slot = o < a.dst_cap[a.NT] ? a.dst_base[a.NT] + o : -1;
     }
-    if (slot >= 0) {
-      a.dx[slot] = sm.x[i];
-      a.dy[slot] = sm.y[i];
-      a.dz[slot] = sm.z[i];
-      a.did[slot] = sm.id[i];
+    if (slot >= 0) {   // streaming stores (evicted from L2 first)
+      __stcs(a.dx + slot, sm.x[i]);
+      __stcs(a.dy + slot, sm.y[i]);
+      __stcs(a.dz + slot, sm.z[i]);
+      __stcs(a.did + slot, sm.id[i]);
     } else {
       atomicOr(a.err, 2);   // overflow bin full: the particle is lost
     }
@@ -747,10 +748,11 @@ __device__ __forceinline__ void move_chunk(const BinArgs<T>& a, const ChunkDesc&
       const uint32_t n4 = (uint32_t)((cnt + 3) & ~3);
       fence_proxy_async_smem();
       mbar_expect_tx(&sm.bar, n4 * (3 * (uint32_t)sizeof(T) + 4));
-      tma_load_1d(sm.x, a.sx + s0, n4 * sizeof(T), &sm.bar);
-      tma_load_1d(sm.y, a.sy + s0, n4 * sizeof(T), &sm.bar);
-      tma_load_1d(sm.z, a.sz + s0, n4 * sizeof(T), &sm.bar);
-      tma_load_1d(sm.id, a.sid + s0, n4 * 4, &sm.bar);
+      const uint64_t pol = l2_policy_evict_first();
+      tma_load_1d_policy(sm.x, a.sx + s0, n4 * sizeof(T), &sm.bar, pol);
+      tma_load_1d_policy(sm.y, a.sy + s0, n4 * sizeof(T), &sm.bar, pol);
+      tma_load_1d_policy(sm.z, a.sz + s0, n4 * sizeof(T), &sm.bar, pol);
+      tma_load_1d_policy(sm.id, a.sid + s0, n4 * 4, &sm.bar, pol);
       if (r0 + R < cur.len) prefetch_round(a, s0 + R, min(R, cur.len - r0 - R));
     }
     for (int k = threadIdx.x; k < kNbr; k += blockDim.x) sm.cnt[k] = 0;
