@@ -2,9 +2,13 @@
 // fixed: the transposes of the deposit I (Algorithm 2), of the gather I*
 // (Algorithm 3) and of the Fourier-side update (Eq. (alpha_hat_update), the
 // filtered spectral gradient of Algorithm 4), and the position derivatives of
-// the weight polynomials of Eqs. (2ord) and (4ord).  Particles are taken in id
-// order; X^{n-1}, the gradient grids g^{n-1} and the cotangent grids are small
-// enough to stay in L2 at the sizes the adjoint serves.
+// the weight polynomials of Eqs. (2ord) and (4ord).  The reverse step takes
+// the particles in the order of the forward step's tile bins (consecutive
+// entries share a grid tile, so the gathers and the cotangent reductions stay
+// local), each entry carrying its particle id; Xbar is kept per particle as a
+// 4-wide record (one vector load and store per entry).  The gradient and
+// cotangent grids are small enough to stay in L2 at the sizes the adjoint
+// serves.
 #include <cuda_runtime.h>
 
 #include "sipf_device.cuh"
@@ -140,6 +144,28 @@ template <> __device__ __forceinline__ void red_node3<double>(double* node, doub
   atomicAdd(node + 2, c);
 }
 
+// Xbar record of one particle: (x, y, z, 0).
+template <typename T> struct Rec4;
+template <> struct Rec4<float> {
+  static __device__ __forceinline__ A3<float> load(const float* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    return {v.x, v.y, v.z};
+  }
+  static __device__ __forceinline__ void store(float* p, float a, float b, float c) {
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, 0.f);
+  }
+};
+template <> struct Rec4<double> {
+  static __device__ __forceinline__ A3<double> load(const double* p) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    return {v.x, v.y, p[2]};
+  }
+  static __device__ __forceinline__ void store(double* p, double a, double b, double c) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+    reinterpret_cast<double2*>(p)[1] = make_double2(c, 0.0);
+  }
+};
+
 // Block sum of two values into FP64 accumulators (one atomic pair per block).
 template <typename T> __device__ __forceinline__ void block_acc2(T a, T b, double* acc) {
   __shared__ double sa[32], sb[32];
@@ -171,11 +197,11 @@ template <typename T> __device__ __forceinline__ void block_acc2(T a, T b, doubl
   }
 }
 
-// One reverse step n for every particle p (id order).  In: X^{n-1}, the
-// gradient grids g^{n-1} as (gx, gy, gz, 0) nodes, phibar^{n-1} and Xbar^n;
-// out: Xbar^{n-1} (in place), the gradient-grid cotangents gbar (H^3
-// interleaved (x, y, z, -) nodes, accumulated) and the sums for dJ/dchi and
-// dJ/ds.
+// One reverse step n for every particle.  In: X^{n-1} (entries in bin order
+// with their ids, or in particle order), the gradient grids g^{n-1} as (gx,
+// gy, gz, 0) nodes, phibar^{n-1} and Xbar^n; out: Xbar^{n-1} (in place), the
+// gradient-grid cotangents gbar (H^3 interleaved (x, y, z, -) nodes,
+// accumulated) and the sums for dJ/dchi and dJ/ds.
 // G2P / P2G: the gather and deposit orders fixed at compile time (0: taken
 // from the arguments at run time); the default pair (2, 4) compiles one
 // stencil of each kind, which keeps the kernel within 80 registers.
@@ -187,9 +213,12 @@ k_adj_step(AdjArgs<T> a) {
   const Geo<T> g = a.g;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.P; p += (int64_t)gridDim.x * blockDim.x) {
     const T x = a.x[p], y = a.y[p], z = a.z[p];
-    const T bx = a.xb[p], by = a.xb[a.P + p], bz = a.xb[2 * a.P + p];
+    const uint32_t id = a.id ? a.id[p] : (uint32_t)p;
+    T* const rec = a.xb4 + (size_t)id * 4;
+    const A3<T> b = Rec4<T>::load(rec);
+    const T bx = b.x, by = b.y, bz = b.z;
     T nz[6];
-    normals6(a.seed, (uint64_t)p, a.n, nz);
+    normals6(a.seed, (uint64_t)id, a.n, nz);
     // point where the drift gradient is gathered: X + W^- (half splitting) or X
     const T qx = a.split == 0 ? x + a.s_noise * nz[0] : x;
     const T qy = a.split == 0 ? y + a.s_noise * nz[1] : y;
@@ -224,9 +253,7 @@ k_adj_step(AdjArgs<T> a) {
     });
     // transpose of the deposit of X^{n-1}
     const A3<T> dp = deposit_adjoint<T>(a.phibar, p2g, x, y, z, a.w_inv_h, g);
-    a.xb[p] = ybx + dp.x;
-    a.xb[a.P + p] = yby + dp.y;
-    a.xb[2 * a.P + p] = ybz + dp.z;
+    Rec4<T>::store(rec, ybx + dp.x, yby + dp.y, ybz + dp.z);
   }
   block_acc2<T>(chi_part, s_part, a.acc);
 }
@@ -246,16 +273,15 @@ __global__ void __launch_bounds__(256) k_adj_planes(T* __restrict__ gbar4, T* __
   }
 }
 
-// Terminal cotangent: Xbar^N = transpose of the deposit at X^N applied to phibar^N.
+// Terminal cotangent: Xbar^N = transpose of the deposit at X^N (particle
+// order) applied to phibar^N.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_adj_terminal(const T* __restrict__ x, const T* __restrict__ y, const T* __restrict__ z, int64_t P,
-               const T* __restrict__ phibar, int p2g, T w_inv_h, Geo<T> g, T* __restrict__ xb) {
+               const T* __restrict__ phibar, int p2g, T w_inv_h, Geo<T> g, T* __restrict__ xb4) {
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
     const A3<T> dp = deposit_adjoint<T>(phibar, p2g, x[p], y[p], z[p], w_inv_h, g);
-    xb[p] = dp.x;
-    xb[P + p] = dp.y;
-    xb[2 * P + p] = dp.z;
+    Rec4<T>::store(xb4 + (size_t)p * 4, dp.x, dp.y, dp.z);
   }
 }
 
@@ -330,9 +356,9 @@ template <typename T> cudaError_t launch_adj_planes(T* gbar4, T* planes, int64_t
 
 template <typename T>
 cudaError_t launch_adj_terminal(const T* x, const T* y, const T* z, int64_t P, const T* phibar, int p2g, T w_inv_h,
-                                Geo<T> g, T* xb, cudaStream_t s) {
+                                Geo<T> g, T* xb4, cudaStream_t s) {
   if (P <= 0) return cudaSuccess;
-  k_adj_terminal<T><<<grid_blocks(P), 256, 0, s>>>(x, y, z, P, phibar, p2g, w_inv_h, g, xb);
+  k_adj_terminal<T><<<grid_blocks(P), 256, 0, s>>>(x, y, z, P, phibar, p2g, w_inv_h, g, xb4);
   return cudaGetLastError();
 }
 

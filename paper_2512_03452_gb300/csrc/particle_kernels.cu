@@ -1291,6 +1291,42 @@ k_gather_slots(const uint32_t* __restrict__ slot_of, const T* __restrict__ bx, c
   }
 }
 
+// The current bins' particles copied into contiguous arrays (x, y, z, id),
+// each work item's particles kept together in bin order, so consecutive
+// entries lie in the same grid tile; items land in the order their blocks
+// reserve their ranges (cursor: zeroed before the launch).
+template <typename T>
+__global__ void __launch_bounds__(1024)
+k_compact(BinArgs<T> a, unsigned long long* cursor, T* __restrict__ ox, T* __restrict__ oy, T* __restrict__ oz,
+          uint32_t* __restrict__ oid) {
+  __shared__ long long s_base;
+  const long long c = blockIdx.x;
+  if (c >= a.chunk_start[a.NT + 1]) return;
+  const ChunkDesc d = a.chunks[c];
+  if (threadIdx.x == 0) s_base = (long long)atomicAdd(cursor, (unsigned long long)d.len);
+  __syncthreads();
+  long long o = s_base;
+  auto copy_run = [&](long long s0, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      ox[o + i] = a.sx[s0 + i];
+      oy[o + i] = a.sy[s0 + i];
+      oz[o + i] = a.sz[s0 + i];
+      oid[o + i] = a.sid[s0 + i];
+    }
+    o += n;
+  };
+  if (d.bin >= 0) {
+    copy_run(d.start, d.len);
+    return;
+  }
+  for (int k = 0; k < kMerge; ++k) {
+    const int b = (int)d.start * kMerge + k;
+    if (b > a.NT) break;
+    const int n = a.src_count[b];
+    if (bin_is_small(b, n, a.NT)) copy_run(a.src_base[b], n);
+  }
+}
+
 // Scatter binned particles back to particle order: out[id] = X[slot].
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -1688,6 +1724,15 @@ cudaError_t launch_partition_pieces(const BinArgs<T>& a, int64_t max_chunks, con
 }
 
 template <typename T>
+cudaError_t launch_compact(const BinArgs<T>& a, int64_t max_chunks, unsigned long long* cursor, T* x, T* y, T* z,
+                           uint32_t* id, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess || max_chunks < 1) return e;
+  k_compact<T><<<(unsigned)max_chunks, 1024, 0, s>>>(a, cursor, x, y, z, id);   // a work item per block
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_read_back_mapped(const BinArgs<T>& a, int64_t max_chunks, uint32_t* slot_of, int64_t P, T* x, T* y,
                                    T* z, cudaStream_t s) {
   if (max_chunks < 1 || P < 1) return cudaSuccess;
@@ -1801,6 +1846,8 @@ template <typename T> cudaError_t launch_alpha_energy(const cpx<T>* alpha, int H
                                                int64_t, T*, T*, T*, cudaStream_t);                             \
   template cudaError_t launch_read_back_mapped<T>(const BinArgs<T>&, int64_t, uint32_t*, int64_t, T*, T*, T*, \
                                                   cudaStream_t);                                              \
+  template cudaError_t launch_compact<T>(const BinArgs<T>&, int64_t, unsigned long long*, T*, T*, T*, uint32_t*, \
+                                         cudaStream_t);                                                       \
   template cudaError_t launch_unbin<T>(const BinArgs<T>&, int64_t, T*, T*, T*, T*, int64_t, cudaStream_t);    \
   template cudaError_t launch_deposit<T>(const T*, const T*, const T*, int64_t, Geo<T>, T, T*, int,           \
                                          cudaStream_t);                                                      \

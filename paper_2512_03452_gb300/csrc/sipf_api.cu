@@ -1717,10 +1717,12 @@ struct sipf_adjoint {
   int nck = 0;
   void* ckX = nullptr;     // nck x 3P T: X^{kC} (x plane, y plane, z plane)
   void* ckA = nullptr;     // nck x S complex T: alpha^{kC}
-  void* segX = nullptr;    // C x 3P T: X^{n-1} of the segment being reversed
+  void* segX = nullptr;    // C x 3P T: X^{n-1} of the segment being reversed, in bin order (x, y, z planes)
+  uint32_t* segI = nullptr;  // C x P: the particle id of each segX entry
   void* segG = nullptr;    // C x 4 H^3 T: g^{n-1} as (gx, gy, gz, 0) nodes
   void* XN = nullptr;      // 3P T: X^N
-  void* xb = nullptr;      // 3P T: Xbar
+  void* xb = nullptr;      // 4P T: Xbar as (x, y, z, 0) per particle
+  unsigned long long* cursor = nullptr;   // scratch of the bin-order copies
   void* abar = nullptr;    // S complex T
   void* spec = nullptr;    // S complex T: L^-3 B abar, then inverse-transform work
   void* gbar = nullptr;    // 3 H^3 T: cotangent planes (the transforms' input)
@@ -1741,8 +1743,8 @@ constexpr int kAdjCheckpoint = 20;
 void adjoint_free(sipf_adjoint* a) {
   if (!a) return;
   if (a->c && a->c->stream) cudaStreamSynchronize(a->c->stream);
-  for (void* p : {a->ckX, a->ckA, a->segX, a->segG, a->XN, a->xb, a->abar, a->spec, a->gbar, a->gbar4, a->ghat,
-                  a->phibar})
+  for (void* p : {a->ckX, a->ckA, a->segX, (void*)a->segI, a->segG, a->XN, a->xb, a->abar, a->spec, a->gbar,
+                  a->gbar4, a->ghat, a->phibar, (void*)a->cursor})
     cudaFree(p);
   cudaFree(a->acc);
   for (cudaEvent_t e : a->ev)
@@ -1823,15 +1825,18 @@ int adjoint_backward_impl(sipf_adjoint* a, const double* rho_bar, double* grad_c
   const double sn = p.splitting == SIPF_SPLIT_HALF ? sqrt(p.mu * p.dt) : sqrt(2.0 * p.mu * p.dt);
   SpecParams sp = spec_params(c);
   T* segX = (T*)a->segX;
+  uint32_t* segI = a->segI;
   T* segG = (T*)a->segG;
   for (int k = a->nck - 1; k >= 0; --k) {
     const int64_t k0 = (int64_t)k * a->C, k1 = std::min<int64_t>(k0 + a->C, a->N);
     int r = load_state<T>(c, (const T*)a->ckX + (size_t)k * 3 * P, (const T*)a->ckA + (size_t)k * 2 * S, k0);
     if (r) return r;
     for (int64_t j = k0; j < k1; ++j) {
+      // X^j in the order of the current tile bins, with the particle ids
       T* X = segX + (size_t)(j - k0) * 3 * P;
-      r = positions_dev_impl<T>(c, X, X + P, X + 2 * P);
-      if (r) return r;
+      SIPF_CK(launch_compact<T>(bin_args<T>(c, c->cur, c->lc, -1, 0), c->max_chunks(), a->cursor, X, X + P, X + 2 * P,
+                                segI + (size_t)(j - k0) * P, s));
+      a->launches += 1;
       r = step_impl<T>(c, 1);
       if (r) return r;
       // after step j+1 the context's gradient buffer holds g^{j}
@@ -1844,9 +1849,10 @@ int adjoint_backward_impl(sipf_adjoint* a, const double* rho_bar, double* grad_c
       aa.x = segX + i * 3 * P;
       aa.y = aa.x + P;
       aa.z = aa.x + 2 * P;
+      aa.id = segI + i * P;
       aa.grad4 = segG + i * 4 * H3;
       aa.phibar = (const T*)a->phibar;
-      aa.xb = xb;
+      aa.xb4 = xb;
       aa.gbar = (T*)a->gbar4;
       aa.acc = a->acc;
       aa.g = geo;
@@ -1882,15 +1888,15 @@ int adjoint_backward_impl(sipf_adjoint* a, const double* rho_bar, double* grad_c
   SIPF_CK(cudaMemcpyAsync(acc, a->acc, sizeof(acc), cudaMemcpyDeviceToHost, s));
   std::vector<T> h;
   if (grad_X0) {
-    h.resize(3 * P);
-    SIPF_CK(cudaMemcpyAsync(h.data(), xb, 3 * P * sizeof(T), cudaMemcpyDeviceToHost, s));
+    h.resize(4 * P);
+    SIPF_CK(cudaMemcpyAsync(h.data(), xb, 4 * P * sizeof(T), cudaMemcpyDeviceToHost, s));
   }
   SIPF_CK(cudaStreamSynchronize(s));
   if (grad_chi) *grad_chi = acc[0];
   if (grad_mu) *grad_mu = acc[1] * sn / (2.0 * p.mu);
   if (grad_X0)
     for (size_t i = 0; i < P; ++i)
-      for (int d = 0; d < 3; ++d) grad_X0[3 * i + d] = (double)h[d * P + i];
+      for (int d = 0; d < 3; ++d) grad_X0[3 * i + d] = (double)h[4 * i + d];
   return SIPF_OK;
 }
 
@@ -1924,9 +1930,11 @@ int sipf_adjoint_init(const sipf_params* p, const double* X0, int64_t nsteps, in
   cudaError_t e = cudaMalloc(&a->ckX, (size_t)a->nck * 3 * P * esz);
   if (e == cudaSuccess) e = cudaMalloc(&a->ckA, (size_t)a->nck * 2 * S * esz);
   if (e == cudaSuccess) e = cudaMalloc(&a->segX, (size_t)a->C * 3 * P * esz);
+  if (e == cudaSuccess) e = cudaMalloc(&a->segI, (size_t)a->C * P * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&a->cursor, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&a->segG, (size_t)a->C * 4 * H3 * esz);
   if (e == cudaSuccess) e = cudaMalloc(&a->XN, 3 * P * esz);
-  if (e == cudaSuccess) e = cudaMalloc(&a->xb, 3 * P * esz);
+  if (e == cudaSuccess) e = cudaMalloc(&a->xb, 4 * P * esz);
   if (e == cudaSuccess) e = cudaMalloc(&a->abar, 2 * S * esz);
   if (e == cudaSuccess) e = cudaMalloc(&a->spec, 2 * S * esz);
   if (e == cudaSuccess) e = cudaMalloc(&a->gbar, 3 * H3 * esz);

@@ -95,15 +95,16 @@ template <typename T> FieldTune field_tune_default(int H);   // the shapes used 
 cudaError_t launch_fp64_fma(int blocks, int iters, double* sink, cudaStream_t s);
 
 // ---- adjoint launchers (adjoint_kernels.cu) ----------------------------------------
-// One reverse step over all particles in id order (see k_adj_step).
+// One reverse step over all particles (see k_adj_step).
 template <typename T>
 struct AdjArgs {
-  const T* x;          // X^{n-1}, P each (id order)
+  const T* x;          // X^{n-1}, P each, in the order of `id`
   const T* y;
   const T* z;
+  const uint32_t* id;  // particle of each entry (NULL: entry p is particle p)
   const T* grad4;      // g^{n-1}: (gx, gy, gz, 0) per node, 4 H^3
   const T* phibar;     // transpose-of-deposit cotangent grid phibar^{n-1}, H^3
-  T* xb;               // Xbar: 3 planes of P (in: Xbar^n, out: Xbar^{n-1})
+  T* xb4;              // Xbar as (x, y, z, 0) per particle, 4 P (in: Xbar^n, out: Xbar^{n-1})
   T* gbar;             // H^3 interleaved (x, y, z, -) nodes (accumulated)
   double* acc;         // [0] += sum tau V.Xbar (dJ/dchi), [1] += dJ/ds terms
   Geo<T> g;
@@ -116,9 +117,10 @@ struct AdjArgs {
 template <typename T> cudaError_t launch_adj_step(const AdjArgs<T>& a, cudaStream_t s);
 // gbar nodes -> three planes of H^3 (and the nodes cleared)
 template <typename T> cudaError_t launch_adj_planes(T* gbar4, T* planes, int64_t H3, cudaStream_t s);
+// Xbar^N as (x, y, z, 0) per particle (xb4: 4 P) from X^N in particle order.
 template <typename T>
 cudaError_t launch_adj_terminal(const T* x, const T* y, const T* z, int64_t P, const T* phibar, int p2g, T w_inv_h,
-                                Geo<T> g, T* xb, cudaStream_t s);
+                                Geo<T> g, T* xb4, cudaStream_t s);
 template <typename T>
 cudaError_t launch_adj_spectral(const cpx<T>* ghat, cpx<T>* abar, cpx<T>* spec, int H, SpecParams sp, cudaStream_t s);
 
@@ -220,6 +222,11 @@ int rebin_plain_max_tiles();
 // the scratch to three arrays.
 template <typename T> cudaError_t launch_unbin_aos(const BinArgs<T>& a, int64_t max_chunks, T* aos, cudaStream_t s);
 template <typename T> cudaError_t launch_aos4_to_soa(const T* aos, int64_t P, T* x, T* y, T* z, cudaStream_t s);
+// The current bins' particles into contiguous x, y, z, id (P each), grouped
+// by work item in bin order (cursor: device scratch, cleared here).
+template <typename T>
+cudaError_t launch_compact(const BinArgs<T>& a, int64_t max_chunks, unsigned long long* cursor, T* x, T* y, T* z,
+                           uint32_t* id, cudaStream_t s);
 // Read-back in particle order by pieces of ids: np pieces, piece k holding ids
 // [b[k], b[k+1]) (b[0] = 0, b[np] = P).
 struct PieceBounds {
