@@ -204,9 +204,10 @@ template <typename T> __device__ __forceinline__ void block_acc2(T a, T b, doubl
 // accumulated) and the sums for dJ/dchi and dJ/ds.
 // G2P / P2G: the gather and deposit orders fixed at compile time (0: taken
 // from the arguments at run time); the default pair (2, 4) compiles one
-// stencil of each kind, which keeps the kernel within 80 registers.
+// stencil of each kind, which fits the kernel in 64 registers (four blocks
+// per SM, no spills).
 template <typename T, int G2P, int P2G>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? ((G2P && P2G) ? 3 : 2) : 1)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? ((G2P && P2G) ? 4 : 2) : 1)
 k_adj_step(AdjArgs<T> a) {
   const int g2p = G2P ? G2P : a.g2p, p2g = P2G ? P2G : a.p2g;
   T chi_part = T(0), s_part = T(0);
@@ -299,10 +300,14 @@ k_adj_spectral(const cpx<T>* __restrict__ ghat, cpx<T>* __restrict__ abar, cpx<T
   const T filt = sp.H0 > 0 ? T(-2.0 * 9.869604401089358 / (sp.H0 * sp.H0)) : T(0);
   const T tau_eps = T(sp.tau / sp.eps), eps_tau = T(sp.eps / sp.tau), k2 = T(sp.k2), tau = T(sp.tau);
   const T inv_L3 = T(sp.inv_L3);
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += (size_t)gridDim.x * blockDim.x) {
-    const int mz = (int)(i % nh);
-    const int my = (int)((i / nh) % H);
-    const int mx = (int)(i / ((size_t)nh * H));
+  // 32-bit index arithmetic (S < 2^31 for H <= 256; a 64-bit division costs
+  // several times more than the element's own work)
+  const unsigned S32 = (unsigned)S, unh = (unsigned)nh, uH = (unsigned)H;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < S32; i += gridDim.x * blockDim.x) {
+    const unsigned row = i / unh;
+    const int mz = (int)(i - row * unh);
+    const int my = (int)(row % uH);
+    const int mx = (int)(row / uH);
     const int qx = mx < H / 2 ? mx : mx - H;
     const int qy = my < H / 2 ? my : my - H;
     const int qz = mz < H / 2 ? mz : mz - H;
