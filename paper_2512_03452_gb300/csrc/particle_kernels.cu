@@ -172,12 +172,15 @@ constexpr int kChunk = 4096;                  // particles per work item
 // 32 reductions per particle.
 constexpr int kWinMinLen = 64;
 // Sparse bins are taken together: the bins with fewer than kSmall particles
-// (the overflow bin excepted) of each window of kMerge consecutive bins form
-// one work item, marked by bin < 0 with the window index in `start` and the
-// bins' total in `len` (at most kMerge (kSmall - 1) < 2048).  A sparse region
-// then costs the move one round per window instead of one per bin.
-constexpr int kMerge = 4;
+// (the overflow bin excepted) of each window of m consecutive bins form one
+// work item, marked by bin = -m with the window index in `start` and the
+// bins' total in `len`.  A sparse region then costs the move one round per
+// window instead of one per bin.  m (a power of two, 2 ... kMergeMax) is set
+// per chunk list: 4 for a single run (longer merged items left the deposit's
+// last blocks idle), 16 for the runs of a batch (many sparse runs).
+constexpr int kMergeMax = 16;
 constexpr int kSmall = 256;
+__device__ __forceinline__ int merge_of(const ChunkDesc& d) { return -d.bin; }
 __device__ __forceinline__ bool bin_is_small(int b, int count, int NT) { return b < NT && count > 0 && count < kSmall; }
 
 // Calls fn(slot) for every particle of work item d, the block's threads
@@ -188,8 +191,9 @@ __device__ __forceinline__ void item_slots(const BinArgs<T>& a, const ChunkDesc&
     for (int i = threadIdx.x; i < d.len; i += blockDim.x) fn(d.start + i);
     return;
   }
-  for (int k = 0; k < kMerge; ++k) {
-    const int b = (int)d.start * kMerge + k;
+  const int m = merge_of(d);
+  for (int k = 0; k < m; ++k) {
+    const int b = (int)d.start * m + k;
     if (b > a.NT) break;
     const int c = a.src_count[b];
     if (!bin_is_small(b, c, a.NT)) continue;
@@ -286,9 +290,13 @@ __device__ __forceinline__ void window_flush(const BinArgs<T>& a, typename WinTy
 }
 
 // One work item of k_binned (deposit and/or re-bin without a move).
+// seg_cnt / seg_base (shared memory, nseg entries; NULL: the item is the
+// contiguous slots start ... start + len - 1): the item's particles are the
+// runs of seg_cnt[k] slots from seg_base[k], one after another.
 template <typename T, bool FIXED, bool MOVE, bool DEPOSIT, bool REBIN, bool WHOLE>
 __device__ __forceinline__ void binned_chunk(const BinArgs<T>& a, const ChunkDesc& cur,
-                                             typename WinType<T>::type* win) {
+                                             typename WinType<T>::type* win, const int* seg_cnt = nullptr,
+                                             const long long* seg_base = nullptr, int nseg = 0) {
   using A = typename WinType<T>::type;
   const int H = a.g.H, mask = a.g.mask;
   const int wslots = WHOLE ? H * H * H : kWinSlots;
@@ -315,13 +323,20 @@ __device__ __forceinline__ void binned_chunk(const BinArgs<T>& a, const ChunkDes
   const int iters = (len + blockDim.x - 1) / blockDim.x;
   // next particle's data is loaded one iteration ahead (streaming loads: the
   // particle arrays are read once per pass, the grids stay in L2)
+  auto slot_of = [&](int i) -> long long {
+    if (!seg_cnt) return start + i;
+    int k = 0;
+    while (k < nseg - 1 && i >= seg_cnt[k]) i -= seg_cnt[k++];
+    return seg_base[k] + i;
+  };
   T px = T(0), py = T(0), pz = T(0);
   uint32_t pid = 0;
   if ((int)threadIdx.x < len) {
-    px = __ldcs(a.sx + start + threadIdx.x);
-    py = __ldcs(a.sy + start + threadIdx.x);
-    pz = __ldcs(a.sz + start + threadIdx.x);
-    pid = __ldcs(a.sid + start + threadIdx.x);
+    const long long s = slot_of(threadIdx.x);
+    px = __ldcs(a.sx + s);
+    py = __ldcs(a.sy + s);
+    pz = __ldcs(a.sz + s);
+    pid = __ldcs(a.sid + s);
   }
   for (int it = 0; it < iters; ++it) {
     const int i = it * blockDim.x + threadIdx.x;
@@ -329,7 +344,7 @@ __device__ __forceinline__ void binned_chunk(const BinArgs<T>& a, const ChunkDes
     T x = px, y = py, z = pz;
     const uint32_t id = pid;
     if (i + (int)blockDim.x < len) {
-      const long long s = start + i + blockDim.x;
+      const long long s = slot_of(i + blockDim.x);
       px = __ldcs(a.sx + s);
       py = __ldcs(a.sy + s);
       pz = __ldcs(a.sz + s);
@@ -461,20 +476,28 @@ __device__ __forceinline__ void binned_item(const BinArgs<T>& a, const ChunkDesc
     return;
   }
   // the window's bins, looked up together
-  __shared__ int s_cnt[kMerge];
-  __shared__ long long s_base[kMerge];
-  if (threadIdx.x < kMerge) {
-    const int b = (int)cur.start * kMerge + threadIdx.x;
+  const int m = merge_of(cur);
+  __shared__ int s_cnt[kMergeMax], s_tiny[kMergeMax];
+  __shared__ long long s_base[kMergeMax];
+  if (threadIdx.x < m) {
+    const int b = (int)cur.start * m + threadIdx.x;
     int c = b <= a.NT ? a.src_count[b] : 0;
     if (!bin_is_small(b, c, a.NT)) c = 0;
     s_cnt[threadIdx.x] = c;
+    s_tiny[threadIdx.x] = !WHOLE && c < kWinMinLen ? c : 0;
     s_base[threadIdx.x] = c ? a.src_base[b] : 0;
   }
   __syncthreads();
-  for (int k = 0; k < kMerge; ++k) {
+  // bins too small for a window: all of them in one pass (global reductions)
+  int tiny = 0;
+  for (int k = 0; k < m; ++k) tiny += s_tiny[k];
+  if (tiny > 0)
+    binned_chunk<T, FIXED, MOVE, DEPOSIT, REBIN, WHOLE>(a, ChunkDesc{0, a.NT, tiny}, win, s_tiny, s_base, m);
+  // the others each with its window
+  for (int k = 0; k < m; ++k) {
     const int c = s_cnt[k];
-    if (c == 0) continue;
-    binned_chunk<T, FIXED, MOVE, DEPOSIT, REBIN, WHOLE>(a, ChunkDesc{s_base[k], (int)cur.start * kMerge + k, c}, win);
+    if (c == 0 || s_tiny[k] != 0) continue;
+    binned_chunk<T, FIXED, MOVE, DEPOSIT, REBIN, WHOLE>(a, ChunkDesc{s_base[k], (int)cur.start * m + k, c}, win);
     __syncthreads();   // the window's flush (which clears it) ends before the next bin adds into it
   }
 }
@@ -586,8 +609,8 @@ struct MoveSmem {
   int meta[R];        // neighbour slot (0..124) | rank << 7, or -1 - tile for far moves
   int cnt[kNbr], base[kNbr], tile[kNbr], cap[kNbr];
   long long gbase[kNbr];   // first slot of each destination bin
-  long long seg_base[kMerge];   // merged items: first slot and particles of each small bin
-  int seg_cnt[kMerge];
+  long long seg_base[kMergeMax];   // merged items: first slot and particles of each small bin
+  int seg_cnt[kMergeMax];
   __align__(8) uint64_t bar;
   int abort;
 };
@@ -670,8 +693,9 @@ template <typename T> __device__ __forceinline__ void move_write_out(const BinAr
 template <typename T, bool MOVE, int G2P>
 __device__ __forceinline__ void move_merged(const BinArgs<T>& a, const ChunkDesc& cur, uint32_t n, MoveSmem<T>& sm) {
   constexpr int R = MoveRound<T>::n;
-  if (threadIdx.x < kMerge) {
-    const int b = (int)cur.start * kMerge + threadIdx.x;
+  const int m = merge_of(cur);
+  if (threadIdx.x < m) {
+    const int b = (int)cur.start * m + threadIdx.x;
     int c = 0;
     long long base = 0;
     if (b <= a.NT) {
@@ -689,7 +713,7 @@ __device__ __forceinline__ void move_merged(const BinArgs<T>& a, const ChunkDesc
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
       // the bin holding item particle r0 + i
       int k = 0, o = r0 + i;
-      while (k < kMerge - 1 && o >= sm.seg_cnt[k]) o -= sm.seg_cnt[k++];
+      while (k < m - 1 && o >= sm.seg_cnt[k]) o -= sm.seg_cnt[k++];
       const long long slot = sm.seg_base[k] + o;
       T x = a.sx[slot], y = a.sy[slot], z = a.sz[slot];
       const uint32_t id = a.sid[slot];
@@ -974,11 +998,11 @@ __device__ __forceinline__ void chunk_count_body(const ChunkListArgs& a, int blk
     ch = small ? 0 : (c + kChunk - 1) / kChunk;
     a.other_cursor[b] = 0;
   }
-  // the first bin of a window (kMerge lanes of a warp) also holds the window's
-  // merged item, if it has small bins
-  const unsigned m = __ballot_sync(0xFFFFFFFFu, small);
-  const int lane = threadIdx.x & 31;
-  if ((lane & (kMerge - 1)) == 0 && ((m >> lane) & ((1u << kMerge) - 1u)) != 0u) ch += 1;
+  // the first bin of a window (a.merge lanes of a warp) also holds the
+  // window's merged item, if it has small bins
+  const unsigned sm = __ballot_sync(0xFFFFFFFFu, small);
+  const int lane = threadIdx.x & 31, mw = a.merge;
+  if ((lane & (mw - 1)) == 0 && ((sm >> lane) & ((1u << mw) - 1u)) != 0u) ch += 1;
   long long total;
   const long long ex = block_exclusive_scan_ll(ch, total);
   if (b < nb) a.chunk_start[b] = ex;
@@ -1015,15 +1039,15 @@ __device__ __forceinline__ void chunk_emit_body(const ChunkListArgs& a, int blk,
       if (s_ls[i + step] <= q) i += step;
     const int bin = blk * kCLBlock + i;
     int j = (int)(q - s_ls[i]);
-    if ((bin & (kMerge - 1)) == 0) {
+    if ((bin & (a.merge - 1)) == 0) {
       int tot = 0;
-      for (int k = 0; k < kMerge && bin + k < nb; ++k) {
+      for (int k = 0; k < a.merge && bin + k < nb; ++k) {
         const int cc = a.count[bin + k];
         if (bin_is_small(bin + k, cc, a.NT)) tot += cc;
       }
       if (tot > 0) {
         if (j == 0) {   // the window's merged item comes first
-          a.chunks[off + q] = ChunkDesc{(long long)(bin / kMerge), -1, tot};
+          a.chunks[off + q] = ChunkDesc{(long long)(bin / a.merge), -a.merge, tot};
           continue;
         }
         j -= 1;
@@ -1319,8 +1343,9 @@ k_compact(BinArgs<T> a, unsigned long long* cursor, T* __restrict__ ox, T* __res
     copy_run(d.start, d.len);
     return;
   }
-  for (int k = 0; k < kMerge; ++k) {
-    const int b = (int)d.start * kMerge + k;
+  const int m = merge_of(d);
+  for (int k = 0; k < m; ++k) {
+    const int b = (int)d.start * m + k;
     if (b > a.NT) break;
     const int n = a.src_count[b];
     if (bin_is_small(b, n, a.NT)) copy_run(a.src_base[b], n);

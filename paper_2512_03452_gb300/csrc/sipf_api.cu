@@ -189,6 +189,9 @@ struct sipf_ctx {
   bool fixed() const { return p.deposit_mode == SIPF_DEPOSIT_DETERMINISTIC; }
   int64_t max_chunks() const { return p.P / binned_chunk() + NT + 2; }
   int resort() const { return p.resort_every > 0 ? p.resort_every : 16; }
+  // bins per merge window of the chunk lists (small bins of a window form one
+  // work item): 4 for a single run, 16 for the runs of a batch
+  int merge = 4;
 };
 
 enum { kDscMass = 0, kDscAlpha0 = 1, kDscM2 = 2, kDscRing = 3, kDscHF = 4, kDscTot = 5, kDscMax = 6, kDscCount = 8 };
@@ -279,7 +282,7 @@ template <typename T> BinArgs<T> bin_args(sipf_ctx* c, int src_buf, int src_lay,
 // Chunk-list arguments: bins of (cursor, cap, base) into the context's chunk
 // arrays; `other` are the cursors to clear for the next pass.
 ChunkListArgs cl_args(sipf_ctx* c, const int* cursor, const int* cap, const long long* base, int* other) {
-  return ChunkListArgs{cursor, cap, base, c->count, c->chunk_start, c->chunks, other, c->NT, c->part};
+  return ChunkListArgs{cursor, cap, base, c->count, c->chunk_start, c->chunks, other, c->NT, c->part, c->merge};
 }
 
 // The current bins are final (positions of step n, before their deposit):
@@ -1567,6 +1570,16 @@ int sipf_batch_init(int32_t nruns, const sipf_params* params, const double* cons
       return v;
     }
     b->runs.push_back(c);
+    // many sparse runs: merge windows of 16 bins; the current bins' chunk
+    // list is made again with them (their counts are unchanged)
+    c->merge = 16;
+    cudaError_t e = launch_chunk_list(cl_args(c, c->cursor[c->cur], c->lcap[c->lc], c->lbase[c->lc],
+                                              c->cursor[1 - c->cur]),
+                                      c->work, nullptr, c->stream);
+    if (e != cudaSuccess) {
+      batch_free(b);
+      return cuda_fail(e, "sipf_batch_init chunk list");
+    }
   }
   for (sipf_ctx* c : b->runs) {
     bool found = false;

@@ -171,6 +171,7 @@ struct ChunkListArgs {
   int* other_cursor;        // cursors of the other buffer (cleared)
   int NT;
   long long* part;          // chunk totals of the blocks of kCLBlock bins (chunk_list_blocks(NT))
+  int merge;                // bins per merge window of the small bins (power of two, 2 ... 16)
 };
 struct LayoutArgs {
   const int* want;
