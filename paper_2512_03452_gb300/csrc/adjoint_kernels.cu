@@ -144,6 +144,21 @@ template <> __device__ __forceinline__ void red_node3<double>(double* node, doub
   atomicAdd(node + 2, c);
 }
 
+// One (x, y, z, -) node of the gradient grids, read through the read-only path.
+template <typename T> struct Node4;
+template <> struct Node4<float> {
+  static __device__ __forceinline__ A3<float> load(const float* p) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return {v.x, v.y, v.z};
+  }
+};
+template <> struct Node4<double> {
+  static __device__ __forceinline__ A3<double> load(const double* p) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    return {v.x, v.y, __ldg(p + 2)};
+  }
+};
+
 // Xbar record of one particle: (x, y, z, 0).
 template <typename T> struct Rec4;
 template <> struct Rec4<float> {
@@ -228,8 +243,8 @@ k_adj_step(AdjArgs<T> a) {
     T V[3] = {T(0), T(0), T(0)};
     T J[3][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
     stencil_grad_visit<T>(g2p, qx, qy, qz, g, [&](int idx, T f, T fx, T fy, T fz) {
-      const T* gp = a.grad4 + (size_t)idx * 4;
-      const T v[3] = {__ldg(gp), __ldg(gp + 1), __ldg(gp + 2)};
+      const A3<T> g3 = Node4<T>::load(a.grad4 + (size_t)idx * 4);   // one vector load per node
+      const T v[3] = {g3.x, g3.y, g3.z};
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         V[d] += f * v[d];
