@@ -131,6 +131,100 @@ __device__ __forceinline__ A3<T> deposit_adjoint(const T* __restrict__ phibar, i
   return A3<T>{s.x * w_inv_h, s.y * w_inv_h, s.z * w_inv_h};
 }
 
+// The same for Gamma_4 from the z-quads of phibar (quad at node (x, y, z):
+// phibar at z - 1, z, z + 1, z + 2): the 32 nodes lie on 12 (x, y) columns,
+// the four inner columns using all four z layers (the z-outer nodes and the
+// inner ones), the x-outer and y-outer columns the two inner z layers; one
+// vector load per column instead of one scalar load per node.
+template <typename T> struct Quad { T v[4]; };
+template <typename T> __device__ __forceinline__ Quad<T> load_quad(const T* p);
+template <> __device__ __forceinline__ Quad<float> load_quad<float>(const float* p) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return {{v.x, v.y, v.z, v.w}};
+}
+template <> __device__ __forceinline__ Quad<double> load_quad<double>(const double* p) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p)), b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  return {{a.x, a.y, b.x, b.y}};
+}
+
+template <typename T>
+__device__ __forceinline__ A3<T> deposit_adjoint4_quads(const T* __restrict__ quads, T px, T py, T pz, T w_inv_h,
+                                                        const Geo<T>& g) {
+  int cx, cy, cz;
+  T lx, ly, lz;
+  cell_lambda(px, g, cx, lx);
+  cell_lambda(py, g, cy, ly);
+  cell_lambda(pz, g, cz, lz);
+  int ix[4], iy[4];
+  axis_layers_global(cx, g.mask, g.H * g.H, ix);
+  axis_layers_global(cy, g.mask, g.H, iy);
+  const int iz = cz & g.mask;
+  const AxisD<T> ax = axis_d(lx), ay = axis_d(ly), az = axis_d(lz);
+  const T B = T(1) + ax.q + ay.q + az.q;
+  A3<T> s{T(0), T(0), T(0)};
+  auto add = [&](T fx, T fy, T fz, T v) {
+    s.x += fx * v;
+    s.y += fy * v;
+    s.z += fz * v;
+  };
+  // inner columns: z-outer node (layer 0, om), inner nodes (layers 1, 2), z-outer node (layer 3, o2)
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const Quad<T> q = load_quad<T>(quads + (size_t)(ix[a + 1] + iy[b + 1] + iz) * 4);
+      const T fxy = ax.f[a] * ay.f[b], dxy = ax.d[a] * ay.f[b], xdy = ax.f[a] * ay.d[b];
+      add(az.om * dxy, az.om * xdy, az.dom * fxy, q.v[0]);
+      add(az.o2 * dxy, az.o2 * xdy, az.do2 * fxy, q.v[3]);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const T tri = fxy * az.f[c];
+        add(ax.dq * tri + B * dxy * az.f[c], ay.dq * tri + B * xdy * az.f[c], az.dq * tri + B * fxy * az.d[c],
+            q.v[c + 1]);
+      }
+    }
+  // x-outer columns (x layer 0: om, 3: o2), inner y and z layers
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    const Quad<T> qm = load_quad<T>(quads + (size_t)(ix[0] + iy[b + 1] + iz) * 4);
+    const Quad<T> qp = load_quad<T>(quads + (size_t)(ix[3] + iy[b + 1] + iz) * 4);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const T yz = ay.f[b] * az.f[c], dyz = ay.d[b] * az.f[c], ydz = ay.f[b] * az.d[c];
+      add(ax.dom * yz, ax.om * dyz, ax.om * ydz, qm.v[c + 1]);
+      add(ax.do2 * yz, ax.o2 * dyz, ax.o2 * ydz, qp.v[c + 1]);
+    }
+  }
+  // y-outer columns (y layer 0: om, 3: o2), inner x and z layers
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const Quad<T> qm = load_quad<T>(quads + (size_t)(ix[a + 1] + iy[0] + iz) * 4);
+    const Quad<T> qp = load_quad<T>(quads + (size_t)(ix[a + 1] + iy[3] + iz) * 4);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const T xz = ax.f[a] * az.f[c], dxz = ax.d[a] * az.f[c], xdz = ax.f[a] * az.d[c];
+      add(ay.om * dxz, ay.dom * xz, ay.om * xdz, qm.v[c + 1]);
+      add(ay.o2 * dxz, ay.do2 * xz, ay.o2 * xdz, qp.v[c + 1]);
+    }
+  }
+  return A3<T>{s.x * w_inv_h, s.y * w_inv_h, s.z * w_inv_h};
+}
+
+// phibar (H^3) -> its z-quads (4 H^3): quad n = phibar at z - 1, z, z + 1, z + 2 (periodic).
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_quads(const T* __restrict__ phibar, T* __restrict__ quads, int H,
+                                                   int64_t H3) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < H3; i += (int64_t)gridDim.x * blockDim.x) {
+    const int z = (int)(i & (H - 1));
+    const int64_t row = i - z;
+    T* q = quads + (size_t)i * 4;
+    q[0] = phibar[row + ((z - 1) & (H - 1))];
+    q[1] = phibar[i];
+    q[2] = phibar[row + ((z + 1) & (H - 1))];
+    q[3] = phibar[row + ((z + 2) & (H - 1))];
+  }
+}
+
 // Add (a, b, c) to one (x, y, z, -) node of the interleaved cotangent grid:
 // one 16-byte vector reduction in single precision (one L2 sector operation
 // instead of three), three scalar ones in double precision.
@@ -268,7 +362,9 @@ k_adj_step(AdjArgs<T> a) {
       red_node3<T>(a.gbar + (size_t)idx * 4, f * cbx, f * cby, f * cbz);
     });
     // transpose of the deposit of X^{n-1}
-    const A3<T> dp = deposit_adjoint<T>(a.phibar, p2g, x, y, z, a.w_inv_h, g);
+    // (the Gamma_4 specialisation reads the z-quads; the run-time-order kernel phibar)
+    const A3<T> dp = P2G == 4 ? deposit_adjoint4_quads<T>(a.phibar4, x, y, z, a.w_inv_h, g)
+                              : deposit_adjoint<T>(a.phibar, p2g, x, y, z, a.w_inv_h, g);
     Rec4<T>::store(rec, ybx + dp.x, yby + dp.y, ybz + dp.z);
   }
   block_acc2<T>(chi_part, s_part, a.acc);
@@ -369,6 +465,12 @@ template <typename T> cudaError_t launch_adj_step(const AdjArgs<T>& a, cudaStrea
   return cudaGetLastError();
 }
 
+template <typename T> cudaError_t launch_adj_quads(const T* phibar, T* quads, int H, cudaStream_t s) {
+  const int64_t H3 = (int64_t)H * H * H;
+  k_adj_quads<T><<<grid_blocks(H3), 256, 0, s>>>(phibar, quads, H, H3);
+  return cudaGetLastError();
+}
+
 template <typename T> cudaError_t launch_adj_planes(T* gbar4, T* planes, int64_t H3, cudaStream_t s) {
   k_adj_planes<T><<<grid_blocks(H3), 256, 0, s>>>(gbar4, planes, H3);
   return cudaGetLastError();
@@ -393,6 +495,7 @@ cudaError_t launch_adj_spectral(const cpx<T>* ghat, cpx<T>* abar, cpx<T>* spec, 
 #define SIPF_ADJ_INST(T)                                                                                          \
   template cudaError_t launch_adj_step<T>(const AdjArgs<T>&, cudaStream_t);                                      \
   template cudaError_t launch_adj_planes<T>(T*, T*, int64_t, cudaStream_t);                                      \
+  template cudaError_t launch_adj_quads<T>(const T*, T*, int, cudaStream_t);                                     \
   template cudaError_t launch_adj_terminal<T>(const T*, const T*, const T*, int64_t, const T*, int, T, Geo<T>, T*, \
                                               cudaStream_t);                                                     \
   template cudaError_t launch_adj_spectral<T>(const cpx<T>*, cpx<T>*, cpx<T>*, int, SpecParams, cudaStream_t);

@@ -1742,6 +1742,7 @@ struct sipf_adjoint {
   void* gbar4 = nullptr;   // 4 H^3 T: cotangents accumulated as (x, y, z, -) nodes, kept zero between steps
   void* ghat = nullptr;    // 3 S complex T
   void* phibar = nullptr;  // H^3 T
+  void* phibar4 = nullptr; // 4 H^3 T: z-quads of phibar (the reverse step's Gamma_4 transpose reads them)
   double* acc = nullptr;   // [dJ/dchi, dJ/ds]
   std::vector<double> X0;
   bool have_forward = false;
@@ -1757,7 +1758,7 @@ void adjoint_free(sipf_adjoint* a) {
   if (!a) return;
   if (a->c && a->c->stream) cudaStreamSynchronize(a->c->stream);
   for (void* p : {a->ckX, a->ckA, a->segX, (void*)a->segI, a->segG, a->XN, a->xb, a->abar, a->spec, a->gbar,
-                  a->gbar4, a->ghat, a->phibar, (void*)a->cursor})
+                  a->gbar4, a->ghat, a->phibar, a->phibar4, (void*)a->cursor})
     cudaFree(p);
   cudaFree(a->acc);
   for (cudaEvent_t e : a->ev)
@@ -1834,6 +1835,7 @@ int adjoint_backward_impl(sipf_adjoint* a, const double* rho_bar, double* grad_c
   a->launches += 1;
   SIPF_CK(cudaMemsetAsync(a->abar, 0, S * 2 * sizeof(T), s));
   SIPF_CK(cudaMemsetAsync(a->phibar, 0, H3 * sizeof(T), s));   // phibar^{N-1} = L^-3 F^-1 (B abar^N) = 0
+  SIPF_CK(cudaMemsetAsync(a->phibar4, 0, 4 * H3 * sizeof(T), s));
   SIPF_CK(cudaMemsetAsync(a->acc, 0, 2 * sizeof(double), s));
   const double sn = p.splitting == SIPF_SPLIT_HALF ? sqrt(p.mu * p.dt) : sqrt(2.0 * p.mu * p.dt);
   SpecParams sp = spec_params(c);
@@ -1865,6 +1867,7 @@ int adjoint_backward_impl(sipf_adjoint* a, const double* rho_bar, double* grad_c
       aa.id = segI + i * P;
       aa.grad4 = segG + i * 4 * H3;
       aa.phibar = (const T*)a->phibar;
+      aa.phibar4 = (const T*)a->phibar4;
       aa.xb4 = xb;
       aa.gbar = (T*)a->gbar4;
       aa.acc = a->acc;
@@ -1893,7 +1896,8 @@ int adjoint_backward_impl(sipf_adjoint* a, const double* rho_bar, double* grad_c
       SIPF_CK(launch_cols<T>(sc, H, 1, H * nh, 1, 0, +1, 1.0, s));
       SIPF_CK(launch_cols<T>(sc, H, H, nh, 1, 0, +1, 1.0, s));
       SIPF_CK(launch_rows_c2r<T>(sc, 1, 0, (T*)a->phibar, H, H * H, nullptr, s));
-      a->launches += 9;
+      SIPF_CK(launch_adj_quads<T>((const T*)a->phibar, (T*)a->phibar4, H, s));
+      a->launches += 10;
     }
   }
   SIPF_CK(cudaEventRecord(a->ev[3], s));
@@ -1955,6 +1959,7 @@ int sipf_adjoint_init(const sipf_params* p, const double* X0, int64_t nsteps, in
   if (e == cudaSuccess) e = cudaMemset(a->gbar4, 0, 4 * H3 * esz);
   if (e == cudaSuccess) e = cudaMalloc(&a->ghat, 3 * 2 * S * esz);
   if (e == cudaSuccess) e = cudaMalloc(&a->phibar, H3 * esz);
+  if (e == cudaSuccess) e = cudaMalloc(&a->phibar4, 4 * H3 * esz);
   if (e == cudaSuccess) e = cudaMalloc(&a->acc, 2 * sizeof(double));
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&a->ev[i]);
   if (e != cudaSuccess) {

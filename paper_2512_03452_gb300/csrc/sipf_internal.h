@@ -104,6 +104,7 @@ struct AdjArgs {
   const uint32_t* id;  // particle of each entry (NULL: entry p is particle p)
   const T* grad4;      // g^{n-1}: (gx, gy, gz, 0) per node, 4 H^3
   const T* phibar;     // transpose-of-deposit cotangent grid phibar^{n-1}, H^3
+  const T* phibar4;    // its z-quads (phibar at z - 1 ... z + 2 per node, 4 H^3), read by the Gamma_4 kernel
   T* xb4;              // Xbar as (x, y, z, 0) per particle, 4 P (in: Xbar^n, out: Xbar^{n-1})
   T* gbar;             // H^3 interleaved (x, y, z, -) nodes (accumulated)
   double* acc;         // [0] += sum tau V.Xbar (dJ/dchi), [1] += dJ/ds terms
@@ -115,6 +116,8 @@ struct AdjArgs {
   int p2g, g2p, split;
 };
 template <typename T> cudaError_t launch_adj_step(const AdjArgs<T>& a, cudaStream_t s);
+// phibar -> z-quads (4 H^3: phibar at z - 1, z, z + 1, z + 2 of each node)
+template <typename T> cudaError_t launch_adj_quads(const T* phibar, T* quads, int H, cudaStream_t s);
 // gbar nodes -> three planes of H^3 (and the nodes cleared)
 template <typename T> cudaError_t launch_adj_planes(T* gbar4, T* planes, int64_t H3, cudaStream_t s);
 // Xbar^N as (x, y, z, 0) per particle (xb4: 4 P) from X^N in particle order.
