@@ -40,17 +40,17 @@ BYTES_PER_PARTICLE = 24
 # (299.6 MB) and deposit (133.6 MB) launches of one step, from ncu captures of
 # the torus workload, keyed by the SHA-256 of the kernel sources they were
 # taken on (a changed kernel reports null until it is captured again).
-MOVE_TRAFFIC = {"bad0c0b2bf81a23c5fc77686f96b272f6b400a286cec9b150fc537bc85e2f47f": 433.24e6}
+MOVE_TRAFFIC = {"af067192ec93fe8a92e48f2ffbff6541e052076bb192cdcf998acd26bf2aac78": 433.24e6}
 FALLBACK_HBM_GBS = 6800.0
 # Warp-instructions of one move + re-bin launch (136.76 M) and one deposit
 # launch (114.26 M) at P = 1e7, H = 128, FP32, from the same ncu captures,
 # keyed like the traffic: the particle kernels against the SMs' issue rate.
-PARTICLE_WARP_INSTR = {"bad0c0b2bf81a23c5fc77686f96b272f6b400a286cec9b150fc537bc85e2f47f": 251.03e6}
+PARTICLE_WARP_INSTR = {"af067192ec93fe8a92e48f2ffbff6541e052076bb192cdcf998acd26bf2aac78": 251.03e6}
 # FP64 form: FP64-pipe thread instructions (DFMA + DADD + DMUL) of one FP64 step
 # at P = 1e7, H = 128 (move 2.580e9, deposit 0.823e9, forward plane 0.112e9,
 # x pass 0.279e9, inverse plane 0.334e9), from an ncu capture of the bench's
 # FP64 leg, keyed by the SHA-256 of the kernel sources it was taken on.
-FP64_PIPE_INSTR = {"e622a9b3c47c35025b13c933fba5cfc79f00fcb2e05d41648be19c468a818200": 4.12745e9}
+FP64_PIPE_INSTR = {"e1bf6e4513cdb693c69be5232586692a8edd6f39b21b971879dcdc4310e0ee61": 4.12745e9}
 
 
 def _env_int(name, default):

@@ -466,8 +466,9 @@ __device__ __forceinline__ void binned_chunk(const BinArgs<T>& a, const ChunkDes
   }
 }
 
-// A work item of k_binned: one bin's chunk, or each small bin of a merged item
-// in turn (each with its own window).
+// A work item of k_binned: one bin's chunk, or a merged item: its bins under
+// kWinMinLen particles in one pass without a window, then each other small
+// bin with its own window.
 template <typename T, bool FIXED, bool MOVE, bool DEPOSIT, bool REBIN, bool WHOLE>
 __device__ __forceinline__ void binned_item(const BinArgs<T>& a, const ChunkDesc& cur,
                                             typename WinType<T>::type* win) {
