@@ -1743,6 +1743,7 @@ struct sipf_adjoint {
   void* ghat = nullptr;    // 3 S complex T
   void* phibar = nullptr;  // H^3 T
   void* phibar4 = nullptr; // 4 H^3 T: z-quads of phibar (the reverse step's Gamma_4 transpose reads them)
+  void* fwd_tab = nullptr; // H >= 32: three FftRun<T> (cotangent plane d -> ghat d) for the plane forward transforms
   double* acc = nullptr;   // [dJ/dchi, dJ/ds]
   std::vector<double> X0;
   bool have_forward = false;
@@ -1758,13 +1759,32 @@ void adjoint_free(sipf_adjoint* a) {
   if (!a) return;
   if (a->c && a->c->stream) cudaStreamSynchronize(a->c->stream);
   for (void* p : {a->ckX, a->ckA, a->segX, (void*)a->segI, a->segG, a->XN, a->xb, a->abar, a->spec, a->gbar,
-                  a->gbar4, a->ghat, a->phibar, a->phibar4, (void*)a->cursor})
+                  a->gbar4, a->ghat, a->phibar, a->phibar4, (void*)a->cursor, a->fwd_tab})
     cudaFree(p);
   cudaFree(a->acc);
   for (cudaEvent_t e : a->ev)
     if (e) cudaEventDestroy(e);
   free_ctx(a->c);
   delete a;
+}
+
+// The three cotangent planes as runs of the batched field-solve kernels, so
+// their forward transforms (rows r2c and the y axis) run as one plane kernel
+// launch (H >= 32); the plane kernel clears each plane as it reads it.
+template <typename T> cudaError_t adjoint_fwd_table(sipf_adjoint* a) {
+  const sipf_ctx* c = a->c;
+  const size_t H3 = (size_t)c->H3(), S = (size_t)c->S();
+  FftRun<T> r[3];
+  for (int d = 0; d < 3; ++d) {
+    r[d] = FftRun<T>{};
+    r[d].phi = (T*)a->gbar + d * H3;
+    r[d].phi_fixed = 0;
+    r[d].in_scale = 1.0;
+    r[d].T1 = (cpx<T>*)a->ghat + d * S;
+  }
+  cudaError_t e = cudaMalloc(&a->fwd_tab, sizeof(r));
+  if (e == cudaSuccess) e = cudaMemcpy(a->fwd_tab, r, sizeof(r), cudaMemcpyHostToDevice);
+  return e;
 }
 
 // Put the context in state (X in id order, alpha, step n): re-bin and deposit.
@@ -1886,8 +1906,14 @@ int adjoint_backward_impl(sipf_adjoint* a, const double* rho_bar, double* grad_c
       SIPF_CK(launch_adj_planes<T>((T*)a->gbar4, (T*)a->gbar, (int64_t)H3, s));
       // ghat = unnormalised DFT of the three cotangent grids
       cpx<T>* gh = (cpx<T>*)a->ghat;
-      SIPF_CK(launch_rows_r2c<T>(a->gbar, 0, 1.0, false, gh, H, 3 * H * H, nullptr, s));
-      SIPF_CK(launch_cols<T>(gh, H, 3 * H, nh, 1, 0, -1, 1.0, s));
+      if (a->fwd_tab) {
+        int fk = 0;
+        SIPF_CK(launch_field_batch<T>((const FftRun<T>*)a->fwd_tab, 3, H, kFieldForward, s, FieldTune{}, &fk));
+        a->launches += fk - 2;
+      } else {
+        SIPF_CK(launch_rows_r2c<T>(a->gbar, 0, 1.0, false, gh, H, 3 * H * H, nullptr, s));
+        SIPF_CK(launch_cols<T>(gh, H, 3 * H, nh, 1, 0, -1, 1.0, s));
+      }
       SIPF_CK(launch_cols<T>(gh, H, 1, H * nh, 3, S, -1, 1.0, s));
       // abar^{n-1} = A abar^n + Gop^T gbar;  spec = L^-3 B abar^{n-1}
       cpx<T>* sc = (cpx<T>*)a->spec;
@@ -1962,6 +1988,8 @@ int sipf_adjoint_init(const sipf_params* p, const double* X0, int64_t nsteps, in
   if (e == cudaSuccess) e = cudaMalloc(&a->phibar4, 4 * H3 * esz);
   if (e == cudaSuccess) e = cudaMalloc(&a->acc, 2 * sizeof(double));
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&a->ev[i]);
+  if (e == cudaSuccess && p->H >= 32)
+    e = p->precision == 64 ? adjoint_fwd_table<double>(a) : adjoint_fwd_table<float>(a);
   if (e != cudaSuccess) {
     adjoint_free(a);
     return cuda_fail(e, "sipf_adjoint_init allocation");
