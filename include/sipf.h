@@ -124,7 +124,8 @@ int sipf_init(const sipf_params* p, const double* X0, void* stream, sipf_ctx** o
  * alpha (Eq. (alpha_hat_update)) with the filtered spectral gradient of
  * alpha^(n-1), three inverse transforms, the particle move (W^-, gather of
  * grad c at X + W^- with I*, drift, W^+, periodic wrap) with re-binning of
- * the particles by grid tile, and the deposit of X^(n) for the next step. */
+ * the particles by grid tile; the deposit of X^(n) is made when the grid is
+ * next read (the next step's first kernel, or a density query). */
 int sipf_step(sipf_ctx* ctx, int64_t nsteps);
 
 /* Advance until n * dt >= T (N_T = ceil(T/dt) steps in total). */
