@@ -802,6 +802,31 @@ def run_batch_case(args):
                           "ms_per_step": e0.elapsed_time(e1) / max(args.steps, 1)}), flush=True)
 
 
+def run_field_case(args):
+    """One grid size's field solve for kernel captures: the ring workload with
+    1e6 particles at H = args.field_case (the field kernels do not depend on
+    P), `warmup` steps, then `steps` steps with the per-stage events; prints
+    the stage times.  Not a benchmark line."""
+    import torch
+
+    from paper_2512_03452_gb300 import Simulation, _abi, build, params_from_workload, workloads
+
+    build.build()
+    _abi.load()
+    w = workloads.torus_ring(H=args.field_case, P=1_000_000)
+    stream = torch.cuda.Stream()
+    with Simulation(params_from_workload(w, precision=32), workloads.sample_positions(w),
+                    stream=stream.cuda_stream) as sim:
+        sim.step(args.warmup)
+        sim.sync()
+        _abi.sipf_timing_enable(sim.ctx, 1)
+        sim.step(args.steps)
+        t = _abi.sipf_timing_read(sim.ctx)
+    n = max(t.steps, 1)
+    print(json.dumps({"case": f"field solve, ring workload, H={args.field_case}, P=1e6, FP32",
+                      **{k: getattr(t, k) / n for k in ("forward_ms", "spectral_ms", "inverse_ms")}}), flush=True)
+
+
 def run_adjoint_case():
     """Only the adjoint leg (for kernel captures); prints its JSON object."""
     import torch
@@ -831,7 +856,12 @@ def main():
     ap.add_argument("--batch-case", action="store_true",
                     help="only run a small 128-run H = 64 batch (for kernel captures) and print its ms per step")
     ap.add_argument("--adjoint-case", action="store_true", help="only run the adjoint leg (for kernel captures)")
+    ap.add_argument("--field-case", type=int, choices=[32, 64, 128, 256], default=0,
+                    help="only run a few steps at this H with stage timing (field-solve kernel captures)")
     args = ap.parse_args()
+    if args.field_case:
+        run_field_case(args)
+        return
     if args.batch_case:
         run_batch_case(args)
         return
