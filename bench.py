@@ -50,7 +50,7 @@ PARTICLE_WARP_INSTR = {"af067192ec93fe8a92e48f2ffbff6541e052076bb192cdcf998acd26
 # at P = 1e7, H = 128 (move 2.580e9, deposit 0.823e9, forward plane 0.112e9,
 # x pass 0.279e9, inverse plane 0.334e9), from an ncu capture of the bench's
 # FP64 leg, keyed by the SHA-256 of the kernel sources it was taken on.
-FP64_PIPE_INSTR = {"e1bf6e4513cdb693c69be5232586692a8edd6f39b21b971879dcdc4310e0ee61": 4.12745e9}
+FP64_PIPE_INSTR = {"eaa1e4f0009f7dd9533feb7aaa01105800b41b45b6b8da64a22e35c42c3b8dcb": 4.12745e9}
 
 
 def _env_int(name, default):
