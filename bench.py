@@ -40,17 +40,17 @@ BYTES_PER_PARTICLE = 24
 # (299.6 MB) and deposit (133.6 MB) launches of one step, from ncu captures of
 # the torus workload, keyed by the SHA-256 of the kernel sources they were
 # taken on (a changed kernel reports null until it is captured again).
-MOVE_TRAFFIC = {"af067192ec93fe8a92e48f2ffbff6541e052076bb192cdcf998acd26bf2aac78": 433.24e6}
+MOVE_TRAFFIC = {"4dcf580b08ec301d09cbd40561b51f6355c651130cf8c66b76a9069438413064": 433.24e6}
 FALLBACK_HBM_GBS = 6800.0
 # Warp-instructions of one move + re-bin launch (136.76 M) and one deposit
 # launch (114.26 M) at P = 1e7, H = 128, FP32, from the same ncu captures,
 # keyed like the traffic: the particle kernels against the SMs' issue rate.
-PARTICLE_WARP_INSTR = {"af067192ec93fe8a92e48f2ffbff6541e052076bb192cdcf998acd26bf2aac78": 251.03e6}
+PARTICLE_WARP_INSTR = {"4dcf580b08ec301d09cbd40561b51f6355c651130cf8c66b76a9069438413064": 251.03e6}
 # FP64 form: FP64-pipe thread instructions (DFMA + DADD + DMUL) of one FP64 step
 # at P = 1e7, H = 128 (move 2.580e9, deposit 0.823e9, forward plane 0.112e9,
 # x pass 0.279e9, inverse plane 0.334e9), from an ncu capture of the bench's
 # FP64 leg, keyed by the SHA-256 of the kernel sources it was taken on.
-FP64_PIPE_INSTR = {"eaa1e4f0009f7dd9533feb7aaa01105800b41b45b6b8da64a22e35c42c3b8dcb": 4.12745e9}
+FP64_PIPE_INSTR = {"abbf5d2a7846741ad101791e36e02233e61004fe83b7c3ba7dfb38f2462ff404": 4.12745e9}
 
 
 def _env_int(name, default):

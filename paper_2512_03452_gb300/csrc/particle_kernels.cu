@@ -7,15 +7,21 @@
 //             of grad c with I* (Algorithm 3), drift, periodic wrap) for rounds
 //             of a bin's particles staged in shared memory by bulk copies,
 //             each particle then written into the bin of its new tile in the
-//             other buffer (one global reservation per round and tile);
-//   chunk lists: per bin, work items of up to 4096 particles;
+//             other buffer (one global reservation per round and tile; the
+//             particles of a merged item reserve one slot each);
+//   chunk lists: work items of up to 4096 particles of one bin, and one
+//             merged item per window of m consecutive bins for the bins
+//             under 256 particles (m = 4 for a single run, 16 in a batch);
 //   k_binned (deposit): the deposit I of the new positions (Algorithm 2), a
 //             block per work item, into a shared-memory integer window over
 //             the tile and the stencil halo (several copies, chosen per lane
 //             so that a warp's atomics fall into distinct banks), then added
 //             to the grid with coalesced reductions.  Particles outside the
 //             window (the overflow bin) deposit with global reductions.
-// Batched forms take the work items of many runs from one counter.
+// Batched forms take the work items of many runs from one counter.  Also
+// here: the re-binning of particle-order arrays, the read-backs to particle
+// order (through a slot map, or by pieces of ids) and the bin-order copy of
+// the positions that the adjoint's segments keep.
 #include <cuda_runtime.h>
 #include <math.h>
 
